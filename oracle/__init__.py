@@ -1,0 +1,34 @@
+"""CPU FP64 oracle for the MDS hot path: TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+and reference legs may import anything from this package; the CUDA product
+path (``paper_2007_11919_gb300``) never does, and the two share no code.
+
+Parity pins (each checked by a ``-m "not gpu"`` test in tests/test_oracle_pins.py):
+  classical_mds        exact recovery of points in R^r, Eq. (1) invariant,
+                       brute force against an independent Jacobi solver.
+  double_center        zero row/column sums, equals the centred Gram matrix
+                       for Euclidean input (Section 2 identity).
+  gower_interpolate    landmarks reproduce X_1; equals LMDS (Prop. 1);
+                       equals the closed-form PCA projection for Euclidean data.
+  lmds_triangulate     Prop. 1 (against gower_interpolate).
+  interpolation_mds    block-size invariance; p = 1 reduces to classical MDS;
+                       Table 1 correlation band.
+  procrustes           exact recovery of a planted orthogonal map + shift.
+  divide_conquer_mds   exact recovery (up to one global orthogonal map) of
+                       rank-r data; p = 1 reduces to classical MDS;
+                       Table 1 correlation band.
+  embed_new            equals interpolation_mds on the same points.
+No oracle function is "parity unpinned".
+"""
+from .mds import (RankError, classical_mds, divide_conquer_mds, divide_conquer_part, double_center,
+                  embed_new, gower_interpolate, interpolation_mds, lmds_triangulate, procrustes,
+                  sign_convention, sq_dist)
+from .compare import aligned_rel_error, column_correlations
+from .jacobi import jacobi_eigh
+
+__all__ = [
+    "RankError", "classical_mds", "divide_conquer_mds", "divide_conquer_part", "double_center",
+    "embed_new", "gower_interpolate", "interpolation_mds", "lmds_triangulate", "procrustes",
+    "sign_convention", "sq_dist", "aligned_rel_error", "column_correlations", "jacobi_eigh",
+]

@@ -1,0 +1,61 @@
+"""Host logic of the seeded input generators (shared by oracle and CUDA path)."""
+import numpy as np
+
+import workloads as W
+
+
+def test_deterministic():
+    a = W.gaussian_dominant(100, 7, 2, seed=3)
+    b = W.gaussian_dominant(100, 7, 2, seed=3)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, W.gaussian_dominant(100, 7, 2, seed=4))
+    assert np.array_equal(W.landmarks(1000, 50, 1), W.landmarks(1000, 50, 1))
+
+
+def test_dominant_variances():
+    Y = W.gaussian_dominant(200_000, 6, 2, seed=0)
+    v = Y.var(axis=0)
+    assert np.allclose(v[:2], 15.0, rtol=0.02) and np.allclose(v[2:], 1.0, rtol=0.02)
+
+
+def test_landmarks_distinct():
+    idx = W.landmarks(1000, 300, 5)
+    assert len(np.unique(idx)) == 300 and idx.min() >= 0 and idx.max() < 1000
+
+
+def test_partitions_cover_once():
+    for part in (W.partitions_uneven(100_000, 20, 800, 1200, 0), W.partitions_equal(10_000, 400, 50, 0)):
+        allidx = np.concatenate([part.anchors, part.own])
+        assert np.array_equal(np.sort(allidx), np.arange(len(allidx)))
+        assert part.ptr[0] == 0 and part.ptr[-1] == len(part.own)
+    part = W.partitions_uneven(100_000, 20, 800, 1200, 0)
+    own = np.diff(part.ptr)
+    assert own.min() >= 800 and own[:-1].max() <= 1200 and own[-1] < 2 * 1200
+    assert np.array_equal(part.sizes(), own + 20)
+
+
+def test_paper_part_count():
+    """Section 3.2: p = ceil(1 + (n - l) / (l - c))."""
+    n, l, c = 10_000, 400, 50
+    part = W.partitions_equal(n, l, c, 0)
+    assert part.p == int(np.ceil(1 + (n - l) / (l - c)))
+
+
+def test_image_like_stats():
+    Y = W.image_like(2000, 784, 0)
+    assert Y.dtype == np.uint8
+    z = (Y == 0).mean()
+    assert 0.78 < z < 0.82
+    nz = Y[Y > 0].astype(float)
+    assert 150 < nz.mean() < 185 and nz.min() >= 1
+
+
+def test_mixture_means():
+    Y = W.gaussian_mixture(40_000, 10, 4, 5.0, 0, dtype=np.float64)
+    m = Y.mean(axis=0)
+    assert np.allclose(m[:4], 5.0 / np.sqrt(2) / 4, atol=0.05) and np.allclose(m[4:], 0, atol=0.05)
+
+
+def test_serve_requests():
+    t, s = W.serve_requests(1000, 1, 50_000, 100.0, 0)
+    assert np.all(np.diff(t) > 0) and s.min() >= 1 and s.max() <= 50_000

@@ -1,0 +1,216 @@
+"""Seeded synthetic inputs for interpolation MDS and divide-and-conquer MDS.
+
+This module is the one thing the CPU oracle (``oracle/``) and the CUDA path
+(``paper_2007_11919_gb300``) share: it draws data matrices, landmark subsets
+and partitions, and holds none of the method's arithmetic (no distances, no
+centering, no eigen-solves, no Procrustes).  Every random choice the method
+makes (the random landmark subset of Section 3.1, the random connecting points
+and random parts of Section 3.2) is drawn here and handed to both sides as
+plain index arrays, so both compute on identical subsets.
+
+Streams are numpy ``Philox`` generators keyed by ``(seed, stream id)``; the
+same key gives the same numbers on x86-64 and aarch64 hosts.
+
+Workload shapes follow the paper's simulation design (Section 4.1: rows drawn
+from N(0, diag(15,...,15,1,...,1)), Euclidean distances) and stand in for the
+EMNIST set of Section 5 with an image-like uint8 matrix of the same shape
+(784 pixels in 0..255, mostly zeros), since the dataset itself is not used.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Stream ids: one independent Philox stream per purpose.
+_S_DATA, _S_LANDMARK, _S_ANCHOR, _S_PART, _S_SIZE, _S_SERVE = range(6)
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[int(seed) & 0xFFFFFFFFFFFFFFFF, stream]))
+
+
+# --------------------------------------------------------------------------- data
+
+
+def gaussian_dominant(n: int, d: int, h: int, seed: int, var_dom: float = 15.0,
+                      dtype=np.float64) -> np.ndarray:
+    """n x d rows from N(0, diag(var_dom x h, 1 x (d-h))) (Section 4.1)."""
+    g = _rng(seed, _S_DATA)
+    sd = np.ones(d)
+    sd[:h] = math.sqrt(var_dom)
+    out = np.empty((n, d), dtype=dtype)
+    step = max(1, (1 << 22) // max(d, 1))
+    for i in range(0, n, step):
+        j = min(n, i + step)
+        out[i:j] = g.standard_normal((j - i, d)) * sd
+    return out
+
+
+def gaussian_mixture(n: int, d: int, k: int, spacing: float, seed: int,
+                     dtype=np.float32) -> np.ndarray:
+    """Equal-weight mixture of k unit-covariance Gaussians in R^d.
+
+    The k means form a regular simplex with pairwise distance ``spacing``:
+    mu_c = (spacing / sqrt(2)) e_c, c = 0..k-1.
+    """
+    g = _rng(seed, _S_DATA)
+    out = np.empty((n, d), dtype=dtype)
+    a = spacing / math.sqrt(2.0)
+    step = max(1, (1 << 22) // max(d, 1))
+    for i in range(0, n, step):
+        j = min(n, i + step)
+        blk = g.standard_normal((j - i, d))
+        comp = g.integers(0, k, size=j - i)
+        blk[np.arange(j - i), comp] += a
+        out[i:j] = blk
+    return out
+
+
+def image_like(n: int, d: int, seed: int, zero_frac: float = 0.8,
+               mean: float = 180.0, sd: float = 60.0) -> np.ndarray:
+    """n x d uint8 'pixels': a fraction ``zero_frac`` are 0, the rest are
+    round(clip(N(mean, sd), 1, 255)); pixels are i.i.d."""
+    g = _rng(seed, _S_DATA)
+    out = np.empty((n, d), dtype=np.uint8)
+    step = max(1, (1 << 21) // max(d, 1))
+    for i in range(0, n, step):
+        j = min(n, i + step)
+        v = np.rint(np.clip(g.normal(mean, sd, size=(j - i, d)), 1.0, 255.0))
+        v[g.random((j - i, d)) < zero_frac] = 0.0
+        out[i:j] = v.astype(np.uint8)
+    return out
+
+
+# ---------------------------------------------------------------- random subsets
+
+
+def landmarks(n: int, l: int, seed: int) -> np.ndarray:
+    """A uniformly random l-subset of range(n), as int64, in draw order."""
+    if not 0 < l <= n:
+        raise ValueError("need 0 < l <= n")
+    return _rng(seed, _S_LANDMARK).permutation(n)[:l].astype(np.int64)
+
+
+@dataclasses.dataclass
+class Partitioning:
+    """Divide-and-conquer layout.
+
+    ``anchors`` (c,) are the connecting points shared by every part;
+    part j owns ``own[ptr[j]:ptr[j+1]]``; the points of part j are
+    ``anchors`` followed by its own points, so n_j = c + own_j.
+    Every index in range(n) is either an anchor or owned by exactly one part.
+    """
+    anchors: np.ndarray
+    ptr: np.ndarray
+    own: np.ndarray
+
+    @property
+    def p(self) -> int:
+        return len(self.ptr) - 1
+
+    @property
+    def c(self) -> int:
+        return len(self.anchors)
+
+    def sizes(self) -> np.ndarray:
+        """n_j, the number of points of each part (anchors included)."""
+        return np.diff(self.ptr) + self.c
+
+    def members(self, j: int) -> np.ndarray:
+        return np.concatenate([self.anchors, self.own[self.ptr[j]:self.ptr[j + 1]]])
+
+
+def partitions_uneven(n: int, c: int, own_lo: int, own_hi: int, seed: int) -> Partitioning:
+    """c random connecting points; the other n-c points in random order are cut
+    into parts whose own sizes are drawn uniformly from [own_lo, own_hi].  A
+    last remainder smaller than own_lo is folded into the part before it."""
+    if c >= n:
+        raise ValueError("need c < n")
+    perm = _rng(seed, _S_ANCHOR).permutation(n).astype(np.int64)
+    anchors, rest = perm[:c], perm[c:]
+    rest = rest[_rng(seed, _S_PART).permutation(len(rest))]
+    gs = _rng(seed, _S_SIZE)
+    sizes = []
+    left = len(rest)
+    while left > 0:
+        s = int(gs.integers(own_lo, own_hi + 1))
+        s = min(s, left)
+        sizes.append(s)
+        left -= s
+    if len(sizes) > 1 and sizes[-1] < own_lo:
+        tail = sizes.pop()
+        sizes[-1] += tail
+    ptr = np.zeros(len(sizes) + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum(sizes)
+    return Partitioning(anchors=anchors, ptr=ptr, own=rest)
+
+
+def partitions_equal(n: int, l: int, c: int, seed: int) -> Partitioning:
+    """The paper's own layout (Section 3.2): parts of l points (c shared
+    connecting points + l-c own points), p = ceil(1 + (n-l)/(l-c)); the last
+    part may be smaller."""
+    if not c < l:
+        raise ValueError("need c < l")
+    perm = _rng(seed, _S_ANCHOR).permutation(n).astype(np.int64)
+    anchors, rest = perm[:c], perm[c:]
+    rest = rest[_rng(seed, _S_PART).permutation(len(rest))]
+    own = l - c
+    nparts = max(1, math.ceil(len(rest) / own))
+    ptr = np.minimum(np.arange(nparts + 1, dtype=np.int64) * own, len(rest))
+    return Partitioning(anchors=anchors, ptr=ptr, own=rest)
+
+
+# -------------------------------------------------------------------- serving
+
+
+def serve_requests(count: int, lo: int, hi: int, rate_per_s: float, seed: int):
+    """Poisson arrivals: (arrival time [s], size) pairs; sizes are
+    floor(exp(U(ln lo, ln(hi+1)))) clipped to [lo, hi] (log-uniform)."""
+    g = _rng(seed, _S_SERVE)
+    t = np.cumsum(g.exponential(1.0 / rate_per_s, size=count))
+    sizes = np.floor(np.exp(g.uniform(math.log(lo), math.log(hi + 1), size=count)))
+    sizes = np.clip(sizes, lo, hi).astype(np.int64)
+    return t, sizes
+
+
+# ------------------------------------------------------------- named workloads
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    kind: str          # "interp", "dc", "serve"
+    n: int
+    d: int
+    r: int
+    prec: str          # distance precision: "f64", "f32", "bf16", "fp8"
+    l: int = 0         # landmarks (interp) / part size (equal dc)
+    c: int = 0         # connecting points (dc)
+    own_lo: int = 0
+    own_hi: int = 0
+
+
+# The five workloads of this project; names say what they are.
+CLASSICAL_INTERP_F64 = Workload("interp_f64_n2000_d10_l300_r3", "interp", 2000, 10, 3, "f64", l=300)
+DC_F32 = Workload("dc_f32_n100000_d100_parts800-1200_c20_r10", "dc", 100_000, 100, 10, "f32",
+                  c=20, own_lo=800, own_hi=1200)
+INTERP_BF16 = Workload("interp_bf16_n1000000_d100_l1000_r10", "interp", 1_000_000, 100, 10, "bf16",
+                       l=1000)
+IMAGE_FP8 = Workload("image_fp8_n814255_d784_l2000_r10", "interp", 814_255, 784, 10, "fp8", l=2000,
+                     c=50)
+
+
+def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
+    """Data matrix of workload ``w`` (optionally only its first n rows)."""
+    n = w.n if n is None else n
+    if w is CLASSICAL_INTERP_F64 or w.name == CLASSICAL_INTERP_F64.name:
+        return gaussian_dominant(n, w.d, 3, seed, dtype=np.float64)
+    if w.name == DC_F32.name:
+        return gaussian_dominant(n, w.d, 5, seed, dtype=np.float32)
+    if w.name == INTERP_BF16.name:
+        return gaussian_mixture(n, w.d, 4, 5.0, seed, dtype=np.float32)
+    if w.name == IMAGE_FP8.name:
+        return image_like(n, w.d, seed)
+    raise KeyError(w.name)
