@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the MDS hot path on GB300.
+
+Default workload: divide-and-conquer MDS (Section 3.2) of n=100,000 points in
+d=100 (5 dominant directions of variance 15, 95 of variance 1), parts of
+800-1,200 own points plus c=20 shared connecting points, r=10, FP32 distance
+arithmetic and FP64 eigen-solves; one step = one mds_divide_conquer call over
+the whole set (norms, all parts' distance tiles and double centering, the
+batched Lanczos eigen-solve, Procrustes alignment and the aligned scatter).
+Metric: points embedded per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload dc|interp]
+
+Under torchrun every rank runs its own independent problem of the same size
+(weak scaling, no data-path collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "points embedded/sec at stated Procrustes error vs oracle"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal dense FP64 rate of a GB300 (the eigen-solver's arithmetic):
+# 1.25 TFLOP/s = 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz.
+FP64_PEAK_TFLOPS = 1.25
+# DRAM traffic per launch of the dominant kernel from an ncu capture, valid
+# only while the kernel source is unchanged (sha256 of the .cu file).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["dc", "interp"], default="dc")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-parts", type=int, default=4, help="parts in the bounded oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def file_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------- CPU oracle leg
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def oracle_dc_sample(Y, part, r, nparts):
+    """Oracle divide-and-conquer on parts 0..nparts-1 (each aligned to part 0).
+    Returns (rows, X rows, seconds, points)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    rows, xs = [], []
+    for j in range(min(nparts, part.p)):
+        rj, Xj, _ = O.divide_conquer_part(Y, part.anchors, part.ptr, part.own, j, r)
+        rows.append(rj)
+        xs.append(Xj)
+    dt = time.perf_counter() - t0
+    rows = np.concatenate(rows)
+    return rows, np.vstack(xs), dt, len(rows)
+
+
+def oracle_interp_sample(Y, idx, r, m):
+    """Oracle interpolation MDS: landmark MDS + Eq. (2) for the first m
+    non-landmark rows.  Returns (rows, X rows, seconds, points)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    L = Y[idx].astype(np.float64)
+    D1 = O.sq_dist(L, L)
+    X1, lam, _, _ = O.classical_mds(D1, r)
+    is_lm = np.zeros(len(Y), dtype=bool)
+    is_lm[idx] = True
+    rest = np.nonzero(~is_lm)[0][:m]
+    Xs = O.gower_interpolate(X1, lam, D1, O.sq_dist(Y[rest].astype(np.float64), L))
+    dt = time.perf_counter() - t0
+    return np.concatenate([idx, rest]), np.vstack([X1, Xs]), dt, len(rest) + len(idx)
+
+
+# ---------------------------------------------------------------- workloads
+
+
+def make_workload(name, seed):
+    if name == "dc":
+        w = W.DC_F32
+        Y = W.make_data(w, seed)
+        part = W.partitions_uneven(w.n, w.c, w.own_lo, w.own_hi, seed)
+        return w, Y, part
+    w = W.INTERP_BF16
+    Y = W.make_data(w, seed)
+    idx = W.landmarks(w.n, w.l, seed)
+    return w, Y, idx
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w, Y, aux = make_workload(args.workload, args.seed)
+    times, pts = [], 0
+    for i in range(args.warmup + args.steps):
+        if args.workload == "dc":
+            _, _, dt, npts = oracle_dc_sample(Y, aux, w.r, args.cpu_parts)
+        else:
+            _, _, dt, npts = oracle_interp_sample(Y, aux, w.r, 20_000)
+        if i >= args.warmup:
+            times.append(dt)
+            pts += npts
+    value = pts / sum(times)
+    sample = (f"parts 0..{args.cpu_parts - 1} of the workload per step" if args.workload == "dc"
+              else "landmark MDS + 20,000 interpolated rows per step")
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic", "config": {"workload": w.name, "n": w.n, "d": w.d, "r": w.r},
+          "cpu_baseline": {"value": value, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle",
+                           "sample": sample},
+          "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# --------------------------------------------------------------- our arm
+
+
+def ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2007_11919_gb300 import build as gbuild
+    gbuild.build()
+    import paper_2007_11919_gb300 as G
+    from paper_2007_11919_gb300 import mds as M
+
+    seed = args.seed + 1000 * rank
+    w, Y, aux = make_workload(args.workload, seed)
+    Yd = torch.from_numpy(Y).to(dev)
+    L = M._lib()
+    if args.workload == "dc":
+        part = aux
+        anc = torch.from_numpy(part.anchors).to(dev)
+        own = torch.from_numpy(part.own).to(dev)
+        import ctypes
+        ptr = np.ascontiguousarray(part.ptr)
+        wsb = L.mds_divide_conquer_workspace_size(w.n, w.d, part.p, ptr.ctypes.data_as(ctypes.c_void_p), w.c,
+                                                  w.r, M.PREC[w.prec])
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+        def step(Yin=Yd, a=anc, o=own):
+            return G.mds_divide_conquer(Yin, a, part.ptr, o, w.r, w.prec, workspace=ws)
+    else:
+        idx = torch.from_numpy(aux).to(dev)
+        wsb = L.mds_interpolate_workspace_size(w.n, w.d, w.l, w.r, M.PREC[w.prec])
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+        def step(Yin=Yd, a=idx, o=None):
+            X, var, _ = G.mds_interpolate(Yin, a, w.r, w.prec, workspace=ws)
+            return X, var
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    M.mds_set_timing(True)
+    for _ in range(args.warmup):
+        X, var = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps, CUDA events per step
+    clocks = ClockSampler(local)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    step_ms, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        X, var = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(M.mds_last_stats())
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * w.n / (ms_per_step / 1e3)
+
+    # ---- dominant kernel roofline (batched Lanczos for D&C; projection for interpolation)
+    eig_ms = [s["stage_ms"]["eig"] for s in stats]
+    if args.workload == "dc":
+        flops = statistics.mean(s["eig_flops"] for s in stats)
+        kms = statistics.mean(eig_ms)
+        achieved = flops / (kms * 1e-3) / 1e12
+        roof = {"kernel": "k_lanczos (batched FP64 Lanczos)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.06 GHz)",
+                "launch_ms": kms, "flops_per_launch": flops,
+                "q_bytes_per_launch": statistics.mean(s["eig_qbytes"] for s in stats)}
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_lanczos.cu")
+    else:
+        kms = statistics.mean(s["stage_ms"]["post"] for s in stats)
+        flops = w.n * (2.0 * w.l * w.d + 2.0 * w.l * w.r)
+        peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+        pk = peaks.get("bf16_tflops", 1900.0)
+        achieved = flops / (kms * 1e-3) / 1e12
+        roof = {"kernel": "k_gower (distance tiles + Gower projection)", "bound": "tensor",
+                "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1.9 PFLOP/s",
+                "launch_ms": kms, "flops_per_launch": flops}
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_proj.cu")
+    tr = NCU_TRAFFIC.get(os.path.basename(src))
+    roof["traffic"] = tr["bytes_per_launch"] if tr and tr["sha"] == file_sha(src) else None
+
+    # ---- end to end through the public API: pinned host input, host output
+    Yh = torch.from_numpy(Y).pin_memory()
+    if args.workload == "dc":
+        anc_h = torch.from_numpy(part.anchors).pin_memory()
+        own_h = torch.from_numpy(part.own).pin_memory()
+        h2d = Yh.numel() * Yh.element_size() + anc_h.numel() * 8 + own_h.numel() * 8
+    else:
+        anc_h = torch.from_numpy(aux).pin_memory()
+        own_h = None
+        h2d = Yh.numel() * Yh.element_size() + anc_h.numel() * 8
+    Ybuf = torch.empty_like(Yd)
+    abuf = torch.empty(anc_h.shape, dtype=torch.int64, device=dev)
+    obuf = torch.empty(own_h.shape, dtype=torch.int64, device=dev) if own_h is not None else None
+    e2e_ms = []
+    d2h = w.n * w.r * 4 + w.r * 8
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ybuf.copy_(Yh, non_blocking=True)
+        abuf.copy_(anc_h, non_blocking=True)
+        if obuf is not None:
+            obuf.copy_(own_h, non_blocking=True)
+        X, var = step(Ybuf, abuf, obuf)
+        Xh = X.cpu()
+        _ = var.cpu()
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = w.n / (statistics.mean(e2e_ms) / 1e3)
+    if world > 1:
+        t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_value = world * w.n / (float(t.item()) / 1e3)
+
+    # ---- CPU oracle leg (rank 0, N = 1 only) and the error against it
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        if args.workload == "dc":
+            rows, Xo, dt, npts = oracle_dc_sample(Y, part, w.r, args.cpu_parts)
+            sample = f"parts 0..{args.cpu_parts - 1} ({npts} points) of the same workload, each part's classical MDS + Procrustes to part 0"
+        else:
+            rows, Xo, dt, npts = oracle_interp_sample(Y, aux, w.r, 20_000)
+            sample = f"landmark MDS + Eq. (2) for {npts - w.l} rows of the same workload"
+        err = O.aligned_rel_error(Xh.double().numpy()[rows], Xo)
+        cpu = {"value": npts / dt, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        peaks_note = None
+        emit({"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": w.prec, "data": "synthetic",
+              "config": {"workload": w.name, "n_per_gpu": w.n, "d": w.d, "r": w.r,
+                         "parts": (part.p if args.workload == "dc" else None),
+                         "c": (w.c if args.workload == "dc" else None),
+                         "l": (w.l if args.workload == "interp" else None),
+                         "eigensolve": "f64 Lanczos", "cluster": stats[-1]["cluster"],
+                         "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
+              "procrustes_rel_err_vs_oracle": err,
+              "stage_ms": {k: statistics.mean(s["stage_ms"][k] for s in stats) for k in stats[0]["stage_ms"]},
+              "eig_steps_per_call": stats[-1]["eig_steps"],
+              "roofline": roof, "cpu_baseline": cpu,
+              "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)},
+              "gpu_launches": int(sum(s["launches"] for s in stats)),
+              "clocks": clk, "gpu": torch.cuda.get_device_name(dev), "note": peaks_note})
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

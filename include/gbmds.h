@@ -1,0 +1,189 @@
+/*
+ * gbmds.h -- C ABI of libgbmds.so: interpolation MDS and divide-and-conquer MDS
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Delicado & Pachon-Garcia, "Multidimensional scaling for big data"
+ * (arXiv 2007.11919).  Classical MDS (Section 2), interpolation MDS with
+ * Gower's formula (Section 3.1, Eq. (2)) and divide-and-conquer MDS with
+ * orthogonal Procrustes alignment (Section 3.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Data Y is row-major n x d (rows are individuals), element type given by
+ *    an mds_dtype.  Distances are squared Euclidean distances between rows.
+ *  - Unless stated otherwise every array argument is a DEVICE pointer owned by
+ *    the caller; the library never frees it and writes only the outputs.
+ *  - Configurations X are row-major n x r: double when opts->prec is
+ *    MDS_PREC_F64, float otherwise.  Eigenvalue / variance outputs are double.
+ *  - Scratch memory: the caller passes opts->workspace (device memory of at
+ *    least the matching *_workspace_size() bytes, 256-byte aligned).  The
+ *    library allocates device memory only inside mds_model handles.
+ *  - Work is queued on opts->stream.  Each call synchronises that stream
+ *    before it returns, to read the device status words (eigen-solver
+ *    convergence, rank); outputs are complete when it returns MDS_OK.
+ *  - Errors never abort the process.  On any status other than MDS_OK the
+ *    outputs are unspecified.
+ *  - Randomness of the method (the random landmark subset of Section 3.1, the
+ *    random connecting points and parts of Section 3.2) is drawn by the
+ *    caller; index arrays are inputs.
+ *  - Eigenvector sign: each eigenvector is flipped so that its entry of
+ *    largest magnitude is positive (lowest row index wins a tie).
+ *  - r <= 32.  Eigenproblems (landmark sets, parts, classical MDS) have at
+ *    most 16384 points.
+ */
+#ifndef GBMDS_H
+#define GBMDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MDS_OK = 0,
+    MDS_ERR_ARG = 1,          /* invalid argument (null pointer, size, index) */
+    MDS_ERR_NOMEM = 2,        /* device allocation inside a model handle failed */
+    MDS_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    MDS_ERR_RANK = 4,         /* fewer than r eigenvalues > rank_tol * lambda_1 */
+    MDS_ERR_NOCONV = 5,       /* eigen-solver hit max_steps before tolerance */
+    MDS_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    MDS_ERR_UNSUPPORTED = 7,  /* precision / dtype combination not built */
+    MDS_ERR_WORKSPACE = 8,    /* opts->workspace missing, misaligned or too small */
+    MDS_ERR_IO = 9            /* model file could not be read or written */
+} mds_status;
+
+typedef enum { MDS_IN_F64 = 0, MDS_IN_F32 = 1, MDS_IN_U8 = 2 } mds_dtype;
+
+/* Arithmetic of the distance contractions.  FP64 eigen-solves, centering
+ * means and Procrustes SVDs are used for every precision. */
+typedef enum {
+    MDS_PREC_F64 = 0,   /* FP64 throughout */
+    MDS_PREC_F32 = 1,   /* FP32 distances, FP64 eigen-solve */
+    MDS_PREC_BF16 = 2,  /* BF16 tensor-core distances, FP32 accumulate */
+    MDS_PREC_FP8 = 3    /* E4M3 tensor-core distances (uint8 data), FP32 accumulate */
+} mds_precision;
+
+typedef struct {
+    int32_t prec;            /* mds_precision */
+    int32_t max_steps;       /* Lanczos step cap per eigenproblem; 0 = 256 */
+    double eig_tol;          /* stop when every wanted Ritz residual
+                                <= eig_tol * lambda_1; 0 = 1e-10 */
+    double rank_tol;         /* MDS_ERR_RANK unless lambda_r > rank_tol * lambda_1;
+                                0 = 1e-12 */
+    void* stream;            /* cudaStream_t; NULL = the legacy default stream */
+    void* workspace;         /* device scratch (see *_workspace_size) */
+    size_t workspace_bytes;
+    int32_t cluster;         /* CTAs per eigenproblem (1..16); 0 = automatic */
+    int32_t flags;           /* reserved, must be 0 */
+} mds_opts;
+
+/* Opaque device-resident landmark configuration of interpolation MDS: the l
+ * landmark rows, their classical-MDS eigenpairs and the Gower projection
+ * operator derived from them (Section 3.1). */
+typedef struct mds_model_s* mds_model;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* mds_status_str(int status);
+
+/* Library ABI version (currently 1). */
+int mds_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Classical MDS of n points (Section 2, steps 1-4).
+ *   Delta = squared distances between the rows of Y (n x d, dtype dt),
+ *   Q = -1/2 P Delta P, top-r eigenpairs (lambda_i, v_i) of Q,
+ *   X = V_r Lambda_r^{1/2}  (n x r), lambda (r, descending).
+ * Fails with MDS_ERR_RANK if lambda_r <= rank_tol * lambda_1. */
+size_t mds_classical_workspace_size(int64_t n, int d, int r, int prec);
+int mds_classical(const void* Y, int dt, int64_t n, int d, int r, const mds_opts* opts,
+                  void* X, double* lambda);
+
+/* Classical MDS of a given n x n squared-distance matrix D2 (row-major,
+ * double, symmetric, zero diagonal; need not be Euclidean) (Section 2). */
+size_t mds_classical_dist_workspace_size(int64_t n, int r);
+int mds_classical_dist(const double* D2, int64_t n, int r, const mds_opts* opts,
+                       double* X, double* lambda);
+
+/* ------------------------------------------------------------------ */
+/* Interpolation MDS (Section 3.1).
+ *   landmark_idx (device, l distinct int64 rows of Y) is the first subset;
+ *   classical MDS of the landmarks gives X_1 = V Lambda^{1/2};
+ *   every other row i is placed by Gower's formula, Eq. (2):
+ *     Xdot_i = 1/(2l) (q_1 - a2_i)^T X_1 S_1^{-1},  S_1 = Lambda / l,
+ *   a2_i = squared distances from row i to the landmarks, q_1 = diag(Q_1).
+ *   Landmark rows receive X_1.  X is n x r in the original row order;
+ *   var (r) = lambda / l, the column-variance estimates.
+ *   If out_model is not NULL a device-resident model (mds_model) is created
+ *   for mds_embed_new; release it with mds_model_free. */
+size_t mds_interpolate_workspace_size(int64_t n, int d, int l, int r, int prec);
+int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
+                    int r, const mds_opts* opts, void* X, double* var, mds_model* out_model);
+
+/* Gower's formula, Eq. (2), for m new rows Ynew (m x d, dtype dt) against a
+ * stored model; X is m x r.  opts->prec must equal the model's precision.
+ * Equal inputs give bitwise-equal outputs regardless of what else is batched
+ * with them: rows are computed independently. */
+size_t mds_embed_new_workspace_size(mds_model model, int64_t m);
+int mds_embed_new(mds_model model, const void* Ynew, int dt, int64_t m, const mds_opts* opts,
+                  void* X);
+
+/* Model inspection / persistence.  lambda may be NULL. */
+int mds_model_info(mds_model model, int* l, int* d, int* r, int* prec, double* lambda);
+int mds_model_save(mds_model model, const char* path);
+int mds_model_load(const char* path, mds_model* out_model);
+void mds_model_free(mds_model model);
+
+/* ------------------------------------------------------------------ */
+/* Divide-and-conquer MDS (Section 3.2).
+ *   anchors   device, c int64 rows: the connecting points shared by all parts.
+ *   part_ptr  HOST, p+1 int64 offsets into part_own (part_ptr[0] = 0).
+ *   part_own  device, part_ptr[p] int64 rows: part j owns
+ *             part_own[part_ptr[j] .. part_ptr[j+1]).
+ *   Part j's points are the c anchors followed by its own rows, n_j = c + own_j.
+ *   Classical MDS of every part gives X_j, lambda^j (all parts in one batched
+ *   launch); each X_j, j >= 1, is aligned to part 0 by orthogonal Procrustes
+ *   on the connecting points, X_0^c ~ X_j^c T_j + 1 t_j^T (T_j orthogonal,
+ *   reflections allowed, no scaling); rows of part j other than the anchors
+ *   receive X_j^a T_j + 1 t_j^T; part 0's rows (anchors included) receive X_0.
+ *   X (n x r) is written only at rows that appear in the parts, in original
+ *   row order.  var (r) = (1/p) sum_j lambda^j / n_j.
+ *   Requires c >= r + 1 and r < n_j for every part. */
+size_t mds_divide_conquer_workspace_size(int64_t n, int d, int p, const int64_t* part_ptr, int c,
+                                         int r, int prec);
+int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int64_t* part_ptr,
+                       const int64_t* part_own, const int64_t* anchors, int c, int r,
+                       const mds_opts* opts, void* X, double* var);
+
+/* ------------------------------------------------------------------ */
+/* Instrumentation (the paper has no counterpart; used by the benchmark).
+ * mds_set_timing(1) makes subsequent calls on the calling host thread record
+ * CUDA events on opts->stream between pipeline stages; mds_last_stats then
+ * returns the stage durations of the last completed call on that thread:
+ *   stage_ms[0] data preparation (norms, BF16 rounding)
+ *   stage_ms[1] squared-distance tiles (Delta_j, Section 2)
+ *   stage_ms[2] double centering (Q_j = -1/2 P Delta_j P)
+ *   stage_ms[3] batched Lanczos eigen-solve (top-r eigenpairs)
+ *   stage_ms[4] Gower projection / Procrustes alignment and output
+ * eig_flops / eig_qbytes: algorithmic FP64 flops of the eigen-solve
+ * (2 n^2 per matrix-vector product, 8 n (j+1) per step for two Gram-Schmidt
+ * passes, 2 n k r for the Ritz vectors) and bytes of Q read (8 n^2 per step),
+ * summed over the problems of the call with their actual step counts. */
+typedef struct {
+    double stage_ms[5];
+    int64_t launches;      /* kernels launched by the call */
+    int64_t eig_steps;     /* Lanczos steps summed over problems */
+    double eig_flops;
+    double eig_qbytes;
+    int32_t problems;      /* eigenproblems in the call */
+    int32_t cluster;       /* CTAs per eigenproblem used */
+} mds_stats;
+
+void mds_set_timing(int on);
+int mds_last_stats(mds_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMDS_H */

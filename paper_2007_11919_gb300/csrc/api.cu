@@ -1,0 +1,702 @@
+// Host side of libgbmds: argument checks, workspace carving and the stream-
+// ordered launch sequences behind the C ABI declared in include/gbmds.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace gbmds;
+
+struct mds_model_s {
+    int l, d, r, prec, device;
+    void* L;        // l x d landmark rows (float, or double for MDS_PREC_F64)
+    double* nrm_l;  // l squared norms (of the rows as stored in L)
+    void* W;        // l x r Gower operator -1/2 V Lambda^{-1/2}
+    double* bias;   // r: 1/2 Lambda^{-1/2} V^T q_1
+    void* X1;       // l x r landmark configuration
+    double* lam;    // r eigenvalues of Q_1
+};
+
+namespace gbmds {
+thread_local int64_t g_launches = 0;
+void note_launch(int count) { g_launches += count; }
+}  // namespace gbmds
+
+namespace {
+
+constexpr int kDefaultSteps = 256;
+
+// ---- per-thread instrumentation (mds_set_timing / mds_last_stats)
+bool g_timing = false;
+thread_local mds_stats g_last = {};
+thread_local cudaEvent_t g_ev[6] = {};
+thread_local bool g_ev_made = false;
+thread_local int g_cluster = 0;
+
+// Marks the start (stage = -1) or the end of a pipeline stage on the stream.
+void tmark(int stage, cudaStream_t st) {
+    if (!g_timing) return;
+    if (!g_ev_made) {
+        for (auto& e : g_ev) cudaEventCreate(&e);
+        g_ev_made = true;
+    }
+    cudaEventRecord(g_ev[stage + 1], st);
+}
+
+void begin_call(cudaStream_t st) {
+    g_launches = 0;
+    g_cluster = 0;
+    g_last = mds_stats{};
+    if (g_timing)
+        for (int i = 0; i <= 5; ++i) tmark(i - 1, st);  // all stages empty by default
+}
+
+struct Arena {
+    char* base;
+    size_t off;
+    template <class T>
+    T* take(size_t count) {
+        off = (size_t)round_up((int64_t)off, 256);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct Opts {
+    int prec;
+    int mmax;
+    double tol;
+    double rank_tol;
+    cudaStream_t st;
+    char* ws;
+    size_t wsb;
+    int cluster;
+};
+
+int read_opts(const mds_opts* o, Opts* out) {
+    if (!o) return MDS_ERR_ARG;
+    if (o->prec < MDS_PREC_F64 || o->prec > MDS_PREC_FP8) return MDS_ERR_ARG;
+    if (o->max_steps < 0 || o->eig_tol < 0 || o->rank_tol < 0 || o->cluster < 0 ||
+        o->cluster > 16 || o->flags != 0)
+        return MDS_ERR_ARG;
+    out->prec = o->prec;
+    out->mmax = o->max_steps ? o->max_steps : kDefaultSteps;
+    out->tol = o->eig_tol > 0 ? o->eig_tol : 1e-10;
+    out->rank_tol = o->rank_tol > 0 ? o->rank_tol : 1e-12;
+    out->st = (cudaStream_t)o->stream;
+    out->ws = (char*)o->workspace;
+    out->wsb = o->workspace_bytes;
+    out->cluster = o->cluster;
+    if (out->mmax < 2) return MDS_ERR_ARG;
+    return MDS_OK;
+}
+
+int check_ws(const Opts& o, size_t need) {
+    if (need == 0) return MDS_OK;
+    if (!o.ws || ((uintptr_t)o.ws & 255) != 0 || o.wsb < need) return MDS_ERR_WORKSPACE;
+    return MDS_OK;
+}
+
+// ----------------------------------------------------------- eigen batches
+
+struct Batch {
+    std::vector<ProbDesc> desc;
+    int p = 0, max_n = 0, max_tiles = 0, mmax = 0, r = 0;
+    size_t q_el = 0, rp_el = 0, rm_el = 0, b_el = 0, v_el = 0;
+    ProbDesc* d_desc = nullptr;
+    double *q = nullptr, *rp = nullptr, *rm = nullptr, *grand = nullptr, *b = nullptr,
+           *v = nullptr, *lam = nullptr, *scr = nullptr;
+    int *status = nullptr, *steps = nullptr;
+};
+
+void plan_batch(Batch& B, const std::vector<int>& sizes, const std::vector<int64_t>& own_off,
+                int c, int r, int mmax, int64_t ny) {
+    B.p = (int)sizes.size();
+    B.r = r;
+    B.mmax = mmax;
+    for (int j = 0; j < B.p; ++j) {
+        const int n = sizes[j];
+        ProbDesc P;
+        P.own_off = own_off[j];
+        P.n = n;
+        P.ldq = (int)round_up(n, 4);
+        P.c = c;
+        P.tiles = (n + kTile - 1) / kTile;
+        P.ny = ny;
+        const int kcap = std::min(mmax, n);
+        P.q_off = (int64_t)B.q_el;
+        P.rp_off = (int64_t)B.rp_el;
+        P.rm_off = (int64_t)B.rm_el;
+        P.b_off = (int64_t)B.b_el;
+        P.v_off = (int64_t)B.v_el;
+        B.q_el += (size_t)n * P.ldq;
+        B.rp_el += (size_t)round_up((int64_t)P.tiles * n, 4);
+        B.rm_el += (size_t)round_up(n, 4);
+        B.b_el += (size_t)(kcap + 1) * P.ldq;
+        B.v_el += (size_t)round_up((int64_t)n * r, 4);
+        B.max_n = std::max(B.max_n, n);
+        B.max_tiles = std::max(B.max_tiles, P.tiles);
+        B.desc.push_back(P);
+    }
+}
+
+void carve_batch(Batch& B, Arena& A) {
+    B.d_desc = A.take<ProbDesc>(B.p);
+    B.q = A.take<double>(B.q_el);
+    B.rp = A.take<double>(B.rp_el);
+    B.rm = A.take<double>(B.rm_el);
+    B.grand = A.take<double>(B.p);
+    B.b = A.take<double>(B.b_el);
+    B.v = A.take<double>(B.v_el);
+    B.lam = A.take<double>((size_t)B.p * B.r);
+    B.scr = A.take<double>((size_t)B.p * lanczos_scratch_per_problem(B.mmax, B.r));
+    B.status = A.take<int>(B.p);
+    B.steps = A.take<int>(B.p);
+}
+
+int pick_cluster(int requested, int p, int max_n, int mmax) {
+    if (requested > 0) return std::min(requested, 16);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int cs;
+    if (p == 1) cs = 16;
+    else cs = std::max(1, std::min(8, (int)std::lround(2.0 * sms / p)));
+    cs = std::min(cs, std::max(1, max_n / 64));
+    while (cs < 16 && lanczos_smem_bytes(max_n, cs, mmax) > kMaxSmem) ++cs;
+    return cs;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return MDS_ERR_CUDA; \
+    } while (0)
+
+// Uploads descriptors, forms Q_j for every problem (squared distances +
+// double centering) and runs the batched eigen-solver.
+int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
+                  const int64_t* anchors, const int64_t* own, int acc_f64, const Opts& o) {
+    CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
+    if (Y) {
+        CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64,
+                                 B.q, B.rp, o.st));
+    }
+    tmark(1, o.st);
+    CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, o.st));
+    LanczosArgs a;
+    a.desc = B.d_desc;
+    a.p = B.p;
+    a.qarena = B.q;
+    a.barena = B.b;
+    a.varena = B.v;
+    a.lam = B.lam;
+    a.status = B.status;
+    a.steps = B.steps;
+    a.scratch = B.scr;
+    a.r = B.r;
+    a.mmax = B.mmax;
+    a.tol = o.tol;
+    a.rank_tol = o.rank_tol;
+    a.max_n = B.max_n;
+    tmark(2, o.st);
+    g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax);
+    CK(launch_lanczos(a, g_cluster, o.st));
+    tmark(3, o.st);
+    return MDS_OK;
+}
+
+// Waits for the stream and folds the device status words into one code.
+int finish(const Batch* B, const int* d_flag, const Opts& o) {
+    tmark(4, o.st);
+    std::vector<int> hs(B ? B->p : 0), steps(B ? B->p : 0);
+    int flag = 0;
+    if (B && B->p) {
+        CK(cudaMemcpyAsync(hs.data(), B->status, sizeof(int) * B->p, cudaMemcpyDeviceToHost, o.st));
+        CK(cudaMemcpyAsync(steps.data(), B->steps, sizeof(int) * B->p, cudaMemcpyDeviceToHost, o.st));
+    }
+    if (d_flag) CK(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, o.st));
+    CK(cudaStreamSynchronize(o.st));
+    CK(cudaGetLastError());
+    g_last.launches = g_launches;
+    g_last.cluster = g_cluster;
+    if (B) {
+        g_last.problems = B->p;
+        for (int j = 0; j < B->p; ++j) {
+            const double n = B->desc[j].n, k = steps[j];
+            g_last.eig_steps += steps[j];
+            g_last.eig_flops += 2.0 * n * n * k + 4.0 * n * k * (k + 1) + 2.0 * n * k * B->r;
+            g_last.eig_qbytes += 8.0 * n * n * k;
+        }
+    }
+    if (g_timing)
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]);
+            g_last.stage_ms[i] = ms;
+        }
+    if (flag) return MDS_ERR_ARG;
+    int worst = MDS_OK;
+    for (int s : hs) {
+        if (s == MDS_ERR_RANK) return MDS_ERR_RANK;
+        if (s != MDS_OK) worst = s;
+    }
+    return worst;
+}
+
+bool valid_dt(int dt) { return dt == MDS_IN_F64 || dt == MDS_IN_F32 || dt == MDS_IN_U8; }
+
+// --------------------------------------------------------------- layouts
+
+struct ClassicalWs {
+    int* flag;
+    double* nrm;
+    int64_t* iota;
+    Batch B;
+};
+
+size_t classical_layout(ClassicalWs& W, char* base, int64_t n, int r, int mmax) {
+    Arena A{base, 0};
+    W.flag = A.take<int>(1);
+    W.nrm = A.take<double>(n);
+    W.iota = A.take<int64_t>(n);
+    plan_batch(W.B, {(int)n}, {0}, 0, r, mmax, n);
+    carve_batch(W.B, A);
+    return A.off;
+}
+
+struct InterpWs {
+    int* flag;
+    double* nrm;
+    void* Yq;
+    Batch B;
+    void* L;
+    double* nrm_l;
+    void* W;
+    double* bias;
+    void* X1;
+};
+
+size_t interp_layout(InterpWs& W, char* base, int64_t n, int d, int l, int r, int prec, int mmax) {
+    Arena A{base, 0};
+    const size_t es = prec == MDS_PREC_F64 ? 8 : 4;
+    W.flag = A.take<int>(1);
+    W.nrm = A.take<double>(n);
+    W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)n * d) : nullptr;
+    plan_batch(W.B, {l}, {0}, 0, r, mmax, n);
+    carve_batch(W.B, A);
+    W.L = A.take<char>((size_t)l * d * es);
+    W.nrm_l = A.take<double>(l);
+    W.W = A.take<char>((size_t)l * r * es);
+    W.bias = A.take<double>(r);
+    W.X1 = A.take<char>((size_t)l * r * es);
+    return A.off;
+}
+
+struct DcWs {
+    int* flag;
+    double* nrm;
+    void* Yq;
+    Batch B;
+    double* Tt;
+};
+
+size_t dc_layout(DcWs& W, char* base, int64_t n, int d, int p, const int64_t* part_ptr, int c,
+                 int r, int prec, int mmax) {
+    Arena A{base, 0};
+    W.flag = A.take<int>(1);
+    W.nrm = A.take<double>(n);
+    W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)n * d) : nullptr;
+    std::vector<int> sizes(p);
+    std::vector<int64_t> offs(p);
+    for (int j = 0; j < p; ++j) {
+        sizes[j] = (int)(part_ptr[j + 1] - part_ptr[j]) + c;
+        offs[j] = part_ptr[j];
+    }
+    plan_batch(W.B, sizes, offs, c, r, mmax, n);
+    carve_batch(W.B, A);
+    W.Tt = A.take<double>((size_t)p * (r * r + r));
+    return A.off;
+}
+
+// Norms (and the BF16-rounded copy) of the data; returns the dtype tag and
+// pointer the distance kernels read.
+int prep_data(const void* Y, int dt, int64_t n, int d, int prec, double* nrm, void* Yq,
+              const Opts& o, const void** Yeff, int* dteff) {
+    if (prec == MDS_PREC_BF16) {
+        CK(launch_quant_bf16(Y, dt, n, d, Yq, nrm, o.st));
+        *Yeff = Yq;
+        *dteff = kDtBF16;
+    } else {
+        CK(launch_rownorm(Y, dt, n, d, prec == MDS_PREC_F64, nrm, o.st));
+        *Yeff = Y;
+        *dteff = dt;
+    }
+    return MDS_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char* mds_status_str(int s) {
+    switch (s) {
+        case MDS_OK: return "ok";
+        case MDS_ERR_ARG: return "invalid argument";
+        case MDS_ERR_NOMEM: return "device allocation failed";
+        case MDS_ERR_CUDA: return "CUDA error";
+        case MDS_ERR_RANK: return "fewer than r positive eigenvalues";
+        case MDS_ERR_NOCONV: return "eigen-solver did not converge";
+        case MDS_ERR_TIMEOUT: return "device wait timed out";
+        case MDS_ERR_UNSUPPORTED: return "unsupported precision or dtype";
+        case MDS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case MDS_ERR_IO: return "model file error";
+        default: return "unknown status";
+    }
+}
+
+int mds_version(void) { return 1; }
+
+void mds_set_timing(int on) { g_timing = on != 0; }
+
+int mds_last_stats(mds_stats* out) {
+    if (!out) return MDS_ERR_ARG;
+    *out = g_last;
+    return MDS_OK;
+}
+
+// ------------------------------------------------------------- classical
+
+size_t mds_classical_workspace_size(int64_t n, int d, int r, int prec) {
+    (void)d;
+    (void)prec;
+    if (n <= 0 || n > kMaxEigN || r <= 0) return 0;
+    ClassicalWs W;
+    return classical_layout(W, nullptr, n, r, kDefaultSteps) + 256;
+}
+
+int mds_classical(const void* Y, int dt, int64_t n, int d, int r, const mds_opts* opts, void* X,
+                  double* lambda) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!Y || !X || !lambda || !valid_dt(dt) || n < 2 || n > kMaxEigN || d <= 0 || r <= 0 ||
+        r > kMaxR || r >= n)
+        return MDS_ERR_ARG;
+    if (o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) return MDS_ERR_UNSUPPORTED;
+    ClassicalWs W;
+    const size_t need = classical_layout(W, nullptr, n, r, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    classical_layout(W, o.ws, n, r, o.mmax);
+    begin_call(o.st);
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(launch_iota(W.iota, n, o.st));
+    const int f64 = o.prec == MDS_PREC_F64;
+    CK(launch_rownorm(Y, dt, n, d, f64, W.nrm, o.st));
+    tmark(0, o.st);
+    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, W.iota, f64, o))) return s;
+    CK(launch_classical_out(W.B.v, W.B.lam, (int)n, r, f64, X, lambda, o.st));
+    return finish(&W.B, W.flag, o);
+}
+
+size_t mds_classical_dist_workspace_size(int64_t n, int r) {
+    if (n <= 0 || n > kMaxEigN || r <= 0) return 0;
+    ClassicalWs W;
+    return classical_layout(W, nullptr, n, r, kDefaultSteps) + 256;
+}
+
+int mds_classical_dist(const double* D2, int64_t n, int r, const mds_opts* opts, double* X,
+                       double* lambda) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!D2 || !X || !lambda || n < 2 || n > kMaxEigN || r <= 0 || r > kMaxR || r >= n)
+        return MDS_ERR_ARG;
+    ClassicalWs W;
+    const size_t need = classical_layout(W, nullptr, n, r, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    classical_layout(W, o.ws, n, r, o.mmax);
+    begin_call(o.st);
+    CK(cudaMemcpyAsync(W.B.d_desc, W.B.desc.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, o.st));
+    tmark(0, o.st);
+    CK(launch_load_dist(D2, W.B.d_desc, W.B.q, W.B.rp, (int)n, W.B.max_tiles, o.st));
+    if ((s = run_eig_batch(W.B, nullptr, 0, 0, nullptr, nullptr, nullptr, 1, o))) return s;
+    CK(launch_classical_out(W.B.v, W.B.lam, (int)n, r, 1, X, lambda, o.st));
+    return finish(&W.B, nullptr, o);
+}
+
+// ---------------------------------------------------------- interpolation
+
+size_t mds_interpolate_workspace_size(int64_t n, int d, int l, int r, int prec) {
+    if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0) return 0;
+    InterpWs W;
+    return interp_layout(W, nullptr, n, d, l, r, prec, kDefaultSteps) + 256;
+}
+
+int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
+                    int r, const mds_opts* opts, void* X, double* var, mds_model* out_model) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (out_model) *out_model = nullptr;
+    if (!Y || !X || !var || !landmark_idx || !valid_dt(dt) || n < 2 || d <= 0 || l < 2 ||
+        l > n || l > kMaxEigN || r <= 0 || r > kMaxR || r >= l)
+        return MDS_ERR_ARG;
+    if (o.prec == MDS_PREC_FP8) return MDS_ERR_UNSUPPORTED;
+    InterpWs W;
+    const size_t need = interp_layout(W, nullptr, n, d, l, r, o.prec, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    interp_layout(W, o.ws, n, d, l, r, o.prec, o.mmax);
+    begin_call(o.st);
+    const int f64 = o.prec == MDS_PREC_F64;
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(launch_check_idx(landmark_idx, l, n, W.flag, o.st));
+    const void* Ye;
+    int dte;
+    if ((s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
+    tmark(0, o.st);
+    // classical MDS of the landmarks (first subset of Section 3.1)
+    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, nullptr, landmark_idx, f64, o))) return s;
+    // Gower operator, landmark rows, projection of every row, landmark rows <- X_1
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, l, r,
+                           f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
+                           f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
+                           var, o.st));
+    CK(launch_gather_rows(Ye, dte, n, d, landmark_idx, l, f64, W.L, W.nrm, W.nrm_l, o.st));
+    CK(launch_gower_proj(Ye, dte, n, d, W.nrm, W.L, W.nrm_l, l, W.W, W.bias, r, f64, X, o.st));
+    CK(launch_scatter_rows(W.X1, landmark_idx, l, r, n, f64, X, o.st));
+    s = finish(&W.B, W.flag, o);
+    if (s != MDS_OK || !out_model) return s;
+
+    // device-resident model for mds_embed_new
+    mds_model m = new (std::nothrow) mds_model_s();
+    if (!m) return MDS_ERR_NOMEM;
+    const size_t es = f64 ? 8 : 4;
+    m->l = l;
+    m->d = d;
+    m->r = r;
+    m->prec = o.prec;
+    cudaGetDevice(&m->device);
+    bool ok = cudaMalloc(&m->L, (size_t)l * d * es) == cudaSuccess &&
+              cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
+              cudaMalloc(&m->W, (size_t)l * r * es) == cudaSuccess &&
+              cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
+              cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
+              cudaMalloc((void**)&m->lam, sizeof(double) * r) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        mds_model_free(m);
+        return MDS_ERR_NOMEM;
+    }
+    ok = cudaMemcpyAsync(m->L, W.L, (size_t)l * d * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->nrm_l, W.nrm_l, sizeof(double) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->W, W.W, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->bias, W.bias, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->X1, W.X1, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->lam, W.B.lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaStreamSynchronize(o.st) == cudaSuccess;
+    if (!ok) {
+        mds_model_free(m);
+        return MDS_ERR_CUDA;
+    }
+    *out_model = m;
+    return MDS_OK;
+}
+
+size_t mds_embed_new_workspace_size(mds_model m, int64_t rows) {
+    if (!m || rows <= 0) return 0;
+    Arena A{nullptr, 0};
+    A.take<double>(rows);
+    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)rows * m->d);
+    return A.off + 256;
+}
+
+int mds_embed_new(mds_model m, const void* Ynew, int dt, int64_t rows, const mds_opts* opts,
+                  void* X) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!m || !Ynew || !X || !valid_dt(dt) || rows <= 0) return MDS_ERR_ARG;
+    if (o.prec != m->prec) return MDS_ERR_ARG;
+    Arena A{nullptr, 0};
+    A.take<double>(rows);
+    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)rows * m->d);
+    if ((s = check_ws(o, A.off))) return s;
+    A = Arena{o.ws, 0};
+    begin_call(o.st);
+    double* nrm = A.take<double>(rows);
+    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)rows * m->d) : nullptr;
+    const void* Ye;
+    int dte;
+    if ((s = prep_data(Ynew, dt, rows, m->d, m->prec, nrm, Yq, o, &Ye, &dte))) return s;
+    tmark(0, o.st);
+    tmark(1, o.st);
+    tmark(2, o.st);
+    tmark(3, o.st);
+    CK(launch_gower_proj(Ye, dte, rows, m->d, nrm, m->L, m->nrm_l, m->l, m->W, m->bias, m->r,
+                         m->prec == MDS_PREC_F64, X, o.st));
+    return finish(nullptr, nullptr, o);
+}
+
+int mds_model_info(mds_model m, int* l, int* d, int* r, int* prec, double* lambda) {
+    if (!m) return MDS_ERR_ARG;
+    if (l) *l = m->l;
+    if (d) *d = m->d;
+    if (r) *r = m->r;
+    if (prec) *prec = m->prec;
+    if (lambda && cudaMemcpy(lambda, m->lam, sizeof(double) * m->r, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MDS_ERR_CUDA;
+    return MDS_OK;
+}
+
+void mds_model_free(mds_model m) {
+    if (!m) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(m->device);
+    cudaFree(m->L);
+    cudaFree(m->nrm_l);
+    cudaFree(m->W);
+    cudaFree(m->bias);
+    cudaFree(m->X1);
+    cudaFree(m->lam);
+    cudaSetDevice(cur);
+    delete m;
+}
+
+static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '1'};
+
+int mds_model_save(mds_model m, const char* path) {
+    if (!m || !path) return MDS_ERR_ARG;
+    const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
+    const size_t szL = (size_t)m->l * m->d * es, szW = (size_t)m->l * m->r * es;
+    std::vector<char> L(szL), W(szW), X1(szW);
+    std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
+    if (cudaMemcpy(L.data(), m->L, szL, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(W.data(), m->W, szW, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(X1.data(), m->X1, szW, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nrm.data(), m->nrm_l, 8 * m->l, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(bias.data(), m->bias, 8 * m->r, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(lam.data(), m->lam, 8 * m->r, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MDS_ERR_CUDA;
+    FILE* f = fopen(path, "wb");
+    if (!f) return MDS_ERR_IO;
+    const int32_t hdr[4] = {m->l, m->d, m->r, m->prec};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 &&
+              fwrite(L.data(), 1, szL, f) == szL && fwrite(nrm.data(), 8, m->l, f) == (size_t)m->l &&
+              fwrite(W.data(), 1, szW, f) == szW && fwrite(bias.data(), 8, m->r, f) == (size_t)m->r &&
+              fwrite(X1.data(), 1, szW, f) == szW && fwrite(lam.data(), 8, m->r, f) == (size_t)m->r;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? MDS_OK : MDS_ERR_IO;
+}
+
+int mds_model_load(const char* path, mds_model* out) {
+    if (!path || !out) return MDS_ERR_ARG;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return MDS_ERR_IO;
+    char magic[8];
+    int32_t hdr[4];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, 4, 4, f) != 4 ||
+        hdr[0] < 2 || hdr[0] > kMaxEigN || hdr[1] <= 0 || hdr[2] <= 0 || hdr[2] > kMaxR ||
+        hdr[3] < MDS_PREC_F64 || hdr[3] > MDS_PREC_FP8) {
+        fclose(f);
+        return MDS_ERR_IO;
+    }
+    mds_model m = new (std::nothrow) mds_model_s();
+    if (!m) {
+        fclose(f);
+        return MDS_ERR_NOMEM;
+    }
+    m->l = hdr[0];
+    m->d = hdr[1];
+    m->r = hdr[2];
+    m->prec = hdr[3];
+    cudaGetDevice(&m->device);
+    const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
+    const size_t szL = (size_t)m->l * m->d * es, szW = (size_t)m->l * m->r * es;
+    std::vector<char> L(szL), W(szW), X1(szW);
+    std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
+    bool ok = fread(L.data(), 1, szL, f) == szL && fread(nrm.data(), 8, m->l, f) == (size_t)m->l &&
+              fread(W.data(), 1, szW, f) == szW && fread(bias.data(), 8, m->r, f) == (size_t)m->r &&
+              fread(X1.data(), 1, szW, f) == szW && fread(lam.data(), 8, m->r, f) == (size_t)m->r;
+    fclose(f);
+    if (!ok) {
+        delete m;
+        return MDS_ERR_IO;
+    }
+    ok = cudaMalloc(&m->L, szL) == cudaSuccess && cudaMalloc((void**)&m->nrm_l, 8 * m->l) == cudaSuccess &&
+         cudaMalloc(&m->W, szW) == cudaSuccess && cudaMalloc((void**)&m->bias, 8 * m->r) == cudaSuccess &&
+         cudaMalloc(&m->X1, szW) == cudaSuccess && cudaMalloc((void**)&m->lam, 8 * m->r) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        mds_model_free(m);
+        return MDS_ERR_NOMEM;
+    }
+    ok = cudaMemcpy(m->L, L.data(), szL, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->nrm_l, nrm.data(), 8 * m->l, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->W, W.data(), szW, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->bias, bias.data(), 8 * m->r, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->X1, X1.data(), szW, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->lam, lam.data(), 8 * m->r, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        mds_model_free(m);
+        return MDS_ERR_CUDA;
+    }
+    *out = m;
+    return MDS_OK;
+}
+
+// -------------------------------------------------------- divide-and-conquer
+
+size_t mds_divide_conquer_workspace_size(int64_t n, int d, int p, const int64_t* part_ptr, int c,
+                                         int r, int prec) {
+    if (n <= 0 || d <= 0 || p <= 0 || !part_ptr || c <= 0 || r <= 0) return 0;
+    for (int j = 0; j < p; ++j)
+        if (part_ptr[j + 1] < part_ptr[j] || part_ptr[j + 1] - part_ptr[j] + c > kMaxEigN) return 0;
+    DcWs W;
+    return dc_layout(W, nullptr, n, d, p, part_ptr, c, r, prec, kDefaultSteps) + 256;
+}
+
+int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int64_t* part_ptr,
+                       const int64_t* part_own, const int64_t* anchors, int c, int r,
+                       const mds_opts* opts, void* X, double* var) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!Y || !X || !var || !part_ptr || !anchors || !valid_dt(dt) || n < 2 || d <= 0 || p <= 0 ||
+        r <= 0 || r > kMaxR || c < r + 1 || c > n || part_ptr[0] != 0)
+        return MDS_ERR_ARG;
+    for (int j = 0; j < p; ++j) {
+        const int64_t own = part_ptr[j + 1] - part_ptr[j];
+        if (own < 0 || own + c > kMaxEigN || own + c <= r) return MDS_ERR_ARG;
+    }
+    if (part_ptr[p] > 0 && !part_own) return MDS_ERR_ARG;
+    if (o.prec == MDS_PREC_FP8) return MDS_ERR_UNSUPPORTED;
+    DcWs W;
+    const size_t need = dc_layout(W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    dc_layout(W, o.ws, n, d, p, part_ptr, c, r, o.prec, o.mmax);
+    begin_call(o.st);
+    const int f64 = o.prec == MDS_PREC_F64;
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(launch_check_idx(anchors, c, n, W.flag, o.st));
+    CK(launch_check_idx(part_own, part_ptr[p], n, W.flag, o.st));
+    const void* Ye;
+    int dte;
+    if ((s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
+    tmark(0, o.st);
+    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, o))) return s;
+    CK(launch_dc_procrustes(W.B.d_desc, p, W.B.v, W.B.lam, r, c, W.Tt, o.st));
+    CK(launch_dc_align(W.B.d_desc, p, W.B.max_n, W.B.v, W.B.lam, W.Tt, r, anchors, part_own, f64, X, o.st));
+    CK(launch_dc_lambda_bar(W.B.d_desc, p, W.B.lam, r, var, o.st));
+    return finish(&W.B, W.flag, o);
+}
+
+}  // extern "C"

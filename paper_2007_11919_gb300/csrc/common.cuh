@@ -1,0 +1,169 @@
+// Internal declarations shared by the libgbmds translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gbmds.h"
+
+namespace gbmds {
+
+constexpr int kMaxR = 32;          // largest supported target dimension r
+constexpr int kMaxEigN = 16384;    // largest eigenproblem (points)
+constexpr int kTile = 64;          // distance tile edge (points)
+constexpr int kDtBF16 = 100;       // internal dtype tag: BF16-rounded copy of the data
+
+// One classical-MDS eigenproblem of a batch (the landmark set of Section 3.1,
+// or one part of Section 3.2).  Row a of the problem is data row
+//   a <  c : anchors[a]
+//   a >= c : own[own_off + a - c]
+// All offsets are in elements of the arena they index.
+struct ProbDesc {
+    int64_t own_off;   // first own row in the own-index array
+    int64_t q_off;     // Q_j (n x ldq, row-major FP64) in the Q arena
+    int64_t rp_off;    // per-tile row sums (tiles x n FP64) in the row-part arena
+    int64_t rm_off;    // row means (n FP64) in the row-mean arena
+    int64_t b_off;     // Lanczos basis ((mmax+1) x ldq, column j at j*ldq) in the basis arena
+    int64_t v_off;     // top-r eigenvectors (n x r, row-major FP64) in the V arena
+    int32_t n;         // points in the problem
+    int32_t ldq;       // leading dimension of Q_j and of the basis (n rounded up to 4)
+    int32_t c;         // leading anchor rows (0 = none)
+    int32_t tiles;     // ceil(n / kTile)
+    int64_t ny;        // rows of the data matrix (indices are clamped to [0, ny))
+};
+
+// Device-side status codes written per problem (a subset of mds_status).
+enum DevStatus : int { kDevOk = 0, kDevRank = MDS_ERR_RANK, kDevNoConv = MDS_ERR_NOCONV };
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Out-of-range caller indices are clamped so that no access leaves Y; the
+// host reports them separately (k_check_idx) as MDS_ERR_ARG.
+__device__ __forceinline__ int64_t member_row(const ProbDesc& P, const int64_t* anchors,
+                                              const int64_t* own, int a) {
+    const int64_t g = a < P.c ? anchors[a] : own[P.own_off + (a - P.c)];
+    return g < 0 ? 0 : (g >= P.ny ? P.ny - 1 : g);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Loads element k of a row as the accumulation type.
+template <typename A, typename T>
+__device__ __forceinline__ A load_as(const T* p) { return static_cast<A>(*p); }
+template <>
+__device__ __forceinline__ float load_as<float, uint8_t>(const uint8_t* p) { return (float)(*p); }
+template <>
+__device__ __forceinline__ double load_as<double, uint8_t>(const uint8_t* p) { return (double)(*p); }
+template <>
+__device__ __forceinline__ float load_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+}
+
+// Kernel launches made by the current host thread (for mds_last_stats).
+void note_launch(int count);
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns cudaGetLastError().
+
+// Squared row norms of an n x d matrix into nrm (length n, FP64 storage),
+// accumulated in A (float or double).
+cudaError_t launch_rownorm(const void* Y, int dt, int64_t n, int d, int acc_f64, double* nrm,
+                           cudaStream_t st);
+
+// Delta_j tiles for every problem of a batch, written as FP64 into the Q arena,
+// plus per-tile row sums.  acc_f64 selects FP64 (else FP32) dot products.
+cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nrm,
+                                  const int64_t* anchors, const int64_t* own,
+                                  const ProbDesc* desc, int p, int max_tiles, int acc_f64,
+                                  double* qarena, double* rparena, cudaStream_t st);
+
+// Copy an external n x n FP64 squared-distance matrix into problem 0's Q slot
+// and form its per-tile row sums.
+cudaError_t launch_load_dist(const double* D2, const ProbDesc* desc, double* qarena,
+                             double* rparena, int n, int tiles, cudaStream_t st);
+
+// Double centering in place: Q = -1/2 (Delta - m 1^T - 1 m^T + g) per problem.
+cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double* qarena,
+                                  const double* rparena, double* rmarena, double* grand,
+                                  cudaStream_t st);
+
+struct LanczosArgs {
+    const ProbDesc* desc;
+    int p;
+    const double* qarena;
+    double* barena;
+    double* varena;
+    double* lam;        // p x r
+    int* status;        // p
+    int* steps;         // p
+    double* scratch;    // p x lanczos_scratch_per_problem(mmax, r) doubles
+    int r;
+    int mmax;
+    double tol;
+    double rank_tol;
+    int max_n;
+};
+__host__ __device__ inline size_t lanczos_scratch_per_problem(int mmax, int r) {
+    return (size_t)r * (mmax + 1) * 7 + 8;
+}
+cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st);
+// Shared memory one CTA of the eigen-solver needs for a cluster of cs CTAs.
+size_t lanczos_smem_bytes(int max_n, int cs, int mmax);
+constexpr size_t kMaxSmem = 220 * 1024;
+
+// Interpolation model from the landmark eigenpairs (FP64):
+//   X1 = V Lambda^{1/2};  W = -1/2 V Lambda^{-1/2};  b = 1/2 Lambda^{-1/2} V^T q1.
+// W and X1 are written in double (w64/x1_64) and float (w32/x1_32) when the
+// pointers are not null.
+cudaError_t launch_interp_model(const double* V, const double* lam, const double* Qdiag_src,
+                                int ldq, int l, int r, double* w64, float* w32, double* x1_64,
+                                float* x1_32, double* bias, double* var_out, cudaStream_t st);
+
+// Gather rows Y[idx[i]] into a dense l x d matrix of the accumulation type.
+cudaError_t launch_gather_rows(const void* Y, int dt, int64_t ny, int d, const int64_t* idx,
+                               int l, int acc_f64, void* out, const double* nrm_src,
+                               double* nrm_out, cudaStream_t st);
+
+// Gower projection, Eq. (2): X_i = sum_j a2_ij W_j + b for m rows of Y
+// (FP32 or FP64 SIMT distance tiles).
+cudaError_t launch_gower_proj(const void* Y, int dt, int64_t m, int d, const double* nrm_y,
+                              const void* L, const double* nrm_l, int l, const void* W,
+                              const double* bias, int r, int acc_f64, void* X, cudaStream_t st);
+
+// flag[0] |= 1 when some idx[i] is outside [0, ny).
+cudaError_t launch_check_idx(const int64_t* idx, int64_t count, int64_t ny, int* flag,
+                             cudaStream_t st);
+
+// out[i] = i, i < n.
+cudaError_t launch_iota(int64_t* out, int64_t n, cudaStream_t st);
+
+// Round an F32/F64 matrix to BF16 (round to nearest even), and the FP32 squared
+// norms of the rounded rows.
+cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
+                              cudaStream_t st);
+
+// X[idx[i]] = X1[i] (landmark rows of interpolation MDS).
+cudaError_t launch_scatter_rows(const void* X1, const int64_t* idx, int l, int r, int64_t nx,
+                                int out_f64, void* X, cudaStream_t st);
+
+// Divide-and-conquer: Procrustes of every part against part 0, then the
+// aligned scatter and the averaged eigenvalues.
+cudaError_t launch_dc_procrustes(const ProbDesc* desc, int p, const double* varena,
+                                 const double* lam, int r, int c, double* Tt, cudaStream_t st);
+cudaError_t launch_dc_align(const ProbDesc* desc, int p, int max_n, const double* varena,
+                            const double* lam, const double* Tt, int r, const int64_t* anchors,
+                            const int64_t* own, int out_f64, void* X, cudaStream_t st);
+cudaError_t launch_dc_lambda_bar(const ProbDesc* desc, int p, const double* lam, int r,
+                                 double* var, cudaStream_t st);
+
+// Classical MDS output X = V Lambda^{1/2} in row order of problem 0.
+cudaError_t launch_classical_out(const double* V, const double* lam, int n, int r, int out_f64,
+                                 void* X, double* lam_out, cudaStream_t st);
+
+}  // namespace gbmds

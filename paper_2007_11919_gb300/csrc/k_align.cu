@@ -1,0 +1,207 @@
+// Divide-and-conquer alignment (Section 3.2 of the paper).
+//
+// Part j (j >= 1) is mapped onto part 0 by orthogonal Procrustes on the c
+// connecting points (rows 0..c-1 of every part): find T_j orthogonal and t_j
+// with X_0^c ~ X_j^c T_j + 1 t_j^T.  Centre both point sets,
+// C = B_c^T A_c (r x r, B = X_j^c, A = X_0^c), C = U Sigma W^T (one-sided
+// Jacobi SVD, FP64), T = U W^T, t = a_bar - T^T b_bar.  Reflections are
+// allowed and there is no dilation.  Rows of part j other than the connecting
+// points then receive X_j^a T_j + 1 t_j^T; part 0 keeps X_0 whole.  The
+// eigenvalue estimate is lambda_bar_i = (1/p) sum_j lambda_i^j / n_j.
+#include "common.cuh"
+
+namespace gbmds {
+namespace {
+
+// One warp per part; lane i owns row i of the r x r matrices.
+__global__ void __launch_bounds__(32) k_procrustes(const ProbDesc* __restrict__ desc,
+                                                   const double* __restrict__ varena,
+                                                   const double* __restrict__ lam, int r, int c,
+                                                   double* __restrict__ Tt) {
+    __shared__ double G[kMaxR][kMaxR + 1];
+    __shared__ double Wm[kMaxR][kMaxR + 1];
+    __shared__ double abar[kMaxR], bbar[kMaxR], sq0[kMaxR], sqj[kMaxR];
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x;
+    double* T = Tt + (size_t)j * (r * r + r);
+    double* t = T + r * r;
+    if (j == 0) {
+        for (int e = lane; e < r * r; e += 32) T[e] = (e / r == e % r) ? 1.0 : 0.0;
+        if (lane < r) t[lane] = 0.0;
+        return;
+    }
+    const double* V0 = varena + desc[0].v_off;
+    const double* Vj = varena + desc[j].v_off;
+    if (lane < r) {
+        sq0[lane] = sqrt(lam[lane]);
+        sqj[lane] = sqrt(lam[(size_t)j * r + lane]);
+    }
+    __syncwarp();
+    if (lane < r) {
+        double sa = 0.0, sb = 0.0;
+        for (int a = 0; a < c; ++a) {
+            sa += V0[(int64_t)a * r + lane] * sq0[lane];
+            sb += Vj[(int64_t)a * r + lane] * sqj[lane];
+        }
+        abar[lane] = sa / c;
+        bbar[lane] = sb / c;
+    }
+    __syncwarp();
+    // C[i][m] = sum_a (B_ai - bbar_i)(A_am - abar_m); lane i builds row i
+    if (lane < r) {
+        for (int m = 0; m < r; ++m) {
+            double s = 0.0;
+            for (int a = 0; a < c; ++a) {
+                const double b = Vj[(int64_t)a * r + lane] * sqj[lane] - bbar[lane];
+                const double av = V0[(int64_t)a * r + m] * sq0[m] - abar[m];
+                s += b * av;
+            }
+            G[lane][m] = s;
+        }
+        for (int m = 0; m < r; ++m) Wm[lane][m] = (lane == m) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    // one-sided Jacobi: rotate column pairs of G (and W) until orthogonal
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < r - 1; ++p) {
+            for (int q = p + 1; q < r; ++q) {
+                const double gp = lane < r ? G[lane][p] : 0.0;
+                const double gq = lane < r ? G[lane][q] : 0.0;
+                const double al = warp_sum(gp * gp);
+                const double be = warp_sum(gq * gq);
+                const double ga = warp_sum(gp * gq);
+                if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
+                    ++rotated;
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + tt * tt);
+                    const double sn = cs * tt;
+                    if (lane < r) {
+                        G[lane][p] = cs * gp - sn * gq;
+                        G[lane][q] = sn * gp + cs * gq;
+                        const double wp = Wm[lane][p], wq = Wm[lane][q];
+                        Wm[lane][p] = cs * wp - sn * wq;
+                        Wm[lane][q] = sn * wp + cs * wq;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (rotated == 0) break;
+    }
+    // U columns = G columns / sigma; complete null directions by Gram-Schmidt
+    double smax = 0.0;
+    for (int m = 0; m < r; ++m) {
+        const double g = lane < r ? G[lane][m] : 0.0;
+        smax = fmax(smax, sqrt(warp_sum(g * g)));
+    }
+    int unit = 0;
+    for (int m = 0; m < r; ++m) {
+        const double g = lane < r ? G[lane][m] : 0.0;
+        const double sg = sqrt(warp_sum(g * g));
+        if (sg > 1e-13 * smax && sg > 0.0) {
+            if (lane < r) G[lane][m] = g / sg;
+        } else {
+            // a unit vector orthogonal to the other (already normalised or later) columns
+            for (; unit < r; ++unit) {
+                double v = lane == unit ? 1.0 : 0.0;
+                for (int o = 0; o < r; ++o) {
+                    if (o == m) continue;
+                    const double go = lane < r ? G[lane][o] : 0.0;
+                    const double no = warp_sum(go * go);
+                    if (no == 0.0) continue;
+                    v -= warp_sum(go * v) / no * go;
+                }
+                const double nv = sqrt(warp_sum(v * v));
+                if (nv > 1e-6) {
+                    if (lane < r) G[lane][m] = v / nv;
+                    ++unit;
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // T = U W^T ; t = abar - T^T bbar
+    if (lane < r) {
+        for (int m = 0; m < r; ++m) {
+            double s = 0.0;
+            for (int k = 0; k < r; ++k) s += G[lane][k] * Wm[m][k];
+            T[lane * r + m] = s;
+        }
+    }
+    __syncwarp();
+    if (lane < r) {
+        double s = 0.0;
+        for (int i = 0; i < r; ++i) s += T[i * r + lane] * bbar[i];
+        t[lane] = abar[lane] - s;
+    }
+}
+
+template <typename A>
+__global__ void __launch_bounds__(256) k_align(const ProbDesc* __restrict__ desc,
+                                               const double* __restrict__ varena,
+                                               const double* __restrict__ lam,
+                                               const double* __restrict__ Tt, int r,
+                                               const int64_t* __restrict__ anchors,
+                                               const int64_t* __restrict__ own,
+                                               A* __restrict__ X) {
+    const int j = blockIdx.y;
+    const ProbDesc P = desc[j];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= P.n) return;
+    if (j > 0 && a < P.c) return;  // connecting points come from part 0
+    const double* V = varena + P.v_off + (int64_t)a * r;
+    const double* T = Tt + (size_t)j * (r * r + r);
+    const double* t = T + r * r;
+    double x[kMaxR];
+#pragma unroll
+    for (int m = 0; m < kMaxR; ++m)
+        if (m < r) x[m] = V[m] * sqrt(lam[(size_t)j * r + m]);
+    const int64_t row = member_row(P, anchors, own, a);
+    for (int i = 0; i < r; ++i) {
+        double s = t[i];
+#pragma unroll
+        for (int m = 0; m < kMaxR; ++m)
+            if (m < r) s += x[m] * T[m * r + i];
+        X[row * r + i] = (A)s;
+    }
+}
+
+__global__ void k_lambda_bar(const ProbDesc* __restrict__ desc, int p,
+                             const double* __restrict__ lam, int r, double* __restrict__ var) {
+    const int i = threadIdx.x;
+    if (i >= r) return;
+    double s = 0.0;
+    for (int j = 0; j < p; ++j) s += lam[(size_t)j * r + i] / desc[j].n;
+    var[i] = s / p;
+}
+
+}  // namespace
+
+cudaError_t launch_dc_procrustes(const ProbDesc* desc, int p, const double* varena,
+                                 const double* lam, int r, int c, double* Tt, cudaStream_t st) {
+    k_procrustes<<<p, 32, 0, st>>>(desc, varena, lam, r, c, Tt);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_align(const ProbDesc* desc, int p, int max_n, const double* varena,
+                            const double* lam, const double* Tt, int r, const int64_t* anchors,
+                            const int64_t* own, int out_f64, void* X, cudaStream_t st) {
+    const dim3 grid((unsigned)((max_n + 255) / 256), (unsigned)p);
+    if (out_f64) k_align<double><<<grid, 256, 0, st>>>(desc, varena, lam, Tt, r, anchors, own, (double*)X);
+    else k_align<float><<<grid, 256, 0, st>>>(desc, varena, lam, Tt, r, anchors, own, (float*)X);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_lambda_bar(const ProbDesc* desc, int p, const double* lam, int r,
+                                 double* var, cudaStream_t st) {
+    k_lambda_bar<<<1, 32, 0, st>>>(desc, p, lam, r, var);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gbmds

@@ -1,0 +1,352 @@
+// Row norms, batched squared-distance tiles and double centering.
+//
+// Section 2 of the paper: for Euclidean rows y_i, d^2_ij = q_ii + q_jj - 2 q_ij,
+// here d^2_ij = ||y_i||^2 + ||y_j||^2 - 2 y_i . y_j (norm form, clamped at 0,
+// exact 0 on the diagonal), and Q = -1/2 P Delta P, i.e.
+// q_ij = -(d2_ij - d2_i. - d2_.j + d2_..)/2 with row / column / grand means.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace gbmds {
+
+namespace {
+
+// ------------------------------------------------------------------ norms
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_rownorm(const T* __restrict__ Y, int64_t n, int d,
+                                                 double* __restrict__ nrm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const T* y = Y + row * (int64_t)d;
+    A s = 0;
+    for (int k = lane; k < d; k += 32) {
+        A v = load_as<A, T>(y + k);
+        s += v * v;
+    }
+    s = warp_sum(s);
+    if (lane == 0) nrm[row] = (double)s;
+}
+
+// ------------------------------------------------------- distance tiles
+// One CTA = one 64 x 64 tile (rows a0.., columns b0..) of Delta_j for problem
+// blockIdx.y.  256 threads, 4 x 4 outputs each; K staged through shared memory
+// 16 at a time.  Writes Delta as FP64 (row-major, ld = ldq) and the tile's row
+// sums into rp[tb * n + a] (summed later in a fixed order).
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
+                                                const double* __restrict__ nrm,
+                                                const int64_t* __restrict__ anchors,
+                                                const int64_t* __restrict__ own,
+                                                const ProbDesc* __restrict__ desc,
+                                                double* __restrict__ qarena,
+                                                double* __restrict__ rparena) {
+    constexpr int KC = 16;
+    constexpr int LD = kTile + 4;
+    __shared__ __align__(16) A As[KC][LD];
+    __shared__ __align__(16) A Bs[KC][LD];
+    __shared__ int64_t rowA[kTile], rowB[kTile];
+
+    const ProbDesc P = desc[blockIdx.y];
+    const int n = P.n;
+    const int t = blockIdx.x;
+    if (t >= P.tiles * P.tiles) return;
+    const int ta = t / P.tiles, tb = t % P.tiles;
+    const int a0 = ta * kTile, b0 = tb * kTile;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+
+    if (tid < kTile) {
+        const int a = a0 + tid;
+        rowA[tid] = a < n ? member_row(P, anchors, own, a) : -1;
+    } else if (tid < 2 * kTile) {
+        const int b = b0 + tid - kTile;
+        rowB[tid - kTile] = b < n ? member_row(P, anchors, own, b) : -1;
+    }
+    __syncthreads();
+
+    A acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0;
+
+    for (int k0 = 0; k0 < d; k0 += KC) {
+#pragma unroll
+        for (int e = tid; e < kTile * KC; e += 256) {
+            const int row = e / KC, kk = e % KC, k = k0 + kk;
+            const int64_t ga = rowA[row], gb = rowB[row];
+            As[kk][row] = (ga >= 0 && k < d) ? load_as<A, T>(Y + ga * d + k) : A(0);
+            Bs[kk][row] = (gb >= 0 && k < d) ? load_as<A, T>(Y + gb * d + k) : A(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            A av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                av[i] = As[kk][ty * 4 + i];
+                bv[i] = Bs[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] += av[i] * bv[jj];
+        }
+        __syncthreads();
+    }
+
+    double* Q = qarena + P.q_off;
+    double* rp = rparena + P.rp_off;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int a = a0 + ty * 4 + i;
+        double rs = 0.0;
+        if (a < n) {
+            const A na = (A)nrm[rowA[ty * 4 + i]];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int b = b0 + tx * 4 + jj;
+                if (b < n) {
+                    const A nb = (A)nrm[rowB[tx * 4 + jj]];
+                    A dist = na + nb - A(2) * acc[i][jj];
+                    dist = dist > A(0) ? dist : A(0);
+                    if (a == b) dist = A(0);
+                    Q[(int64_t)a * P.ldq + b] = (double)dist;
+                    rs += (double)dist;
+                }
+            }
+        }
+        // sum over the 16 column-threads of this row (same warp, lanes xor 1..8)
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        if (tx == 0 && a < n) rp[(int64_t)tb * n + a] = rs;
+    }
+}
+
+// Copy an external squared-distance matrix into Q's slot with tile row sums.
+__global__ void __launch_bounds__(256) k_load_dist(const double* __restrict__ D2,
+                                                   const ProbDesc* __restrict__ desc,
+                                                   double* __restrict__ qarena,
+                                                   double* __restrict__ rparena) {
+    const ProbDesc P = desc[0];
+    const int n = P.n;
+    const int a = blockIdx.x;
+    if (a >= n) return;
+    __shared__ double red[8];
+    double* Q = qarena + P.q_off + (int64_t)a * P.ldq;
+    const double* src = D2 + (int64_t)a * n;
+    double* rp = rparena + P.rp_off;
+    for (int tb = 0; tb < P.tiles; ++tb) {
+        const int b = tb * kTile + (threadIdx.x & 63);
+        double v = 0.0;
+        if (threadIdx.x < kTile && b < n) {
+            v = src[b];
+            Q[b] = v;
+        }
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) rp[(int64_t)tb * n + a] = red[0] + red[1];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ centering
+
+__global__ void __launch_bounds__(256) k_rowmean(const ProbDesc* __restrict__ desc,
+                                                 const double* __restrict__ rparena,
+                                                 double* __restrict__ rmarena,
+                                                 double* __restrict__ grand) {
+    const ProbDesc P = desc[blockIdx.x];
+    const int n = P.n;
+    const double* rp = rparena + P.rp_off;
+    double* rm = rmarena + P.rm_off;
+    __shared__ double red[8];
+    double loc = 0.0;
+    for (int a = threadIdx.x; a < n; a += 256) {
+        double s = 0.0;
+        for (int tb = 0; tb < P.tiles; ++tb) s += rp[(int64_t)tb * n + a];
+        const double m = s / n;
+        rm[a] = m;
+        loc += m;
+    }
+    loc = warp_sum(loc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        grand[blockIdx.x] = s / n;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_center(const ProbDesc* __restrict__ desc,
+                                                double* __restrict__ qarena,
+                                                const double* __restrict__ rmarena,
+                                                const double* __restrict__ grand) {
+    const ProbDesc P = desc[blockIdx.y];
+    const int a = blockIdx.x;
+    if (a >= P.n) return;
+    const double* rm = rmarena + P.rm_off;
+    const double g = grand[blockIdx.y];
+    const double ma = rm[a];
+    double* Q = qarena + P.q_off + (int64_t)a * P.ldq;
+    for (int b = threadIdx.x; b < P.n; b += 256) Q[b] = -0.5 * (Q[b] - ma - rm[b] + g);
+}
+
+__global__ void k_check_idx(const int64_t* __restrict__ idx, int64_t count, int64_t ny,
+                            int* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count && (idx[i] < 0 || idx[i] >= ny)) atomicOr(flag, 1);
+}
+
+__global__ void k_iota(int64_t* __restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_quant_bf16(const T* __restrict__ Y, int64_t n, int d,
+                                                    __nv_bfloat16* __restrict__ Yq,
+                                                    double* __restrict__ nrm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= n) return;
+    float s = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        const __nv_bfloat16 q = __float2bfloat16_rn((float)Y[row * d + k]);
+        Yq[row * d + k] = q;
+        const float v = __bfloat162float(q);
+        s += v * v;
+    }
+    s = warp_sum(s);
+    if (lane == 0) nrm[row] = (double)s;
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_gather(const T* __restrict__ Y, int d,
+                                                const int64_t* __restrict__ idx, int l,
+                                                int64_t ny, A* __restrict__ out,
+                                                const double* __restrict__ nrm_src,
+                                                double* __restrict__ nrm_out) {
+    const int i = blockIdx.x;
+    if (i >= l) return;
+    int64_t g = idx[i];
+    g = g < 0 ? 0 : (g >= ny ? ny - 1 : g);
+    for (int k = threadIdx.x; k < d; k += blockDim.x) out[(int64_t)i * d + k] = load_as<A, T>(Y + g * d + k);
+    if (threadIdx.x == 0 && nrm_out) nrm_out[i] = nrm_src[g];
+}
+
+}  // namespace
+
+cudaError_t launch_rownorm(const void* Y, int dt, int64_t n, int d, int acc_f64, double* nrm,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((n + 7) / 8)), block(256);
+    if (acc_f64) {
+        if (dt == MDS_IN_F64) k_rownorm<double, double><<<grid, block, 0, st>>>((const double*)Y, n, d, nrm);
+        else if (dt == MDS_IN_F32) k_rownorm<float, double><<<grid, block, 0, st>>>((const float*)Y, n, d, nrm);
+        else k_rownorm<uint8_t, double><<<grid, block, 0, st>>>((const uint8_t*)Y, n, d, nrm);
+    } else {
+        if (dt == MDS_IN_F64) k_rownorm<double, float><<<grid, block, 0, st>>>((const double*)Y, n, d, nrm);
+        else if (dt == MDS_IN_F32) k_rownorm<float, float><<<grid, block, 0, st>>>((const float*)Y, n, d, nrm);
+        else k_rownorm<uint8_t, float><<<grid, block, 0, st>>>((const uint8_t*)Y, n, d, nrm);
+    }
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nrm,
+                                  const int64_t* anchors, const int64_t* own,
+                                  const ProbDesc* desc, int p, int max_tiles, int acc_f64,
+                                  double* qarena, double* rparena, cudaStream_t st) {
+    if (p <= 0) return cudaSuccess;
+    dim3 grid((unsigned)(max_tiles * max_tiles), (unsigned)p), block(256);
+    if (acc_f64) {
+        if (dt == MDS_IN_F64)
+            k_sqdist<double, double><<<grid, block, 0, st>>>((const double*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+        else if (dt == MDS_IN_F32)
+            k_sqdist<float, double><<<grid, block, 0, st>>>((const float*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+        else
+            k_sqdist<uint8_t, double><<<grid, block, 0, st>>>((const uint8_t*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+    } else {
+        if (dt == MDS_IN_F64)
+            k_sqdist<double, float><<<grid, block, 0, st>>>((const double*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+        else if (dt == kDtBF16)
+            k_sqdist<__nv_bfloat16, float><<<grid, block, 0, st>>>((const __nv_bfloat16*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+        else if (dt == MDS_IN_F32)
+            k_sqdist<float, float><<<grid, block, 0, st>>>((const float*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+        else
+            k_sqdist<uint8_t, float><<<grid, block, 0, st>>>((const uint8_t*)Y, d, nrm, anchors, own, desc, qarena, rparena);
+    }
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_dist(const double* D2, const ProbDesc* desc, double* qarena,
+                             double* rparena, int n, int tiles, cudaStream_t st) {
+    (void)tiles;
+    k_load_dist<<<n, 256, 0, st>>>(D2, desc, qarena, rparena);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double* qarena,
+                                  const double* rparena, double* rmarena, double* grand,
+                                  cudaStream_t st) {
+    if (p <= 0) return cudaSuccess;
+    k_rowmean<<<p, 256, 0, st>>>(desc, rparena, rmarena, grand);
+    k_center<<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const void* Y, int dt, int64_t ny, int d, const int64_t* idx,
+                               int l, int acc_f64, void* out, const double* nrm_src, double* nrm_out,
+                               cudaStream_t st) {
+    if (l <= 0) return cudaSuccess;
+    if (acc_f64) {
+        if (dt == MDS_IN_F64) k_gather<double, double><<<l, 128, 0, st>>>((const double*)Y, d, idx, l, ny, (double*)out, nrm_src, nrm_out);
+        else if (dt == MDS_IN_F32) k_gather<float, double><<<l, 128, 0, st>>>((const float*)Y, d, idx, l, ny, (double*)out, nrm_src, nrm_out);
+        else k_gather<uint8_t, double><<<l, 128, 0, st>>>((const uint8_t*)Y, d, idx, l, ny, (double*)out, nrm_src, nrm_out);
+    } else {
+        if (dt == MDS_IN_F64) k_gather<double, float><<<l, 128, 0, st>>>((const double*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
+        else if (dt == kDtBF16) k_gather<__nv_bfloat16, float><<<l, 128, 0, st>>>((const __nv_bfloat16*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
+        else if (dt == MDS_IN_F32) k_gather<float, float><<<l, 128, 0, st>>>((const float*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
+        else k_gather<uint8_t, float><<<l, 128, 0, st>>>((const uint8_t*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
+    }
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_idx(const int64_t* idx, int64_t count, int64_t ny, int* flag,
+                             cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_check_idx<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(idx, count, ny, flag);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int64_t* out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_iota<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((n + 7) / 8));
+    if (dt == MDS_IN_F64) k_quant_bf16<double><<<grid, 256, 0, st>>>((const double*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
+    else if (dt == MDS_IN_F32) k_quant_bf16<float><<<grid, 256, 0, st>>>((const float*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
+    else k_quant_bf16<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gbmds

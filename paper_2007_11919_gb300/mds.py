@@ -1,0 +1,259 @@
+"""Python binding of libgbmds.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (see
+include/gbmds.h): it checks tensor placement and dtypes, allocates the output
+tensors and the scratch workspace with PyTorch on the data's device, passes
+raw pointers and the current CUDA stream, and turns a non-zero status into
+``MdsError``.  All arithmetic happens in the CUDA kernels behind the C ABI;
+there is no CPU fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbmds.so")
+
+PREC = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
+DTYPE = {torch.float64: 0, torch.float32: 1, torch.uint8: 2}
+STATUS = {0: "MDS_OK", 1: "MDS_ERR_ARG", 2: "MDS_ERR_NOMEM", 3: "MDS_ERR_CUDA", 4: "MDS_ERR_RANK",
+          5: "MDS_ERR_NOCONV", 6: "MDS_ERR_TIMEOUT", 7: "MDS_ERR_UNSUPPORTED",
+          8: "MDS_ERR_WORKSPACE", 9: "MDS_ERR_IO"}
+
+
+class MdsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib().mds_status_str(status).decode()})")
+
+
+class MdsOpts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("eig_tol", ctypes.c_double), ("rank_tol", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("cluster", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+_L = None
+_P, _I, _I32, _I64, _D, _SZ = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
+                               ctypes.c_double, ctypes.c_size_t)
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_2007_11919_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "mds_status_str": (ctypes.c_char_p, [_I]),
+            "mds_version": (_I, []),
+            "mds_classical_workspace_size": (_SZ, [_I64, _I, _I, _I]),
+            "mds_classical": (_I, [_P, _I, _I64, _I, _I, _P, _P, _P]),
+            "mds_classical_dist_workspace_size": (_SZ, [_I64, _I]),
+            "mds_classical_dist": (_I, [_P, _I64, _I, _P, _P, _P]),
+            "mds_interpolate_workspace_size": (_SZ, [_I64, _I, _I, _I, _I]),
+            "mds_interpolate": (_I, [_P, _I, _I64, _I, _P, _I, _I, _P, _P, _P, _P]),
+            "mds_embed_new_workspace_size": (_SZ, [_P, _I64]),
+            "mds_embed_new": (_I, [_P, _P, _I, _I64, _P, _P]),
+            "mds_model_info": (_I, [_P, _P, _P, _P, _P, _P]),
+            "mds_model_save": (_I, [_P, ctypes.c_char_p]),
+            "mds_model_load": (_I, [ctypes.c_char_p, _P]),
+            "mds_model_free": (None, [_P]),
+            "mds_divide_conquer_workspace_size": (_SZ, [_I64, _I, _I, _P, _I, _I, _I]),
+            "mds_divide_conquer": (_I, [_P, _I, _I64, _I, _I, _P, _P, _P, _I, _I, _P, _P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _L = L
+    return _L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise MdsError(status, where)
+
+
+def _opts(device, prec, nbytes, stream=None, max_steps=0, eig_tol=0.0, rank_tol=0.0, cluster=0,
+          workspace=None):
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    o = MdsOpts(prec=PREC[prec], max_steps=max_steps, eig_tol=eig_tol, rank_tol=rank_tol,
+                stream=ctypes.c_void_p(st.cuda_stream), workspace=_ptr(workspace),
+                workspace_bytes=workspace.numel(), cluster=cluster, flags=0)
+    return o, workspace
+
+
+def _data(Y):
+    if not (isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()):
+        raise ValueError("data must be a contiguous 2-D CUDA tensor")
+    if Y.dtype not in DTYPE:
+        raise ValueError(f"unsupported dtype {Y.dtype}")
+    return DTYPE[Y.dtype]
+
+
+def _idx(t, device):
+    t = torch.as_tensor(t, dtype=torch.int64)
+    return t.to(device).contiguous()
+
+
+def _xdtype(prec):
+    return torch.float64 if prec == "f64" else torch.float32
+
+
+def mds_version() -> int:
+    return _lib().mds_version()
+
+
+def mds_classical(Y, r, prec="f64", **kw):
+    """Classical MDS of the rows of Y (Section 2). Returns (X n x r, lambda r)."""
+    dt = _data(Y)
+    n, d = Y.shape
+    L = _lib()
+    o, ws = _opts(Y.device, prec, L.mds_classical_workspace_size(n, d, r, PREC[prec]), **kw)
+    X = torch.empty((n, r), dtype=_xdtype(prec), device=Y.device)
+    lam = torch.empty(r, dtype=torch.float64, device=Y.device)
+    _check(L.mds_classical(_ptr(Y), dt, n, d, r, ctypes.byref(o), _ptr(X), _ptr(lam)), "mds_classical")
+    return X, lam
+
+
+def mds_classical_dist(D2, r, **kw):
+    """Classical MDS of an n x n squared-distance matrix (FP64, on the GPU)."""
+    if not (D2.is_cuda and D2.dtype == torch.float64 and D2.is_contiguous() and D2.dim() == 2):
+        raise ValueError("D2 must be a contiguous n x n float64 CUDA tensor")
+    n = D2.shape[0]
+    L = _lib()
+    o, ws = _opts(D2.device, "f64", L.mds_classical_dist_workspace_size(n, r), **kw)
+    X = torch.empty((n, r), dtype=torch.float64, device=D2.device)
+    lam = torch.empty(r, dtype=torch.float64, device=D2.device)
+    _check(L.mds_classical_dist(_ptr(D2), n, r, ctypes.byref(o), _ptr(X), _ptr(lam)), "mds_classical_dist")
+    return X, lam
+
+
+class Model:
+    """Owner of an mds_model handle (device-resident landmark configuration)."""
+
+    def __init__(self, handle: int, device):
+        self.handle = ctypes.c_void_p(handle)
+        self.device = torch.device(device)
+
+    def info(self):
+        l, d, r, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().mds_model_info(self.handle, ctypes.byref(l), ctypes.byref(d), ctypes.byref(r),
+                                     ctypes.byref(p), None), "mds_model_info")
+        lam = (ctypes.c_double * r.value)()
+        _check(_lib().mds_model_info(self.handle, None, None, None, None, lam), "mds_model_info")
+        inv = {v: k for k, v in PREC.items()}
+        return {"l": l.value, "d": d.value, "r": r.value, "prec": inv[p.value], "lambda": list(lam)}
+
+    def save(self, path: str):
+        _check(_lib().mds_model_save(self.handle, path.encode()), "mds_model_save")
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        h = ctypes.c_void_p()
+        with torch.cuda.device(torch.device(device)):
+            _check(_lib().mds_model_load(path.encode(), ctypes.byref(h)), "mds_model_load")
+        return cls(h.value, device)
+
+    def free(self):
+        if self.handle and self.handle.value:
+            _lib().mds_model_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mds_interpolate(Y, landmark_idx, r, prec="f32", want_model=False, **kw):
+    """Interpolation MDS (Section 3.1). Returns (X n x r, var r, Model or None)."""
+    dt = _data(Y)
+    n, d = Y.shape
+    idx = _idx(landmark_idx, Y.device)
+    l = idx.numel()
+    L = _lib()
+    o, ws = _opts(Y.device, prec, L.mds_interpolate_workspace_size(n, d, l, r, PREC[prec]), **kw)
+    X = torch.empty((n, r), dtype=_xdtype(prec), device=Y.device)
+    var = torch.empty(r, dtype=torch.float64, device=Y.device)
+    h = ctypes.c_void_p()
+    _check(L.mds_interpolate(_ptr(Y), dt, n, d, _ptr(idx), l, r, ctypes.byref(o), _ptr(X), _ptr(var),
+                             ctypes.byref(h) if want_model else None), "mds_interpolate")
+    return X, var, (Model(h.value, Y.device) if want_model else None)
+
+
+def mds_embed_new(model: Model, Ynew, prec=None, **kw):
+    """Gower's formula (Eq. (2)) for new rows against a stored model."""
+    dt = _data(Ynew)
+    m = Ynew.shape[0]
+    info_prec = prec if prec is not None else model.info()["prec"]
+    r = model.info()["r"] if "r" not in kw else kw.pop("r")
+    L = _lib()
+    o, ws = _opts(Ynew.device, info_prec, L.mds_embed_new_workspace_size(model.handle, m), **kw)
+    X = torch.empty((m, r), dtype=_xdtype(info_prec), device=Ynew.device)
+    _check(L.mds_embed_new(model.handle, _ptr(Ynew), dt, m, ctypes.byref(o), _ptr(X)), "mds_embed_new")
+    return X
+
+
+def mds_divide_conquer(Y, anchors, part_ptr, part_own, r, prec="f32", **kw):
+    """Divide-and-conquer MDS (Section 3.2). ``part_ptr`` is host data (p+1
+    offsets); ``anchors`` and ``part_own`` index rows of Y.  Returns (X, var)."""
+    dt = _data(Y)
+    n, d = Y.shape
+    anc = _idx(anchors, Y.device)
+    own = _idx(part_own, Y.device)
+    ptr = np.ascontiguousarray(np.asarray(part_ptr, dtype=np.int64))
+    p = len(ptr) - 1
+    c = anc.numel()
+    pp = ptr.ctypes.data_as(ctypes.c_void_p)
+    L = _lib()
+    o, ws = _opts(Y.device, prec, L.mds_divide_conquer_workspace_size(n, d, p, pp, c, r, PREC[prec]), **kw)
+    X = torch.zeros((n, r), dtype=_xdtype(prec), device=Y.device)
+    var = torch.empty(r, dtype=torch.float64, device=Y.device)
+    _check(L.mds_divide_conquer(_ptr(Y), dt, n, d, p, pp, _ptr(own), _ptr(anc), c, r, ctypes.byref(o),
+                                _ptr(X), _ptr(var)), "mds_divide_conquer")
+    return X, var
+
+
+class MdsStats(ctypes.Structure):
+    _fields_ = [("stage_ms", ctypes.c_double * 5), ("launches", ctypes.c_int64),
+                ("eig_steps", ctypes.c_int64), ("eig_flops", ctypes.c_double),
+                ("eig_qbytes", ctypes.c_double), ("problems", ctypes.c_int32),
+                ("cluster", ctypes.c_int32)]
+
+
+STAGES = ("prep", "dist", "center", "eig", "post")
+
+
+def mds_set_timing(on: bool):
+    """Record CUDA events between pipeline stages of later calls (this thread)."""
+    L = _lib()
+    L.mds_set_timing.argtypes = [_I]
+    L.mds_set_timing.restype = None
+    L.mds_set_timing(1 if on else 0)
+
+
+def mds_last_stats() -> dict:
+    """Stage times, launch count and eigen-solver work of the last call (this thread)."""
+    L = _lib()
+    L.mds_last_stats.argtypes = [_P]
+    L.mds_last_stats.restype = _I
+    s = MdsStats()
+    _check(L.mds_last_stats(ctypes.byref(s)), "mds_last_stats")
+    return {"stage_ms": dict(zip(STAGES, list(s.stage_ms))), "launches": s.launches,
+            "eig_steps": s.eig_steps, "eig_flops": s.eig_flops, "eig_qbytes": s.eig_qbytes,
+            "problems": s.problems, "cluster": s.cluster}

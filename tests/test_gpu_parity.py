@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (relative Frobenius error after the best orthogonal alignment,
+Section 4.1's Procrustes comparison):
+  FP64 path                 1e-10   (eigenvalues 1e-10 relative)
+  FP32 path                 1e-5    (eigenvalues 1e-6 relative)
+  BF16 distance path        2e-3
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 2e-3}
+LAM_TOL = {"f64": 1e-10, "f32": 1e-6, "bf16": 2e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gb():
+    from paper_2007_11919_gb300 import build
+    build.build()
+    import paper_2007_11919_gb300 as G
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return G
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.abs(np.asarray(b))))
+
+
+# ------------------------------------------------------------- classical
+
+
+@pytest.mark.parametrize("n,d,r", [(300, 10, 3), (64, 5, 2), (129, 40, 6)])
+def test_classical_f64(gb, n, d, r):
+    Y = W.gaussian_dominant(n, d, r, seed=n)
+    Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), r)
+    X, lam = gb.mds_classical(dev(Y), r, "f64")
+    assert rel(host(lam), lo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+    # same sign convention on both sides: elementwise agreement
+    assert np.max(np.abs(host(X) - Xo)) < 1e-8 * np.max(np.abs(Xo))
+
+
+def test_classical_dist_non_euclidean(gb):
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((257, 6)) * np.array([5, 4, 3, 2, 1, 1.0])
+    D = O.sq_dist(Y, Y)
+    E = rng.uniform(0, 0.5, size=D.shape)
+    D = D + E + E.T
+    np.fill_diagonal(D, 0.0)
+    Xo, lo, _, _ = O.classical_mds(D, 4)
+    X, lam = gb.mds_classical_dist(dev(D), 4)
+    assert rel(host(lam), lo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+
+
+def test_classical_f32(gb):
+    Y = W.gaussian_dominant(500, 20, 4, seed=5, dtype=np.float32)
+    Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 4)
+    X, lam = gb.mds_classical(dev(Y), 4, "f32")
+    assert X.dtype == torch.float32
+    assert rel(host(lam), lo) < LAM_TOL["f32"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f32"]
+
+
+def test_classical_uint8(gb):
+    Y = W.image_like(300, 64, seed=2)
+    Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 5)
+    X, lam = gb.mds_classical(dev(Y), 5, "f64")
+    assert rel(host(lam), lo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 3, 8, 16])
+def test_cluster_sizes_agree(gb, cluster):
+    Y = W.gaussian_dominant(1000, 30, 5, seed=9)
+    Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 5)
+    X, lam = gb.mds_classical(dev(Y), 5, "f64", cluster=cluster)
+    assert rel(host(lam), lo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+
+
+def test_tiny_problems(gb):
+    Y = W.gaussian_dominant(5, 4, 3, seed=1)                   # n = r + 2
+    Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 3)
+    X, lam = gb.mds_classical(dev(Y), 3, "f64")
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+    Y1 = np.random.default_rng(0).standard_normal((40, 1))     # d = 1, r = 1
+    Xo1, lo1, _, _ = O.classical_mds(O.sq_dist(Y1, Y1), 1)
+    X1, l1 = gb.mds_classical(dev(Y1), 1, "f64")
+    assert O.aligned_rel_error(host(X1), Xo1) < TOL["f64"] and rel(host(l1), lo1) < 1e-10
+
+
+def test_rank_error(gb):
+    rng = np.random.default_rng(7)
+    Y = rng.standard_normal((80, 2)) @ rng.standard_normal((2, 6))   # rank 2
+    with pytest.raises(gb.MdsError) as e:
+        gb.mds_classical(dev(Y), 3, "f64")
+    assert e.value.status == 4
+
+
+# ---------------------------------------------------------- interpolation
+
+
+def test_interp_f64_small_config(gb):
+    """n=2,000 points in d=10, N(0, diag(15,15,15,1,...)), l=300, r=3, FP64."""
+    w = W.CLASSICAL_INTERP_F64
+    Y = W.make_data(w, seed=0)
+    idx = W.landmarks(w.n, w.l, seed=0)
+    Xo, vo, _ = O.interpolation_mds(Y, idx, w.r)
+    X, var, _ = gb.mds_interpolate(dev(Y), dev(idx), w.r, "f64")
+    assert rel(host(var), vo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+    assert np.max(np.abs(host(X) - Xo)) < 1e-8 * np.max(np.abs(Xo))
+
+
+@pytest.mark.parametrize("n,l", [(5000, 500), (3001, 130)])
+def test_interp_f32(gb, n, l):
+    Y = W.gaussian_dominant(n, 100, 10, seed=l, dtype=np.float32)
+    idx = W.landmarks(n, l, seed=l)
+    Xo, vo, _ = O.interpolation_mds(Y, idx, 10)
+    X, var, _ = gb.mds_interpolate(dev(Y), dev(idx), 10, "f32")
+    assert rel(host(var), vo) < LAM_TOL["f32"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f32"]
+
+
+def test_interp_bf16(gb):
+    Y = W.gaussian_mixture(8000, 100, 4, 5.0, seed=1)
+    idx = W.landmarks(8000, 1000, seed=1)
+    Xo, vo, _ = O.interpolation_mds(Y, idx, 10)
+    X, var, _ = gb.mds_interpolate(dev(Y), dev(idx), 10, "bf16")
+    assert rel(host(var), vo) < LAM_TOL["bf16"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["bf16"]
+
+
+def test_interp_l_equals_n_is_classical(gb):
+    Y = W.gaussian_dominant(200, 8, 3, seed=4)
+    idx = np.arange(200)
+    X, var, _ = gb.mds_interpolate(dev(Y), dev(idx), 3, "f64")
+    Xc, lc, _, _ = O.classical_mds(O.sq_dist(Y, Y), 3)
+    assert O.aligned_rel_error(host(X), Xc) < TOL["f64"]
+    assert rel(host(var) * 200, lc) < 1e-10
+
+
+def test_interp_full_size_sampled(gb):
+    """n=1,000,000, d=100 mixture, l=1,000, r=10, BF16 distances: sampled rows
+    against the oracle (landmark MDS + Eq. (2) for each sampled row)."""
+    w = W.INTERP_BF16
+    Y = W.make_data(w, seed=0)
+    idx = W.landmarks(w.n, w.l, seed=0)
+    X, var, _ = gb.mds_interpolate(dev(Y), dev(idx), w.r, "bf16")
+    Xh = host(X)
+    L = Y[idx].astype(np.float64)
+    D1 = O.sq_dist(L, L)
+    X1, lam, _, _ = O.classical_mds(D1, w.r)
+    rng = np.random.default_rng(0)
+    rows = np.setdiff1d(rng.choice(w.n, 3000, replace=False), idx)
+    Xs = O.gower_interpolate(X1, lam, D1, O.sq_dist(Y[rows], L))
+    both = np.vstack([Xh[rows], Xh[idx]])
+    ref = np.vstack([Xs, X1])
+    assert O.aligned_rel_error(both, ref) < TOL["bf16"]
+    assert rel(host(var), lam / w.l) < LAM_TOL["bf16"]
+    assert np.all(np.isfinite(Xh))
+
+
+def test_bad_landmark_index(gb):
+    Y = W.gaussian_dominant(500, 10, 3, seed=2)
+    idx = W.landmarks(500, 100, seed=2)
+    idx[17] = 500                                           # out of range
+    with pytest.raises(gb.MdsError) as e:
+        gb.mds_interpolate(dev(Y), dev(idx), 3, "f64")
+    assert e.value.status == 1
+
+
+def test_workspace_too_small(gb):
+    Y = dev(W.gaussian_dominant(500, 10, 3, seed=2))
+    idx = dev(W.landmarks(500, 100, seed=2))
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    # pass an explicit, too-small workspace through the raw ABI
+    import ctypes
+    from paper_2007_11919_gb300.mds import MdsOpts, _lib
+    o = MdsOpts(prec=0, stream=ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                workspace=ctypes.c_void_p(ws.data_ptr()), workspace_bytes=1024)
+    X = torch.empty((500, 3), dtype=torch.float64, device="cuda")
+    v = torch.empty(3, dtype=torch.float64, device="cuda")
+    s = _lib().mds_interpolate(ctypes.c_void_p(Y.data_ptr()), 0, 500, 10, ctypes.c_void_p(idx.data_ptr()),
+                               100, 3, ctypes.byref(o), ctypes.c_void_p(X.data_ptr()),
+                               ctypes.c_void_p(v.data_ptr()), None)
+    assert s == 8
+
+
+# ------------------------------------------------------ embed / model
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_embed_new_matches_interpolate(gb, prec, tmp_path):
+    dt = np.float64 if prec == "f64" else np.float32
+    Y = W.gaussian_dominant(3000, 50, 5, seed=11, dtype=dt)
+    idx = W.landmarks(3000, 400, seed=11)
+    X, var, model = gb.mds_interpolate(dev(Y), dev(idx), 5, prec, want_model=True)
+    info = model.info()
+    assert info["l"] == 400 and info["r"] == 5 and info["prec"] == prec
+    Xe = gb.mds_embed_new(model, dev(Y))
+    rest = np.setdiff1d(np.arange(3000), idx)
+    # the same kernel computes both: bitwise equal on non-landmark rows
+    assert torch.equal(Xe[rest], X[rest])
+    # landmarks interpolate onto themselves (Gower's formula reproduces X_1)
+    assert O.aligned_rel_error(host(Xe[idx]), host(X[idx])) < 10 * TOL[prec]
+    # each row alone equals the row in a batch
+    one = gb.mds_embed_new(model, dev(Y[rest[5:6]]))
+    assert torch.equal(one[0], X[rest[5]])
+    path = str(tmp_path / "m.gbmds")
+    model.save(path)
+    m2 = gb.Model.load(path)
+    assert torch.equal(gb.mds_embed_new(m2, dev(Y[:100])), Xe[:100])
+
+
+# ------------------------------------------------------ divide-and-conquer
+
+
+def test_dc_f64_small(gb):
+    Y = W.gaussian_dominant(3000, 10, 3, seed=3)
+    part = W.partitions_uneven(3000, 10, 300, 420, seed=3)
+    Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 3)
+    X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), 3, "f64")
+    assert rel(host(var), lo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+
+
+def test_dc_f32(gb):
+    Y = W.gaussian_dominant(12_000, 100, 5, seed=4, dtype=np.float32)
+    part = W.partitions_uneven(12_000, 20, 800, 1200, seed=4)
+    Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 10)
+    X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), 10, "f32")
+    assert rel(host(var), lo) < LAM_TOL["f32"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f32"]
+
+
+def test_dc_exact_rank_r(gb):
+    """Points exactly in R^4: D&C returns them up to one orthogonal map."""
+    rng = np.random.default_rng(8)
+    Z = rng.standard_normal((4000, 4)) * np.array([6, 4, 3, 2.0])
+    Y = Z @ np.linalg.qr(rng.standard_normal((9, 4)))[0].T
+    part = W.partitions_uneven(4000, 12, 500, 700, seed=8)
+    X, _ = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), 4, "f64")
+    assert O.aligned_rel_error(host(X), Z - Z.mean(axis=0)) < 1e-10
+
+
+def test_dc_full_size_sampled(gb):
+    """n=100,000, d=100, parts of 800-1,200 own points + 20 connecting points,
+    r=10, FP32: parts 0, 1, p/2 and p-1 against the oracle."""
+    w = W.DC_F32
+    Y = W.make_data(w, seed=0)
+    part = W.partitions_uneven(w.n, w.c, w.own_lo, w.own_hi, seed=0)
+    X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), w.r, "f32")
+    Xh = host(X)
+    rows, ref = [], []
+    for j in sorted({0, 1, part.p // 2, part.p - 1}):
+        rj, Xj, _ = O.divide_conquer_part(Y, part.anchors, part.ptr, part.own, j, w.r)
+        rows.append(rj)
+        ref.append(Xj)
+    rows = np.concatenate(rows)
+    assert O.aligned_rel_error(Xh[rows], np.vstack(ref)) < TOL["f32"]
+    assert np.all(np.isfinite(Xh)) and np.all(host(var) > 0)
+
+
+def test_dc_deterministic(gb):
+    Y = dev(W.gaussian_dominant(5000, 20, 4, seed=6, dtype=np.float32))
+    part = W.partitions_uneven(5000, 10, 600, 900, seed=6)
+    a = gb.mds_divide_conquer(Y, dev(part.anchors), part.ptr, dev(part.own), 4, "f32")[0]
+    b = gb.mds_divide_conquer(Y, dev(part.anchors), part.ptr, dev(part.own), 4, "f32")[0]
+    assert torch.equal(a, b)

@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/gbmds.h; host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbmds.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_11919_gb300 import build
+    path = build.build()
+    from paper_2007_11919_gb300.mds import _lib
+    assert os.path.samefile(path, os.path.join(ROOT, "paper_2007_11919_gb300", "libgbmds.so"))
+    return _lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(mds_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_four_calls():
+    names = declared_functions()
+    for n in ("mds_classical", "mds_interpolate", "mds_divide_conquer", "mds_embed_new"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), f"{n} not exported"
+
+
+def test_status_strings(lib):
+    assert lib.mds_version() == 1
+    for s in range(10):
+        assert lib.mds_status_str(s)
+    assert lib.mds_status_str(4) == b"fewer than r positive eigenvalues"
+
+
+def _opts(**kw):
+    from paper_2007_11919_gb300.mds import MdsOpts
+    return MdsOpts(**kw)
+
+
+def test_argument_checks_without_gpu(lib):
+    o = _opts(prec=1)
+    p = ctypes.c_void_p(8)
+    # null data / bad sizes / bad r are rejected before any CUDA call
+    assert lib.mds_classical(None, 1, 100, 3, 2, ctypes.byref(o), p, p) == 1
+    assert lib.mds_classical(p, 1, 100, 3, 100, ctypes.byref(o), p, p) == 1
+    assert lib.mds_classical(p, 7, 100, 3, 2, ctypes.byref(o), p, p) == 1
+    assert lib.mds_interpolate(p, 1, 100, 3, p, 200, 2, ctypes.byref(o), p, p, None) == 1
+    assert lib.mds_interpolate(p, 1, 100, 3, p, 50, 40, ctypes.byref(o), p, p, None) == 1
+    bad = _opts(prec=9)
+    assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(bad), p, p) == 1
+    flags = _opts(prec=1, flags=1)
+    assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(flags), p, p) == 1
+    # divide-and-conquer: c must exceed r (Procrustes needs c >= r + 1)
+    ptr = np.array([0, 100, 200], dtype=np.int64)
+    pp = ptr.ctypes.data_as(ctypes.c_void_p)
+    assert lib.mds_divide_conquer(p, 1, 220, 3, 2, pp, p, p, 3, 3, ctypes.byref(o), p, p) == 1
+    ptr_bad = np.array([5, 100, 200], dtype=np.int64)
+    assert lib.mds_divide_conquer(p, 1, 220, 3, 2, ptr_bad.ctypes.data_as(ctypes.c_void_p), p, p, 10, 3,
+                                  ctypes.byref(o), p, p) == 1
+    # missing workspace is reported as such (still no GPU work)
+    assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(o), p, p) == 8
+    # FP8 needs uint8 data paths not built for classical MDS
+    o8 = _opts(prec=3)
+    assert lib.mds_classical(p, 2, 100, 3, 2, ctypes.byref(o8), p, p) == 7
+
+
+def test_workspace_sizes(lib):
+    s_small = lib.mds_classical_workspace_size(100, 3, 2, 1)
+    s_big = lib.mds_classical_workspace_size(1000, 3, 2, 1)
+    assert 0 < s_small < s_big
+    assert lib.mds_classical_workspace_size(0, 3, 2, 1) == 0
+    # Q (n x n FP64) dominates the classical workspace
+    assert s_big >= 1000 * 1000 * 8
+    ptr = np.array([0] + list(np.cumsum([1000] * 10)), dtype=np.int64)
+    w = lib.mds_divide_conquer_workspace_size(10_020, 100, 10, ptr.ctypes.data_as(ctypes.c_void_p), 20, 10, 1)
+    assert w >= 10 * 1020 * 1020 * 8
+    assert lib.mds_interpolate_workspace_size(10_000, 100, 500, 10, 2) > lib.mds_interpolate_workspace_size(
+        10_000, 100, 500, 10, 1)
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2007_11919_gb300.mds as M
+    monkeypatch.setattr(M, "_L", None)
+    monkeypatch.setattr(M, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        M._lib()
