@@ -115,6 +115,7 @@ struct Batch {
 
 void plan_batch(Batch& B, const std::vector<int>& sizes, const std::vector<int64_t>& own_off,
                 int c, int r, int mmax, int64_t ny) {
+    B = Batch();
     B.p = (int)sizes.size();
     B.r = r;
     B.mmax = mmax;
@@ -393,7 +394,7 @@ int mds_classical(const void* Y, int dt, int64_t n, int d, int r, const mds_opts
     ClassicalWs W;
     const size_t need = classical_layout(W, nullptr, n, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
-    classical_layout(W, o.ws, n, r, o.mmax);
+    if (classical_layout(W, o.ws, n, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(launch_iota(W.iota, n, o.st));
@@ -421,7 +422,7 @@ int mds_classical_dist(const double* D2, int64_t n, int r, const mds_opts* opts,
     ClassicalWs W;
     const size_t need = classical_layout(W, nullptr, n, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
-    classical_layout(W, o.ws, n, r, o.mmax);
+    if (classical_layout(W, o.ws, n, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     CK(cudaMemcpyAsync(W.B.d_desc, W.B.desc.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, o.st));
     tmark(0, o.st);
@@ -452,7 +453,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     InterpWs W;
     const size_t need = interp_layout(W, nullptr, n, d, l, r, o.prec, o.mmax);
     if ((s = check_ws(o, need))) return s;
-    interp_layout(W, o.ws, n, d, l, r, o.prec, o.mmax);
+    if (interp_layout(W, o.ws, n, d, l, r, o.prec, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
@@ -682,7 +683,7 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
     DcWs W;
     const size_t need = dc_layout(W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
     if ((s = check_ws(o, need))) return s;
-    dc_layout(W, o.ws, n, d, p, part_ptr, c, r, o.prec, o.mmax);
+    if (dc_layout(W, o.ws, n, d, p, part_ptr, c, r, o.prec, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
