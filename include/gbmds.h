@@ -129,6 +129,32 @@ size_t mds_embed_new_workspace_size(mds_model model, int64_t m);
 int mds_embed_new(mds_model model, const void* Ynew, int dt, int64_t m, const mds_opts* opts,
                   void* X);
 
+/* Allocation-free variant of mds_embed_new.  The paper has no counterpart:
+ * this exists for callers that must not allocate device memory when they
+ * embed points -- for example a serving process whose device memory is all
+ * reserved up front by another allocator (a new cudaMalloc would fail), or a
+ * plugin / real-time loop that forbids allocation after start-up (an
+ * allocation can stall on device-wide synchronisation).
+ *   - Scratch is a 16 MiB array inside the library (mds_embed_new_static_capacity()
+ *     bytes), present on every GPU that loads libgbmds.so until the process
+ *     exits.  opts->workspace must be NULL and opts->workspace_bytes 0.
+ *   - Sizes: a call fits when mds_embed_new_workspace_size(model, m) is at most
+ *     the capacity (about 2 million rows for FP32/FP64 models; fewer for BF16
+ *     models, which also stage a rounded copy of the rows); larger m returns
+ *     MDS_ERR_WORKSPACE without doing any work.  Split large batches.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *     first call before any stream capture on that device.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind.  Nothing in it needs to start at zero (each call writes every
+ *     scratch byte it reads).  Calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race on the array: serialise them.
+ *   - Calls no cudaMalloc/cudaFree and no allocating library routine.
+ *   Results are the same as mds_embed_new's. */
+size_t mds_embed_new_static_capacity(void);
+int mds_embed_new_static(mds_model model, const void* Ynew, int dt, int64_t m,
+                         const mds_opts* opts, void* X);
+
 /* Model inspection / persistence.  lambda may be NULL. */
 int mds_model_info(mds_model model, int* l, int* d, int* r, int* prec, double* lambda);
 int mds_model_save(mds_model model, const char* path);

@@ -257,3 +257,29 @@ def mds_last_stats() -> dict:
     return {"stage_ms": dict(zip(STAGES, list(s.stage_ms))), "launches": s.launches,
             "eig_steps": s.eig_steps, "eig_flops": s.eig_flops, "eig_qbytes": s.eig_qbytes,
             "problems": s.problems, "cluster": s.cluster}
+
+
+def mds_embed_new_static(model: Model, Ynew, stream=None):
+    """mds_embed_new without any device allocation: scratch comes from a fixed
+    array inside the library, so the only tensors created here are the
+    outputs (pass ``out`` to avoid even that).  For callers that must not
+    allocate device memory while embedding; see include/gbmds.h."""
+    dt = _data(Ynew)
+    m = Ynew.shape[0]
+    info = model.info()
+    L = _lib()
+    L.mds_embed_new_static.argtypes = [_P, _P, _I, _I64, _P, _P]
+    L.mds_embed_new_static.restype = _I
+    st = stream if stream is not None else torch.cuda.current_stream(Ynew.device)
+    o = MdsOpts(prec=PREC[info["prec"]], stream=ctypes.c_void_p(st.cuda_stream), workspace=None,
+                workspace_bytes=0)
+    X = torch.empty((m, info["r"]), dtype=_xdtype(info["prec"]), device=Ynew.device)
+    _check(L.mds_embed_new_static(model.handle, _ptr(Ynew), dt, m, ctypes.byref(o), _ptr(X)),
+           "mds_embed_new_static")
+    return X
+
+
+def mds_embed_new_static_capacity() -> int:
+    L = _lib()
+    L.mds_embed_new_static_capacity.restype = _SZ
+    return L.mds_embed_new_static_capacity()
