@@ -159,7 +159,7 @@ void carve_batch(Batch& B, Arena& A) {
     B.steps = A.take<int>(B.p);
 }
 
-int pick_cluster(int requested, int p, int max_n, int mmax) {
+int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
     if (requested > 0) return std::min(requested, 16);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -168,7 +168,7 @@ int pick_cluster(int requested, int p, int max_n, int mmax) {
     if (p == 1) cs = 16;
     else cs = std::max(1, std::min(8, (int)std::lround(2.0 * sms / p)));
     cs = std::min(cs, std::max(1, max_n / 64));
-    while (cs < 16 && lanczos_smem_bytes(max_n, cs, mmax) > kMaxSmem) ++cs;
+    while (cs < 16 && lanczos_smem_bytes(max_n, cs, mmax, r) > kMaxSmem) ++cs;
     return cs;
 }
 
@@ -205,7 +205,7 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.rank_tol = o.rank_tol;
     a.max_n = B.max_n;
     tmark(2, o.st);
-    g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax);
+    g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r);
     CK(launch_lanczos(a, g_cluster, o.st));
     tmark(3, o.st);
     return MDS_OK;
@@ -273,6 +273,7 @@ size_t classical_layout(ClassicalWs& W, char* base, int64_t n, int r, int mmax) 
 struct InterpWs {
     int* flag;
     double* nrm;
+    double* nrm_raw;  // BF16 path: FP32 norms of the unrounded rows (landmark problem)
     void* Yq;
     Batch B;
     void* L;
@@ -287,7 +288,8 @@ size_t interp_layout(InterpWs& W, char* base, int64_t n, int d, int l, int r, in
     const size_t es = prec == MDS_PREC_F64 ? 8 : 4;
     W.flag = A.take<int>(1);
     W.nrm = A.take<double>(n);
-    W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)n * d) : nullptr;
+    W.nrm_raw = prec == MDS_PREC_BF16 ? A.take<double>(n) : nullptr;
+    W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * n * split_ld(d)) : nullptr;
     plan_batch(W.B, {l}, {0}, 0, r, mmax, n);
     carve_batch(W.B, A);
     W.L = A.take<char>((size_t)l * d * es);
@@ -311,7 +313,7 @@ size_t dc_layout(DcWs& W, char* base, int64_t n, int d, int p, const int64_t* pa
     Arena A{base, 0};
     W.flag = A.take<int>(1);
     W.nrm = A.take<double>(n);
-    W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)n * d) : nullptr;
+    W.Yq = nullptr;
     std::vector<int> sizes(p);
     std::vector<int64_t> offs(p);
     for (int j = 0; j < p; ++j) {
@@ -461,9 +463,20 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     const void* Ye;
     int dte;
     if ((s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
+    // The landmark problem is small: its distances come from the unrounded data
+    // in FP32 even on the BF16 path, which rounds only the bulk of Eq. (2).
+    const void* Yl = Ye;
+    int dtl = dte;
+    const double* nrml = W.nrm;
+    if (o.prec == MDS_PREC_BF16) {
+        CK(launch_rownorm(Y, dt, n, d, 0, W.nrm_raw, o.st));
+        Yl = Y;
+        dtl = dt;
+        nrml = W.nrm_raw;
+    }
     tmark(0, o.st);
     // classical MDS of the landmarks (first subset of Section 3.1)
-    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, nullptr, landmark_idx, f64, o))) return s;
+    if ((s = run_eig_batch(W.B, Yl, dtl, d, nrml, nullptr, landmark_idx, f64, o))) return s;
     // Gower operator, landmark rows, projection of every row, landmark rows <- X_1
     CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, l, r,
                            f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
@@ -514,7 +527,7 @@ size_t mds_embed_new_workspace_size(mds_model m, int64_t rows) {
     if (!m || rows <= 0) return 0;
     Arena A{nullptr, 0};
     A.take<double>(rows);
-    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)rows * m->d);
+    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
     return A.off + 256;
 }
 
@@ -527,12 +540,12 @@ int mds_embed_new(mds_model m, const void* Ynew, int dt, int64_t rows, const mds
     if (o.prec != m->prec) return MDS_ERR_ARG;
     Arena A{nullptr, 0};
     A.take<double>(rows);
-    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)rows * m->d);
+    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
     if ((s = check_ws(o, A.off))) return s;
     A = Arena{o.ws, 0};
     begin_call(o.st);
     double* nrm = A.take<double>(rows);
-    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)rows * m->d) : nullptr;
+    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * rows * split_ld(m->d)) : nullptr;
     const void* Ye;
     int dte;
     if ((s = prep_data(Ynew, dt, rows, m->d, m->prec, nrm, Yq, o, &Ye, &dte))) return s;
@@ -679,7 +692,7 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
         if (own < 0 || own + c > kMaxEigN || own + c <= r) return MDS_ERR_ARG;
     }
     if (part_ptr[p] > 0 && !part_own) return MDS_ERR_ARG;
-    if (o.prec == MDS_PREC_FP8) return MDS_ERR_UNSUPPORTED;
+    if (o.prec == MDS_PREC_FP8 || o.prec == MDS_PREC_BF16) return MDS_ERR_UNSUPPORTED;
     DcWs W;
     const size_t need = dc_layout(W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
     if ((s = check_ws(o, need))) return s;

@@ -12,7 +12,7 @@ namespace gbmds {
 constexpr int kMaxR = 32;          // largest supported target dimension r
 constexpr int kMaxEigN = 16384;    // largest eigenproblem (points)
 constexpr int kTile = 64;          // distance tile edge (points)
-constexpr int kDtBF16 = 100;       // internal dtype tag: BF16-rounded copy of the data
+constexpr int kDtBF16 = 100;       // internal dtype tag: BF16 hi/lo split planes of the data
 
 // One classical-MDS eigenproblem of a batch (the landmark set of Section 3.1,
 // or one part of Section 3.2).  Row a of the problem is data row
@@ -68,6 +68,29 @@ __device__ __forceinline__ float load_as<float, __nv_bfloat16>(const __nv_bfloat
 // Kernel launches made by the current host thread (for mds_last_stats).
 void note_launch(int count);
 
+// Row readers for the CUDA-core kernels.  RowLoad: element k of row i of a
+// row-major matrix with leading dimension ld.  SplitLoad: BF16 split data,
+// value = hi + lo, with the hi plane at p and the lo plane at p + plane.
+template <typename T>
+struct RowLoad {
+    const T* p;
+    int64_t ld;
+    template <typename A>
+    __device__ __forceinline__ A get(int64_t i, int k) const { return load_as<A, T>(p + i * ld + k); }
+};
+struct SplitLoad {
+    const __nv_bfloat16* p;
+    int64_t ld, plane;
+    template <typename A>
+    __device__ __forceinline__ A get(int64_t i, int k) const {
+        const __nv_bfloat16* q = p + i * ld + k;
+        return (A)__bfloat162float(q[0]) + (A)__bfloat162float(q[plane]);
+    }
+};
+
+// Padded row length (elements) of the BF16 split planes: 16-byte rows.
+__host__ __device__ inline int split_ld(int d) { return (int)round_up(d, 8); }
+
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `st` and returns cudaGetLastError().
 
@@ -110,11 +133,11 @@ struct LanczosArgs {
     int max_n;
 };
 __host__ __device__ inline size_t lanczos_scratch_per_problem(int mmax, int r) {
-    return (size_t)r * (mmax + 1) * 7 + 8;
+    return (size_t)(r * 7 + 2) * (mmax + 1) + 8;
 }
 cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st);
 // Shared memory one CTA of the eigen-solver needs for a cluster of cs CTAs.
-size_t lanczos_smem_bytes(int max_n, int cs, int mmax);
+size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r);
 constexpr size_t kMaxSmem = 220 * 1024;
 
 // Interpolation model from the landmark eigenpairs (FP64):
@@ -126,12 +149,13 @@ cudaError_t launch_interp_model(const double* V, const double* lam, const double
                                 float* x1_32, double* bias, double* var_out, cudaStream_t st);
 
 // Gather rows Y[idx[i]] into a dense l x d matrix of the accumulation type.
+// For dt == kDtBF16, Y is the split planes of an ny-row matrix.
 cudaError_t launch_gather_rows(const void* Y, int dt, int64_t ny, int d, const int64_t* idx,
                                int l, int acc_f64, void* out, const double* nrm_src,
                                double* nrm_out, cudaStream_t st);
 
 // Gower projection, Eq. (2): X_i = sum_j a2_ij W_j + b for m rows of Y
-// (FP32 or FP64 SIMT distance tiles).
+// (FP32 or FP64 SIMT distance tiles).  For dt == kDtBF16, Y is split planes.
 cudaError_t launch_gower_proj(const void* Y, int dt, int64_t m, int d, const double* nrm_y,
                               const void* L, const double* nrm_l, int l, const void* W,
                               const double* bias, int r, int acc_f64, void* X, cudaStream_t st);
@@ -143,8 +167,10 @@ cudaError_t launch_check_idx(const int64_t* idx, int64_t count, int64_t ny, int*
 // out[i] = i, i < n.
 cudaError_t launch_iota(int64_t* out, int64_t n, cudaStream_t st);
 
-// Round an F32/F64 matrix to BF16 (round to nearest even), and the FP32 squared
-// norms of the rounded rows.
+// Split an F32/F64/U8 matrix into BF16 planes hi = bf16(y), lo = bf16(y - hi)
+// (round to nearest even; rows padded with zeros to split_ld(d)), hi plane
+// first, lo plane n * split_ld(d) elements later; nrm = FP32 sum of
+// hi^2 + 2 hi lo (the products a split tensor-core dot product forms).
 cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
                               cudaStream_t st);
 

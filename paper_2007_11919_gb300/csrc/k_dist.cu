@@ -216,19 +216,26 @@ __global__ void __launch_bounds__(256) k_quant_bf16(const T* __restrict__ Y, int
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= n) return;
+    const int ld = split_ld(d);
+    __nv_bfloat16* hi = Yq + row * ld;
+    __nv_bfloat16* lo = hi + n * (int64_t)ld;
     float s = 0.f;
-    for (int k = lane; k < d; k += 32) {
-        const __nv_bfloat16 q = __float2bfloat16_rn((float)Y[row * d + k]);
-        Yq[row * d + k] = q;
-        const float v = __bfloat162float(q);
-        s += v * v;
+    for (int k = lane; k < ld; k += 32) {
+        const float y = k < d ? (float)Y[row * d + k] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(y);
+        const float hf = __bfloat162float(h);
+        const __nv_bfloat16 l = __float2bfloat16_rn(y - hf);
+        hi[k] = h;
+        lo[k] = l;
+        const float lf = __bfloat162float(l);
+        s += hf * hf + 2.f * hf * lf;
     }
     s = warp_sum(s);
     if (lane == 0) nrm[row] = (double)s;
 }
 
-template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_gather(const T* __restrict__ Y, int d,
+template <typename Ld, typename A>
+__global__ void __launch_bounds__(256) k_gather(Ld Y, int d,
                                                 const int64_t* __restrict__ idx, int l,
                                                 int64_t ny, A* __restrict__ out,
                                                 const double* __restrict__ nrm_src,
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(256) k_gather(const T* __restrict__ Y, int d,
     if (i >= l) return;
     int64_t g = idx[i];
     g = g < 0 ? 0 : (g >= ny ? ny - 1 : g);
-    for (int k = threadIdx.x; k < d; k += blockDim.x) out[(int64_t)i * d + k] = load_as<A, T>(Y + g * d + k);
+    for (int k = threadIdx.x; k < d; k += blockDim.x) out[(int64_t)i * d + k] = Y.template get<A>(g, k);
     if (threadIdx.x == 0 && nrm_out) nrm_out[i] = nrm_src[g];
 }
 
@@ -276,8 +283,6 @@ cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nr
     } else {
         if (dt == MDS_IN_F64)
             k_sqdist<double, float><<<grid, block, 0, st>>>((const double*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-        else if (dt == kDtBF16)
-            k_sqdist<__nv_bfloat16, float><<<grid, block, 0, st>>>((const __nv_bfloat16*)Y, d, nrm, anchors, own, desc, qarena, rparena);
         else if (dt == MDS_IN_F32)
             k_sqdist<float, float><<<grid, block, 0, st>>>((const float*)Y, d, nrm, anchors, own, desc, qarena, rparena);
         else
@@ -306,18 +311,22 @@ cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double
 }
 
 cudaError_t launch_gather_rows(const void* Y, int dt, int64_t ny, int d, const int64_t* idx,
-                               int l, int acc_f64, void* out, const double* nrm_src, double* nrm_out,
-                               cudaStream_t st) {
+                               int l, int acc_f64, void* out, const double* nrm_src,
+                               double* nrm_out, cudaStream_t st) {
     if (l <= 0) return cudaSuccess;
     if (acc_f64) {
-        if (dt == MDS_IN_F64) k_gather<double, double><<<l, 128, 0, st>>>((const double*)Y, d, idx, l, ny, (double*)out, nrm_src, nrm_out);
-        else if (dt == MDS_IN_F32) k_gather<float, double><<<l, 128, 0, st>>>((const float*)Y, d, idx, l, ny, (double*)out, nrm_src, nrm_out);
-        else k_gather<uint8_t, double><<<l, 128, 0, st>>>((const uint8_t*)Y, d, idx, l, ny, (double*)out, nrm_src, nrm_out);
+        double* o = (double*)out;
+        if (dt == MDS_IN_F64) k_gather<<<l, 128, 0, st>>>(RowLoad<double>{(const double*)Y, d}, d, idx, l, ny, o, nrm_src, nrm_out);
+        else if (dt == MDS_IN_F32) k_gather<<<l, 128, 0, st>>>(RowLoad<float>{(const float*)Y, d}, d, idx, l, ny, o, nrm_src, nrm_out);
+        else k_gather<<<l, 128, 0, st>>>(RowLoad<uint8_t>{(const uint8_t*)Y, d}, d, idx, l, ny, o, nrm_src, nrm_out);
     } else {
-        if (dt == MDS_IN_F64) k_gather<double, float><<<l, 128, 0, st>>>((const double*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
-        else if (dt == kDtBF16) k_gather<__nv_bfloat16, float><<<l, 128, 0, st>>>((const __nv_bfloat16*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
-        else if (dt == MDS_IN_F32) k_gather<float, float><<<l, 128, 0, st>>>((const float*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
-        else k_gather<uint8_t, float><<<l, 128, 0, st>>>((const uint8_t*)Y, d, idx, l, ny, (float*)out, nrm_src, nrm_out);
+        float* o = (float*)out;
+        if (dt == kDtBF16) {
+            const int ld = split_ld(d);
+            k_gather<<<l, 128, 0, st>>>(SplitLoad{(const __nv_bfloat16*)Y, ld, ny * ld}, d, idx, l, ny, o, nrm_src, nrm_out);
+        } else if (dt == MDS_IN_F64) k_gather<<<l, 128, 0, st>>>(RowLoad<double>{(const double*)Y, d}, d, idx, l, ny, o, nrm_src, nrm_out);
+        else if (dt == MDS_IN_F32) k_gather<<<l, 128, 0, st>>>(RowLoad<float>{(const float*)Y, d}, d, idx, l, ny, o, nrm_src, nrm_out);
+        else k_gather<<<l, 128, 0, st>>>(RowLoad<uint8_t>{(const uint8_t*)Y, d}, d, idx, l, ny, o, nrm_src, nrm_out);
     }
     note_launch(1);
     return cudaGetLastError();

@@ -10,14 +10,13 @@
 //   vectors, alpha_j = v_j . Q v_j, beta_j = ||w||, v_{j+1} = w / beta_j.
 //   The Rayleigh quotient T_k = V_k^T Q V_k is the tridiagonal of the alphas
 //   and betas.  Every few steps the r largest eigenvalues theta_i of T_k are
-//   found by Sturm-count multisection, and the Ritz residuals
-//   ||Q y_i - theta_i y_i|| = beta_{k-1} |s_{k-1,i}| from the last component of
-//   T_k's eigenvector (an O(k) recurrence of the characteristic polynomial and
-//   its derivative: s_k^2 = -p_{k-1}(theta) / p_k'(theta)).  The run stops when
-//   every residual is below tol * theta_0, at an invariant subspace (beta ~ 0),
-//   or at the step cap (status NOCONV).  Eigenvectors s_i of T_k come from
-//   inverse iteration (tridiagonal LU with partial pivoting), Ritz vectors
-//   are y_i = V_k s_i.
+//   found by Sturm-count multisection and their eigenvectors s_i by inverse
+//   iteration (tridiagonal LU with partial pivoting); the Ritz residuals are
+//   ||Q y_i - theta_i y_i|| = beta_{k-1} |s_i[k-1]|.  The run stops when every
+//   residual is below tol * theta_0, at an invariant subspace (beta ~ 0), or
+//   at the step cap (status NOCONV).  The s_i of the last check are
+//   orthonormalised (modified Gram-Schmidt) and the Ritz vectors are
+//   y_i = V_k s_i.
 //
 // Layout: Q_j row-major FP64 (ld = ldq).  The cluster's CTAs own contiguous
 // row slices; each CTA's slice of the current Lanczos vector lives in its
@@ -51,12 +50,13 @@ struct Smem {
     double* resid;   // kMaxR
     double* red;     // 3 * kWarps * ... scratch (64)
     double* sgn;     // 3 * kMaxR : (|max|, row, signed) per eigenvector
+    double* inv;     // 4 * r * (mmax + 1): per wanted vector U bands u0, u1, u2 and x
 };
 
-__host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax) {
+__host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
     return round_up(max_n, 2) + 2 * round_up(rmax, 2) + 3 * (size_t)(mmax + 2) +
-           3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 3 * kMaxR + 8;
+           3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 3 * kMaxR + 4 * (size_t)r * (mmax + 1) + 8;
 }
 
 __device__ Smem carve(double* base, int max_n, int cs, int mmax) {
@@ -76,6 +76,7 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax) {
     s.resid = p; p += kMaxR;
     s.red = p; p += 64;
     s.sgn = p; p += 3 * kMaxR;
+    s.inv = p;
     return s;
 }
 
@@ -118,29 +119,6 @@ __device__ int sturm_count(const double* al, const double* b2, int k, double x, 
     return c;
 }
 
-// Squared last component of the unit eigenvector of T for eigenvalue x:
-// s_k^2 = -p_{k-1}(x) / p_k'(x), through d_t = p_t/p_{t-1} and
-// g_t = p_t'/p_{t-1}.
-__device__ double last_comp2(const double* al, const double* b2, int k, double x, double pivmin) {
-    if (k == 1) return 1.0;
-    double d_prev = al[0] - x;   // d_{t-1}
-    if (fabs(d_prev) < pivmin) d_prev = -pivmin;
-    double g_prev2 = -1.0;                       // g_1
-    double g_prev = -1.0 - (al[1] - x) / d_prev;  // g_2
-    if (k == 2) return -1.0 / g_prev;
-    // advance: compute d_2 then g_3 ... g_k
-    for (int t = 3; t <= k; ++t) {
-        double d_cur = (al[t - 2] - x) - b2[t - 3] / d_prev;  // d_{t-1}
-        if (fabs(d_cur) < pivmin) d_cur = -pivmin;
-        const double g = -1.0 + ((al[t - 1] - x) * g_prev - b2[t - 2] * g_prev2 / d_prev) / d_cur;
-        d_prev = d_cur;
-        g_prev2 = g_prev;
-        g_prev = g;
-    }
-    const double s2 = -1.0 / g_prev;
-    return isfinite(s2) ? fmax(0.0, s2) : 0.0;
-}
-
 // Warp-cooperative multisection for the i-th largest eigenvalue of T.
 __device__ double kth_largest(const double* al, const double* b2, int k, int i, double gl, double gu,
                               double pivmin) {
@@ -163,55 +141,49 @@ __device__ double kth_largest(const double* al, const double* b2, int k, int i, 
     return 0.5 * (lo + hi);
 }
 
-// Inverse iteration for the eigenvector of T for eigenvalue th (unit 2-norm).
-// d, du, dl, du2, x: k doubles each; piv: k doubles (0/1 flags).
+// Inverse iteration for the eigenvector of T for eigenvalue th (unit 2-norm),
+// all in shared memory.  Each iteration factors T - th I = P L U by Gaussian
+// elimination with partial pivoting (U has the bands u0, u1, u2) while it
+// applies the same row operations to the right-hand side x, then solves with
+// U from the bottom up.  Three iterations from a fixed positive start vector.
 __device__ void tri_inverse_iteration(const double* al, const double* be, int k, double th,
-                                      double pert, double* d, double* du, double* dl, double* du2,
-                                      double* piv, double* x) {
-    for (int t = 0; t < k; ++t) {
-        d[t] = al[t] - th;
-        du2[t] = 0.0;
-        if (t < k - 1) {
-            du[t] = be[t];
-            dl[t] = be[t];
-        }
-    }
-    for (int t = 0; t < k - 1; ++t) {
-        if (fabs(d[t]) >= fabs(dl[t])) {
-            piv[t] = 0.0;
-            if (d[t] == 0.0) d[t] = pert;
-            const double f = dl[t] / d[t];
-            dl[t] = f;
-            d[t + 1] -= f * du[t];
-        } else {
-            piv[t] = 1.0;
-            const double f = d[t] / dl[t];
-            d[t] = dl[t];
-            dl[t] = f;
-            const double tmp = du[t];
-            du[t] = d[t + 1];
-            d[t + 1] = tmp - f * d[t + 1];
-            if (t < k - 2) {
-                du2[t] = du[t + 1];
-                du[t + 1] = -f * du[t + 1];
-            }
-        }
-    }
-    if (d[k - 1] == 0.0) d[k - 1] = pert;
+                                      double pert, double* u0, double* u1, double* u2,
+                                      double* x) {
     for (int t = 0; t < k; ++t) x[t] = 1.0 + 0.25 * (double)((t * 7919) % 13) / 13.0;
     for (int it = 0; it < 3; ++it) {
+        // working row t: entries (w0, w1) in columns t, t+1 and right-hand side yw
+        double w0 = al[0] - th, w1 = k > 1 ? be[0] : 0.0, yw = x[0];
         for (int t = 0; t < k - 1; ++t) {
-            if (piv[t] == 0.0) {
-                x[t + 1] -= dl[t] * x[t];
-            } else {
-                const double tmp = x[t];
-                x[t] = x[t + 1];
-                x[t + 1] = tmp - dl[t] * x[t];
+            const double l0 = be[t];                           // row t+1, column t
+            const double l1 = al[t + 1] - th;                  // row t+1, column t+1
+            const double l2 = t + 2 < k ? be[t + 1] : 0.0;     // row t+1, column t+2
+            const double yl = x[t + 1];
+            if (fabs(w0) >= fabs(l0)) {                        // pivot on the working row
+                if (w0 == 0.0) w0 = pert;
+                const double f = l0 / w0;
+                u0[t] = w0;
+                u1[t] = w1;
+                u2[t] = 0.0;
+                x[t] = yw;
+                w0 = l1 - f * w1;
+                w1 = l2;
+                yw = yl - f * yw;
+            } else {                                           // pivot on row t+1
+                const double f = w0 / l0;
+                u0[t] = l0;
+                u1[t] = l1;
+                u2[t] = l2;
+                x[t] = yl;
+                w0 = w1 - f * l1;
+                w1 = -f * l2;
+                yw = yw - f * yl;
             }
         }
-        x[k - 1] /= d[k - 1];
-        if (k > 1) x[k - 2] = (x[k - 2] - du[k - 2] * x[k - 1]) / d[k - 2];
-        for (int t = k - 3; t >= 0; --t) x[t] = (x[t] - du[t] * x[t + 1] - du2[t] * x[t + 2]) / d[t];
+        if (w0 == 0.0) w0 = pert;
+        u0[k - 1] = w0;
+        x[k - 1] = yw / w0;
+        if (k > 1) x[k - 2] = (x[k - 2] - u1[k - 2] * x[k - 1]) / u0[k - 2];
+        for (int t = k - 3; t >= 0; --t) x[t] = (x[t] - u1[t] * x[t + 1] - u2[t] * x[t + 2]) / u0[t];
         double mx = 0.0;
         for (int t = 0; t < k; ++t) mx = fmax(mx, fabs(x[t]));
         if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
@@ -234,7 +206,80 @@ __device__ __forceinline__ double start_entry(int row) {
     return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
+// w[i] = Q[row i, :] . v for this CTA's rows: four rows per warp, two
+// 16-byte loads per row in flight per lane.
+__device__ __forceinline__ void matvec_rows(const double* __restrict__ Q, int ldq, int n, int r0,
+                                            int nr, const double* v, double* w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int neven = n & ~1;
+    for (int i = 4 * warp; i < nr; i += 4 * kWarps) {
+        const double* q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = Q + (int64_t)(r0 + min(i + u, nr - 1)) * ldq;
+        double acc[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll 2
+        for (int kk = 2 * lane; kk < neven; kk += 64) {
+            const double2 vv = *reinterpret_cast<const double2*>(v + kk);
+            double2 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const double2*>(q[u] + kk);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc[u][0] = fma(x[u].x, vv.x, acc[u][0]);
+                acc[u][1] = fma(x[u].y, vv.y, acc[u][1]);
+            }
+        }
+        if ((n & 1) && lane == 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u][0] = fma(q[u][n - 1], v[n - 1], acc[u][0]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double s = warp_sum(acc[u][0] + acc[u][1]);
+            if (lane == 0 && i + u < nr) w[i + u] = s;
+        }
+    }
+}
+
+// part[i] = sum over this CTA's rows of B[i][row] * w[row], i <= j (warp per i).
+// B is written by this kernel (new Lanczos vectors), so it must never be read
+// through the non-coherent read-only path: no __restrict__ on it.
+__device__ __forceinline__ void cgs_dots(const double* B, int ldq, int r0, int nr, int j,
+                                         const double* w, double* part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i <= j; i += kWarps) {
+        const double* bi = B + (int64_t)i * ldq + r0;
+        double s0 = 0.0, s1 = 0.0;
+        int rr = lane;
+        for (; rr + 32 < nr; rr += 64) {
+            s0 = fma(bi[rr], w[rr], s0);
+            s1 = fma(bi[rr + 32], w[rr + 32], s1);
+        }
+        if (rr < nr) s0 = fma(bi[rr], w[rr], s0);
+        const double s = warp_sum(s0 + s1);
+        if (lane == 0) part[i] = s;
+    }
+}
+
+// w[row] -= sum_{i <= j} B[i][row] * c[i] (thread per row).
+__device__ __forceinline__ void cgs_update(const double* B, int ldq, int r0, int nr, int j,
+                                           const double* c, double* w) {
+    for (int rr = threadIdx.x; rr < nr; rr += kThreads) {
+        const double* b = B + r0 + rr;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int i = 0;
+        for (; i + 3 <= j; i += 4) {
+            s0 = fma(b[(int64_t)i * ldq], c[i], s0);
+            s1 = fma(b[(int64_t)(i + 1) * ldq], c[i + 1], s1);
+            s2 = fma(b[(int64_t)(i + 2) * ldq], c[i + 2], s2);
+            s3 = fma(b[(int64_t)(i + 3) * ldq], c[i + 3], s3);
+        }
+        for (; i <= j; ++i) s0 = fma(b[(int64_t)i * ldq], c[i], s0);
+        w[rr] -= (s0 + s1) + (s2 + s3);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
@@ -245,14 +290,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
     const int R = (n + cs - 1) / cs;
     const int r0 = min(n, q * R), r1 = min(n, r0 + R), nr = r1 - r0;
     const double* __restrict__ Q = A.qarena + P.q_off;
-    double* __restrict__ B = A.barena + P.b_off;
+    double* B = A.barena + P.b_off;
     const int kmax = min(A.mmax, n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = A.mmax + 1;
+    // per-problem global scratch: the final tridiagonal T_k (diagonal, off-diagonal)
+    double* scr = A.scratch + (size_t)pj * lanczos_scratch_per_problem(A.mmax, r);
 
     extern __shared__ __align__(16) double smraw[];
     Smem S = carve(smraw, A.max_n, cs, A.mmax);
     double* part[2] = {S.part0, S.part1};
     int pb = 0;
+    __shared__ int s_flag;
 
     // ---- start vector: pseudo-random, unit norm
     double loc = 0.0;
@@ -273,11 +322,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
         }
     }
 
-    const int check_every = cs == 1 ? 4 : 8;
     const int kmin = min(kmax, max(2 * r, 8));
+    int next_check = kmin;
     double tnorm = 0.0;
     int k = 0;
-    bool converged = false;
+    bool converged = false, have_vectors = false;
 
     for (int j = 0; j < kmax; ++j) {
         // ---- gather v_j from all ranks
@@ -288,44 +337,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
         }
         __syncthreads();
 
-        // ---- w = Q v_j on this CTA's rows (one warp per row)
-        for (int i = warp; i < nr; i += kWarps) {
-            const double* qr = Q + (int64_t)(r0 + i) * ldq;
-            double s0 = 0.0, s1 = 0.0;
-#pragma unroll 4
-            for (int kk = 2 * lane; kk < n; kk += 64) {
-                if (kk + 1 < n) {
-                    const double2 qv = *reinterpret_cast<const double2*>(qr + kk);
-                    const double2 vv = *reinterpret_cast<const double2*>(S.vfull + kk);
-                    s0 = fma(qv.x, vv.x, s0);
-                    s1 = fma(qv.y, vv.y, s1);
-                } else {
-                    s0 = fma(qr[kk], S.vfull[kk], s0);
-                }
-            }
-            const double s = warp_sum(s0 + s1);
-            if (lane == 0) S.wloc[i] = s;
-        }
+        // ---- w = Q v_j on this CTA's rows
+        matvec_rows(Q, ldq, n, r0, nr, S.vfull, S.wloc);
         __syncthreads();
 
         // ---- two passes of classical Gram-Schmidt against v_0..v_j
         double alpha_j = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
-            for (int i = warp; i <= j; i += kWarps) {
-                const double* bi = B + (int64_t)i * ldq + r0;
-                double s = 0.0;
-                for (int rr = lane; rr < nr; rr += 32) s = fma(bi[rr], S.wloc[rr], s);
-                s = warp_sum(s);
-                if (lane == 0) part[pb][i] = s;
-            }
+            cgs_dots(B, ldq, r0, nr, j, S.wloc, part[pb]);
             __syncthreads();
             cluster_allreduce(cl, part[pb], S.cfull, j + 1, cs);
             pb ^= 1;
-            for (int rr = tid; rr < nr; rr += kThreads) {
-                double s = 0.0;
-                for (int i = 0; i <= j; ++i) s = fma(B[(int64_t)i * ldq + r0 + rr], S.cfull[i], s);
-                S.wloc[rr] -= s;
-            }
+            cgs_update(B, ldq, r0, nr, j, S.cfull, S.wloc);
             alpha_j += S.cfull[j];
             __syncthreads();
         }
@@ -350,33 +373,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
         __syncthreads();
 
         const bool breakdown = beta_j <= 1e-12 * tnorm || k == n;
-        const bool do_check =
-            breakdown || k == kmax || (k >= kmin && ((k - kmin) % check_every) == 0);
+        const bool do_check = breakdown || k == kmax || k >= next_check;
         if (do_check && k >= r) {
-            // Gershgorin bounds of T_k
-            double gl = DBL_MAX, gu = -DBL_MAX, bmax2 = 1.0;
-            for (int t = 0; t < k; ++t) {
-                const double off = (t > 0 ? S.beta[t - 1] : 0.0) + (t < k - 1 ? S.beta[t] : 0.0);
-                gl = fmin(gl, S.alpha[t] - off);
-                gu = fmax(gu, S.alpha[t] + off);
-                if (t < k - 1) bmax2 = fmax(bmax2, S.beta2[t]);
-            }
-            const double pad = 2.0 * DBL_EPSILON * fmax(fabs(gl), fabs(gu)) * k + DBL_MIN;
-            gl -= pad;
-            gu += pad;
-            const double pivmin = 1e-290 * bmax2;
-            for (int i = warp; i < r; i += kWarps) {
-                const double th = kth_largest(S.alpha, S.beta2, k, i, gl, gu, pivmin);
-                if (lane == 0) {
-                    S.theta[i] = th;
-                    S.resid[i] = beta_j * sqrt(last_comp2(S.alpha, S.beta2, k, th, pivmin));
+            // Rank 0 finds the r largest Ritz values and their residuals
+            // beta_j |x_i[k-1]| from inverse-iteration eigenvectors x_i of T_k,
+            // then every CTA reads the verdict through DSMEM.
+            if (q == 0) {
+                double gl = DBL_MAX, gu = -DBL_MAX, bmax2 = 1.0;
+                for (int t = 0; t < k; ++t) {
+                    const double off = (t > 0 ? S.beta[t - 1] : 0.0) + (t < k - 1 ? S.beta[t] : 0.0);
+                    gl = fmin(gl, S.alpha[t] - off);
+                    gu = fmax(gu, S.alpha[t] + off);
+                    if (t < k - 1) bmax2 = fmax(bmax2, S.beta2[t]);
+                }
+                const double pad = 2.0 * DBL_EPSILON * fmax(fabs(gl), fabs(gu)) * k + DBL_MIN;
+                gl -= pad;
+                gu += pad;
+                const double pivmin = 1e-290 * bmax2;
+                for (int i = warp; i < r; i += kWarps) {
+                    const double th = kth_largest(S.alpha, S.beta2, k, i, gl, gu, pivmin);
+                    if (lane == 0) S.theta[i] = th;
+                }
+                __syncthreads();
+                if (tid < r) {
+                    double* iv = S.inv + (size_t)tid * 4 * L;
+                    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+                    tri_inverse_iteration(S.alpha, S.beta, k, S.theta[tid], pert, iv, iv + L,
+                                          iv + 2 * L, iv + 3 * L);
+                    S.resid[tid] = beta_j * fabs(iv[3 * L + k - 1]);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    bool ok = true;
+                    double worst = 0.0;
+                    const double th0 = fabs(S.theta[0]);
+                    for (int i = 0; i < r; ++i) {
+                        ok = ok && (S.resid[i] <= A.tol * th0 || breakdown);
+                        worst = fmax(worst, S.resid[i] / fmax(th0, DBL_MIN));
+                    }
+                    s_flag = (ok ? 1 : 0) | (worst < 1e-6 ? 2 : 0);
                 }
             }
+            cl.sync();
+            if (q != 0) {
+                if (tid < r) {
+                    S.theta[tid] = cl.map_shared_rank(S.theta, 0)[tid];
+                    S.resid[tid] = cl.map_shared_rank(S.resid, 0)[tid];
+                }
+                if (tid == 0) s_flag = *cl.map_shared_rank(&s_flag, 0);
+            }
             __syncthreads();
-            bool ok = true;
-            const double thr = A.tol * fabs(S.theta[0]);
-            for (int i = 0; i < r; ++i) ok = ok && (S.resid[i] <= thr || breakdown);
-            if (ok) {
+            have_vectors = true;
+            next_check = k + ((s_flag & 2) ? 4 : 8);
+            if (s_flag & 1) {
                 converged = true;
                 break;
             }
@@ -393,66 +442,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
         __syncthreads();
     }
 
-    // ---- finish: status, eigenvectors of T_k (rank 0), Ritz vectors (all)
-    double* scr = A.scratch + (size_t)pj * lanczos_scratch_per_problem(A.mmax, r);
-    double* Sv = scr;  // r x (mmax+1): eigenvectors of T_k
+    // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
     int status = kDevOk;
-    if (k < r) {
+    if (k < r || !have_vectors) {
         status = kDevRank;
     } else {
         if (!converged) status = kDevNoConv;
         if (!(S.theta[r - 1] > 0.0) || !(S.theta[r - 1] > A.rank_tol * S.theta[0])) status = kDevRank;
     }
-    if (q == 0 && k >= r) {
-        const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-        for (int i = tid; i < r; i += kThreads) {
-            double* base = scr + (size_t)r * (A.mmax + 1) + (size_t)i * 6 * (A.mmax + 1);
-            const int L = A.mmax + 1;
-            tri_inverse_iteration(S.alpha, S.beta, k, S.theta[i], pert, base, base + L, base + 2 * L,
-                                  base + 3 * L, base + 4 * L, base + 5 * L);
-            for (int t = 0; t < k; ++t) Sv[(size_t)i * L + t] = base[5 * L + t];
-        }
-        __syncthreads();
-        // modified Gram-Schmidt across the r vectors (warp 0)
-        if (warp == 0) {
-            const int L = A.mmax + 1;
-            for (int i = 0; i < r; ++i) {
-                double* xi = Sv + (size_t)i * L;
-                for (int m = 0; m < i; ++m) {
-                    const double* xm = Sv + (size_t)m * L;
-                    double s = 0.0;
-                    for (int t = lane; t < k; t += 32) s += xi[t] * xm[t];
-                    s = warp_sum(s);
-                    for (int t = lane; t < k; t += 32) xi[t] -= s * xm[t];
-                    __syncwarp();
-                }
+    if (q == 0 && status != kDevRank && warp == 0) {
+        // modified Gram-Schmidt across the r inverse-iteration vectors (shared memory)
+        for (int i = 0; i < r; ++i) {
+            double* xi = S.inv + (size_t)i * 4 * L + 3 * L;
+            for (int m = 0; m < i; ++m) {
+                const double* xm = S.inv + (size_t)m * 4 * L + 3 * L;
                 double s = 0.0;
-                for (int t = lane; t < k; t += 32) s += xi[t] * xi[t];
+                for (int t = lane; t < k; t += 32) s += xi[t] * xm[t];
                 s = warp_sum(s);
-                const double inv = 1.0 / sqrt(s);
-                for (int t = lane; t < k; t += 32) xi[t] *= inv;
+                for (int t = lane; t < k; t += 32) xi[t] -= s * xm[t];
                 __syncwarp();
             }
+            double s = 0.0;
+            for (int t = lane; t < k; t += 32) s += xi[t] * xi[t];
+            s = warp_sum(s);
+            const double inv = 1.0 / sqrt(s);
+            for (int t = lane; t < k; t += 32) xi[t] *= inv;
+            __syncwarp();
         }
-        __threadfence();
     }
     cl.sync();
-    if (k < r) {
+    if (status == kDevRank) {
         if (q == 0 && tid == 0) {
             A.status[pj] = status;
             A.steps[pj] = k;
         }
         return;
     }
+    // the other CTAs copy the eigenvectors of T_k from rank 0 (DSMEM)
+    if (q != 0) {
+        const double* src = cl.map_shared_rank(S.inv, 0);
+        for (int e = tid; e < r * k; e += kThreads) {
+            const int i = e / k, t = e % k;
+            S.inv[(size_t)i * 4 * L + 3 * L + t] = src[(size_t)i * 4 * L + 3 * L + t];
+        }
+    }
+    __syncthreads();
 
     // Ritz vectors y_i = V_k s_i for this CTA's rows; per-column |max| for the sign rule.
     double* V = A.varena + P.v_off;
-    const int L = A.mmax + 1;
     for (int rr = tid; rr < nr; rr += kThreads) {
         for (int i = 0; i < r; ++i) {
-            const double* si = Sv + (size_t)i * L;
+            const double* si = S.inv + (size_t)i * 4 * L + 3 * L;
             double s = 0.0;
-            for (int t = 0; t < k; ++t) s = fma(B[(int64_t)t * ldq + r0 + rr], __ldcg(si + t), s);
+            for (int t = 0; t < k; ++t) s = fma(B[(int64_t)t * ldq + r0 + rr], si[t], s);
             V[(int64_t)(r0 + rr) * r + i] = s;
         }
     }
@@ -508,18 +550,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_lanczos(LanczosArgs A) {
         A.status[pj] = status;
         A.steps[pj] = k;
     }
+    if (q == 0)
+        for (int t = tid; t < k; t += kThreads) {
+            scr[t] = S.alpha[t];
+            scr[L + t] = S.beta[t];
+        }
 }
 
 }  // namespace
 
-size_t lanczos_smem_bytes(int max_n, int cs, int mmax) {
-    return smem_doubles(max_n, cs, mmax) * sizeof(double) + kMaxR * sizeof(double);
+size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
+    return smem_doubles(max_n, cs, mmax, r) * sizeof(double) + kMaxR * sizeof(double);
 }
 
 cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
     if (a.p <= 0) return cudaSuccess;
     const int cs = cluster < 1 ? 1 : (cluster > 16 ? 16 : cluster);
-    const size_t smem = smem_doubles(a.max_n, cs, a.mmax) * sizeof(double);
+    const size_t smem = smem_doubles(a.max_n, cs, a.mmax, a.r) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_lanczos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (cs > 8) {

@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(256) k_interp_model(const double* __restrict__
 
 // One CTA: 64 rows of Y against all l landmarks.  T: element type of Y,
 // A: arithmetic type (float or double).  L is dense l x d in type A.
-template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_gower(const T* __restrict__ Y, int64_t m, int d,
+template <typename Ld, typename A>
+__global__ void __launch_bounds__(256) k_gower(Ld Y, int64_t m, int d,
                                                const double* __restrict__ nrm_y,
                                                const A* __restrict__ L,
                                                const double* __restrict__ nrm_l, int l,
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) k_gower(const T* __restrict__ Y, int64_t 
                 const int row = e / KC, kk = e % KC, k = k0 + kk;
                 const int64_t gi = i0 + row;
                 const int gj = j0 + row;
-                Ys[kk][row] = (gi < m && k < d) ? load_as<A, T>(Y + gi * d + k) : A(0);
+                Ys[kk][row] = (gi < m && k < d) ? Y.template get<A>(gi, k) : A(0);
                 Ls[kk][row] = (gj < l && k < d) ? L[(int64_t)gj * d + k] : A(0);
             }
             __syncthreads();
@@ -175,42 +175,35 @@ cudaError_t launch_interp_model(const double* V, const double* lam, const double
     return cudaGetLastError();
 }
 
+template <typename Ld, typename A>
+static cudaError_t gower_launch(Ld Y, int64_t m, int d, const double* nrm_y, const void* L,
+                                const double* nrm_l, int l, const void* W, const double* bias,
+                                int r, void* X, cudaStream_t st) {
+    const dim3 grid((unsigned)((m + kTile - 1) / kTile)), block(256);
+    const size_t smem = (2 * 16 * (kTile + 4) + kTile * (kTile + 1) + kTile * kMaxR) * sizeof(A);
+    cudaError_t e = cudaFuncSetAttribute(k_gower<Ld, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gower<Ld, A><<<grid, block, smem, st>>>(Y, m, d, nrm_y, (const A*)L, nrm_l, l, (const A*)W, bias, r, (A*)X);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gower_proj(const void* Y, int dt, int64_t m, int d, const double* nrm_y,
                               const void* L, const double* nrm_l, int l, const void* W,
                               const double* bias, int r, int acc_f64, void* X, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((m + kTile - 1) / kTile)), block(256);
-    const size_t elems = 2 * 16 * (kTile + 4) + kTile * (kTile + 1) + kTile * kMaxR;
-    const size_t smem = elems * (acc_f64 ? sizeof(double) : sizeof(float));
-    cudaError_t e = acc_f64
-        ? cudaFuncSetAttribute(k_gower<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-        : cudaSuccess;
-    if (e != cudaSuccess) return e;
     if (acc_f64) {
-        cudaFuncSetAttribute(k_gower<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_gower<uint8_t, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (dt == MDS_IN_F64) return gower_launch<RowLoad<double>, double>(RowLoad<double>{(const double*)Y, d}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
+        if (dt == MDS_IN_F32) return gower_launch<RowLoad<float>, double>(RowLoad<float>{(const float*)Y, d}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
+        return gower_launch<RowLoad<uint8_t>, double>(RowLoad<uint8_t>{(const uint8_t*)Y, d}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
     }
-    if (acc_f64) {
-        const double *Ld = (const double*)L, *Wd = (const double*)W;
-        if (dt == MDS_IN_F64)
-            k_gower<double, double><<<grid, block, smem, st>>>((const double*)Y, m, d, nrm_y, Ld, nrm_l, l, Wd, bias, r, (double*)X);
-        else if (dt == MDS_IN_F32)
-            k_gower<float, double><<<grid, block, smem, st>>>((const float*)Y, m, d, nrm_y, Ld, nrm_l, l, Wd, bias, r, (double*)X);
-        else
-            k_gower<uint8_t, double><<<grid, block, smem, st>>>((const uint8_t*)Y, m, d, nrm_y, Ld, nrm_l, l, Wd, bias, r, (double*)X);
-    } else {
-        const float *Lf = (const float*)L, *Wf = (const float*)W;
-        if (dt == kDtBF16)
-            k_gower<__nv_bfloat16, float><<<grid, block, smem, st>>>((const __nv_bfloat16*)Y, m, d, nrm_y, Lf, nrm_l, l, Wf, bias, r, (float*)X);
-        else if (dt == MDS_IN_F64)
-            k_gower<double, float><<<grid, block, smem, st>>>((const double*)Y, m, d, nrm_y, Lf, nrm_l, l, Wf, bias, r, (float*)X);
-        else if (dt == MDS_IN_F32)
-            k_gower<float, float><<<grid, block, smem, st>>>((const float*)Y, m, d, nrm_y, Lf, nrm_l, l, Wf, bias, r, (float*)X);
-        else
-            k_gower<uint8_t, float><<<grid, block, smem, st>>>((const uint8_t*)Y, m, d, nrm_y, Lf, nrm_l, l, Wf, bias, r, (float*)X);
+    if (dt == kDtBF16) {
+        const int ld = split_ld(d);
+        return gower_launch<SplitLoad, float>(SplitLoad{(const __nv_bfloat16*)Y, ld, m * ld}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
     }
-    note_launch(1);
-    return cudaGetLastError();
+    if (dt == MDS_IN_F64) return gower_launch<RowLoad<double>, float>(RowLoad<double>{(const double*)Y, d}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
+    if (dt == MDS_IN_F32) return gower_launch<RowLoad<float>, float>(RowLoad<float>{(const float*)Y, d}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
+    return gower_launch<RowLoad<uint8_t>, float>(RowLoad<uint8_t>{(const uint8_t*)Y, d}, m, d, nrm_y, L, nrm_l, l, W, bias, r, X, st);
 }
 
 cudaError_t launch_scatter_rows(const void* X1, const int64_t* idx, int l, int r, int64_t nx,
