@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-parts", type=int, default=4, help="parts in the bounded oracle sample")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="CTAs per eigenproblem (default: the library's choice; for profiling)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="points per GPU (default: the workload's full size; smaller sizes are for profiling)")
     return ap.parse_args()
 
 
@@ -183,14 +187,19 @@ def oracle_interp_sample(Y, idx, r, m):
 # ---------------------------------------------------------------- workloads
 
 
-def make_workload(name, seed):
+def make_workload(name, seed, n=0):
+    import dataclasses
     if name == "dc":
         w = W.DC_F32
-        Y = W.make_data(w, seed)
+        if n:
+            w = dataclasses.replace(w, n=n, name=w.name.replace(f"n{W.DC_F32.n}", f"n{n}"))
+        Y = W.make_data(W.DC_F32, seed, n=w.n)
         part = W.partitions_uneven(w.n, w.c, w.own_lo, w.own_hi, seed)
         return w, Y, part
     w = W.INTERP_BF16
-    Y = W.make_data(w, seed)
+    if n:
+        w = dataclasses.replace(w, n=n, name=w.name.replace(f"n{W.INTERP_BF16.n}", f"n{n}"))
+    Y = W.make_data(W.INTERP_BF16, seed, n=w.n)
     idx = W.landmarks(w.n, w.l, seed)
     return w, Y, idx
 
@@ -199,7 +208,7 @@ def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w, Y, aux = make_workload(args.workload, args.seed)
+    w, Y, aux = make_workload(args.workload, args.seed, args.n)
     times, pts = [], 0
     for i in range(args.warmup + args.steps):
         if args.workload == "dc":
@@ -240,7 +249,7 @@ def ours(args):
     from paper_2007_11919_gb300 import mds as M
 
     seed = args.seed + 1000 * rank
-    w, Y, aux = make_workload(args.workload, seed)
+    w, Y, aux = make_workload(args.workload, seed, args.n)
     Yd = torch.from_numpy(Y).to(dev)
     L = M._lib()
     if args.workload == "dc":
@@ -254,14 +263,14 @@ def ours(args):
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
 
         def step(Yin=Yd, a=anc, o=own):
-            return G.mds_divide_conquer(Yin, a, part.ptr, o, w.r, w.prec, workspace=ws)
+            return G.mds_divide_conquer(Yin, a, part.ptr, o, w.r, w.prec, workspace=ws, cluster=args.cluster)
     else:
         idx = torch.from_numpy(aux).to(dev)
         wsb = L.mds_interpolate_workspace_size(w.n, w.d, w.l, w.r, M.PREC[w.prec])
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
 
         def step(Yin=Yd, a=idx, o=None):
-            X, var, _ = G.mds_interpolate(Yin, a, w.r, w.prec, workspace=ws)
+            X, var, _ = G.mds_interpolate(Yin, a, w.r, w.prec, workspace=ws, cluster=args.cluster)
             return X, var
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2

@@ -111,6 +111,8 @@ struct Batch {
     double *q = nullptr, *rp = nullptr, *rm = nullptr, *grand = nullptr, *b = nullptr,
            *v = nullptr, *lam = nullptr, *scr = nullptr;
     int *status = nullptr, *steps = nullptr;
+    std::vector<int> order;            // problems, largest first (eigen-solver queue order)
+    int *d_order = nullptr, *counter = nullptr;
 };
 
 void plan_batch(Batch& B, const std::vector<int>& sizes, const std::vector<int64_t>& own_off,
@@ -143,6 +145,10 @@ void plan_batch(Batch& B, const std::vector<int>& sizes, const std::vector<int64
         B.max_tiles = std::max(B.max_tiles, P.tiles);
         B.desc.push_back(P);
     }
+    B.order.resize(B.p);
+    for (int j = 0; j < B.p; ++j) B.order[j] = j;
+    std::stable_sort(B.order.begin(), B.order.end(),
+                     [&](int x, int y) { return B.desc[x].n > B.desc[y].n; });
 }
 
 void carve_batch(Batch& B, Arena& A) {
@@ -157,6 +163,8 @@ void carve_batch(Batch& B, Arena& A) {
     B.scr = A.take<double>((size_t)B.p * lanczos_scratch_per_problem(B.mmax, B.r));
     B.status = A.take<int>(B.p);
     B.steps = A.take<int>(B.p);
+    B.d_order = A.take<int>(B.p);
+    B.counter = A.take<int>(1);
 }
 
 int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
@@ -165,8 +173,10 @@ int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int cs;
+    // Persistent queue: about 1.5 parts per cluster slot (two CTAs per SM)
+    // lets largest-first scheduling even out uneven part sizes.
     if (p == 1) cs = 16;
-    else cs = std::max(1, std::min(8, (int)std::lround(2.0 * sms / p)));
+    else cs = std::max(1, std::min(8, (int)std::lround(2.0 * sms * 1.5 / p)));
     cs = std::min(cs, std::max(1, max_n / 64));
     while (cs < 16 && lanczos_smem_bytes(max_n, cs, mmax, r) > kMaxSmem) ++cs;
     return cs;
@@ -183,6 +193,8 @@ int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
 int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
                   const int64_t* anchors, const int64_t* own, int acc_f64, const Opts& o) {
     CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
+    CK(cudaMemcpyAsync(B.d_order, B.order.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
+    CK(cudaMemsetAsync(B.counter, 0, sizeof(int), o.st));
     if (Y) {
         CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64,
                                  B.q, B.rp, o.st));
@@ -199,6 +211,8 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.status = B.status;
     a.steps = B.steps;
     a.scratch = B.scr;
+    a.order = B.d_order;
+    a.counter = B.counter;
     a.r = B.r;
     a.mmax = B.mmax;
     a.tol = o.tol;

@@ -126,6 +126,8 @@ struct LanczosArgs {
     int* status;        // p
     int* steps;         // p
     double* scratch;    // p x lanczos_scratch_per_problem(mmax, r) doubles
+    const int* order;   // p problem indices, the order in which clusters take them
+    int* counter;       // queue head, zero before the launch
     int r;
     int mmax;
     double tol;

@@ -49,14 +49,14 @@ struct Smem {
     double* theta;   // kMaxR
     double* resid;   // kMaxR
     double* red;     // 3 * kWarps * ... scratch (64)
-    double* sgn;     // 3 * kMaxR : (|max|, row, signed) per eigenvector
+    double* sgn;     // 4 * kMaxR : (|max|, row, signed) per eigenvector, then sign flips
     double* inv;     // 4 * r * (mmax + 1): per wanted vector U bands u0, u1, u2 and x
 };
 
 __host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
     return round_up(max_n, 2) + 2 * round_up(rmax, 2) + 3 * (size_t)(mmax + 2) +
-           3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 3 * kMaxR + 4 * (size_t)r * (mmax + 1) + 8;
+           3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 4 * (size_t)r * (mmax + 1) + 8;
 }
 
 __device__ Smem carve(double* base, int max_n, int cs, int mmax) {
@@ -75,7 +75,7 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax) {
     s.theta = p; p += kMaxR;
     s.resid = p; p += kMaxR;
     s.red = p; p += 64;
-    s.sgn = p; p += 3 * kMaxR;
+    s.sgn = p; p += 4 * kMaxR;
     s.inv = p;
     return s;
 }
@@ -105,52 +105,59 @@ __device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* o
     __syncthreads();
 }
 
-// Number of eigenvalues of T (alpha, beta^2) smaller than x.
-__device__ int sturm_count(const double* al, const double* b2, int k, double x, double pivmin) {
-    int c = 0;
-    double dd = al[0] - x;
-    if (fabs(dd) < pivmin) dd = -pivmin;
-    if (dd < 0.0) ++c;
+// Number of eigenvalues of T (alpha, beta^2) smaller than x: the sign changes
+// of the Sturm sequence p_0 = 1, p_t = det(T_t - x I) =
+// (alpha_{t-1} - x) p_{t-1} - beta_{t-2}^2 p_{t-2} (a sign change between
+// p_{t-1} and p_t is a negative pivot of T - x I = L D L^T).  No division: the
+// pair (p_{t-1}, p_t) is rescaled by exact powers of two to stay in range, and
+// an exact zero counts as a sign change (a tiny negative pivot).
+__device__ int sturm_count(const double* al, const double* b2, int k, double x) {
+    double pm = 1.0, p = al[0] - x;
+    if (p == 0.0) p = -1e-300;
+    int c = p < 0.0;
     for (int t = 1; t < k; ++t) {
-        dd = (al[t] - x) - b2[t - 1] / dd;
-        if (fabs(dd) < pivmin) dd = -pivmin;
-        if (dd < 0.0) ++c;
+        double pn = fma(al[t] - x, p, -b2[t - 1] * pm);
+        if (pn == 0.0) pn = -p * 1e-300;
+        c += (pn < 0.0) != (p < 0.0);
+        pm = p;
+        p = pn;
+        const double ap = fabs(p);
+        if (ap > 0x1p+500) {
+            p *= 0x1p-500;
+            pm *= 0x1p-500;
+        } else if (ap < 0x1p-500 && fabs(pm) < 0x1p-500) {
+            p *= 0x1p+500;
+            pm *= 0x1p+500;
+        }
     }
     return c;
 }
 
-// Warp-cooperative multisection for the i-th largest eigenvalue of T.
-__device__ double kth_largest(const double* al, const double* b2, int k, int i, double gl, double gu,
-                              double pivmin) {
-    const int lane = threadIdx.x & 31;
-    const int target = k - 1 - i;  // ascending index
-    double lo = gl, hi = gu;
-    for (int round = 0; round < 24; ++round) {
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-        const int cnt = sturm_count(al, b2, k, x, pivmin);
-        const unsigned ball = __ballot_sync(0xffffffffu, cnt > target);
-        const int first = ball ? __ffs(ball) - 1 : 32;
-        const double xf = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
-        const double xp = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
-        const double nhi = first < 32 ? xf : hi;
-        const double nlo = first > 0 ? xp : lo;
-        lo = nlo;
-        hi = nhi;
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+// The i-th largest eigenvalue of T by bisection on [lo, hi] (one thread),
+// which must satisfy count(lo) <= k-1-i < count(hi).
+__device__ double kth_largest(const double* al, const double* b2, int k, int i, double lo, double hi) {
+    const int target = k - 1 - i;
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (sturm_count(al, b2, k, mid) > target) hi = mid;
+        else lo = mid;
+        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) break;
     }
     return 0.5 * (lo + hi);
 }
 
 // Inverse iteration for the eigenvector of T for eigenvalue th (unit 2-norm),
 // all in shared memory.  Each iteration factors T - th I = P L U by Gaussian
-// elimination with partial pivoting (U has the bands u0, u1, u2) while it
+// elimination with partial pivoting (U has the bands 1/u0, u1, u2) while it
 // applies the same row operations to the right-hand side x, then solves with
-// U from the bottom up.  Three iterations from a fixed positive start vector.
+// U from the bottom up: one division per row.  Two iterations from a fixed
+// positive start vector (th is accurate to a few ulps).
 __device__ void tri_inverse_iteration(const double* al, const double* be, int k, double th,
-                                      double pert, double* u0, double* u1, double* u2,
+                                      double pert, double* u0i, double* u1, double* u2,
                                       double* x) {
     for (int t = 0; t < k; ++t) x[t] = 1.0 + 0.25 * (double)((t * 7919) % 13) / 13.0;
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < 2; ++it) {
         // working row t: entries (w0, w1) in columns t, t+1 and right-hand side yw
         double w0 = al[0] - th, w1 = k > 1 ? be[0] : 0.0, yw = x[0];
         for (int t = 0; t < k - 1; ++t) {
@@ -160,8 +167,9 @@ __device__ void tri_inverse_iteration(const double* al, const double* be, int k,
             const double yl = x[t + 1];
             if (fabs(w0) >= fabs(l0)) {                        // pivot on the working row
                 if (w0 == 0.0) w0 = pert;
-                const double f = l0 / w0;
-                u0[t] = w0;
+                const double inv = 1.0 / w0;
+                const double f = l0 * inv;
+                u0i[t] = inv;
                 u1[t] = w1;
                 u2[t] = 0.0;
                 x[t] = yw;
@@ -169,8 +177,9 @@ __device__ void tri_inverse_iteration(const double* al, const double* be, int k,
                 w1 = l2;
                 yw = yl - f * yw;
             } else {                                           // pivot on row t+1
-                const double f = w0 / l0;
-                u0[t] = l0;
+                const double inv = 1.0 / l0;
+                const double f = w0 * inv;
+                u0i[t] = inv;
                 u1[t] = l1;
                 u2[t] = l2;
                 x[t] = yl;
@@ -180,16 +189,17 @@ __device__ void tri_inverse_iteration(const double* al, const double* be, int k,
             }
         }
         if (w0 == 0.0) w0 = pert;
-        u0[k - 1] = w0;
-        x[k - 1] = yw / w0;
-        if (k > 1) x[k - 2] = (x[k - 2] - u1[k - 2] * x[k - 1]) / u0[k - 2];
-        for (int t = k - 3; t >= 0; --t) x[t] = (x[t] - u1[t] * x[t + 1] - u2[t] * x[t + 2]) / u0[t];
+        u0i[k - 1] = 1.0 / w0;
+        x[k - 1] = yw * u0i[k - 1];
+        if (k > 1) x[k - 2] = (x[k - 2] - u1[k - 2] * x[k - 1]) * u0i[k - 2];
+        for (int t = k - 3; t >= 0; --t) x[t] = (x[t] - u1[t] * x[t + 1] - u2[t] * x[t + 2]) * u0i[t];
         double mx = 0.0;
         for (int t = 0; t < k; ++t) mx = fmax(mx, fabs(x[t]));
         if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
+        const double imx = 1.0 / mx;
         double ss = 0.0;
         for (int t = 0; t < k; ++t) {
-            x[t] /= mx;
+            x[t] *= imx;
             ss += x[t] * x[t];
         }
         const double inv = 1.0 / sqrt(ss);
@@ -244,9 +254,16 @@ __device__ __forceinline__ void matvec_rows(const double* __restrict__ Q, int ld
 // part[i] = sum over this CTA's rows of B[i][row] * w[row], i <= j (warp per i).
 // B is written by this kernel (new Lanczos vectors), so it must never be read
 // through the non-coherent read-only path: no __restrict__ on it.
+// With with_norm, part[j+1] also receives the partial sum of w[row]^2.
 __device__ __forceinline__ void cgs_dots(const double* B, int ldq, int r0, int nr, int j,
-                                         const double* w, double* part) {
+                                         const double* w, double* part, bool with_norm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (with_norm && warp == (j + 1) % kWarps) {
+        double s0 = 0.0;
+        for (int rr = lane; rr < nr; rr += 32) s0 = fma(w[rr], w[rr], s0);
+        s0 = warp_sum(s0);
+        if (lane == 0) part[j + 1] = s0;
+    }
     for (int i = warp; i <= j; i += kWarps) {
         const double* bi = B + (int64_t)i * ldq + r0;
         double s0 = 0.0, s1 = 0.0;
@@ -279,12 +296,9 @@ __device__ __forceinline__ void cgs_update(const double* B, int ldq, int r0, int
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int cs = (int)cl.num_blocks();
-    const int q = (int)cl.block_rank();
-    const int pj = blockIdx.x / cs;
-    if (pj >= A.p) return;  // the whole cluster shares pj
+// One eigenproblem (part pj) solved by the calling cluster.
+__device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q,
+                              double* smraw, int& s_flag) {
     const ProbDesc P = A.desc[pj];
     const int n = P.n, ldq = P.ldq, r = A.r;
     const int R = (n + cs - 1) / cs;
@@ -297,11 +311,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     // per-problem global scratch: the final tridiagonal T_k (diagonal, off-diagonal)
     double* scr = A.scratch + (size_t)pj * lanczos_scratch_per_problem(A.mmax, r);
 
-    extern __shared__ __align__(16) double smraw[];
     Smem S = carve(smraw, A.max_n, cs, A.mmax);
     double* part[2] = {S.part0, S.part1};
     int pb = 0;
-    __shared__ int s_flag;
 
     // ---- start vector: pseudo-random, unit norm
     double loc = 0.0;
@@ -324,8 +336,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
 
     const int kmin = min(kmax, max(2 * r, 8));
     int next_check = kmin;
-    double tnorm = 0.0;
-    int k = 0;
+    double tnorm = 0.0, prev_worst = -1.0;
+    int k = 0, prev_k = 0;
     bool converged = false, have_vectors = false;
 
     for (int j = 0; j < kmax; ++j) {
@@ -341,28 +353,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
         matvec_rows(Q, ldq, n, r0, nr, S.vfull, S.wloc);
         __syncthreads();
 
-        // ---- two passes of classical Gram-Schmidt against v_0..v_j
+        // ---- two passes of classical Gram-Schmidt against v_0..v_j; the
+        // second pass also reduces ||w_1||^2, and ||w_2||^2 = ||w_1||^2 - ||c_2||^2.
         double alpha_j = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
-            cgs_dots(B, ldq, r0, nr, j, S.wloc, part[pb]);
+            cgs_dots(B, ldq, r0, nr, j, S.wloc, part[pb], pass == 1);
             __syncthreads();
-            cluster_allreduce(cl, part[pb], S.cfull, j + 1, cs);
+            cluster_allreduce(cl, part[pb], S.cfull, j + 1 + pass, cs);
             pb ^= 1;
             cgs_update(B, ldq, r0, nr, j, S.cfull, S.wloc);
             alpha_j += S.cfull[j];
+            if (pass == 1 && tid == 0) {
+                double c2 = 0.0;
+                for (int i = 0; i <= j; ++i) c2 = fma(S.cfull[i], S.cfull[i], c2);
+                S.red[kWarps] = sqrt(fmax(S.cfull[j + 1] - c2, 0.0));
+            }
             __syncthreads();
         }
-
-        // ---- beta_j = ||w||
-        loc = 0.0;
-        for (int rr = tid; rr < nr; rr += kThreads) loc += S.wloc[rr] * S.wloc[rr];
-        {
-            const double s = block_sum(loc, S.red);
-            if (tid == 0) part[pb][0] = s;
-            cluster_allreduce(cl, part[pb], S.cfull, 1, cs);
-            pb ^= 1;
-        }
-        const double beta_j = sqrt(S.cfull[0]);
+        const double beta_j = S.red[kWarps];
         if (tid == 0) {
             S.alpha[j] = alpha_j;
             S.beta[j] = beta_j;
@@ -375,35 +383,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
         const bool breakdown = beta_j <= 1e-12 * tnorm || k == n;
         const bool do_check = breakdown || k == kmax || k >= next_check;
         if (do_check && k >= r) {
-            // Rank 0 finds the r largest Ritz values and their residuals
-            // beta_j |x_i[k-1]| from inverse-iteration eigenvectors x_i of T_k,
-            // then every CTA reads the verdict through DSMEM.
-            if (q == 0) {
-                double gl = DBL_MAX, gu = -DBL_MAX, bmax2 = 1.0;
-                for (int t = 0; t < k; ++t) {
+            // Warp 0 of rank 0 finds the r largest Ritz values (one bisection per
+            // lane) and their residuals beta_j |x_i[k-1]| from inverse-iteration
+            // eigenvectors x_i of T_k; every CTA reads the verdict through DSMEM.
+            if (q == 0 && warp == 0) {
+                double gl = DBL_MAX, gu = -DBL_MAX;
+                for (int t = lane; t < k; t += 32) {
                     const double off = (t > 0 ? S.beta[t - 1] : 0.0) + (t < k - 1 ? S.beta[t] : 0.0);
                     gl = fmin(gl, S.alpha[t] - off);
                     gu = fmax(gu, S.alpha[t] + off);
-                    if (t < k - 1) bmax2 = fmax(bmax2, S.beta2[t]);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+                    gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
                 }
                 const double pad = 2.0 * DBL_EPSILON * fmax(fabs(gl), fabs(gu)) * k + DBL_MIN;
                 gl -= pad;
                 gu += pad;
-                const double pivmin = 1e-290 * bmax2;
-                for (int i = warp; i < r; i += kWarps) {
-                    const double th = kth_largest(S.alpha, S.beta2, k, i, gl, gu, pivmin);
-                    if (lane == 0) S.theta[i] = th;
-                }
-                __syncthreads();
-                if (tid < r) {
-                    double* iv = S.inv + (size_t)tid * 4 * L;
+                if (lane < r) {
+                    // warm bracket from the previous check (Ritz values of T_k
+                    // interlace those of T_{k'} for k' < k), checked by Sturm counts
+                    double lo = gl, hi = gu;
+                    if (have_vectors) {
+                        const int target = k - 1 - lane;
+                        const double t0 = S.theta[lane];
+                        const double t1 = t0 + 4.0 * S.resid[lane] + 64.0 * DBL_EPSILON * fabs(t0);
+                        if (t0 > gl && sturm_count(S.alpha, S.beta2, k, t0) <= target) lo = t0;
+                        if (t1 < gu && t1 > lo && sturm_count(S.alpha, S.beta2, k, t1) > target) hi = t1;
+                    }
+                    const double th = kth_largest(S.alpha, S.beta2, k, lane, lo, hi);
+                    double* iv = S.inv + (size_t)lane * 4 * L;
                     const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-                    tri_inverse_iteration(S.alpha, S.beta, k, S.theta[tid], pert, iv, iv + L,
-                                          iv + 2 * L, iv + 3 * L);
-                    S.resid[tid] = beta_j * fabs(iv[3 * L + k - 1]);
+                    tri_inverse_iteration(S.alpha, S.beta, k, th, pert, iv, iv + L, iv + 2 * L, iv + 3 * L);
+                    S.theta[lane] = th;
+                    S.resid[lane] = beta_j * fabs(iv[3 * L + k - 1]);
                 }
-                __syncthreads();
-                if (tid == 0) {
+                __syncwarp();
+                if (lane == 0) {
                     bool ok = true;
                     double worst = 0.0;
                     const double th0 = fabs(S.theta[0]);
@@ -411,8 +427,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
                         ok = ok && (S.resid[i] <= A.tol * th0 || breakdown);
                         worst = fmax(worst, S.resid[i] / fmax(th0, DBL_MIN));
                     }
-                    s_flag = (ok ? 1 : 0) | (worst < 1e-6 ? 2 : 0);
+                    S.red[kWarps + 1] = worst;
+                    s_flag = ok ? 1 : 0;
                 }
+                __syncwarp();
             }
             cl.sync();
             if (q != 0) {
@@ -420,15 +438,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
                     S.theta[tid] = cl.map_shared_rank(S.theta, 0)[tid];
                     S.resid[tid] = cl.map_shared_rank(S.resid, 0)[tid];
                 }
-                if (tid == 0) s_flag = *cl.map_shared_rank(&s_flag, 0);
+                if (tid == 0) {
+                    s_flag = *cl.map_shared_rank(&s_flag, 0);
+                    S.red[kWarps + 1] = cl.map_shared_rank(S.red, 0)[kWarps + 1];
+                }
             }
             __syncthreads();
             have_vectors = true;
-            next_check = k + ((s_flag & 2) ? 4 : 8);
             if (s_flag & 1) {
                 converged = true;
                 break;
             }
+            // next check: extrapolate the residual decay seen between checks
+            const double worst = S.red[kWarps + 1];
+            int gap = 8;
+            if (prev_worst > 0.0 && worst > 0.0 && worst < prev_worst) {
+                const double rate = (log(prev_worst) - log(worst)) / (double)(k - prev_k);
+                const double need = (log(worst) - log(A.tol)) / rate;
+                gap = (int)fmin(16.0, fmax(2.0, ceil(need) + 1.0));
+            } else if (worst < 1e-6) {
+                gap = 4;
+            }
+            prev_worst = worst;
+            prev_k = k;
+            next_check = k + gap;
         }
         if (breakdown) break;  // k < r: fewer Ritz values than wanted
 
@@ -529,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
         }
     }
     cl.sync();
-    __shared__ double flip[kMaxR];
+    double* flip = S.sgn + 3 * kMaxR;  // kMaxR slots after the (|max|, row, value) triples
     if (tid < r) {
         double best = -1.0, bestv = 0.0, brow = 1e300;
         for (int qq = 0; qq < cs; ++qq) {
@@ -557,6 +590,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
         }
 }
 
+// Persistent batched solver: each cluster takes parts from an atomic queue in
+// the host's order (largest first), so uneven part sizes balance across the
+// clusters that fit on the GPU at once.
+__global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks();
+    const int q = (int)cl.block_rank();
+    extern __shared__ __align__(16) double smraw[];
+    __shared__ int s_flag, s_next;
+    for (;;) {
+        if (q == 0 && threadIdx.x == 0) s_next = atomicAdd(A.counter, 1);
+        cl.sync();
+        const int next = q == 0 ? s_next : *cl.map_shared_rank(&s_next, 0);
+        cl.sync();  // every CTA has read the index before rank 0 takes another
+        if (next >= A.p) break;
+        solve_problem(A, A.order[next], cl, cs, q, smraw, s_flag);
+    }
+}
+
 }  // namespace
 
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
@@ -578,13 +630,19 @@ cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
+    cudaLaunchAttribute attr0[1];
+    attr0[0].id = cudaLaunchAttributeClusterDimension;
+    attr0[0].val.clusterDim.x = cs;
+    attr0[0].val.clusterDim.y = 1;
+    attr0[0].val.clusterDim.z = 1;
+    cfg.attrs = attr0;
     cfg.numAttrs = 1;
+    int resident = 0;
+    e = cudaOccupancyMaxActiveClusters(&resident, k_lanczos, &cfg);
+    if (e != cudaSuccess) return e;
+    if (resident < 1) return cudaErrorInvalidConfiguration;
+    const int clusters = resident < a.p ? resident : a.p;
+    cfg.gridDim = dim3((unsigned)(clusters * cs));
     note_launch(1);
     return cudaLaunchKernelEx(&cfg, k_lanczos, a);
 }
