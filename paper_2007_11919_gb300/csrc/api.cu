@@ -200,7 +200,10 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
                                  B.q, B.rp, o.st));
     }
     tmark(1, o.st);
-    CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, o.st));
+    // FP64 precision keeps an IEEE FP64 product; the other precisions, whose Q
+    // carries FP32-level distance rounding anyway, use the double-FP32 product.
+    const int q_df = o.prec != MDS_PREC_F64;
+    CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, q_df, o.st));
     LanczosArgs a;
     a.desc = B.d_desc;
     a.p = B.p;
@@ -212,6 +215,7 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.steps = B.steps;
     a.scratch = B.scr;
     a.order = B.d_order;
+    a.q_df = q_df;
     a.counter = B.counter;
     a.r = B.r;
     a.mmax = B.mmax;
@@ -492,7 +496,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     // classical MDS of the landmarks (first subset of Section 3.1)
     if ((s = run_eig_batch(W.B, Yl, dtl, d, nrml, nullptr, landmark_idx, f64, o))) return s;
     // Gower operator, landmark rows, projection of every row, landmark rows <- X_1
-    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, l, r,
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, o.prec != MDS_PREC_F64, l, r,
                            f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
                            f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
                            var, o.st));

@@ -111,9 +111,11 @@ cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nr
 cudaError_t launch_load_dist(const double* D2, const ProbDesc* desc, double* qarena,
                              double* rparena, int n, int tiles, cudaStream_t st);
 
-// Double centering in place: Q = -1/2 (Delta - m 1^T - 1 m^T + g) per problem.
+// Double centering in place: Q = -1/2 (Delta - m 1^T - 1 m^T + g) per problem,
+// computed in FP64; stored as FP64, or (q_df) as the float pair
+// (hi = fl32(q), lo = fl32(q - hi)) in the same 8 bytes.
 cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double* qarena,
-                                  const double* rparena, double* rmarena, double* grand,
+                                  const double* rparena, double* rmarena, double* grand, int q_df,
                                   cudaStream_t st);
 
 struct LanczosArgs {
@@ -127,6 +129,7 @@ struct LanczosArgs {
     int* steps;         // p
     double* scratch;    // p x lanczos_scratch_per_problem(mmax, r) doubles
     const int* order;   // p problem indices, the order in which clusters take them
+    int q_df;           // Q stored as double-FP32 (hi, lo) float pairs, product in double-FP32
     int* counter;       // queue head, zero before the launch
     int r;
     int mmax;
@@ -147,8 +150,9 @@ constexpr size_t kMaxSmem = 220 * 1024;
 // W and X1 are written in double (w64/x1_64) and float (w32/x1_32) when the
 // pointers are not null.
 cudaError_t launch_interp_model(const double* V, const double* lam, const double* Qdiag_src,
-                                int ldq, int l, int r, double* w64, float* w32, double* x1_64,
-                                float* x1_32, double* bias, double* var_out, cudaStream_t st);
+                                int ldq, int q_df, int l, int r, double* w64, float* w32,
+                                double* x1_64, float* x1_32, double* bias, double* var_out,
+                                cudaStream_t st);
 
 // Gather rows Y[idx[i]] into a dense l x d matrix of the accumulation type.
 // For dt == kDtBF16, Y is the split planes of an ny-row matrix.

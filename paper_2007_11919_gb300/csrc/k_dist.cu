@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(256) k_rowmean(const ProbDesc* __restrict__ de
     }
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(256) k_center(const ProbDesc* __restrict__ desc,
                                                 double* __restrict__ qarena,
                                                 const double* __restrict__ rmarena,
@@ -195,7 +196,15 @@ __global__ void __launch_bounds__(256) k_center(const ProbDesc* __restrict__ des
     const double g = grand[blockIdx.y];
     const double ma = rm[a];
     double* Q = qarena + P.q_off + (int64_t)a * P.ldq;
-    for (int b = threadIdx.x; b < P.n; b += 256) Q[b] = -0.5 * (Q[b] - ma - rm[b] + g);
+    for (int b = threadIdx.x; b < P.n; b += 256) {
+        const double qv = -0.5 * (Q[b] - ma - rm[b] + g);
+        if (DF) {
+            const float h = (float)qv;
+            reinterpret_cast<float2*>(Q)[b] = make_float2(h, (float)(qv - (double)h));
+        } else {
+            Q[b] = qv;
+        }
+    }
 }
 
 __global__ void k_check_idx(const int64_t* __restrict__ idx, int64_t count, int64_t ny,
@@ -301,11 +310,12 @@ cudaError_t launch_load_dist(const double* D2, const ProbDesc* desc, double* qar
 }
 
 cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double* qarena,
-                                  const double* rparena, double* rmarena, double* grand,
+                                  const double* rparena, double* rmarena, double* grand, int q_df,
                                   cudaStream_t st) {
     if (p <= 0) return cudaSuccess;
     k_rowmean<<<p, 256, 0, st>>>(desc, rparena, rmarena, grand);
-    k_center<<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
+    if (q_df) k_center<true><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
+    else k_center<false><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
     note_launch(2);
     return cudaGetLastError();
 }

@@ -252,6 +252,74 @@ __device__ __forceinline__ void matvec_rows(const double* __restrict__ Q, int ld
 }
 
 // part[i] = sum over this CTA's rows of B[i][row] * w[row], i <= j (warp per i).
+// Double-FP32 arithmetic (Dekker 1971; Knuth's TwoSum): a value is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits).  The
+// products run on the FP32 pipe, whose rate on GB300 is ~57x the FP64 rate.
+// __fmul_rn / __fadd_rn / __fsub_rn keep the compiler from contracting the
+// error-free transforms into FMAs.
+__device__ __forceinline__ void df_madd(float& sh, float& sl, float qh, float ql, float vh,
+                                        float vl) {
+    const float p = __fmul_rn(qh, vh);
+    float e = fmaf(qh, vh, -p);          // exact rounding error of qh * vh
+    e = fmaf(qh, vl, e);
+    e = fmaf(ql, vh, e);
+    const float s = __fadd_rn(sh, p);    // TwoSum(sh, p) = s + t exactly
+    const float z = __fsub_rn(s, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+    sh = s;
+}
+
+__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
+    const float s = __fadd_rn(sh, oh);
+    const float z = __fsub_rn(s, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(oh, z));
+    sl = __fadd_rn(sl, __fadd_rn(t, ol));
+    sh = s;
+}
+
+// w[i] = Q[row i, :] . v with Q stored as (hi, lo) float pairs and v as
+// (hi, lo) pairs in shared memory; four rows per warp, two elements per
+// 16-byte load.  The warp reduction stays in double-FP32.
+__device__ __forceinline__ void matvec_rows_df(const float2* __restrict__ Q, int ldq, int n,
+                                               int r0, int nr, const float2* v, double* w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int neven = n & ~1;
+    for (int i = 4 * warp; i < nr; i += 4 * kWarps) {
+        const float2* q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = Q + (int64_t)(r0 + min(i + u, nr - 1)) * ldq;
+        float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int kk = 2 * lane; kk < neven; kk += 64) {
+            const float4 vv = *reinterpret_cast<const float4*>(v + kk);
+            float4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(q[u] + kk);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                df_madd(sh[u], sl[u], x[u].x, x[u].y, vv.x, vv.y);
+                df_madd(sh[u], sl[u], x[u].z, x[u].w, vv.z, vv.w);
+            }
+        }
+        if ((n & 1) && lane == 0) {
+            const float2 vv = v[n - 1];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) df_madd(sh[u], sl[u], q[u][n - 1].x, q[u][n - 1].y, vv.x, vv.y);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh[u], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl[u], o);
+                df_add(sh[u], sl[u], oh, ol);
+            }
+            if (lane == 0 && i + u < nr) w[i + u] = (double)sh[u] + (double)sl[u];
+        }
+    }
+}
+
 // B is written by this kernel (new Lanczos vectors), so it must never be read
 // through the non-coherent read-only path: no __restrict__ on it.
 // With with_norm, part[j+1] also receives the partial sum of w[row]^2.
@@ -296,7 +364,9 @@ __device__ __forceinline__ void cgs_update(const double* B, int ldq, int r0, int
     }
 }
 
-// One eigenproblem (part pj) solved by the calling cluster.
+// One eigenproblem (part pj) solved by the calling cluster.  DF: Q is stored
+// as double-FP32 pairs and the matrix-vector product runs in double-FP32.
+template <bool DF>
 __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q,
                               double* smraw, int& s_flag) {
     const ProbDesc P = A.desc[pj];
@@ -345,12 +415,22 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         cl.sync();
         for (int i = tid; i < n; i += kThreads) {
             const int src = i / R;
-            S.vfull[i] = cl.map_shared_rank(S.vloc, src)[i - src * R];
+            const double v = cl.map_shared_rank(S.vloc, src)[i - src * R];
+            if (DF) {
+                const float h = (float)v;
+                reinterpret_cast<float2*>(S.vfull)[i] = make_float2(h, (float)(v - (double)h));
+            } else {
+                S.vfull[i] = v;
+            }
         }
         __syncthreads();
 
         // ---- w = Q v_j on this CTA's rows
-        matvec_rows(Q, ldq, n, r0, nr, S.vfull, S.wloc);
+        if (DF)
+            matvec_rows_df(reinterpret_cast<const float2*>(Q), ldq, n, r0, nr,
+                           reinterpret_cast<const float2*>(S.vfull), S.wloc);
+        else
+            matvec_rows(Q, ldq, n, r0, nr, S.vfull, S.wloc);
         __syncthreads();
 
         // ---- two passes of classical Gram-Schmidt against v_0..v_j; the
@@ -593,6 +673,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
 // Persistent batched solver: each cluster takes parts from an atomic queue in
 // the host's order (largest first), so uneven part sizes balance across the
 // clusters that fit on the GPU at once.
+template <bool DF>
 __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks();
@@ -605,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
         const int next = q == 0 ? s_next : *cl.map_shared_rank(&s_next, 0);
         cl.sync();  // every CTA has read the index before rank 0 takes another
         if (next >= A.p) break;
-        solve_problem(A, A.order[next], cl, cs, q, smraw, s_flag);
+        solve_problem<DF>(A, A.order[next], cl, cs, q, smraw, s_flag);
     }
 }
 
@@ -615,14 +696,13 @@ size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
     return smem_doubles(max_n, cs, mmax, r) * sizeof(double) + kMaxR * sizeof(double);
 }
 
-cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
-    if (a.p <= 0) return cudaSuccess;
-    const int cs = cluster < 1 ? 1 : (cluster > 16 ? 16 : cluster);
+template <bool DF>
+static cudaError_t launch_lanczos_t(const LanczosArgs& a, int cs, cudaStream_t st) {
     const size_t smem = smem_doubles(a.max_n, cs, a.mmax, a.r) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_lanczos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_lanczos<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (cs > 8) {
-        e = cudaFuncSetAttribute(k_lanczos, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_lanczos<DF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -630,21 +710,27 @@ cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr0[1];
-    attr0[0].id = cudaLaunchAttributeClusterDimension;
-    attr0[0].val.clusterDim.x = cs;
-    attr0[0].val.clusterDim.y = 1;
-    attr0[0].val.clusterDim.z = 1;
-    cfg.attrs = attr0;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
     cfg.numAttrs = 1;
     int resident = 0;
-    e = cudaOccupancyMaxActiveClusters(&resident, k_lanczos, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&resident, k_lanczos<DF>, &cfg);
     if (e != cudaSuccess) return e;
     if (resident < 1) return cudaErrorInvalidConfiguration;
     const int clusters = resident < a.p ? resident : a.p;
     cfg.gridDim = dim3((unsigned)(clusters * cs));
     note_launch(1);
-    return cudaLaunchKernelEx(&cfg, k_lanczos, a);
+    return cudaLaunchKernelEx(&cfg, k_lanczos<DF>, a);
+}
+
+cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
+    if (a.p <= 0) return cudaSuccess;
+    const int cs = cluster < 1 ? 1 : (cluster > 16 ? 16 : cluster);
+    return a.q_df ? launch_lanczos_t<true>(a, cs, st) : launch_lanczos_t<false>(a, cs, st);
 }
 
 }  // namespace gbmds
