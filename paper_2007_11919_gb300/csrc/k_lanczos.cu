@@ -133,18 +133,36 @@ __device__ int sturm_count(const double* al, const double* b2, int k, double x) 
     return c;
 }
 
-// The i-th largest eigenvalue of T by bisection on [lo, hi] (one thread),
-// which must satisfy count(lo) <= k-1-i < count(hi).
+// The i-th largest eigenvalue of T on [lo, hi] (count(lo) <= k-1-i < count(hi))
+// by 32-way multisection: each lane of the calling warp counts at its own probe,
+// so every FP64 warp instruction (which occupies the SMSP's FP64 unit for the
+// whole warp whatever the mask) does 32 useful Sturm steps.  ~11 rounds.
 __device__ double kth_largest(const double* al, const double* b2, int k, int i, double lo, double hi) {
+    const int lane = threadIdx.x & 31;
     const int target = k - 1 - i;
-    for (int it = 0; it < 80; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi)) break;
-        if (sturm_count(al, b2, k, mid) > target) hi = mid;
-        else lo = mid;
+    for (int round = 0; round < 16; ++round) {
+        const double step = (hi - lo) * (1.0 / 33.0);
+        const double x = fmin(fma((double)(lane + 1), step, lo), hi);
+        const unsigned ball = __ballot_sync(0xffffffffu, sturm_count(al, b2, k, x) > target);
+        const int first = ball ? __ffs(ball) - 1 : 32;
+        const double xf = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
+        const double xp = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+        if (first < 32) hi = xf;
+        if (first > 0) lo = xp;
         if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) break;
     }
     return 0.5 * (lo + hi);
+}
+
+// 1/x by Newton-Raphson iteration y <- y (2 - x y) from the FP32 reciprocal:
+// 24 -> 48 -> 96 correct bits (limited by FP64), in four FP64 instructions.
+__device__ __forceinline__ double rcp_newton(double x) {
+    const float xf = (float)x;
+    if (!(fabsf(xf) > 1e-30f && fabsf(xf) < 1e30f)) return 1.0 / x;
+    double y = (double)__frcp_rn(xf);
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    return y;
 }
 
 // Inverse iteration for the eigenvector of T for eigenvalue th (unit 2-norm),
@@ -167,7 +185,7 @@ __device__ void tri_inverse_iteration(const double* al, const double* be, int k,
             const double yl = x[t + 1];
             if (fabs(w0) >= fabs(l0)) {                        // pivot on the working row
                 if (w0 == 0.0) w0 = pert;
-                const double inv = 1.0 / w0;
+                const double inv = rcp_newton(w0);
                 const double f = l0 * inv;
                 u0i[t] = inv;
                 u1[t] = w1;
@@ -177,7 +195,7 @@ __device__ void tri_inverse_iteration(const double* al, const double* be, int k,
                 w1 = l2;
                 yw = yl - f * yw;
             } else {                                           // pivot on row t+1
-                const double inv = 1.0 / l0;
+                const double inv = rcp_newton(l0);
                 const double f = w0 * inv;
                 u0i[t] = inv;
                 u1[t] = l1;
@@ -189,7 +207,7 @@ __device__ void tri_inverse_iteration(const double* al, const double* be, int k,
             }
         }
         if (w0 == 0.0) w0 = pert;
-        u0i[k - 1] = 1.0 / w0;
+        u0i[k - 1] = rcp_newton(w0);
         x[k - 1] = yw * u0i[k - 1];
         if (k > 1) x[k - 2] = (x[k - 2] - u1[k - 2] * x[k - 1]) * u0i[k - 2];
         for (int t = k - 3; t >= 0; --t) x[t] = (x[t] - u1[t] * x[t + 1] - u2[t] * x[t + 2]) * u0i[t];
@@ -463,10 +481,16 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         const bool breakdown = beta_j <= 1e-12 * tnorm || k == n;
         const bool do_check = breakdown || k == kmax || k >= next_check;
         if (do_check && k >= r) {
-            // Warp 0 of rank 0 finds the r largest Ritz values (one bisection per
-            // lane) and their residuals beta_j |x_i[k-1]| from inverse-iteration
-            // eigenvectors x_i of T_k; every CTA reads the verdict through DSMEM.
-            if (q == 0 && warp == 0) {
+            // Ritz values and residuals.  Eigenvalue i belongs to CTA i % cs and,
+            // there, to warp m % 4, lane m / 4 (m = i / cs): every FP64 warp
+            // instruction occupies an SMSP's FP64 unit for tens of cycles, so the
+            // r bisections run on as many SMSPs of the cluster as possible.  Each
+            // owner finds theta_i (bisection on Sturm counts, warm-bracketed by the
+            // previous check), the eigenvector x_i of T_k (inverse iteration) and
+            // the residual beta_j |x_i[k-1]|; all CTAs then read every theta and
+            // residual through DSMEM and take the same decision.
+            const int mine = (r - q + cs - 1) / cs;  // eigenvalues owned by this CTA
+            if (warp < mine) {
                 double gl = DBL_MAX, gu = -DBL_MAX;
                 for (int t = lane; t < k; t += 32) {
                     const double off = (t > 0 ? S.beta[t - 1] : 0.0) + (t < k - 1 ? S.beta[t] : 0.0);
@@ -480,50 +504,52 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const double pad = 2.0 * DBL_EPSILON * fmax(fabs(gl), fabs(gu)) * k + DBL_MIN;
                 gl -= pad;
                 gu += pad;
-                if (lane < r) {
-                    // warm bracket from the previous check (Ritz values of T_k
-                    // interlace those of T_{k'} for k' < k), checked by Sturm counts
+                const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+                for (int m = warp; m < mine; m += kWarps) {   // one warp per eigenvalue
+                    const int i = q + cs * m;
                     double lo = gl, hi = gu;
                     if (have_vectors) {
-                        const int target = k - 1 - lane;
-                        const double t0 = S.theta[lane];
-                        const double t1 = t0 + 4.0 * S.resid[lane] + 64.0 * DBL_EPSILON * fabs(t0);
-                        if (t0 > gl && sturm_count(S.alpha, S.beta2, k, t0) <= target) lo = t0;
-                        if (t1 < gu && t1 > lo && sturm_count(S.alpha, S.beta2, k, t1) > target) hi = t1;
+                        // lane 0 tests the lower end, lane 1 the upper end of the warm bracket
+                        const int target = k - 1 - i;
+                        const double t0 = S.theta[i];
+                        const double t1 = t0 + 4.0 * S.resid[i] + 64.0 * DBL_EPSILON * fabs(t0);
+                        const double xt = lane == 0 ? t0 : t1;
+                        const int c = sturm_count(S.alpha, S.beta2, k, xt);
+                        const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
+                        if (t0 > gl && c0 <= target) lo = t0;
+                        if (t1 < gu && t1 > lo && c1 > target) hi = t1;
                     }
-                    const double th = kth_largest(S.alpha, S.beta2, k, lane, lo, hi);
-                    double* iv = S.inv + (size_t)lane * 4 * L;
-                    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-                    tri_inverse_iteration(S.alpha, S.beta, k, th, pert, iv, iv + L, iv + 2 * L, iv + 3 * L);
-                    S.theta[lane] = th;
-                    S.resid[lane] = beta_j * fabs(iv[3 * L + k - 1]);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    bool ok = true;
-                    double worst = 0.0;
-                    const double th0 = fabs(S.theta[0]);
-                    for (int i = 0; i < r; ++i) {
-                        ok = ok && (S.resid[i] <= A.tol * th0 || breakdown);
-                        worst = fmax(worst, S.resid[i] / fmax(th0, DBL_MIN));
+                    const double th = kth_largest(S.alpha, S.beta2, k, i, lo, hi);
+                    if (lane == 0) {
+                        double* iv = S.inv + (size_t)i * 4 * L;
+                        tri_inverse_iteration(S.alpha, S.beta, k, th, pert, iv, iv + L, iv + 2 * L, iv + 3 * L);
+                        S.theta[i] = th;
+                        S.resid[i] = beta_j * fabs(iv[3 * L + k - 1]);
                     }
-                    S.red[kWarps + 1] = worst;
-                    s_flag = ok ? 1 : 0;
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             cl.sync();
-            if (q != 0) {
-                if (tid < r) {
-                    S.theta[tid] = cl.map_shared_rank(S.theta, 0)[tid];
-                    S.resid[tid] = cl.map_shared_rank(S.resid, 0)[tid];
-                }
-                if (tid == 0) {
-                    s_flag = *cl.map_shared_rank(&s_flag, 0);
-                    S.red[kWarps + 1] = cl.map_shared_rank(S.red, 0)[kWarps + 1];
+            for (int i = tid; i < r; i += kThreads) {
+                const int owner = i % cs;
+                if (owner != q) {
+                    S.theta[i] = cl.map_shared_rank(S.theta, owner)[i];
+                    S.resid[i] = cl.map_shared_rank(S.resid, owner)[i];
                 }
             }
             __syncthreads();
+            if (tid == 0) {
+                bool ok = true;
+                double worst = 0.0;
+                const double th0 = fabs(S.theta[0]);
+                for (int i = 0; i < r; ++i) {
+                    ok = ok && (S.resid[i] <= A.tol * th0 || breakdown);
+                    worst = fmax(worst, S.resid[i] / fmax(th0, DBL_MIN));
+                }
+                S.red[kWarps + 1] = worst;
+                s_flag = ok ? 1 : 0;
+            }
+            cl.sync();  // owners keep theta/resid until every CTA has read them
             have_vectors = true;
             if (s_flag & 1) {
                 converged = true;
@@ -562,6 +588,16 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     } else {
         if (!converged) status = kDevNoConv;
         if (!(S.theta[r - 1] > 0.0) || !(S.theta[r - 1] > A.rank_tol * S.theta[0])) status = kDevRank;
+    }
+    if (q == 0 && status != kDevRank) {
+        // rank 0 collects the eigenvectors of T_k computed by the other CTAs
+        for (int e = tid; e < r * k; e += kThreads) {
+            const int i = e / k, t = e % k;
+            if (i % cs != 0)
+                S.inv[(size_t)i * 4 * L + 3 * L + t] =
+                    cl.map_shared_rank(S.inv, i % cs)[(size_t)i * 4 * L + 3 * L + t];
+        }
+        __syncthreads();
     }
     if (q == 0 && status != kDevRank && warp == 0) {
         // modified Gram-Schmidt across the r inverse-iteration vectors (shared memory)
