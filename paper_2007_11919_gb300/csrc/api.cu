@@ -12,8 +12,10 @@ using namespace gbmds;
 
 struct mds_model_s {
     int l, d, r, prec, device;
-    void* L;        // l x d landmark rows (float, or double for MDS_PREC_F64)
-    double* nrm_l;  // l squared norms (of the rows as stored in L)
+    void* L;        // landmark rows: l x d double (F64), l x d float (F32), or BF16
+                    // split planes hi | lo of l x split_ld(d) each (BF16)
+    double* nrm_l;  // l squared norms of the rows as stored in L (F64 / F32 models)
+    float* nrm_lf;  // the same as float (BF16 models)
     void* W;        // l x r Gower operator -1/2 V Lambda^{-1/2}
     double* bias;   // r: 1/2 Lambda^{-1/2} V^T q_1
     void* X1;       // l x r landmark configuration
@@ -28,6 +30,11 @@ void note_launch(int count) { g_launches += count; }
 namespace {
 
 constexpr int kDefaultSteps = 256;
+
+size_t model_L_bytes(int prec, int l, int d) {
+    if (prec == MDS_PREC_BF16) return (size_t)2 * l * split_ld(d) * sizeof(uint16_t);
+    return (size_t)l * d * (prec == MDS_PREC_F64 ? 8 : 4);
+}
 
 // ---- per-thread instrumentation (mds_set_timing / mds_last_stats)
 bool g_timing = false;
@@ -230,10 +237,11 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
 }
 
 // Waits for the stream and folds the device status words into one code.
-int finish(const Batch* B, const int* d_flag, const Opts& o) {
+int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr = nullptr) {
     tmark(4, o.st);
     std::vector<int> hs(B ? B->p : 0), steps(B ? B->p : 0);
-    int flag = 0;
+    int flag = 0, kerr = 0;
+    if (d_kerr) CK(cudaMemcpyAsync(&kerr, d_kerr, sizeof(int), cudaMemcpyDeviceToHost, o.st));
     if (B && B->p) {
         CK(cudaMemcpyAsync(hs.data(), B->status, sizeof(int) * B->p, cudaMemcpyDeviceToHost, o.st));
         CK(cudaMemcpyAsync(steps.data(), B->steps, sizeof(int) * B->p, cudaMemcpyDeviceToHost, o.st));
@@ -259,6 +267,7 @@ int finish(const Batch* B, const int* d_flag, const Opts& o) {
             g_last.stage_ms[i] = ms;
         }
     if (flag) return MDS_ERR_ARG;
+    if (kerr) return kerr;
     int worst = MDS_OK;
     for (int s : hs) {
         if (s == MDS_ERR_RANK) return MDS_ERR_RANK;
@@ -290,6 +299,8 @@ size_t classical_layout(ClassicalWs& W, char* base, int64_t n, int r, int mmax) 
 
 struct InterpWs {
     int* flag;
+    int* kerr;        // device error word of the tensor-core kernel
+    float* nrm_lf;    // BF16 path: landmark norms as float
     double* nrm;
     double* nrm_raw;  // BF16 path: FP32 norms of the unrounded rows (landmark problem)
     void* Yq;
@@ -305,12 +316,14 @@ size_t interp_layout(InterpWs& W, char* base, int64_t n, int d, int l, int r, in
     Arena A{base, 0};
     const size_t es = prec == MDS_PREC_F64 ? 8 : 4;
     W.flag = A.take<int>(1);
+    W.kerr = A.take<int>(1);
+    W.nrm_lf = A.take<float>(l);
     W.nrm = A.take<double>(n);
     W.nrm_raw = prec == MDS_PREC_BF16 ? A.take<double>(n) : nullptr;
     W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * n * split_ld(d)) : nullptr;
     plan_batch(W.B, {l}, {0}, 0, r, mmax, n);
     carve_batch(W.B, A);
-    W.L = A.take<char>((size_t)l * d * es);
+    W.L = A.take<char>(model_L_bytes(prec, l, d));
     W.nrm_l = A.take<double>(l);
     W.W = A.take<char>((size_t)l * r * es);
     W.bias = A.take<double>(r);
@@ -470,6 +483,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
         l > n || l > kMaxEigN || r <= 0 || r > kMaxR || r >= l)
         return MDS_ERR_ARG;
     if (o.prec == MDS_PREC_FP8) return MDS_ERR_UNSUPPORTED;
+    if (o.prec == MDS_PREC_BF16 && !gower_tc_supported(d, r)) return MDS_ERR_UNSUPPORTED;
     InterpWs W;
     const size_t need = interp_layout(W, nullptr, n, d, l, r, o.prec, o.mmax);
     if ((s = check_ws(o, need))) return s;
@@ -477,6 +491,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     begin_call(o.st);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
     CK(launch_check_idx(landmark_idx, l, n, W.flag, o.st));
     const void* Ye;
     int dte;
@@ -500,10 +515,17 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
                            f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
                            f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
                            var, o.st));
-    CK(launch_gather_rows(Ye, dte, n, d, landmark_idx, l, f64, W.L, W.nrm, W.nrm_l, o.st));
-    CK(launch_gower_proj(Ye, dte, n, d, W.nrm, W.L, W.nrm_l, l, W.W, W.bias, r, f64, X, o.st));
+    if (o.prec == MDS_PREC_BF16) {
+        // tensor-core distance tiles fused with the Gower projection
+        CK(launch_gather_split(Ye, n, d, landmark_idx, l, W.L, W.nrm, W.nrm_lf, o.st));
+        CK(launch_gower_tc(Ye, n, d, W.nrm, W.L, W.nrm_lf, l, (const float*)W.W, W.bias, r,
+                           (float*)X, W.kerr, o.st));
+    } else {
+        CK(launch_gather_rows(Ye, dte, n, d, landmark_idx, l, f64, W.L, W.nrm, W.nrm_l, o.st));
+        CK(launch_gower_proj(Ye, dte, n, d, W.nrm, W.L, W.nrm_l, l, W.W, W.bias, r, f64, X, o.st));
+    }
     CK(launch_scatter_rows(W.X1, landmark_idx, l, r, n, f64, X, o.st));
-    s = finish(&W.B, W.flag, o);
+    s = finish(&W.B, W.flag, o, W.kerr);
     if (s != MDS_OK || !out_model) return s;
 
     // device-resident model for mds_embed_new
@@ -515,8 +537,10 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     m->r = r;
     m->prec = o.prec;
     cudaGetDevice(&m->device);
-    bool ok = cudaMalloc(&m->L, (size_t)l * d * es) == cudaSuccess &&
+    const size_t szL = model_L_bytes(o.prec, l, d);
+    bool ok = cudaMalloc(&m->L, szL) == cudaSuccess &&
               cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
+              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * l) == cudaSuccess &&
               cudaMalloc(&m->W, (size_t)l * r * es) == cudaSuccess &&
               cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
               cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
@@ -526,8 +550,9 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
         mds_model_free(m);
         return MDS_ERR_NOMEM;
     }
-    ok = cudaMemcpyAsync(m->L, W.L, (size_t)l * d * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+    ok = cudaMemcpyAsync(m->L, W.L, szL, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->nrm_l, W.nrm_l, sizeof(double) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->W, W.W, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->bias, W.bias, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->X1, W.X1, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
@@ -544,6 +569,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
 size_t mds_embed_new_workspace_size(mds_model m, int64_t rows) {
     if (!m || rows <= 0) return 0;
     Arena A{nullptr, 0};
+    A.take<int>(1);
     A.take<double>(rows);
     if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
     return A.off + 256;
@@ -557,11 +583,13 @@ int mds_embed_new(mds_model m, const void* Ynew, int dt, int64_t rows, const mds
     if (!m || !Ynew || !X || !valid_dt(dt) || rows <= 0) return MDS_ERR_ARG;
     if (o.prec != m->prec) return MDS_ERR_ARG;
     Arena A{nullptr, 0};
+    A.take<int>(1);
     A.take<double>(rows);
     if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
     if ((s = check_ws(o, A.off))) return s;
     A = Arena{o.ws, 0};
     begin_call(o.st);
+    int* kerr = A.take<int>(1);
     double* nrm = A.take<double>(rows);
     void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * rows * split_ld(m->d)) : nullptr;
     const void* Ye;
@@ -571,6 +599,12 @@ int mds_embed_new(mds_model m, const void* Ynew, int dt, int64_t rows, const mds
     tmark(1, o.st);
     tmark(2, o.st);
     tmark(3, o.st);
+    if (m->prec == MDS_PREC_BF16) {
+        CK(cudaMemsetAsync(kerr, 0, sizeof(int), o.st));
+        CK(launch_gower_tc(Ye, rows, m->d, nrm, m->L, m->nrm_lf, m->l, (const float*)m->W, m->bias,
+                           m->r, (float*)X, kerr, o.st));
+        return finish(nullptr, nullptr, o, kerr);
+    }
     CK(launch_gower_proj(Ye, dte, rows, m->d, nrm, m->L, m->nrm_l, m->l, m->W, m->bias, m->r,
                          m->prec == MDS_PREC_F64, X, o.st));
     return finish(nullptr, nullptr, o);
@@ -594,6 +628,7 @@ void mds_model_free(mds_model m) {
     cudaSetDevice(m->device);
     cudaFree(m->L);
     cudaFree(m->nrm_l);
+    cudaFree(m->nrm_lf);
     cudaFree(m->W);
     cudaFree(m->bias);
     cudaFree(m->X1);
@@ -602,15 +637,17 @@ void mds_model_free(mds_model m) {
     delete m;
 }
 
-static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '1'};
+static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '2'};
 
 int mds_model_save(mds_model m, const char* path) {
     if (!m || !path) return MDS_ERR_ARG;
     const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
-    const size_t szL = (size_t)m->l * m->d * es, szW = (size_t)m->l * m->r * es;
+    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = (size_t)m->l * m->r * es;
     std::vector<char> L(szL), W(szW), X1(szW);
     std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
+    std::vector<float> nrmf(m->l);
     if (cudaMemcpy(L.data(), m->L, szL, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nrmf.data(), m->nrm_lf, 4 * m->l, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(W.data(), m->W, szW, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(X1.data(), m->X1, szW, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(nrm.data(), m->nrm_l, 8 * m->l, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -623,7 +660,8 @@ int mds_model_save(mds_model m, const char* path) {
     bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 &&
               fwrite(L.data(), 1, szL, f) == szL && fwrite(nrm.data(), 8, m->l, f) == (size_t)m->l &&
               fwrite(W.data(), 1, szW, f) == szW && fwrite(bias.data(), 8, m->r, f) == (size_t)m->r &&
-              fwrite(X1.data(), 1, szW, f) == szW && fwrite(lam.data(), 8, m->r, f) == (size_t)m->r;
+              fwrite(X1.data(), 1, szW, f) == szW && fwrite(lam.data(), 8, m->r, f) == (size_t)m->r &&
+              fwrite(nrmf.data(), 4, m->l, f) == (size_t)m->l;
     ok = (fclose(f) == 0) && ok;
     return ok ? MDS_OK : MDS_ERR_IO;
 }
@@ -652,18 +690,21 @@ int mds_model_load(const char* path, mds_model* out) {
     m->prec = hdr[3];
     cudaGetDevice(&m->device);
     const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
-    const size_t szL = (size_t)m->l * m->d * es, szW = (size_t)m->l * m->r * es;
+    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = (size_t)m->l * m->r * es;
     std::vector<char> L(szL), W(szW), X1(szW);
     std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
+    std::vector<float> nrmf(m->l);
     bool ok = fread(L.data(), 1, szL, f) == szL && fread(nrm.data(), 8, m->l, f) == (size_t)m->l &&
               fread(W.data(), 1, szW, f) == szW && fread(bias.data(), 8, m->r, f) == (size_t)m->r &&
-              fread(X1.data(), 1, szW, f) == szW && fread(lam.data(), 8, m->r, f) == (size_t)m->r;
+              fread(X1.data(), 1, szW, f) == szW && fread(lam.data(), 8, m->r, f) == (size_t)m->r &&
+              fread(nrmf.data(), 4, m->l, f) == (size_t)m->l;
     fclose(f);
     if (!ok) {
         delete m;
         return MDS_ERR_IO;
     }
     ok = cudaMalloc(&m->L, szL) == cudaSuccess && cudaMalloc((void**)&m->nrm_l, 8 * m->l) == cudaSuccess &&
+         cudaMalloc((void**)&m->nrm_lf, 4 * m->l) == cudaSuccess &&
          cudaMalloc(&m->W, szW) == cudaSuccess && cudaMalloc((void**)&m->bias, 8 * m->r) == cudaSuccess &&
          cudaMalloc(&m->X1, szW) == cudaSuccess && cudaMalloc((void**)&m->lam, 8 * m->r) == cudaSuccess;
     if (!ok) {
@@ -673,6 +714,7 @@ int mds_model_load(const char* path, mds_model* out) {
     }
     ok = cudaMemcpy(m->L, L.data(), szL, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->nrm_l, nrm.data(), 8 * m->l, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->nrm_lf, nrmf.data(), 4 * m->l, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->W, W.data(), szW, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->bias, bias.data(), 8 * m->r, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->X1, X1.data(), szW, cudaMemcpyHostToDevice) == cudaSuccess &&

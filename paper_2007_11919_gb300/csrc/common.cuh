@@ -180,6 +180,18 @@ cudaError_t launch_iota(int64_t* out, int64_t n, cudaStream_t st);
 cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
                               cudaStream_t st);
 
+// Tensor-core Gower projection for BF16 split data (tcgen05 + TMA): X (m x r,
+// float) = A^2 W + b with A^2 from the split planes of Y (m rows) and of the l
+// landmarks.  Requires gower_tc_supported(d, r).  *err receives
+// MDS_ERR_TIMEOUT if a bounded wait gives up.
+bool gower_tc_supported(int d, int r);
+cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
+                            const void* Lsplit, const float* nrm_l, int l, const float* W,
+                            const double* bias, int r, float* X, int* err, cudaStream_t st);
+// Landmark rows of split planes into split planes, norms as float.
+cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int64_t* idx, int l,
+                                void* Lsplit, const double* nrm, float* nrm_l, cudaStream_t st);
+
 // X[idx[i]] = X1[i] (landmark rows of interpolation MDS).
 cudaError_t launch_scatter_rows(const void* X1, const int64_t* idx, int l, int r, int64_t nx,
                                 int out_f64, void* X, cudaStream_t st);

@@ -283,3 +283,24 @@ def test_dc_deterministic(gb):
     a = gb.mds_divide_conquer(Y, dev(part.anchors), part.ptr, dev(part.own), 4, "f32")[0]
     b = gb.mds_divide_conquer(Y, dev(part.anchors), part.ptr, dev(part.own), 4, "f32")[0]
     assert torch.equal(a, b)
+
+
+# ------------------------------------------- tensor-core Gower (BF16 split)
+
+
+@pytest.mark.parametrize("n,d,l,r", [(200, 16, 130, 3), (1000, 100, 256, 10), (777, 64, 129, 16),
+                                     (4000, 128, 1000, 10), (130, 8, 128, 1)])
+def test_bf16_tensor_core_embed(gb, n, d, l, r):
+    """embed_new on the tcgen05 path (ragged tiles and chunks, one and two K
+    atoms, r = 1..16) against Eq. (2) on the same landmark model."""
+    Y = W.gaussian_mixture(n + l, d, 4, 5.0, seed=d + l, dtype=np.float32)
+    idx = np.arange(n, n + l)
+    X, var, model = gb.mds_interpolate(dev(Y), dev(idx), r, "bf16", want_model=True)
+    L = Y[idx].astype(np.float64)
+    D1 = O.sq_dist(L, L)
+    X1, lam, _, _ = O.classical_mds(D1, r)
+    Xo = O.gower_interpolate(X1, lam, D1, O.sq_dist(Y[:n], L))
+    Xe = host(gb.mds_embed_new(model, dev(Y[:n])))
+    assert np.all(np.isfinite(Xe))
+    assert O.aligned_rel_error(Xe, Xo) < TOL["bf16"]
+    assert O.aligned_rel_error(host(X)[:n], Xo) < TOL["bf16"]
