@@ -31,6 +31,12 @@ namespace {
 
 constexpr int kDefaultSteps = 256;
 
+// BF16 models keep W padded to the tensor-core kernel's width.
+size_t model_W_bytes(int prec, int l, int r) {
+    if (prec == MDS_PREC_BF16) return (size_t)l * gower_tc_rp(r) * 4;
+    return (size_t)l * r * (prec == MDS_PREC_F64 ? 8 : 4);
+}
+
 size_t model_L_bytes(int prec, int l, int d) {
     if (prec == MDS_PREC_BF16) return (size_t)2 * l * split_ld(d) * sizeof(uint16_t);
     return (size_t)l * d * (prec == MDS_PREC_F64 ? 8 : 4);
@@ -300,7 +306,8 @@ size_t classical_layout(ClassicalWs& W, char* base, int64_t n, int r, int mmax) 
 struct InterpWs {
     int* flag;
     int* kerr;        // device error word of the tensor-core kernel
-    float* nrm_lf;    // BF16 path: landmark norms as float
+    float* nrm_lf;    // BF16 path: landmark norms as float (zero-padded to 4)
+    float* Wpad;      // BF16 path: W padded to gower_tc_rp(r) columns
     double* nrm;
     double* nrm_raw;  // BF16 path: FP32 norms of the unrounded rows (landmark problem)
     void* Yq;
@@ -317,7 +324,8 @@ size_t interp_layout(InterpWs& W, char* base, int64_t n, int d, int l, int r, in
     const size_t es = prec == MDS_PREC_F64 ? 8 : 4;
     W.flag = A.take<int>(1);
     W.kerr = A.take<int>(1);
-    W.nrm_lf = A.take<float>(l);
+    W.nrm_lf = A.take<float>(round_up(l, 4));
+    W.Wpad = A.take<float>((size_t)l * 16);
     W.nrm = A.take<double>(n);
     W.nrm_raw = prec == MDS_PREC_BF16 ? A.take<double>(n) : nullptr;
     W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * n * split_ld(d)) : nullptr;
@@ -517,9 +525,11 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
                            var, o.st));
     if (o.prec == MDS_PREC_BF16) {
         // tensor-core distance tiles fused with the Gower projection
+        CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * round_up(l, 4), o.st));
         CK(launch_gather_split(Ye, n, d, landmark_idx, l, W.L, W.nrm, W.nrm_lf, o.st));
-        CK(launch_gower_tc(Ye, n, d, W.nrm, W.L, W.nrm_lf, l, (const float*)W.W, W.bias, r,
-                           (float*)X, W.kerr, o.st));
+        CK(launch_pad_w((const float*)W.W, l, r, W.Wpad, o.st));
+        CK(launch_gower_tc(Ye, n, d, W.nrm, W.L, W.nrm_lf, l, W.Wpad, W.bias, r, (float*)X,
+                           W.kerr, o.st));
     } else {
         CK(launch_gather_rows(Ye, dte, n, d, landmark_idx, l, f64, W.L, W.nrm, W.nrm_l, o.st));
         CK(launch_gower_proj(Ye, dte, n, d, W.nrm, W.L, W.nrm_l, l, W.W, W.bias, r, f64, X, o.st));
@@ -538,10 +548,11 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     m->prec = o.prec;
     cudaGetDevice(&m->device);
     const size_t szL = model_L_bytes(o.prec, l, d);
+    const size_t szW = model_W_bytes(o.prec, l, r);
     bool ok = cudaMalloc(&m->L, szL) == cudaSuccess &&
               cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
-              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * l) == cudaSuccess &&
-              cudaMalloc(&m->W, (size_t)l * r * es) == cudaSuccess &&
+              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * round_up(l, 4)) == cudaSuccess &&
+              cudaMalloc(&m->W, szW) == cudaSuccess &&
               cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
               cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
               cudaMalloc((void**)&m->lam, sizeof(double) * r) == cudaSuccess;
@@ -552,8 +563,8 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     }
     ok = cudaMemcpyAsync(m->L, W.L, szL, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->nrm_l, W.nrm_l, sizeof(double) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->W, W.W, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * round_up(l, 4), cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->W, o.prec == MDS_PREC_BF16 ? (void*)W.Wpad : W.W, szW, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->bias, W.bias, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->X1, W.X1, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->lam, W.B.lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
@@ -642,14 +653,15 @@ static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '2'};
 int mds_model_save(mds_model m, const char* path) {
     if (!m || !path) return MDS_ERR_ARG;
     const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
-    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = (size_t)m->l * m->r * es;
-    std::vector<char> L(szL), W(szW), X1(szW);
+    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = model_W_bytes(m->prec, m->l, m->r);
+    const size_t szX = (size_t)m->l * m->r * es, nlf = (size_t)round_up(m->l, 4);
+    std::vector<char> L(szL), W(szW), X1(szX);
     std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
-    std::vector<float> nrmf(m->l);
+    std::vector<float> nrmf(nlf);
     if (cudaMemcpy(L.data(), m->L, szL, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(nrmf.data(), m->nrm_lf, 4 * m->l, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nrmf.data(), m->nrm_lf, 4 * nlf, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(W.data(), m->W, szW, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(X1.data(), m->X1, szW, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(X1.data(), m->X1, szX, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(nrm.data(), m->nrm_l, 8 * m->l, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(bias.data(), m->bias, 8 * m->r, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(lam.data(), m->lam, 8 * m->r, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -660,8 +672,8 @@ int mds_model_save(mds_model m, const char* path) {
     bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 &&
               fwrite(L.data(), 1, szL, f) == szL && fwrite(nrm.data(), 8, m->l, f) == (size_t)m->l &&
               fwrite(W.data(), 1, szW, f) == szW && fwrite(bias.data(), 8, m->r, f) == (size_t)m->r &&
-              fwrite(X1.data(), 1, szW, f) == szW && fwrite(lam.data(), 8, m->r, f) == (size_t)m->r &&
-              fwrite(nrmf.data(), 4, m->l, f) == (size_t)m->l;
+              fwrite(X1.data(), 1, szX, f) == szX && fwrite(lam.data(), 8, m->r, f) == (size_t)m->r &&
+              fwrite(nrmf.data(), 4, nlf, f) == nlf;
     ok = (fclose(f) == 0) && ok;
     return ok ? MDS_OK : MDS_ERR_IO;
 }
@@ -690,23 +702,24 @@ int mds_model_load(const char* path, mds_model* out) {
     m->prec = hdr[3];
     cudaGetDevice(&m->device);
     const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
-    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = (size_t)m->l * m->r * es;
-    std::vector<char> L(szL), W(szW), X1(szW);
+    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = model_W_bytes(m->prec, m->l, m->r);
+    const size_t szX = (size_t)m->l * m->r * es, nlf = (size_t)round_up(m->l, 4);
+    std::vector<char> L(szL), W(szW), X1(szX);
     std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
-    std::vector<float> nrmf(m->l);
+    std::vector<float> nrmf(nlf);
     bool ok = fread(L.data(), 1, szL, f) == szL && fread(nrm.data(), 8, m->l, f) == (size_t)m->l &&
               fread(W.data(), 1, szW, f) == szW && fread(bias.data(), 8, m->r, f) == (size_t)m->r &&
-              fread(X1.data(), 1, szW, f) == szW && fread(lam.data(), 8, m->r, f) == (size_t)m->r &&
-              fread(nrmf.data(), 4, m->l, f) == (size_t)m->l;
+              fread(X1.data(), 1, szX, f) == szX && fread(lam.data(), 8, m->r, f) == (size_t)m->r &&
+              fread(nrmf.data(), 4, nlf, f) == nlf;
     fclose(f);
     if (!ok) {
         delete m;
         return MDS_ERR_IO;
     }
     ok = cudaMalloc(&m->L, szL) == cudaSuccess && cudaMalloc((void**)&m->nrm_l, 8 * m->l) == cudaSuccess &&
-         cudaMalloc((void**)&m->nrm_lf, 4 * m->l) == cudaSuccess &&
+         cudaMalloc((void**)&m->nrm_lf, 4 * nlf) == cudaSuccess &&
          cudaMalloc(&m->W, szW) == cudaSuccess && cudaMalloc((void**)&m->bias, 8 * m->r) == cudaSuccess &&
-         cudaMalloc(&m->X1, szW) == cudaSuccess && cudaMalloc((void**)&m->lam, 8 * m->r) == cudaSuccess;
+         cudaMalloc(&m->X1, szX) == cudaSuccess && cudaMalloc((void**)&m->lam, 8 * m->r) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         mds_model_free(m);
@@ -714,10 +727,10 @@ int mds_model_load(const char* path, mds_model* out) {
     }
     ok = cudaMemcpy(m->L, L.data(), szL, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->nrm_l, nrm.data(), 8 * m->l, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(m->nrm_lf, nrmf.data(), 4 * m->l, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->nrm_lf, nrmf.data(), 4 * nlf, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->W, W.data(), szW, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->bias, bias.data(), 8 * m->r, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(m->X1, X1.data(), szW, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->X1, X1.data(), szX, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(m->lam, lam.data(), 8 * m->r, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         mds_model_free(m);

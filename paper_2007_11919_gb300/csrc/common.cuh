@@ -188,6 +188,10 @@ bool gower_tc_supported(int d, int r);
 cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
                             const void* Lsplit, const float* nrm_l, int l, const float* W,
                             const double* bias, int r, float* X, int* err, cudaStream_t st);
+// Padded width (4, 8, 12 or 16) of W rows for the tensor-core kernel, and the
+// padding of an l x r W into l x RP (zero columns).
+int gower_tc_rp(int r);
+cudaError_t launch_pad_w(const float* W, int l, int r, float* Wp, cudaStream_t st);
 // Landmark rows of split planes into split planes, norms as float.
 cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int64_t* idx, int l,
                                 void* Lsplit, const double* nrm, float* nrm_l, cudaStream_t st);

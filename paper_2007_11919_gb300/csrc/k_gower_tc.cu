@@ -41,6 +41,8 @@ struct TcSmem {
     // operand tiles first (1024-byte aligned for the 128-byte swizzle)
     uint8_t y[kTileBytes];           // [plane hi/lo][atom][128 rows x 128 B]
     uint8_t l[2][kTileBytes];        // landmark chunk ring
+    float w[2][kChunk * kTcMaxR];    // W rows of the chunk (padded width RP)
+    float nl[2][kChunk];             // landmark norms of the chunk
     uint64_t y_full, y_empty;
     uint64_t l_full[2], l_empty[2];
     uint64_t acc_full[2], acc_empty[2];
@@ -110,6 +112,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
     return false;
 }
 
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
     asm volatile(
@@ -174,13 +183,14 @@ struct TcArgs {
     int ksteps;           // MMA K-steps of 16 (ceil(d_pad / 16))
     int r;
     const double* nrm_y;  // m
-    const float* nrm_l;   // l
-    const float* W;       // l x r
+    const float* nrm_l;   // l, zero-padded to a multiple of 4
+    const float* W;       // l x RP (columns r..RP-1 zero)
     const double* bias;   // r
     float* X;             // m x r
     int* err;
 };
 
+template <int RP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_gower_tc(const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                const __grid_constant__ CUtensorMap tm_lhi, const __grid_constant__ CUtensorMap tm_llo,
@@ -235,12 +245,23 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                 for (int c = 0; c < nchunks; ++c, ++gc) {
                     const int s = (int)(gc & 1);
                     const long long use = gc >> 1;
-                    if (use > 0 && !mbar_wait(&S.l_empty[s], (uint32_t)((use - 1) & 1), abort, a.err)) break;
-                    mbar_expect_tx(&S.l_full[s], tile_tx);
+                    // stage s is free when the MMAs of its previous chunk are done
+                    // (l_empty) and the epilogue has read that chunk's W and norms
+                    // (acc_empty of the same use)
+                    if (use > 0 && (!mbar_wait(&S.l_empty[s], (uint32_t)((use - 1) & 1), abort, a.err) ||
+                                    !mbar_wait(&S.acc_empty[s], (uint32_t)((use - 1) & 1), abort, a.err)))
+                        break;
+                    const int j0 = c * kChunk;
+                    const int nc = min(kChunk, a.l - j0);
+                    const uint32_t wbytes = (uint32_t)(nc * RP * 4);
+                    const uint32_t nbytes = (uint32_t)(((nc + 3) & ~3) * 4);
+                    mbar_expect_tx(&S.l_full[s], tile_tx + wbytes + nbytes);
                     for (int at = 0; at < a.natoms; ++at) {
-                        tma_load_2d(S.l[s] + (0 * kMaxAtoms + at) * kPlaneBytes, &tm_lhi, at * kAtomK, c * kChunk, &S.l_full[s]);
-                        tma_load_2d(S.l[s] + (1 * kMaxAtoms + at) * kPlaneBytes, &tm_llo, at * kAtomK, c * kChunk, &S.l_full[s]);
+                        tma_load_2d(S.l[s] + (0 * kMaxAtoms + at) * kPlaneBytes, &tm_lhi, at * kAtomK, j0, &S.l_full[s]);
+                        tma_load_2d(S.l[s] + (1 * kMaxAtoms + at) * kPlaneBytes, &tm_llo, at * kAtomK, j0, &S.l_full[s]);
                     }
+                    bulk_load(S.w[s], a.W + (int64_t)j0 * RP, wbytes, &S.l_full[s]);
+                    bulk_load(S.nl[s], a.nrm_l + j0, nbytes, &S.l_full[s]);
                 }
             }
             // drain: wait (bounded) for the copies this thread issued that may
@@ -290,7 +311,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             mbar_drain(&S.mma_done, 0, a.err);
         }
     } else {
-        // ---------------- epilogue: warps 2-5, one accumulator row per thread
+        // ---------------- epilogue: warps 2-5, one accumulator row per thread.
+        // The chunk's W rows and norms come from shared memory, loaded with the
+        // landmark tiles; the producer refills the stage only after this epilogue
+        // has arrived on acc_empty.
         const int quad = warp & 3;                 // TMEM lane quadrant this warp may read
         const int row = quad * 32 + lane;
         const int r = a.r;
@@ -298,32 +322,50 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
             const int64_t gi = t * kRows + row;
             const float ny = gi < a.m ? (float)a.nrm_y[gi] : 0.f;
-            float x[kTcMaxR];
+            float x[RP];
 #pragma unroll
-            for (int o = 0; o < kTcMaxR; ++o) x[o] = 0.f;
+            for (int o = 0; o < RP; ++o) x[o] = 0.f;
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 const int s = (int)(gc & 1);
                 ok = mbar_wait(&S.acc_full[s], (uint32_t)((gc >> 1) & 1), abort, a.err);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int j0 = c * kChunk;
-                const int nc = min(kChunk, a.l - j0);
+                const int nc = min(kChunk, a.l - c * kChunk);
+                const float* ws = S.w[s];
+                const float* ns = S.nl[s];
 #pragma unroll 1
                 for (int cb = 0; cb < kChunk; cb += 32) {
                     float v[32];
                     tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kChunk + cb), v);
-                    if (cb < nc) {
+                    if (cb + 32 <= nc) {
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
-                            const int j = j0 + cb + e;
-                            if (cb + e < nc) {
-                                float a2 = ny + __ldg(a.nrm_l + j) - 2.f * v[e];
-                                a2 = fmaxf(a2, 0.f);
-                                const float* w = a.W + (int64_t)j * r;
+                            const float a2 = fmaxf(fmaf(-2.f, v[e], ny + ns[cb + e]), 0.f);
+                            const float4* w4 = reinterpret_cast<const float4*>(ws + (cb + e) * RP);
 #pragma unroll
-                                for (int o = 0; o < kTcMaxR; ++o)
-                                    if (o < r) x[o] = fmaf(a2, __ldg(w + o), x[o]);
+                            for (int q4 = 0; q4 < RP / 4; ++q4) {
+                                const float4 w = w4[q4];
+                                x[4 * q4 + 0] = fmaf(a2, w.x, x[4 * q4 + 0]);
+                                x[4 * q4 + 1] = fmaf(a2, w.y, x[4 * q4 + 1]);
+                                x[4 * q4 + 2] = fmaf(a2, w.z, x[4 * q4 + 2]);
+                                x[4 * q4 + 3] = fmaf(a2, w.w, x[4 * q4 + 3]);
+                            }
+                        }
+                    } else if (cb < nc) {
+                        for (int e = 0; e < nc - cb; ++e) {
+                            float ve = v[0];
+#pragma unroll
+                            for (int u = 1; u < 32; ++u) ve = u == e ? v[u] : ve;
+                            const float a2 = fmaxf(fmaf(-2.f, ve, ny + ns[cb + e]), 0.f);
+                            const float4* w4 = reinterpret_cast<const float4*>(ws + (cb + e) * RP);
+#pragma unroll
+                            for (int q4 = 0; q4 < RP / 4; ++q4) {
+                                const float4 w = w4[q4];
+                                x[4 * q4 + 0] = fmaf(a2, w.x, x[4 * q4 + 0]);
+                                x[4 * q4 + 1] = fmaf(a2, w.y, x[4 * q4 + 1]);
+                                x[4 * q4 + 2] = fmaf(a2, w.z, x[4 * q4 + 2]);
+                                x[4 * q4 + 3] = fmaf(a2, w.w, x[4 * q4 + 3]);
                             }
                         }
                     }
@@ -334,7 +376,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             if (!ok) break;
             if (gi < a.m) {
 #pragma unroll
-                for (int o = 0; o < kTcMaxR; ++o)
+                for (int o = 0; o < RP; ++o)
                     if (o < r) a.X[gi * r + o] = x[o] + (float)a.bias[o];
             }
         }
@@ -376,7 +418,21 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int cols_pad) {
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+__global__ void k_pad_w(const float* __restrict__ W, int l, int r, int rp, float* __restrict__ Wp) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= l * rp) return;
+    const int j = e / rp, o = e % rp;
+    Wp[e] = o < r ? W[j * r + o] : 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_pad_w(const float* W, int l, int r, float* Wp, cudaStream_t st) {
+    const int rp = gower_tc_rp(r);
+    k_pad_w<<<(l * rp + 255) / 256, 256, 0, st>>>(W, l, r, rp, Wp);
+    note_launch(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int64_t* idx, int l,
                                 void* Lsplit, const double* nrm, float* nrm_l, cudaStream_t st) {
@@ -388,6 +444,18 @@ cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int
 }
 
 bool gower_tc_supported(int d, int r) { return d >= 1 && split_ld(d) <= kMaxAtoms * kAtomK && r >= 1 && r <= kTcMaxR; }
+
+int gower_tc_rp(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : (r <= 12 ? 12 : 16)); }
+
+template <int RP>
+static cudaError_t launch_rp(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
+                             const CUtensorMap& b1, const TcArgs& a, int grid, size_t smem,
+                             cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_gower_tc<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gower_tc<RP><<<grid, kThreadsTc, smem, st>>>(a0, a1, b0, b1, a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
                             const void* Lsplit, const float* nrm_l, int l, const float* W,
@@ -414,16 +482,18 @@ cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* 
     a.X = X;
     a.err = err;
     const size_t smem = sizeof(TcSmem) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_gower_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = (m + kRows - 1) / kRows;
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    k_gower_tc<<<grid, kThreadsTc, smem, st>>>(m_yhi, m_ylo, m_lhi, m_llo, a);
     note_launch(1);
-    return cudaGetLastError();
+    switch (gower_tc_rp(r)) {
+        case 4: return launch_rp<4>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
+        case 8: return launch_rp<8>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
+        case 12: return launch_rp<12>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
+        default: return launch_rp<16>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
+    }
 }
 
 }  // namespace gbmds
