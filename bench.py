@@ -42,7 +42,12 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic per launch of the dominant kernel from an ncu capture, valid
 # only while the kernel source is unchanged (sha256 of the .cu file).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # small-case captures scaled to a full launch by algorithmic bytes / rows
+    # (profiles/k_lanczos_dc_f32_n100000.md, profiles/k_gower_tc_interp_bf16_n1000000.md)
+    "k_lanczos.cu": {"sha": "13b1ea186f3151ae", "bytes_per_launch": 50.8e9},
+    "k_gower_tc.cu": {"sha": "36af15e74c95328c", "bytes_per_launch": 452e6},
+}
 
 
 def parse():
@@ -333,11 +338,11 @@ def ours(args):
         peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
         pk = peaks.get("bf16_tflops", 1900.0)
         achieved = flops / (kms * 1e-3) / 1e12
-        roof = {"kernel": "k_gower (distance tiles + Gower projection)", "bound": "tensor",
+        roof = {"kernel": "k_gower_tc (tcgen05 distance tiles fused with the Gower projection)", "bound": "tensor",
                 "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1.9 PFLOP/s",
                 "launch_ms": kms, "flops_per_launch": flops}
-        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_proj.cu")
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_gower_tc.cu")
     tr = NCU_TRAFFIC.get(os.path.basename(src))
     roof["traffic"] = tr["bytes_per_launch"] if tr and tr["sha"] == file_sha(src) else None
 
