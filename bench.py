@@ -74,6 +74,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(seed, rank):
+    """Each rank embeds its own independent workload of the same size."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, device=None):
+    """Max of a per-rank float over the default process group (identity
+    when there is none): the job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_per_rank, ms_per_step):
+    """Points embedded by all ranks per second of the slowest rank's step."""
+    return world * n_per_rank / (ms_per_step / 1e3)
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -253,7 +275,7 @@ def ours(args):
     import paper_2007_11919_gb300 as G
     from paper_2007_11919_gb300 import mds as M
 
-    seed = args.seed + 1000 * rank
+    seed = rank_seed(args.seed, rank)
     w, Y, aux = make_workload(args.workload, seed, args.n)
     Yd = torch.from_numpy(Y).to(dev)
     L = M._lib()
@@ -306,13 +328,8 @@ def ours(args):
     if world > 1:
         tdist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * w.n / (ms_per_step / 1e3)
+    ms_per_step = max_over_ranks(sum(step_ms), dev) / args.steps
+    value = job_throughput(world, w.n, ms_per_step)
 
     # ---- dominant kernel roofline (batched Lanczos for D&C; projection for interpolation)
     eig_ms = [s["stage_ms"]["eig"] for s in stats]
@@ -373,11 +390,7 @@ def ours(args):
         _ = var.cpu()
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = w.n / (statistics.mean(e2e_ms) / 1e3)
-    if world > 1:
-        t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_value = world * w.n / (float(t.item()) / 1e3)
+    e2e_value = job_throughput(world, w.n, max_over_ranks(statistics.mean(e2e_ms), dev))
 
     # ---- CPU oracle leg (rank 0, N = 1 only) and the error against it
     cpu = None

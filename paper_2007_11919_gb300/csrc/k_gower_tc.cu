@@ -19,6 +19,7 @@
 // roles; every wait is bounded and reports a timeout through *err instead of
 // hanging.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 
@@ -407,15 +408,33 @@ __global__ void k_gather_split(const __nv_bfloat16* __restrict__ Y, int64_t ny, 
     if (threadIdx.x == 0) nrm_l[i] = (float)nrm[g];
 }
 
+// cuTensorMapEncodeTiled is a driver-API call.  It is looked up through the
+// runtime at first use rather than linked, so libgbmds.so loads on hosts
+// without a GPU driver (where only the argument checks can run).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
 bool make_map(CUtensorMap* map, const void* base, int64_t rows, int cols_pad) {
+    const auto encode = encode_tiled();
+    if (!encode) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols_pad, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols_pad * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kAtomK, (cuuint32_t)kRows};
     const cuuint32_t estr[2] = {1, 1};
-    return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
-                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 __global__ void k_pad_w(const float* __restrict__ W, int l, int r, int rp, float* __restrict__ Wp) {
