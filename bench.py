@@ -10,7 +10,13 @@ batched Lanczos eigen-solve, Procrustes alignment and the aligned scatter).
 Metric: points embedded per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dc|interp]
+                    [--workload dc|interp|serve]
+
+Every line also carries a short serving leg ("serve"): three resident BF16
+models (l, r) = (500, 2), (1000, 5), (2000, 10) over d=100 Gaussian data,
+Poisson arrivals of embed requests of 1-50,000 points (log-uniform) at a
+fixed fraction of the measured capacity, continuous batching in the
+library's server; p50/p99 latency from submit to results in host memory.
 
 Under torchrun every rank runs its own independent problem of the same size
 (weak scaling, no data-path collective); the step time is the max over ranks.
@@ -56,12 +62,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["dc", "interp"], default="dc")
+    ap.add_argument("--workload", choices=["dc", "interp", "serve"], default="dc")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-parts", type=int, default=4, help="parts in the bounded oracle sample")
     ap.add_argument("--cluster", type=int, default=0,
                     help="CTAs per eigenproblem (default: the library's choice; for profiling)")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests per serving run (the serving leg of every line; per step for --workload serve)")
+    ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of measured capacity")
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--n", type=int, default=0,
                     help="points per GPU (default: the workload's full size; smaller sizes are for profiling)")
     return ap.parse_args()
@@ -257,6 +267,75 @@ def reference_arm(args):
           "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
+# --------------------------------------------------------------- serving leg
+
+
+def serve_leg(dev, seed, n_req, warm_req, load, slots):
+    """Embed requests arriving as a Poisson process onto three resident
+    models through the library's continuous-batching server.  Returns the
+    served points/s over the timed requests, their p50/p99 latency, and the
+    capacity the arrival rate was derived from."""
+    import torch
+    from paper_2007_11919_gb300 import mds as M
+
+    w = W.SERVE_BF16
+    base = torch.from_numpy(W.make_data(w, seed, n=max(l for l, _ in W.SERVE_MODELS) * 3)).to(dev)
+    models = []
+    for k, (l, r) in enumerate(W.SERVE_MODELS):
+        idx = torch.from_numpy(W.landmarks(base.shape[0], l, seed + 11 * k)).to(dev)
+        models.append(M.mds_interpolate(base, idx, r, "bf16", want_model=True)[2])
+    total = warm_req + n_req
+    _, sizes = W.serve_requests(total, *W.SERVE_SIZES, rate_per_s=1.0, seed=seed)
+    which = np.random.default_rng(seed).integers(0, len(models), size=total)
+    pool_rows = int(min(sizes.sum(), 400_000))
+    pool = torch.from_numpy(W.make_data(w, seed + 1, n=pool_rows)).pin_memory()
+    starts = np.random.default_rng(seed + 2).integers(0, pool_rows - sizes + 1)
+    outs = torch.empty(int(sizes.sum()) * max(r for _, r in W.SERVE_MODELS), dtype=torch.float32).pin_memory()
+    ooff = np.concatenate([[0], np.cumsum(sizes * np.array([W.SERVE_MODELS[k][1] for k in which]))])
+
+    def req(i):
+        r = W.SERVE_MODELS[which[i]][1]
+        return (int(which[i]), pool[starts[i]:starts[i] + sizes[i]],
+                outs[ooff[i]:ooff[i + 1]].view(int(sizes[i]), r))
+
+    with M.Server(models, slots=slots) as srv:
+        # capacity: every request of the warm-up set submitted at once
+        t0 = time.perf_counter()
+        tk = [srv.submit(*req(i)) for i in range(warm_req)]
+        for t in tk:
+            srv.wait(t)
+        cap = float(sizes[:warm_req].sum()) / (time.perf_counter() - t0)
+        # timed: Poisson arrivals at `load` x capacity
+        rate = load * cap / float(sizes.mean())
+        gaps = np.random.default_rng(seed + 3).exponential(1.0 / rate, size=n_req)
+        due = np.cumsum(gaps)
+        sub, tk = [], []
+        t0 = time.perf_counter()
+        for j in range(n_req):
+            while time.perf_counter() - t0 < due[j]:
+                pass
+            sub.append(time.perf_counter() - t0)
+            tk.append(srv.submit(*req(warm_req + j)))
+        lat = np.array([srv.wait(t)[1] for t in tk])
+        st = srv.stats()
+    done = np.array(sub) + lat / 1e3
+    pts = float(sizes[warm_req:].sum())
+    tw = which[warm_req:]
+    lr = np.array(W.SERVE_MODELS, dtype=np.float64)[tw]            # (l, r) per timed request
+    flops = float(np.sum(sizes[warm_req:] * (2.0 * lr[:, 0] * w.d + 2.0 * lr[:, 0] * lr[:, 1])))
+    d2h = int(np.sum(sizes[warm_req:] * lr[:, 1] * 4))
+    for m in models:
+        m.free()
+    return {"points_per_s": pts / float(done.max()), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "load": load, "capacity_points_per_s": cap,
+            "requests": n_req, "points": int(pts), "slots": slots, "batches": int(st["batches"]),
+            "max_in_flight": int(st["max_in_flight"]), "wall_s": float(done.max()),
+            "h2d_bytes": int(pts * w.d * 4), "d2h_bytes": d2h, "tensor_flops": flops,
+            "batches_timed_and_warm": int(st["batches"]),
+            "models": [f"l{l}_r{r}_bf16" for l, r in W.SERVE_MODELS],
+            "timing": "host clock, submit to results in pinned host memory"}
+
+
 # --------------------------------------------------------------- our arm
 
 
@@ -276,6 +355,8 @@ def ours(args):
     from paper_2007_11919_gb300 import mds as M
 
     seed = rank_seed(args.seed, rank)
+    if args.workload == "serve":
+        return serve_main(args, rank, world, dev)
     w, Y, aux = make_workload(args.workload, seed, args.n)
     Yd = torch.from_numpy(Y).to(dev)
     L = M._lib()
@@ -406,6 +487,8 @@ def ours(args):
         err = O.aligned_rel_error(Xh.double().numpy()[rows], Xo)
         cpu = {"value": npts / dt, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle", "sample": sample}
 
+    serve = serve_leg(dev, seed, args.serve_requests, 50, args.serve_load, args.serve_slots) if rank == 0 else None
+
     if rank == 0:
         peaks_note = None
         emit({"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -424,9 +507,64 @@ def ours(args):
               "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)},
               "gpu_launches": int(sum(s["launches"] for s in stats)),
-              "clocks": clk, "gpu": torch.cuda.get_device_name(dev), "note": peaks_note})
+              "clocks": clk, "gpu": torch.cuda.get_device_name(dev), "note": peaks_note, "serve": serve})
     if world > 1:
         tdist.destroy_process_group()
+
+
+def serve_main(args, rank, world, dev):
+    """--workload serve: the serving run is the measurement; one step is a
+    window of --serve-requests arrivals."""
+    import torch
+    import torch.distributed as tdist
+
+    seed = rank_seed(args.seed, rank)
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        tdist.barrier()
+    clocks.start()
+    res = serve_leg(dev, seed, args.steps * args.serve_requests, max(args.warmup, 1) * 50, args.serve_load,
+                    args.serve_slots)
+    clk = clocks.stop()
+    wall = max_over_ranks(res["wall_s"], dev)
+    pts = -max_over_ranks(-res["points"], dev) if world > 1 else res["points"]
+    value = world * pts / wall
+    w = W.SERVE_BF16
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        base = W.make_data(w, seed, n=6000)
+        l, r = W.SERVE_MODELS[-1]
+        idx = W.landmarks(len(base), l, seed + 22)
+        t0 = time.perf_counter()
+        _, _, ex = O.interpolation_mds(base[idx], np.arange(l), r)
+        ex["L"] = base[idx].astype(np.float64)
+        Ynew = W.make_data(w, seed + 5, n=10_000)
+        O.embed_new(ex, Ynew)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 10_000 / dt, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"landmark MDS (l={l}, r={r}) + Eq. (2) for 10,000 new points"}
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    pk = peaks.get("bf16_tflops", 1900.0)
+    achieved = res["tensor_flops"] / res["wall_s"] / 1e12
+    roof = {"kernel": "k_gower_tc (served batches)", "bound": "tensor", "achieved": achieved, "peak": pk,
+            "unit": "TFLOP/s", "frac": achieved / pk,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)" if peaks else "fallback 1.9 PFLOP/s",
+            "traffic": None,
+            "note": "algorithmic flops of the served points over the serving wall time at the offered load "
+                    "(idle gaps and copies included), a lower bound on the kernel's own rate"}
+    if rank == 0:
+        emit({"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+              "config": {"workload": w.name, "d": w.d, "models": res["models"],
+                         "request_sizes": "log-uniform 1-50,000", "arrivals": "Poisson",
+                         "load": args.serve_load, "slots": args.serve_slots,
+                         "l2": "not flushed: requests stream from host memory", "parallelism": f"replicas{world}"},
+              "serve": res, "roofline": roof, "cpu_baseline": cpu,
+              "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": res["h2d_bytes"] // args.steps,
+                      "d2h_bytes_per_step": res["d2h_bytes"] // args.steps},
+              "gpu_launches": 2 * res["batches"], "clocks": clk, "gpu": torch.cuda.get_device_name(dev)})
 
 
 def main():

@@ -183,6 +183,66 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
                        const mds_opts* opts, void* X, double* var);
 
 /* ------------------------------------------------------------------ */
+/* Serving: continuous batching of embed requests (Section 3.1, Eq. (2),
+ * applied to points that arrive after the landmark configurations were built;
+ * the paper embeds its new points in fixed blocks and has no request loop).
+ *
+ * A server owns `slots` CUDA streams, each with its own device arena of
+ * slot_bytes bytes, and one host scheduler thread.  Requests name one of the
+ * server's resident models.  Whenever a slot is free the scheduler fills it
+ * with a batch: rows of waiting requests for the model of the oldest waiting
+ * request, in arrival order, as many as the slot's arena holds (staged input
+ * rows, scratch and results); a request too large for one slot is split
+ * across batches.  The batch is copied in, embedded by one launch of the
+ * model's projection kernel and copied out on the slot's stream, so batches
+ * on different slots (copies and kernels) overlap on the device, and requests
+ * that arrive while others are on the GPU join the next free slot.  Every row
+ * is computed from its own input and the model only: a result is bitwise the
+ * same whether its request ran alone or in a mix.
+ *
+ *   models     the resident configurations (mds_interpolate / mds_model_load),
+ *              all on the calling thread's current device; the server keeps
+ *              the handles (the caller frees them after mds_server_destroy).
+ *   slots      concurrent batches, 1..16 (0: 4).
+ *   slot_bytes device bytes per slot (0: 64 MiB); allocated at creation.
+ *   max_batch_rows  cap on rows per batch (0: whatever fits).
+ *   flags      must be 0.
+ * Submit: Y is a HOST pointer to m x d rows of the model's d (dtype dt); X a
+ * HOST pointer to m x r outputs (double for MDS_PREC_F64 models, float
+ * otherwise).  Both must stay valid until mds_server_wait returns for the
+ * ticket; page-locked (cudaHostAlloc / pinned) buffers let copies overlap,
+ * pageable ones serialise the scheduler on each copy.  Submit only queues the
+ * request and returns at once.
+ * Wait: blocks until the request is complete or timeout_s passes (returns
+ * MDS_ERR_TIMEOUT, request still pending; wait again).  On completion *status
+ * is the request's status and *latency_ms the time from submit to the end of
+ * its last batch on the device; the ticket is then released.
+ * Destroy: drains all queued work, then frees the slots. */
+typedef struct mds_server_s* mds_server;
+
+typedef struct {
+    int32_t slots;
+    int32_t flags;
+    size_t slot_bytes;
+    int64_t max_batch_rows;
+} mds_server_opts;
+
+typedef struct {
+    int64_t requests;       /* completed */
+    int64_t rows;           /* rows embedded */
+    int64_t batches;        /* batches launched */
+    int32_t max_in_flight;  /* most slots busy at once */
+    int32_t slots;
+} mds_server_stats;
+
+int mds_server_create(const mds_model* models, int nmodels, const mds_server_opts* opts, mds_server* out);
+int mds_server_submit(mds_server srv, int model, const void* Y, int dt, int64_t m, void* X,
+                      uint64_t* ticket);
+int mds_server_wait(mds_server srv, uint64_t ticket, double timeout_s, int* status, double* latency_ms);
+int mds_server_get_stats(mds_server srv, mds_server_stats* out);
+int mds_server_destroy(mds_server srv);
+
+/* ------------------------------------------------------------------ */
 /* Instrumentation (the paper has no counterpart; used by the benchmark).
  * mds_set_timing(1) makes subsequent calls on the calling host thread record
  * CUDA events on opts->stream between pipeline stages; mds_last_stats then

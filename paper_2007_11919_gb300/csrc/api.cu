@@ -10,18 +10,6 @@
 
 using namespace gbmds;
 
-struct mds_model_s {
-    int l, d, r, prec, device;
-    void* L;        // landmark rows: l x d double (F64), l x d float (F32), or BF16
-                    // split planes hi | lo of l x split_ld(d) each (BF16)
-    double* nrm_l;  // l squared norms of the rows as stored in L (F64 / F32 models)
-    float* nrm_lf;  // the same as float (BF16 models)
-    void* W;        // l x r Gower operator -1/2 V Lambda^{-1/2}
-    double* bias;   // r: 1/2 Lambda^{-1/2} V^T q_1
-    void* X1;       // l x r landmark configuration
-    double* lam;    // r eigenvalues of Q_1
-};
-
 namespace gbmds {
 thread_local int64_t g_launches = 0;
 void note_launch(int count) { g_launches += count; }
@@ -383,6 +371,38 @@ int prep_data(const void* Y, int dt, int64_t n, int d, int prec, double* nrm, vo
 
 }  // namespace
 
+// Queues the embedding of `rows` new points on `st` without waiting: norms
+// (and the BF16 split for BF16 models), then the fused distance + Gower
+// projection kernel.  `ws` holds at least mds_embed_new_workspace_size() - 256
+// bytes, 256-byte aligned; *kerr receives the device status word (zero when
+// the kernel succeeded), which lives at the start of ws.
+int gbmds::embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, char* ws, cudaStream_t st,
+                         void* X, int** kerr_out) {
+    Opts o{};
+    o.prec = m->prec;
+    o.st = st;
+    o.ws = ws;
+    Arena A{ws, 0};
+    int* kerr = A.take<int>(1);
+    double* nrm = A.take<double>(rows);
+    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * rows * split_ld(m->d)) : nullptr;
+    *kerr_out = kerr;
+    CK(cudaMemsetAsync(kerr, 0, sizeof(int), st));
+    const void* Ye;
+    int dte;
+    int s = prep_data(Ynew, dt, rows, m->d, m->prec, nrm, Yq, o, &Ye, &dte);
+    if (s) return s;
+    for (int i = 0; i < 4; ++i) tmark(i, st);   // stage 0 = preparation, stage 4 = projection
+    if (m->prec == MDS_PREC_BF16) {
+        CK(launch_gower_tc(Ye, rows, m->d, nrm, m->L, m->nrm_lf, m->l, (const float*)m->W, m->bias,
+                           m->r, (float*)X, kerr, st));
+        return MDS_OK;
+    }
+    CK(launch_gower_proj(Ye, dte, rows, m->d, nrm, m->L, m->nrm_l, m->l, m->W, m->bias, m->r,
+                         m->prec == MDS_PREC_F64, X, st));
+    return MDS_OK;
+}
+
 // =================================================================== C ABI
 
 extern "C" {
@@ -593,32 +613,11 @@ int mds_embed_new(mds_model m, const void* Ynew, int dt, int64_t rows, const mds
     if (s) return s;
     if (!m || !Ynew || !X || !valid_dt(dt) || rows <= 0) return MDS_ERR_ARG;
     if (o.prec != m->prec) return MDS_ERR_ARG;
-    Arena A{nullptr, 0};
-    A.take<int>(1);
-    A.take<double>(rows);
-    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
-    if ((s = check_ws(o, A.off))) return s;
-    A = Arena{o.ws, 0};
+    if ((s = check_ws(o, mds_embed_new_workspace_size(m, rows) - 256))) return s;
     begin_call(o.st);
-    int* kerr = A.take<int>(1);
-    double* nrm = A.take<double>(rows);
-    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * rows * split_ld(m->d)) : nullptr;
-    const void* Ye;
-    int dte;
-    if ((s = prep_data(Ynew, dt, rows, m->d, m->prec, nrm, Yq, o, &Ye, &dte))) return s;
-    tmark(0, o.st);
-    tmark(1, o.st);
-    tmark(2, o.st);
-    tmark(3, o.st);
-    if (m->prec == MDS_PREC_BF16) {
-        CK(cudaMemsetAsync(kerr, 0, sizeof(int), o.st));
-        CK(launch_gower_tc(Ye, rows, m->d, nrm, m->L, m->nrm_lf, m->l, (const float*)m->W, m->bias,
-                           m->r, (float*)X, kerr, o.st));
-        return finish(nullptr, nullptr, o, kerr);
-    }
-    CK(launch_gower_proj(Ye, dte, rows, m->d, nrm, m->L, m->nrm_l, m->l, m->W, m->bias, m->r,
-                         m->prec == MDS_PREC_F64, X, o.st));
-    return finish(nullptr, nullptr, o);
+    int* kerr = nullptr;
+    if ((s = gbmds::embed_enqueue(m, Ynew, dt, rows, o.ws, o.st, X, &kerr))) return s;
+    return finish(nullptr, nullptr, o, kerr);
 }
 
 int mds_model_info(mds_model m, int* l, int* d, int* r, int* prec, double* lambda) {

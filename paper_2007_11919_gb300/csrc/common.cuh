@@ -7,6 +7,19 @@
 
 #include "../../include/gbmds.h"
 
+// Device-resident landmark configuration behind an mds_model handle.
+struct mds_model_s {
+    int l, d, r, prec, device;
+    void* L;        // landmark rows: l x d double (F64), l x d float (F32), or BF16
+                    // split planes hi | lo of l x split_ld(d) each (BF16)
+    double* nrm_l;  // l squared norms of the rows as stored in L (F64 / F32 models)
+    float* nrm_lf;  // the same as float (BF16 models)
+    void* W;        // l x r Gower operator -1/2 V Lambda^{-1/2}
+    double* bias;   // r: 1/2 Lambda^{-1/2} V^T q_1
+    void* X1;       // l x r landmark configuration
+    double* lam;    // r eigenvalues of Q_1
+};
+
 namespace gbmds {
 
 constexpr int kMaxR = 32;          // largest supported target dimension r
@@ -213,5 +226,9 @@ cudaError_t launch_dc_lambda_bar(const ProbDesc* desc, int p, const double* lam,
 // Classical MDS output X = V Lambda^{1/2} in row order of problem 0.
 cudaError_t launch_classical_out(const double* V, const double* lam, int n, int r, int out_f64,
                                  void* X, double* lam_out, cudaStream_t st);
+
+// Host side (api.cu): queue an embedding against a model without waiting.
+int embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, char* ws, cudaStream_t st, void* X,
+                  int** kerr_out);
 
 }  // namespace gbmds

@@ -283,3 +283,93 @@ def mds_embed_new_static_capacity() -> int:
     L = _lib()
     L.mds_embed_new_static_capacity.restype = _SZ
     return L.mds_embed_new_static_capacity()
+
+
+class MdsServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("flags", ctypes.c_int32), ("slot_bytes", ctypes.c_size_t),
+                ("max_batch_rows", ctypes.c_int64)]
+
+
+class MdsServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("rows", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("max_in_flight", ctypes.c_int32), ("slots", ctypes.c_int32)]
+
+
+def _server_lib():
+    L = _lib()
+    if not getattr(L, "_server_sigs", False):
+        for name, res, args in [
+            ("mds_server_create", _I, [_P, _I, _P, _P]),
+            ("mds_server_submit", _I, [_P, _I, _P, _I, _I64, _P, _P]),
+            ("mds_server_wait", _I, [_P, ctypes.c_uint64, _D, _P, _P]),
+            ("mds_server_get_stats", _I, [_P, _P]),
+            ("mds_server_destroy", _I, [_P]),
+        ]:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        L._server_sigs = True
+    return L
+
+
+class Server:
+    """Continuous-batching embed server over resident models (mds_server_*).
+
+    ``submit`` takes a CPU tensor of rows (pinned memory lets copies overlap)
+    and returns a ticket; ``wait`` returns the CPU result tensor and the
+    request's latency in ms.  Tensors are kept alive until their request is
+    waited for."""
+
+    def __init__(self, models, slots=4, slot_bytes=64 << 20, max_batch_rows=0):
+        L = _server_lib()
+        self.models = list(models)
+        self.info = [m.info() for m in self.models]
+        arr = (ctypes.c_void_p * len(self.models))(*[m.handle.value for m in self.models])
+        o = MdsServerOpts(slots=slots, flags=0, slot_bytes=slot_bytes, max_batch_rows=max_batch_rows)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.models[0].device):
+            _check(L.mds_server_create(arr, len(self.models), ctypes.byref(o), ctypes.byref(h)),
+                   "mds_server_create")
+        self.handle = h
+        self._live = {}
+
+    def submit(self, model: int, Y, out=None) -> int:
+        if not (isinstance(Y, torch.Tensor) and not Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()):
+            raise ValueError("rows must be a contiguous 2-D CPU tensor")
+        if Y.dtype not in DTYPE:
+            raise ValueError(f"unsupported dtype {Y.dtype}")
+        inf = self.info[model]
+        if Y.shape[1] != inf["d"]:
+            raise ValueError(f"model {model} has d={inf['d']}, rows have {Y.shape[1]}")
+        if out is None:
+            out = torch.empty((Y.shape[0], inf["r"]), dtype=_xdtype(inf["prec"]), pin_memory=Y.is_pinned())
+        t = ctypes.c_uint64()
+        _check(_server_lib().mds_server_submit(self.handle, model, _ptr(Y), DTYPE[Y.dtype], Y.shape[0], _ptr(out),
+                                               ctypes.byref(t)), "mds_server_submit")
+        self._live[t.value] = (Y, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = 120.0):
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        _check(_server_lib().mds_server_wait(self.handle, ticket, timeout, ctypes.byref(st), ctypes.byref(lat)),
+               "mds_server_wait")
+        _, out = self._live.pop(ticket)
+        _check(st.value, "mds_server request")
+        return out, lat.value
+
+    def stats(self) -> dict:
+        s = MdsServerStats()
+        _check(_server_lib().mds_server_get_stats(self.handle, ctypes.byref(s)), "mds_server_get_stats")
+        return {k: getattr(s, k) for k, _ in MdsServerStats._fields_}
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _check(_server_lib().mds_server_destroy(self.handle), "mds_server_destroy")
+            self.handle = ctypes.c_void_p(0)
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

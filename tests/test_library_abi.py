@@ -99,3 +99,21 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(M, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         M._lib()
+
+
+def test_server_argument_checks_without_gpu(lib):
+    from paper_2007_11919_gb300.mds import MdsServerOpts, _server_lib
+    L = _server_lib()
+    o = MdsServerOpts(slots=4, flags=0, slot_bytes=0, max_batch_rows=0)
+    h = ctypes.c_void_p()
+    assert L.mds_server_create(None, 1, ctypes.byref(o), ctypes.byref(h)) == 1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.mds_server_create(arr, 1, ctypes.byref(o), ctypes.byref(h)) == 1   # null model
+    bad = MdsServerOpts(slots=99, flags=0, slot_bytes=0, max_batch_rows=0)
+    assert L.mds_server_create(arr, 1, ctypes.byref(bad), ctypes.byref(h)) == 1
+    t = ctypes.c_uint64()
+    p = ctypes.c_void_p(8)
+    assert L.mds_server_submit(None, 0, p, 1, 10, p, ctypes.byref(t)) == 1
+    st = ctypes.c_int()
+    assert L.mds_server_wait(None, 1, 1.0, ctypes.byref(st), None) == 1
+    assert L.mds_server_destroy(None) == 1

@@ -59,3 +59,15 @@ def test_mixture_means():
 def test_serve_requests():
     t, s = W.serve_requests(1000, 1, 50_000, 100.0, 0)
     assert np.all(np.diff(t) > 0) and s.min() >= 1 and s.max() <= 50_000
+
+
+def test_graded_variances_and_serve_sizes():
+    Y = W.gaussian_graded(200_000, 14, seed=0)
+    v = Y.var(axis=0)
+    assert np.allclose(v[:10], 15.0 * 0.85 ** np.arange(10), rtol=0.03)
+    assert np.allclose(v[10:], 1.0, rtol=0.03)
+    t, sizes = W.serve_requests(20_000, *W.SERVE_SIZES, rate_per_s=1000.0, seed=0)
+    assert np.all(np.diff(t) > 0) and sizes.min() >= 1 and sizes.max() <= 50_000
+    # log-uniform sizes: mean (hi - lo) / ln(hi / lo) within sampling error
+    assert abs(sizes.mean() / (50_000 / np.log(50_001)) - 1) < 0.05
+    assert abs(len(t) / t[-1] / 1000.0 - 1) < 0.05

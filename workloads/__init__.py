@@ -68,6 +68,23 @@ def gaussian_mixture(n: int, d: int, k: int, spacing: float, seed: int,
     return out
 
 
+def gaussian_graded(n: int, d: int, seed: int, top: int = 10, var_top: float = 15.0,
+                    decay: float = 0.85, dtype=np.float32) -> np.ndarray:
+    """n x d rows from N(0, diag(s)) with s_k = var_top * decay^k for the first
+    ``top`` coordinates and 1 for the rest: distinct leading variances, so the
+    top-r principal subspace is well separated for every r <= top."""
+    g = _rng(seed, _S_DATA)
+    sd = np.ones(d)
+    k = min(top, d)
+    sd[:k] = np.sqrt(var_top * decay ** np.arange(k))
+    out = np.empty((n, d), dtype=dtype)
+    step = max(1, (1 << 22) // max(d, 1))
+    for i in range(0, n, step):
+        j = min(n, i + step)
+        out[i:j] = g.standard_normal((j - i, d)) * sd
+    return out
+
+
 def image_like(n: int, d: int, seed: int, zero_frac: float = 0.8,
                mean: float = 180.0, sd: float = 60.0) -> np.ndarray:
     """n x d uint8 'pixels': a fraction ``zero_frac`` are 0, the rest are
@@ -198,6 +215,11 @@ DC_F32 = Workload("dc_f32_n100000_d100_parts800-1200_c20_r10", "dc", 100_000, 10
                   c=20, own_lo=800, own_hi=1200)
 INTERP_BF16 = Workload("interp_bf16_n1000000_d100_l1000_r10", "interp", 1_000_000, 100, 10, "bf16",
                        l=1000)
+SERVE_BF16 = Workload("serve_bf16_d100_l500r2_l1000r5_l2000r10_req1-50000", "serve", 200_000, 100, 10,
+                      "bf16", l=2000)
+# Resident models of the serving workload: (landmarks, r).
+SERVE_MODELS = ((500, 2), (1000, 5), (2000, 10))
+SERVE_SIZES = (1, 50_000)
 IMAGE_FP8 = Workload("image_fp8_n814255_d784_l2000_r10", "interp", 814_255, 784, 10, "fp8", l=2000,
                      c=50)
 
@@ -211,6 +233,8 @@ def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
         return gaussian_dominant(n, w.d, 5, seed, dtype=np.float32)
     if w.name == INTERP_BF16.name:
         return gaussian_mixture(n, w.d, 4, 5.0, seed, dtype=np.float32)
+    if w.name == SERVE_BF16.name:
+        return gaussian_graded(n, w.d, seed)
     if w.name == IMAGE_FP8.name:
         return image_like(n, w.d, seed)
     raise KeyError(w.name)
