@@ -338,6 +338,8 @@ class Server:
             raise ValueError("rows must be a contiguous 2-D CPU tensor")
         if Y.dtype not in DTYPE:
             raise ValueError(f"unsupported dtype {Y.dtype}")
+        if not 0 <= model < len(self.info):
+            raise ValueError(f"model index {model} out of range 0..{len(self.info) - 1}")
         inf = self.info[model]
         if Y.shape[1] != inf["d"]:
             raise ValueError(f"model {model} has d={inf['d']}, rows have {Y.shape[1]}")

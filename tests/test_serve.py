@@ -106,7 +106,12 @@ def test_pageable_and_errors(gb, resident):
         assert X.shape == (300, W.SERVE_MODELS[0][1]) and torch.isfinite(X).all()
         with pytest.raises(ValueError):
             srv.submit(0, Y[:, :50].contiguous())
-        with pytest.raises(MdsError):
+        with pytest.raises(ValueError):
             srv.submit(3, Y)
+        import ctypes
+        from paper_2007_11919_gb300.mds import _ptr, _server_lib
+        t = ctypes.c_uint64()
+        out = torch.empty(300, 2)
+        assert _server_lib().mds_server_submit(srv.handle, 3, _ptr(Y), 1, 300, _ptr(out), ctypes.byref(t)) == 1
         with pytest.raises(MdsError):
             srv.wait(123456)
