@@ -19,16 +19,36 @@ namespace {
 
 constexpr int kDefaultSteps = 256;
 
-// BF16 models keep W padded to the tensor-core kernel's width.
-size_t model_W_bytes(int prec, int l, int r) {
+// Model kinds: how the landmark rows are stored and which kernel projects.
+constexpr int kKindRows = 0;               // FP64 / FP32 rows (k_gower) or BF16 split planes (k_gower_tc)
+constexpr int kKindU8Bf16 = 1 + kTckBf16;  // byte rows as exact BF16 (k_gower_tck)
+constexpr int kKindU8Fp8 = 1 + kTckFp8;    // byte rows as exact E4M3 nibble planes (k_gower_tck)
+
+// Kind for a precision and input dtype; -1 when the pair is not built.
+int model_kind(int prec, int dt, int d, int r) {
+    if (prec == MDS_PREC_FP8) return dt == MDS_IN_U8 && gower_tck_supported(d, r) ? kKindU8Fp8 : -1;
+    if (prec == MDS_PREC_BF16) {
+        if (dt == MDS_IN_U8) return gower_tck_supported(d, r) ? kKindU8Bf16 : -1;
+        return gower_tc_supported(d, r) ? kKindRows : -1;
+    }
+    return kKindRows;
+}
+
+// Tensor-core models keep W padded to the kernel's width (and, for byte-row
+// kinds, to tck_lpad(l) rows).
+size_t model_W_bytes(int kind, int prec, int l, int r) {
+    if (kind != kKindRows) return (size_t)tck_lpad(l) * gower_tc_rp(r) * 4;
     if (prec == MDS_PREC_BF16) return (size_t)l * gower_tc_rp(r) * 4;
     return (size_t)l * r * (prec == MDS_PREC_F64 ? 8 : 4);
 }
 
-size_t model_L_bytes(int prec, int l, int d) {
+size_t model_L_bytes(int kind, int prec, int l, int d) {
+    if (kind != kKindRows) return tck_landmark_bytes(kind - 1, l, d);
     if (prec == MDS_PREC_BF16) return (size_t)2 * l * split_ld(d) * sizeof(uint16_t);
     return (size_t)l * d * (prec == MDS_PREC_F64 ? 8 : 4);
 }
+
+size_t model_nlf_count(int kind, int l) { return kind != kKindRows ? (size_t)tck_lpad(l) : (size_t)round_up(l, 4); }
 
 // ---- per-thread instrumentation (mds_set_timing / mds_last_stats)
 bool g_timing = false;
@@ -294,10 +314,11 @@ size_t classical_layout(ClassicalWs& W, char* base, int64_t n, int r, int mmax) 
 struct InterpWs {
     int* flag;
     int* kerr;        // device error word of the tensor-core kernel
-    float* nrm_lf;    // BF16 path: landmark norms as float (zero-padded to 4)
-    float* Wpad;      // BF16 path: W padded to gower_tc_rp(r) columns
+    float* nrm_lf;    // tensor-core paths: landmark norms as float (zero-padded)
+    float* Wpad;      // tensor-core paths: W padded to gower_tc_rp(r) columns
     double* nrm;
     double* nrm_raw;  // BF16 path: FP32 norms of the unrounded rows (landmark problem)
+    float* nrm_f;     // byte-row paths: exact norms of the rows as float
     void* Yq;
     Batch B;
     void* L;
@@ -307,19 +328,22 @@ struct InterpWs {
     void* X1;
 };
 
-size_t interp_layout(InterpWs& W, char* base, int64_t n, int d, int l, int r, int prec, int mmax) {
+size_t interp_layout(InterpWs& W, char* base, int64_t n, int d, int l, int r, int prec, int kind, int mmax) {
     Arena A{base, 0};
     const size_t es = prec == MDS_PREC_F64 ? 8 : 4;
+    const bool split = prec == MDS_PREC_BF16 && kind == kKindRows;
     W.flag = A.take<int>(1);
     W.kerr = A.take<int>(1);
-    W.nrm_lf = A.take<float>(round_up(l, 4));
-    W.Wpad = A.take<float>((size_t)l * 16);
+    W.nrm_lf = A.take<float>(model_nlf_count(kind, l));
+    W.Wpad = A.take<float>(model_W_bytes(kind, prec, l, r) / 4 + 16 * (size_t)l);
     W.nrm = A.take<double>(n);
-    W.nrm_raw = prec == MDS_PREC_BF16 ? A.take<double>(n) : nullptr;
-    W.Yq = prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * n * split_ld(d)) : nullptr;
+    W.nrm_raw = (split || kind != kKindRows) ? A.take<double>(n) : nullptr;
+    W.nrm_f = kind != kKindRows ? A.take<float>(n) : nullptr;
+    W.Yq = split ? (void*)A.take<uint16_t>((size_t)2 * n * split_ld(d))
+                 : (kind != kKindRows ? (void*)A.take<char>(tck_operand_bytes(kind - 1, n, d)) : nullptr);
     plan_batch(W.B, {l}, {0}, 0, r, mmax, n);
     carve_batch(W.B, A);
-    W.L = A.take<char>(model_L_bytes(prec, l, d));
+    W.L = A.take<char>(model_L_bytes(kind, prec, l, d));
     W.nrm_l = A.take<double>(l);
     W.W = A.take<char>((size_t)l * r * es);
     W.bias = A.take<double>(r);
@@ -385,8 +409,20 @@ int gbmds::embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, ch
     Arena A{ws, 0};
     int* kerr = A.take<int>(1);
     double* nrm = A.take<double>(rows);
-    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * rows * split_ld(m->d)) : nullptr;
     *kerr_out = kerr;
+    if (m->kind != kKindRows) {
+        // byte-row models project byte rows only (the operands are exact)
+        if (dt != MDS_IN_U8) return MDS_ERR_ARG;
+        void* Yk = A.take<char>(tck_operand_bytes(m->kind - 1, rows, m->d));
+        float* nf = reinterpret_cast<float*>(nrm);
+        CK(cudaMemsetAsync(kerr, 0, sizeof(int), st));
+        CK(launch_encode_u8(m->kind - 1, (const uint8_t*)Ynew, rows, m->d, Yk, nf, st));
+        for (int i = 0; i < 4; ++i) tmark(i, st);
+        CK(launch_gower_tck(m->kind - 1, Yk, rows, m->d, nf, m->L, m->l, m->nrm_lf, (const float*)m->W, m->bias,
+                            m->r, (float*)X, kerr, st));
+        return MDS_OK;
+    }
+    void* Yq = m->prec == MDS_PREC_BF16 ? (void*)A.take<uint16_t>((size_t)2 * rows * split_ld(m->d)) : nullptr;
     CK(cudaMemsetAsync(kerr, 0, sizeof(int), st));
     const void* Ye;
     int dte;
@@ -497,8 +533,18 @@ int mds_classical_dist(const double* D2, int64_t n, int r, const mds_opts* opts,
 
 size_t mds_interpolate_workspace_size(int64_t n, int d, int l, int r, int prec) {
     if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0) return 0;
+    // the precision alone does not fix the kind (BF16 of byte rows differs from
+    // BF16 of float rows): size for the larger of the kinds it may take
     InterpWs W;
-    return interp_layout(W, nullptr, n, d, l, r, prec, kDefaultSteps) + 256;
+    size_t need = 0;
+    const int kinds[3] = {kKindRows, kKindU8Bf16, kKindU8Fp8};
+    for (int k : kinds) {
+        if (k == kKindRows && prec == MDS_PREC_FP8) continue;
+        if (k != kKindRows && (k == kKindU8Fp8) != (prec == MDS_PREC_FP8)) continue;
+        if (k == kKindU8Bf16 && prec != MDS_PREC_BF16) continue;
+        need = std::max(need, interp_layout(W, nullptr, n, d, l, r, prec, k, kDefaultSteps));
+    }
+    return need + 256;
 }
 
 int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
@@ -510,26 +556,32 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     if (!Y || !X || !var || !landmark_idx || !valid_dt(dt) || n < 2 || d <= 0 || l < 2 ||
         l > n || l > kMaxEigN || r <= 0 || r > kMaxR || r >= l)
         return MDS_ERR_ARG;
-    if (o.prec == MDS_PREC_FP8) return MDS_ERR_UNSUPPORTED;
-    if (o.prec == MDS_PREC_BF16 && !gower_tc_supported(d, r)) return MDS_ERR_UNSUPPORTED;
+    const int kind = model_kind(o.prec, dt, d, r);
+    if (kind < 0) return MDS_ERR_UNSUPPORTED;
     InterpWs W;
-    const size_t need = interp_layout(W, nullptr, n, d, l, r, o.prec, o.mmax);
+    const size_t need = interp_layout(W, nullptr, n, d, l, r, o.prec, kind, o.mmax);
     if ((s = check_ws(o, need))) return s;
-    if (interp_layout(W, o.ws, n, d, l, r, o.prec, o.mmax) != need) return MDS_ERR_WORKSPACE;
+    if (interp_layout(W, o.ws, n, d, l, r, o.prec, kind, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
     CK(launch_check_idx(landmark_idx, l, n, W.flag, o.st));
-    const void* Ye;
-    int dte;
-    if ((s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
+    const void* Ye = nullptr;
+    int dte = dt;
+    if (kind == kKindRows) {
+        if ((s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
+    } else {
+        // byte rows: exact tensor-core operands and exact norms
+        CK(launch_encode_u8(kind - 1, (const uint8_t*)Y, n, d, W.Yq, W.nrm_f, o.st));
+    }
     // The landmark problem is small: its distances come from the unrounded data
-    // in FP32 even on the BF16 path, which rounds only the bulk of Eq. (2).
+    // in FP32 even on the BF16 / FP8 paths, which use the tensor cores only for
+    // the bulk of Eq. (2).
     const void* Yl = Ye;
     int dtl = dte;
     const double* nrml = W.nrm;
-    if (o.prec == MDS_PREC_BF16) {
+    if (o.prec == MDS_PREC_BF16 || o.prec == MDS_PREC_FP8) {
         CK(launch_rownorm(Y, dt, n, d, 0, W.nrm_raw, o.st));
         Yl = Y;
         dtl = dt;
@@ -543,7 +595,13 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
                            f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
                            f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
                            var, o.st));
-    if (o.prec == MDS_PREC_BF16) {
+    if (kind != kKindRows) {
+        // tensor-core distance tiles of byte rows fused with the Gower projection
+        CK(launch_encode_landmarks_u8(kind - 1, (const uint8_t*)Y, n, d, landmark_idx, l, W.L, W.nrm_lf, o.st));
+        CK(launch_pad_w_rows((const float*)W.W, l, r, W.Wpad, o.st));
+        CK(launch_gower_tck(kind - 1, W.Yq, n, d, W.nrm_f, W.L, l, W.nrm_lf, W.Wpad, W.bias, r, (float*)X, W.kerr,
+                            o.st));
+    } else if (o.prec == MDS_PREC_BF16) {
         // tensor-core distance tiles fused with the Gower projection
         CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * round_up(l, 4), o.st));
         CK(launch_gather_split(Ye, n, d, landmark_idx, l, W.L, W.nrm, W.nrm_lf, o.st));
@@ -566,12 +624,14 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     m->d = d;
     m->r = r;
     m->prec = o.prec;
+    m->kind = kind;
     cudaGetDevice(&m->device);
-    const size_t szL = model_L_bytes(o.prec, l, d);
-    const size_t szW = model_W_bytes(o.prec, l, r);
+    const size_t szL = model_L_bytes(kind, o.prec, l, d);
+    const size_t szW = model_W_bytes(kind, o.prec, l, r);
+    const size_t nlf = model_nlf_count(kind, l);
     bool ok = cudaMalloc(&m->L, szL) == cudaSuccess &&
               cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
-              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * round_up(l, 4)) == cudaSuccess &&
+              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * nlf) == cudaSuccess &&
               cudaMalloc(&m->W, szW) == cudaSuccess &&
               cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
               cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
@@ -583,8 +643,9 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     }
     ok = cudaMemcpyAsync(m->L, W.L, szL, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->nrm_l, W.nrm_l, sizeof(double) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * round_up(l, 4), cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->W, o.prec == MDS_PREC_BF16 ? (void*)W.Wpad : W.W, szW, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * nlf, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->W, (kind != kKindRows || o.prec == MDS_PREC_BF16) ? (void*)W.Wpad : W.W, szW,
+                         cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->bias, W.bias, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->X1, W.X1, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
          cudaMemcpyAsync(m->lam, W.B.lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
@@ -602,7 +663,8 @@ size_t mds_embed_new_workspace_size(mds_model m, int64_t rows) {
     Arena A{nullptr, 0};
     A.take<int>(1);
     A.take<double>(rows);
-    if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
+    if (m->kind != kKindRows) A.take<char>(tck_operand_bytes(m->kind - 1, rows, m->d));
+    else if (m->prec == MDS_PREC_BF16) A.take<uint16_t>((size_t)2 * rows * split_ld(m->d));
     return A.off + 256;
 }
 
@@ -647,13 +709,13 @@ void mds_model_free(mds_model m) {
     delete m;
 }
 
-static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '2'};
+static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '3'};
 
 int mds_model_save(mds_model m, const char* path) {
     if (!m || !path) return MDS_ERR_ARG;
     const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
-    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = model_W_bytes(m->prec, m->l, m->r);
-    const size_t szX = (size_t)m->l * m->r * es, nlf = (size_t)round_up(m->l, 4);
+    const size_t szL = model_L_bytes(m->kind, m->prec, m->l, m->d), szW = model_W_bytes(m->kind, m->prec, m->l, m->r);
+    const size_t szX = (size_t)m->l * m->r * es, nlf = model_nlf_count(m->kind, m->l);
     std::vector<char> L(szL), W(szW), X1(szX);
     std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
     std::vector<float> nrmf(nlf);
@@ -667,8 +729,8 @@ int mds_model_save(mds_model m, const char* path) {
         return MDS_ERR_CUDA;
     FILE* f = fopen(path, "wb");
     if (!f) return MDS_ERR_IO;
-    const int32_t hdr[4] = {m->l, m->d, m->r, m->prec};
-    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 &&
+    const int32_t hdr[5] = {m->l, m->d, m->r, m->prec, m->kind};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 4, 5, f) == 5 &&
               fwrite(L.data(), 1, szL, f) == szL && fwrite(nrm.data(), 8, m->l, f) == (size_t)m->l &&
               fwrite(W.data(), 1, szW, f) == szW && fwrite(bias.data(), 8, m->r, f) == (size_t)m->r &&
               fwrite(X1.data(), 1, szX, f) == szX && fwrite(lam.data(), 8, m->r, f) == (size_t)m->r &&
@@ -683,10 +745,11 @@ int mds_model_load(const char* path, mds_model* out) {
     FILE* f = fopen(path, "rb");
     if (!f) return MDS_ERR_IO;
     char magic[8];
-    int32_t hdr[4];
-    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, 4, 4, f) != 4 ||
+    int32_t hdr[5];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 || fread(hdr, 4, 5, f) != 5 ||
         hdr[0] < 2 || hdr[0] > kMaxEigN || hdr[1] <= 0 || hdr[2] <= 0 || hdr[2] > kMaxR ||
-        hdr[3] < MDS_PREC_F64 || hdr[3] > MDS_PREC_FP8) {
+        hdr[3] < MDS_PREC_F64 || hdr[3] > MDS_PREC_FP8 || hdr[4] < kKindRows || hdr[4] > kKindU8Fp8 ||
+        model_kind(hdr[3], hdr[4] == kKindRows ? MDS_IN_F32 : MDS_IN_U8, hdr[1], hdr[2]) != hdr[4]) {
         fclose(f);
         return MDS_ERR_IO;
     }
@@ -699,10 +762,11 @@ int mds_model_load(const char* path, mds_model* out) {
     m->d = hdr[1];
     m->r = hdr[2];
     m->prec = hdr[3];
+    m->kind = hdr[4];
     cudaGetDevice(&m->device);
     const size_t es = m->prec == MDS_PREC_F64 ? 8 : 4;
-    const size_t szL = model_L_bytes(m->prec, m->l, m->d), szW = model_W_bytes(m->prec, m->l, m->r);
-    const size_t szX = (size_t)m->l * m->r * es, nlf = (size_t)round_up(m->l, 4);
+    const size_t szL = model_L_bytes(m->kind, m->prec, m->l, m->d), szW = model_W_bytes(m->kind, m->prec, m->l, m->r);
+    const size_t szX = (size_t)m->l * m->r * es, nlf = model_nlf_count(m->kind, m->l);
     std::vector<char> L(szL), W(szW), X1(szX);
     std::vector<double> nrm(m->l), bias(m->r), lam(m->r);
     std::vector<float> nrmf(nlf);

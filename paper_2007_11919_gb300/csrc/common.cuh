@@ -10,6 +10,8 @@
 // Device-resident landmark configuration behind an mds_model handle.
 struct mds_model_s {
     int l, d, r, prec, device;
+    int kind;       // 0: FP64/FP32 rows or BF16 split planes; 1 + kTckBf16 / 1 + kTckFp8:
+                    // byte rows encoded for k_gower_tck (norms and W padded to tck_lpad(l))
     void* L;        // landmark rows: l x d double (F64), l x d float (F32), or BF16
                     // split planes hi | lo of l x split_ld(d) each (BF16)
     double* nrm_l;  // l squared norms of the rows as stored in L (F64 / F32 models)
@@ -226,6 +228,25 @@ cudaError_t launch_dc_lambda_bar(const ProbDesc* desc, int p, const double* lam,
 // Classical MDS output X = V Lambda^{1/2} in row order of problem 0.
 cudaError_t launch_classical_out(const double* V, const double* lam, int n, int r, int out_f64,
                                  void* X, double* lam_out, cudaStream_t st);
+
+// Tensor-core Gower projection for byte-valued rows of any width
+// (k_gower_tck.cu).  kTckBf16: exact BF16 operands; kTckFp8: exact E4M3
+// nibble planes.  Operands come from launch_encode_u8 (rows) and
+// launch_encode_landmarks_u8 (landmarks, norms padded to tck_lpad(l)); W is
+// padded by launch_pad_w_rows to tck_lpad(l) x gower_tc_rp(r).
+constexpr int kTckBf16 = 0;
+constexpr int kTckFp8 = 1;
+int tck_lpad(int l);
+size_t tck_operand_bytes(int mode, int64_t rows, int d);
+size_t tck_landmark_bytes(int mode, int l, int d);
+bool gower_tck_supported(int d, int r);
+cudaError_t launch_encode_u8(int mode, const uint8_t* Y, int64_t n, int d, void* out, float* nrm, cudaStream_t st);
+cudaError_t launch_encode_landmarks_u8(int mode, const uint8_t* Y, int64_t ny, int d, const int64_t* idx, int l,
+                                       void* B, float* nrm_l, cudaStream_t st);
+cudaError_t launch_pad_w_rows(const float* W, int l, int r, float* Wp, cudaStream_t st);
+cudaError_t launch_gower_tck(int mode, const void* A, int64_t m, int d, const float* nrm_y, const void* B, int l,
+                             const float* nrm_l, const float* Wp, const double* bias, int r, float* X, int* err,
+                             cudaStream_t st);
 
 // Host side (api.cu): queue an embedding against a model without waiting.
 int embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, char* ws, cudaStream_t st, void* X,

@@ -304,3 +304,68 @@ def test_bf16_tensor_core_embed(gb, n, d, l, r):
     assert np.all(np.isfinite(Xe))
     assert O.aligned_rel_error(Xe, Xo) < TOL["bf16"]
     assert O.aligned_rel_error(host(X)[:n], Xo) < TOL["bf16"]
+
+
+# ------------------------------------------------- byte rows on the tensor cores
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,d,l,r", [(3000, 784, 300, 10), (1000, 100, 257, 5), (777, 37, 129, 3),
+                                     (300, 784, 256, 16)])
+def test_u8_tensor_core_interp(gb, prec, n, d, l, r, tmp_path):
+    """Image-like byte rows: exact BF16 operands or exact E4M3 nibble planes on
+    tcgen05 (ragged tiles, ragged landmark chunks, d not a multiple of 16)."""
+    Y = W.image_like(n, d, seed=d + l)
+    idx = W.landmarks(n, l, seed=n + r)
+    X, var, model = gb.mds_interpolate(dev(Y), dev(idx), r, prec, want_model=True)
+    Xo, vo, _ = O.interpolation_mds(Y.astype(np.float64), idx, r)
+    err = O.aligned_rel_error(host(X), Xo)
+    assert err < TOL["bf16"], err
+    assert rel(host(var), vo) < LAM_TOL["f32"]
+    rest = np.setdiff1d(np.arange(n), idx)
+    Xe = gb.mds_embed_new(model, dev(Y))
+    assert torch.equal(Xe[rest], X[rest])
+    path = str(tmp_path / "u8.gbmds")
+    model.save(path)
+    m2 = gb.Model.load(path)
+    assert torch.equal(gb.mds_embed_new(m2, dev(Y[:50])), Xe[:50])
+    with pytest.raises(gb.MdsError):
+        gb.mds_embed_new(model, dev(Y[:50].astype(np.float32)))
+
+
+def test_u8_bf16_and_fp8_agree(gb):
+    """Both encodings give exact products: the two projections agree far
+    below the BF16 / FP8 tolerance."""
+    Y = W.image_like(5000, 784, seed=5)
+    idx = W.landmarks(5000, 500, seed=5)
+    Xb, _, _ = gb.mds_interpolate(dev(Y), dev(idx), 10, "bf16")
+    Xf, _, _ = gb.mds_interpolate(dev(Y), dev(idx), 10, "fp8")
+    scale = float(torch.linalg.norm(Xb))
+    assert float(torch.linalg.norm(Xb - Xf)) / scale < 1e-5
+
+
+def test_fp8_needs_byte_rows(gb):
+    Y = W.gaussian_dominant(500, 20, 3, seed=1, dtype=np.float32)
+    with pytest.raises(gb.MdsError) as e:
+        gb.mds_interpolate(dev(Y), dev(W.landmarks(500, 100, seed=1)), 3, "fp8")
+    assert e.value.status == 7
+
+
+def test_image_fp8_full_size_sampled(gb):
+    """The image-like configuration at full size (814,255 x 784 bytes, l = 2000,
+    r = 10, FP8 nibble planes): sampled rows against the oracle's landmark MDS
+    and Eq. (2)."""
+    w = W.IMAGE_FP8
+    Y = W.make_data(w, seed=0)
+    idx = W.landmarks(w.n, w.l, seed=0)
+    X, var, _ = gb.mds_interpolate(dev(Y), dev(idx), w.r, "fp8")
+    X = host(X)
+    L = Y[idx].astype(np.float64)
+    D1 = O.sq_dist(L, L)
+    X1, lam, _, _ = O.classical_mds(D1, w.r)
+    rows = np.random.default_rng(0).choice(np.setdiff1d(np.arange(w.n), idx), 3000, replace=False)
+    Xs = O.gower_interpolate(X1, lam, D1, O.sq_dist(Y[rows].astype(np.float64), L))
+    both = np.concatenate([X[idx], X[rows]])
+    ref = np.concatenate([X1, Xs])
+    assert O.aligned_rel_error(both, ref) < TOL["bf16"]
+    assert rel(host(var), lam / w.l) < LAM_TOL["f32"]
