@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["dc", "interp", "serve"], default="dc")
+    ap.add_argument("--workload", choices=["dc", "interp", "image", "image_dc", "serve"], default="dc")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-parts", type=int, default=4, help="parts in the bounded oracle sample")
@@ -224,21 +224,38 @@ def oracle_interp_sample(Y, idx, r, m):
 # ---------------------------------------------------------------- workloads
 
 
+WORKLOADS = {"dc": W.DC_F32, "interp": W.INTERP_BF16, "image": W.IMAGE_FP8, "image_dc": W.IMAGE_DC}
+
+
+def is_dc(name):
+    return WORKLOADS[name].kind == "dc"
+
+
+def oracle_sample(name, Y, aux, r, cpu_parts):
+    """Bounded oracle sample of a workload: a few parts (D&C) or the landmark
+    MDS plus a block of interpolated rows (interpolation)."""
+    wide = Y.shape[1] > 200
+    if is_dc(name):
+        k = min(cpu_parts, 2) if wide else cpu_parts
+        rows, Xo, dt, npts = oracle_dc_sample(Y, aux, r, k)
+        return rows, Xo, dt, npts, f"parts 0..{k - 1} ({npts} points) of the same workload, each part's classical MDS + Procrustes to part 0"
+    m = 2_000 if wide else 20_000
+    rows, Xo, dt, npts = oracle_interp_sample(Y, aux, r, m)
+    return rows, Xo, dt, npts, f"landmark MDS + Eq. (2) for {npts - len(aux)} rows of the same workload"
+
+
 def make_workload(name, seed, n=0):
     import dataclasses
-    if name == "dc":
-        w = W.DC_F32
-        if n:
-            w = dataclasses.replace(w, n=n, name=w.name.replace(f"n{W.DC_F32.n}", f"n{n}"))
-        Y = W.make_data(W.DC_F32, seed, n=w.n)
-        part = W.partitions_uneven(w.n, w.c, w.own_lo, w.own_hi, seed)
-        return w, Y, part
-    w = W.INTERP_BF16
+    base = WORKLOADS[name]
+    w = base
     if n:
-        w = dataclasses.replace(w, n=n, name=w.name.replace(f"n{W.INTERP_BF16.n}", f"n{n}"))
-    Y = W.make_data(W.INTERP_BF16, seed, n=w.n)
-    idx = W.landmarks(w.n, w.l, seed)
-    return w, Y, idx
+        w = dataclasses.replace(base, n=n, name=base.name.replace(f"n{base.n}", f"n{n}"))
+    Y = W.make_data(base, seed, n=w.n)
+    if name == "dc":
+        return w, Y, W.partitions_uneven(w.n, w.c, w.own_lo, w.own_hi, seed)
+    if name == "image_dc":
+        return w, Y, W.partitions_equal(w.n, w.l, w.c, seed)
+    return w, Y, W.landmarks(w.n, w.l, seed)
 
 
 def reference_arm(args):
@@ -248,16 +265,11 @@ def reference_arm(args):
     w, Y, aux = make_workload(args.workload, args.seed, args.n)
     times, pts = [], 0
     for i in range(args.warmup + args.steps):
-        if args.workload == "dc":
-            _, _, dt, npts = oracle_dc_sample(Y, aux, w.r, args.cpu_parts)
-        else:
-            _, _, dt, npts = oracle_interp_sample(Y, aux, w.r, 20_000)
+        _, _, dt, npts, sample = oracle_sample(args.workload, Y, aux, w.r, args.cpu_parts)
         if i >= args.warmup:
             times.append(dt)
             pts += npts
     value = pts / sum(times)
-    sample = (f"parts 0..{args.cpu_parts - 1} of the workload per step" if args.workload == "dc"
-              else "landmark MDS + 20,000 interpolated rows per step")
     emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -360,7 +372,7 @@ def ours(args):
     w, Y, aux = make_workload(args.workload, seed, args.n)
     Yd = torch.from_numpy(Y).to(dev)
     L = M._lib()
-    if args.workload == "dc":
+    if is_dc(args.workload):
         part = aux
         anc = torch.from_numpy(part.anchors).to(dev)
         own = torch.from_numpy(part.own).to(dev)
@@ -414,7 +426,7 @@ def ours(args):
 
     # ---- dominant kernel roofline (batched Lanczos for D&C; projection for interpolation)
     eig_ms = [s["stage_ms"]["eig"] for s in stats]
-    if args.workload == "dc":
+    if is_dc(args.workload):
         # The batched Lanczos streams every part's Q (8 bytes per entry) once
         # per step through a double-FP32 product on the FP32 pipe: HBM-bound.
         flops = statistics.mean(s["eig_flops"] for s in stats)
@@ -435,18 +447,25 @@ def ours(args):
         flops = w.n * (2.0 * w.l * w.d + 2.0 * w.l * w.r)
         peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
         pk = peaks.get("bf16_tflops", 1900.0)
+        src_note = "MEASURED_PEAKS.json bf16_tflops (burst, of measured)" if peaks else "fallback 1.9 PFLOP/s"
+        if w.prec == "fp8":
+            # FP8 dense rate = measured BF16 x the nominal 4.5 / 2.25 ratio
+            pk *= 2.0
+            src_note += " x 2 (nominal FP8 / BF16 ratio)"
+        byte_rows = Y.dtype == np.uint8
+        kname = ("k_gower_tck (tcgen05 distance tiles of byte rows, K streamed, fused with the Gower projection)"
+                 if byte_rows else "k_gower_tc (tcgen05 distance tiles fused with the Gower projection)")
         achieved = flops / (kms * 1e-3) / 1e12
-        roof = {"kernel": "k_gower_tc (tcgen05 distance tiles fused with the Gower projection)", "bound": "tensor",
+        roof = {"kernel": kname, "bound": "tensor",
                 "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1.9 PFLOP/s",
-                "launch_ms": kms, "flops_per_launch": flops}
-        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_gower_tc.cu")
+                "peak_source": src_note, "launch_ms": kms, "flops_per_launch": flops}
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_gower_tck.cu" if byte_rows else "k_gower_tc.cu")
     tr = NCU_TRAFFIC.get(os.path.basename(src))
     roof["traffic"] = tr["bytes_per_launch"] if tr and tr["sha"] == file_sha(src) else None
 
     # ---- end to end through the public API: pinned host input, host output
     Yh = torch.from_numpy(Y).pin_memory()
-    if args.workload == "dc":
+    if is_dc(args.workload):
         anc_h = torch.from_numpy(part.anchors).pin_memory()
         own_h = torch.from_numpy(part.own).pin_memory()
         h2d = Yh.numel() * Yh.element_size() + anc_h.numel() * 8 + own_h.numel() * 8
@@ -478,12 +497,7 @@ def ours(args):
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
-        if args.workload == "dc":
-            rows, Xo, dt, npts = oracle_dc_sample(Y, part, w.r, args.cpu_parts)
-            sample = f"parts 0..{args.cpu_parts - 1} ({npts} points) of the same workload, each part's classical MDS + Procrustes to part 0"
-        else:
-            rows, Xo, dt, npts = oracle_interp_sample(Y, aux, w.r, 20_000)
-            sample = f"landmark MDS + Eq. (2) for {npts - w.l} rows of the same workload"
+        rows, Xo, dt, npts, sample = oracle_sample(args.workload, Y, aux, w.r, args.cpu_parts)
         err = O.aligned_rel_error(Xh.double().numpy()[rows], Xo)
         cpu = {"value": npts / dt, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle", "sample": sample}
 
@@ -495,9 +509,9 @@ def ours(args):
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": w.prec, "data": "synthetic",
               "config": {"workload": w.name, "n_per_gpu": w.n, "d": w.d, "r": w.r,
-                         "parts": (part.p if args.workload == "dc" else None),
-                         "c": (w.c if args.workload == "dc" else None),
-                         "l": (w.l if args.workload == "interp" else None),
+                         "parts": (part.p if is_dc(args.workload) else None),
+                         "c": (w.c if is_dc(args.workload) else None),
+                         "l": (w.l if not is_dc(args.workload) else None),
                          "eigensolve": "f64 Lanczos", "cluster": stats[-1]["cluster"],
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
               "procrustes_rel_err_vs_oracle": err,

@@ -222,6 +222,10 @@ SERVE_MODELS = ((500, 2), (1000, 5), (2000, 10))
 SERVE_SIZES = (1, 50_000)
 IMAGE_FP8 = Workload("image_fp8_n814255_d784_l2000_r10", "interp", 814_255, 784, 10, "fp8", l=2000,
                      c=50)
+# The same image-like set by divide-and-conquer: parts of l = 2000 points with
+# c = 50 shared connecting points (Section 3.2 layout), FP32 distances.
+IMAGE_DC = Workload("image_dc_f32_n814255_d784_parts2000_c50_r10", "dc", 814_255, 784, 10, "f32", l=2000,
+                    c=50)
 
 
 def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
@@ -235,6 +239,6 @@ def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
         return gaussian_mixture(n, w.d, 4, 5.0, seed, dtype=np.float32)
     if w.name == SERVE_BF16.name:
         return gaussian_graded(n, w.d, seed)
-    if w.name == IMAGE_FP8.name:
+    if w.name in (IMAGE_FP8.name, IMAGE_DC.name):
         return image_like(n, w.d, seed)
     raise KeyError(w.name)
