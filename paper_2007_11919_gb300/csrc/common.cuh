@@ -49,7 +49,7 @@ struct ProbDesc {
 };
 
 // Device-side status codes written per problem (a subset of mds_status).
-enum DevStatus : int { kDevOk = 0, kDevRank = MDS_ERR_RANK, kDevNoConv = MDS_ERR_NOCONV };
+enum DevStatus : int { kDevOk = 0, kDevRank = MDS_ERR_RANK, kDevNoConv = MDS_ERR_NOCONV, kDevTimeout = MDS_ERR_TIMEOUT };
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

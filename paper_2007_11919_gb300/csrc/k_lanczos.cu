@@ -23,10 +23,18 @@
 // shared memory and is gathered through distributed shared memory; dot
 // products are reduced across the cluster through DSMEM in rank order, so
 // every CTA holds bitwise-identical scalars and takes identical decisions.
+//
+// Streaming: Q is read once per step and does not change, so each warp
+// streams its rows of Q through its own ring of shared-memory stages with
+// asynchronous bulk copies (cp.async.bulk, completion on an mbarrier per
+// stage).  The warp re-issues a stage as soon as it has consumed it, running
+// one ring ahead into the next step: the copies for step j+1 are in flight
+// while the cluster does step j's Gram-Schmidt passes and reductions.
 #include <cooperative_groups.h>
 #include <float.h>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -35,6 +43,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kRing = 3;           // stages per warp
+constexpr int kChunkB = 4096;      // bytes per stage (a row segment of Q)
+constexpr size_t kRingBytes = (size_t)kWarps * kRing * kChunkB;
 
 struct Smem {
     double* vfull;   // max_n     : full current Lanczos vector
@@ -50,20 +61,28 @@ struct Smem {
     double* resid;   // kMaxR
     double* red;     // 3 * kWarps * ... scratch (64)
     double* sgn;     // 4 * kMaxR : (|max|, row, signed) per eigenvector, then sign flips
-    double* inv;     // 4 * r * (mmax + 1): per wanted vector U bands u0, u1, u2 and x
+    double* xv;      // r * (mmax + 1): eigenvectors x_i of T_k, one row of mmax + 1 per i
+    double* band;    // ceil(r / cs) * 3 * (mmax + 1): U bands of this CTA's inverse iterations
+    uint8_t* ring;   // kWarps * kRing * kChunkB bytes: per-warp Q stages
+    uint64_t* full;  // kWarps * kRing mbarriers
 };
+
+__host__ __device__ inline int owned_max(int r, int cs) { return (r + cs - 1) / cs; }
 
 __host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
-    return round_up(max_n, 2) + 2 * round_up(rmax, 2) + 3 * (size_t)(mmax + 2) +
-           3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 4 * (size_t)r * (mmax + 1) + 8;
+    return kRingBytes / 8 + (size_t)kWarps * kRing + round_up(max_n + 1, 2) + 2 * round_up(rmax, 2) +
+           3 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR +
+           (size_t)r * (mmax + 1) + 3 * (size_t)owned_max(r, cs) * (mmax + 1) + 8;
 }
 
-__device__ Smem carve(double* base, int max_n, int cs, int mmax) {
+__device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     Smem s;
     const int rmax = (max_n + cs - 1) / cs;
     double* p = base;
-    s.vfull = p; p += round_up(max_n, 2);
+    s.ring = reinterpret_cast<uint8_t*>(p); p += kRingBytes / 8;
+    s.full = reinterpret_cast<uint64_t*>(p); p += kWarps * kRing;
+    s.vfull = p; p += round_up(max_n + 1, 2);
     s.vloc = p; p += round_up(rmax, 2);
     s.wloc = p; p += round_up(rmax, 2);
     s.part0 = p; p += mmax + 2;
@@ -76,7 +95,8 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax) {
     s.resid = p; p += kMaxR;
     s.red = p; p += 64;
     s.sgn = p; p += 4 * kMaxR;
-    s.inv = p;
+    s.xv = p; p += (size_t)r * (mmax + 1);
+    s.band = p;
     return s;
 }
 
@@ -234,42 +254,6 @@ __device__ __forceinline__ double start_entry(int row) {
     return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// w[i] = Q[row i, :] . v for this CTA's rows: four rows per warp, two
-// 16-byte loads per row in flight per lane.
-__device__ __forceinline__ void matvec_rows(const double* __restrict__ Q, int ldq, int n, int r0,
-                                            int nr, const double* v, double* w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int neven = n & ~1;
-    for (int i = 4 * warp; i < nr; i += 4 * kWarps) {
-        const double* q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = Q + (int64_t)(r0 + min(i + u, nr - 1)) * ldq;
-        double acc[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-#pragma unroll 2
-        for (int kk = 2 * lane; kk < neven; kk += 64) {
-            const double2 vv = *reinterpret_cast<const double2*>(v + kk);
-            double2 x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const double2*>(q[u] + kk);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                acc[u][0] = fma(x[u].x, vv.x, acc[u][0]);
-                acc[u][1] = fma(x[u].y, vv.y, acc[u][1]);
-            }
-        }
-        if ((n & 1) && lane == 0) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u][0] = fma(q[u][n - 1], v[n - 1], acc[u][0]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const double s = warp_sum(acc[u][0] + acc[u][1]);
-            if (lane == 0 && i + u < nr) w[i + u] = s;
-        }
-    }
-}
-
-// part[i] = sum over this CTA's rows of B[i][row] * w[row], i <= j (warp per i).
 // Double-FP32 arithmetic (Dekker 1971; Knuth's TwoSum): a value is an
 // unevaluated sum hi + lo of two floats (about 48 significant bits).  The
 // products run on the FP32 pipe, whose rate on GB300 is ~57x the FP64 rate.
@@ -296,48 +280,132 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol)
     sh = s;
 }
 
-// w[i] = Q[row i, :] . v with Q stored as (hi, lo) float pairs and v as
-// (hi, lo) pairs in shared memory; four rows per warp, two elements per
-// 16-byte load.  The warp reduction stays in double-FP32.
-__device__ __forceinline__ void matvec_rows_df(const float2* __restrict__ Q, int ldq, int n,
-                                               int r0, int nr, const float2* v, double* w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int neven = n & ~1;
-    for (int i = 4 * warp; i < nr; i += 4 * kWarps) {
-        const float2* q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = Q + (int64_t)(r0 + min(i + u, nr - 1)) * ldq;
-        float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-        for (int kk = 2 * lane; kk < neven; kk += 64) {
-            const float4 vv = *reinterpret_cast<const float4*>(v + kk);
-            float4 x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(q[u] + kk);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                df_madd(sh[u], sl[u], x[u].x, x[u].y, vv.x, vv.y);
-                df_madd(sh[u], sl[u], x[u].z, x[u].w, vv.z, vv.w);
-            }
-        }
-        if ((n & 1) && lane == 0) {
-            const float2 vv = v[n - 1];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) df_madd(sh[u], sl[u], q[u][n - 1].x, q[u][n - 1].y, vv.x, vv.y);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float oh = __shfl_xor_sync(0xffffffffu, sh[u], o);
-                const float ol = __shfl_xor_sync(0xffffffffu, sl[u], o);
-                df_add(sh[u], sl[u], oh, ol);
-            }
-            if (lane == 0 && i + u < nr) w[i + u] = (double)sh[u] + (double)sl[u];
-        }
+// ---------------------------------------------------------------- Q stream
+//
+// Warp w of a CTA owns rows [wr0, wr1) of the CTA's slice and streams them in
+// row segments of at most kChunkB bytes through stages ring[w][0..kRing).
+// Chunk g (counted per warp across steps and problems, so the mbarrier phase
+// of stage g % kRing is (g / kRing) & 1) is segment u = (g - g0) % per_step of
+// the warp's rows, g0 being the problem's first chunk.
+struct QStream {
+    const uint8_t* q;   // Q of the problem (bytes)
+    size_t row_stride;  // ldq * 8
+    int rowbytes;       // round_up(n, 2) * 8: what one row's copies cover
+    int segs;           // segments per row
+    int wr0, wr1;       // this warp's rows
+    int per_step;       // (wr1 - wr0) * segs
+    long long g0;       // first chunk of the problem
+    long long issued;   // chunks issued (valid in lane 0)
+    uint8_t* ring;      // this warp's stages
+    uint64_t* full;     // this warp's barriers
+};
+
+__device__ __forceinline__ void qs_issue(QStream& Qs, long long g) {
+    const int u = (int)((g - Qs.g0) % Qs.per_step);
+    const int row = Qs.wr0 + u / Qs.segs, seg = u % Qs.segs;
+    const int off = seg * kChunkB;
+    const int bytes = min(kChunkB, Qs.rowbytes - off);
+    const int st = (int)(g % kRing);
+    tc::mbar_expect_tx(&Qs.full[st], (uint32_t)bytes);
+    tc::bulk_load(Qs.ring + (size_t)st * kChunkB, Qs.q + (size_t)row * Qs.row_stride + off, (uint32_t)bytes,
+                  &Qs.full[st]);
+}
+
+// Bounded wait on a stage; false after ~2 s (the copy source is ordinary
+// device memory, so this only guards against a broken launch).
+__device__ __forceinline__ bool qs_wait(uint64_t* bar, uint32_t parity) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = tc::global_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (tc::mbar_try_wait(bar, parity)) return true;
+        if (tc::global_ns() - t0 > tc::kWaitNs) return false;
     }
 }
 
+// Sets up this warp's stream for a problem and issues its first kRing chunks.
+__device__ __forceinline__ void qs_begin(QStream& Qs, const Smem& S, const double* Q, int ldq, int n, int r0,
+                                         int nr, long long g) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per_warp = (nr + kWarps - 1) / kWarps;
+    Qs.q = reinterpret_cast<const uint8_t*>(Q);
+    Qs.row_stride = (size_t)ldq * 8;
+    Qs.rowbytes = (int)round_up(n, 2) * 8;
+    Qs.segs = (Qs.rowbytes + kChunkB - 1) / kChunkB;
+    Qs.wr0 = r0 + min(nr, warp * per_warp);
+    Qs.wr1 = r0 + min(nr, (warp + 1) * per_warp);
+    Qs.per_step = (Qs.wr1 - Qs.wr0) * Qs.segs;
+    Qs.g0 = g;
+    Qs.issued = g;
+    Qs.ring = S.ring + (size_t)warp * kRing * kChunkB;
+    Qs.full = S.full + warp * kRing;
+    if (Qs.per_step > 0 && lane == 0)
+        for (int i = 0; i < kRing; ++i) qs_issue(Qs, Qs.issued++);
+}
+
+// Waits (bounded) for the chunks still in flight at the end of a problem.
+__device__ __forceinline__ long long qs_end(QStream& Qs, long long consumed, bool& timeout) {
+    if (Qs.per_step > 0) {
+        for (long long g = consumed; g < consumed + kRing; ++g)
+            if (!qs_wait(&Qs.full[g % kRing], (uint32_t)((g / kRing) & 1))) timeout = true;
+    }
+    __syncwarp();
+    return Qs.per_step > 0 ? consumed + kRing : consumed;
+}
+
+// w[row - r0] = Q[row, :] . v for this warp's rows, consuming one step of the
+// stream and re-issuing every stage it frees.  DF: Q entries and v are
+// (hi, lo) float pairs and the products run in double-FP32; else FP64.
+template <bool DF>
+__device__ __forceinline__ long long qs_matvec(QStream& Qs, long long g, int n, int r0, const double* vfull,
+                                               double* w, bool& timeout) {
+    const int lane = threadIdx.x & 31;
+    float sh = 0.f, sl = 0.f;
+    double acc = 0.0;
+    for (int u = 0; u < Qs.per_step; ++u, ++g) {
+        const int st = (int)(g % kRing);
+        if (!qs_wait(&Qs.full[st], (uint32_t)((g / kRing) & 1))) timeout = true;
+        const int row = Qs.wr0 + u / Qs.segs, seg = u % Qs.segs;
+        const int col0 = seg * (kChunkB / 8);
+        const int bytes = min(kChunkB, Qs.rowbytes - seg * kChunkB);
+        const uint8_t* stage = Qs.ring + (size_t)st * kChunkB;
+        for (int t = lane; t < bytes / 16; t += 32) {
+            const int c = col0 + 2 * t;
+            if (DF) {
+                const float4 x = reinterpret_cast<const float4*>(stage)[t];
+                const float4 vv = reinterpret_cast<const float4*>(vfull)[c >> 1];
+                df_madd(sh, sl, x.x, x.y, vv.x, vv.y);
+                if (c + 1 < n) df_madd(sh, sl, x.z, x.w, vv.z, vv.w);
+            } else {
+                const double2 x = reinterpret_cast<const double2*>(stage)[t];
+                const double2 vv = reinterpret_cast<const double2*>(vfull)[c >> 1];
+                acc = fma(x.x, vv.x, acc);
+                if (c + 1 < n) acc = fma(x.y, vv.y, acc);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) qs_issue(Qs, Qs.issued++);   // the stage is free: next chunk in the periodic stream
+        if (seg == Qs.segs - 1) {
+            if (DF) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+                    df_add(sh, sl, oh, ol);
+                }
+                if (lane == 0) w[row - r0] = (double)sh + (double)sl;
+                sh = sl = 0.f;
+            } else {
+                acc = warp_sum(acc);
+                if (lane == 0) w[row - r0] = acc;
+                acc = 0.0;
+            }
+        }
+    }
+    return g;
+}
+
+// part[i] = sum over this CTA's rows of B[i][row] * w[row], i <= j (warp per i).
 // B is written by this kernel (new Lanczos vectors), so it must never be read
 // through the non-coherent read-only path: no __restrict__ on it.
 // With with_norm, part[j+1] also receives the partial sum of w[row]^2.
@@ -386,7 +454,7 @@ __device__ __forceinline__ void cgs_update(const double* B, int ldq, int r0, int
 // as double-FP32 pairs and the matrix-vector product runs in double-FP32.
 template <bool DF>
 __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q,
-                              double* smraw, int& s_flag) {
+                              double* smraw, int& s_flag, long long& qchunk) {
     const ProbDesc P = A.desc[pj];
     const int n = P.n, ldq = P.ldq, r = A.r;
     const int R = (n + cs - 1) / cs;
@@ -399,9 +467,15 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     // per-problem global scratch: the final tridiagonal T_k (diagonal, off-diagonal)
     double* scr = A.scratch + (size_t)pj * lanczos_scratch_per_problem(A.mmax, r);
 
-    Smem S = carve(smraw, A.max_n, cs, A.mmax);
+    Smem S = carve(smraw, A.max_n, cs, A.mmax, r);
     double* part[2] = {S.part0, S.part1};
     int pb = 0;
+    // start streaming this CTA's rows of Q right away
+    QStream Qs;
+    qs_begin(Qs, S, Q, ldq, n, r0, nr, qchunk);
+    long long g = qchunk;
+    bool qtimeout = false;
+    if (tid == 0) S.red[40] = 0.0;   // set to 1 by any thread whose stage wait timed out
 
     // ---- start vector: pseudo-random, unit norm
     double loc = 0.0;
@@ -428,6 +502,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     int k = 0, prev_k = 0;
     bool converged = false, have_vectors = false;
 
+    if (tid == 0) S.vfull[n] = 0.0;   // guard entry read by the paired loads when n is odd
     for (int j = 0; j < kmax; ++j) {
         // ---- gather v_j from all ranks
         cl.sync();
@@ -443,12 +518,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         }
         __syncthreads();
 
-        // ---- w = Q v_j on this CTA's rows
-        if (DF)
-            matvec_rows_df(reinterpret_cast<const float2*>(Q), ldq, n, r0, nr,
-                           reinterpret_cast<const float2*>(S.vfull), S.wloc);
-        else
-            matvec_rows(Q, ldq, n, r0, nr, S.vfull, S.wloc);
+        // ---- w = Q v_j on this CTA's rows (streamed)
+        g = qs_matvec<DF>(Qs, g, n, r0, S.vfull, S.wloc, qtimeout);
         __syncthreads();
 
         // ---- two passes of classical Gram-Schmidt against v_0..v_j; the
@@ -521,10 +592,11 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                     }
                     const double th = kth_largest(S.alpha, S.beta2, k, i, lo, hi);
                     if (lane == 0) {
-                        double* iv = S.inv + (size_t)i * 4 * L;
-                        tri_inverse_iteration(S.alpha, S.beta, k, th, pert, iv, iv + L, iv + 2 * L, iv + 3 * L);
+                        double* bd = S.band + (size_t)m * 3 * L;
+                        double* x = S.xv + (size_t)i * L;
+                        tri_inverse_iteration(S.alpha, S.beta, k, th, pert, bd, bd + L, bd + 2 * L, x);
                         S.theta[i] = th;
-                        S.resid[i] = beta_j * fabs(iv[3 * L + k - 1]);
+                        S.resid[i] = beta_j * fabs(x[k - 1]);
                     }
                     __syncwarp();
                 }
@@ -582,6 +654,13 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     }
 
     // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
+    qchunk = qs_end(Qs, g, qtimeout);
+    if (qtimeout) S.red[40] = 1.0;
+    __syncthreads();
+    cl.sync();
+    bool any_timeout = false;
+    for (int qq = 0; qq < cs; ++qq) any_timeout |= cl.map_shared_rank(S.red, qq)[40] != 0.0;
+    cl.sync();   // every CTA has read the flags before S.red is reused
     int status = kDevOk;
     if (k < r || !have_vectors) {
         status = kDevRank;
@@ -589,22 +668,21 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         if (!converged) status = kDevNoConv;
         if (!(S.theta[r - 1] > 0.0) || !(S.theta[r - 1] > A.rank_tol * S.theta[0])) status = kDevRank;
     }
+    if (any_timeout) status = kDevTimeout;
     if (q == 0 && status != kDevRank) {
         // rank 0 collects the eigenvectors of T_k computed by the other CTAs
         for (int e = tid; e < r * k; e += kThreads) {
             const int i = e / k, t = e % k;
-            if (i % cs != 0)
-                S.inv[(size_t)i * 4 * L + 3 * L + t] =
-                    cl.map_shared_rank(S.inv, i % cs)[(size_t)i * 4 * L + 3 * L + t];
+            if (i % cs != 0) S.xv[(size_t)i * L + t] = cl.map_shared_rank(S.xv, i % cs)[(size_t)i * L + t];
         }
         __syncthreads();
     }
     if (q == 0 && status != kDevRank && warp == 0) {
         // modified Gram-Schmidt across the r inverse-iteration vectors (shared memory)
         for (int i = 0; i < r; ++i) {
-            double* xi = S.inv + (size_t)i * 4 * L + 3 * L;
+            double* xi = S.xv + (size_t)i * L;
             for (int m = 0; m < i; ++m) {
-                const double* xm = S.inv + (size_t)m * 4 * L + 3 * L;
+                const double* xm = S.xv + (size_t)m * L;
                 double s = 0.0;
                 for (int t = lane; t < k; t += 32) s += xi[t] * xm[t];
                 s = warp_sum(s);
@@ -629,10 +707,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     }
     // the other CTAs copy the eigenvectors of T_k from rank 0 (DSMEM)
     if (q != 0) {
-        const double* src = cl.map_shared_rank(S.inv, 0);
+        const double* src = cl.map_shared_rank(S.xv, 0);
         for (int e = tid; e < r * k; e += kThreads) {
             const int i = e / k, t = e % k;
-            S.inv[(size_t)i * 4 * L + 3 * L + t] = src[(size_t)i * 4 * L + 3 * L + t];
+            S.xv[(size_t)i * L + t] = src[(size_t)i * L + t];
         }
     }
     __syncthreads();
@@ -641,7 +719,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     double* V = A.varena + P.v_off;
     for (int rr = tid; rr < nr; rr += kThreads) {
         for (int i = 0; i < r; ++i) {
-            const double* si = S.inv + (size_t)i * 4 * L + 3 * L;
+            const double* si = S.xv + (size_t)i * L;
             double s = 0.0;
             for (int t = 0; t < k; ++t) s = fma(B[(int64_t)t * ldq + r0 + rr], si[t], s);
             V[(int64_t)(r0 + rr) * r + i] = s;
@@ -716,13 +794,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     const int q = (int)cl.block_rank();
     extern __shared__ __align__(16) double smraw[];
     __shared__ int s_flag, s_next;
+    {
+        const Smem S = carve(smraw, A.max_n, cs, A.mmax, A.r);
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < kWarps * kRing; ++i) tc::mbar_init(&S.full[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
+    long long qchunk = 0;   // Q-stream chunks this warp has consumed (all problems)
     for (;;) {
         if (q == 0 && threadIdx.x == 0) s_next = atomicAdd(A.counter, 1);
         cl.sync();
         const int next = q == 0 ? s_next : *cl.map_shared_rank(&s_next, 0);
         cl.sync();  // every CTA has read the index before rank 0 takes another
         if (next >= A.p) break;
-        solve_problem<DF>(A, A.order[next], cl, cs, q, smraw, s_flag);
+        solve_problem<DF>(A, A.order[next], cl, cs, q, smraw, s_flag, qchunk);
     }
 }
 
