@@ -1,4 +1,4 @@
-// Batched top-r symmetric eigen-solver in FP64: Lanczos with full
+// Batched top-r symmetric eigen-solver: Lanczos with full
 // re-orthogonalisation, one thread-block cluster per eigenproblem.
 //
 // The paper computes the classical-MDS eigenpairs of each l x l matrix Q with a
@@ -6,32 +6,42 @@
 // classical MDS keep the r largest eigenvalues and their eigenvectors.  Here:
 //
 //   Krylov basis v_0, v_1, ... of Q from a fixed pseudo-random start vector;
-//   w = Q v_j, two passes of classical Gram-Schmidt against all previous
-//   vectors, alpha_j = v_j . Q v_j, beta_j = ||w||, v_{j+1} = w / beta_j.
-//   The Rayleigh quotient T_k = V_k^T Q V_k is the tridiagonal of the alphas
-//   and betas.  Every few steps the r largest eigenvalues theta_i of T_k are
-//   found by Sturm-count multisection and their eigenvectors s_i by inverse
-//   iteration (tridiagonal LU with partial pivoting); the Ritz residuals are
-//   ||Q y_i - theta_i y_i|| = beta_{k-1} |s_i[k-1]|.  The run stops when every
-//   residual is below tol * theta_0, at an invariant subspace (beta ~ 0), or
-//   at the step cap (status NOCONV).  The s_i of the last check are
-//   orthonormalised (modified Gram-Schmidt) and the Ritz vectors are
-//   y_i = V_k s_i.
+//   w = Q v_j, a local Gram-Schmidt pass against v_{j-1} and v_j (the
+//   three-term recurrence, with computed coefficients) and a full classical
+//   Gram-Schmidt pass against v_0..v_j; alpha_j = v_j . Q v_j, beta_j = ||w||,
+//   v_{j+1} = w / beta_j.  The Rayleigh quotient T_k = V_k^T Q V_k is the
+//   tridiagonal of the alphas and betas.  Every few steps the r largest
+//   eigenvalues theta_i of T_k are found by Sturm-count multisection and their
+//   eigenvectors s_i by inverse iteration (tridiagonal LU with partial
+//   pivoting); the Ritz residuals are ||Q y_i - theta_i y_i|| =
+//   beta_{k-1} |s_i[k-1]|.  The run stops when every residual is below
+//   tol * theta_0, at an invariant subspace (beta ~ 0), or at the step cap
+//   (status NOCONV).  The s_i of the last check are orthonormalised (modified
+//   Gram-Schmidt) and the Ritz vectors are y_i = V_k s_i.
 //
-// Layout: Q_j row-major FP64 (ld = ldq).  The cluster's CTAs own contiguous
-// row slices; each CTA's slice of the current Lanczos vector lives in its
-// shared memory and is gathered through distributed shared memory; dot
-// products are reduced across the cluster through DSMEM in rank order, so
-// every CTA holds bitwise-identical scalars and takes identical decisions.
+// Arithmetic: the scalars (alpha, beta, Gram-Schmidt coefficients) and the
+// tridiagonal work are FP64.  The O(n^2) matrix-vector product and the O(n k)
+// vector work are FP64 for FP64 problems and double-FP32 otherwise (a value is
+// an unevaluated pair of floats, ~48 significant bits): GB300 issues FP64 at
+// 1/64 of its FP32 rate.  Q, the basis and the working vectors take 8 bytes
+// per entry either way.
+//
+// Layout: Q_j row-major (ld = ldq).  The cluster's CTAs own contiguous row
+// slices; each CTA's slice of the current Lanczos vector lives in its shared
+// memory and is gathered through distributed shared memory; dot products are
+// reduced across the cluster through DSMEM in rank order, so every CTA holds
+// bitwise-identical scalars and takes identical decisions.
 //
 // Streaming: Q is read once per step and does not change, so each warp
-// streams its rows of Q through its own ring of shared-memory stages with
-// asynchronous bulk copies (cp.async.bulk, completion on an mbarrier per
-// stage).  The warp re-issues a stage as soon as it has consumed it, running
-// one ring ahead into the next step: the copies for step j+1 are in flight
-// while the cluster does step j's Gram-Schmidt passes and reductions.
+// streams its rows of Q in row segments of at most 4 KB through its own ring
+// of shared-memory stages with asynchronous bulk copies (cp.async.bulk,
+// completion on one mbarrier per stage), refilling a stage as soon as it has
+// been consumed and running into the next step, so the copies for step j+1
+// are in flight during step j's Gram-Schmidt passes.  Before a convergence
+// check the rings are drained and their memory holds the check's workspace.
 #include <cooperative_groups.h>
 #include <float.h>
+#include <limits.h>
 
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -43,51 +53,63 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRing = 3;           // stages per warp
-constexpr int kChunkB = 4096;      // bytes per stage (a row segment of Q)
+constexpr int kRing = 2;           // stages per warp
+constexpr int kChunkB = 4096;      // bytes per stage (at most one row segment of Q)
 constexpr size_t kRingBytes = (size_t)kWarps * kRing * kChunkB;
 
 struct Smem {
-    double* vfull;   // max_n     : full current Lanczos vector
-    double* vloc;    // rmax      : this CTA's slice of v_j
-    double* wloc;    // rmax      : this CTA's slice of w
-    double* part0;   // mmax + 2  : partial sums published to the cluster
+    uint8_t* ring;   // per-warp Q stages while streaming; the check workspace otherwise
+    double* xv;      // (in the ring) r x (mmax + 1): eigenvectors x_i of T_k
+    double* band;    // (in the ring) per eigenvalue-owning warp 3 x (mmax + 1): U bands
+    uint64_t* full;  // kWarps * kRing stage mbarriers
+    double* vfull;   // max_n + 2 entries: the full current Lanczos vector
+    double* vloc;    // rmax : this CTA's slice of v_j
+    double* wloc;    // rmax : this CTA's slice of w
+    double* part0;   // mmax + 2 : partial sums published to the cluster
     double* part1;   // mmax + 2
-    double* cfull;   // mmax + 2  : reduced coefficients
+    double* cfull;   // mmax + 2 : reduced coefficients
+    double* cdf;     // mmax + 2 : the same as double-FP32 pairs
     double* alpha;   // mmax + 1
     double* beta;    // mmax + 1
     double* beta2;   // mmax + 1
     double* theta;   // kMaxR
     double* resid;   // kMaxR
-    double* red;     // 3 * kWarps * ... scratch (64)
+    double* red;     // 64 : scratch
     double* sgn;     // 4 * kMaxR : (|max|, row, signed) per eigenvector, then sign flips
-    double* xv;      // r * (mmax + 1): eigenvectors x_i of T_k, one row of mmax + 1 per i
-    double* band;    // ceil(r / cs) * 3 * (mmax + 1): U bands of this CTA's inverse iterations
-    uint8_t* ring;   // kWarps * kRing * kChunkB bytes: per-warp Q stages
-    uint64_t* full;  // kWarps * kRing mbarriers
 };
 
 __host__ __device__ inline int owned_max(int r, int cs) { return (r + cs - 1) / cs; }
 
+// Doubles of the ring region: the Q stages or the check workspace, whichever is larger.
+__host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
+    const int own = owned_max(r, cs) < kWarps ? owned_max(r, cs) : kWarps;
+    const size_t check = (size_t)(r + 3 * own) * (mmax + 1);
+    const size_t q = kRingBytes / 8;
+    return (size_t)round_up((int64_t)(q > check ? q : check), 16);
+}
+
 __host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
-    return kRingBytes / 8 + (size_t)kWarps * kRing + round_up(max_n + 1, 2) + 2 * round_up(rmax, 2) +
-           3 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR +
-           (size_t)r * (mmax + 1) + 3 * (size_t)owned_max(r, cs) * (mmax + 1) + 8;
+    return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 2, 2) + 2 * round_up(rmax, 2) +
+           4 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8;
 }
 
 __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     Smem s;
     const int rmax = (max_n + cs - 1) / cs;
     double* p = base;
-    s.ring = reinterpret_cast<uint8_t*>(p); p += kRingBytes / 8;
+    s.ring = reinterpret_cast<uint8_t*>(p);
+    s.xv = p;
+    s.band = p + (size_t)r * (mmax + 1);
+    p += ring_doubles(cs, mmax, r);
     s.full = reinterpret_cast<uint64_t*>(p); p += kWarps * kRing;
-    s.vfull = p; p += round_up(max_n + 1, 2);
+    s.vfull = p; p += round_up(max_n + 2, 2);
     s.vloc = p; p += round_up(rmax, 2);
     s.wloc = p; p += round_up(rmax, 2);
     s.part0 = p; p += mmax + 2;
     s.part1 = p; p += mmax + 2;
     s.cfull = p; p += mmax + 2;
+    s.cdf = p; p += mmax + 2;
     s.alpha = p; p += mmax + 1;
     s.beta = p; p += mmax + 1;
     s.beta2 = p; p += mmax + 1;
@@ -95,8 +117,6 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     s.resid = p; p += kMaxR;
     s.red = p; p += 64;
     s.sgn = p; p += 4 * kMaxR;
-    s.xv = p; p += (size_t)r * (mmax + 1);
-    s.band = p;
     return s;
 }
 
@@ -114,13 +134,18 @@ __device__ double block_sum(double v, double* red) {
     return s;
 }
 
-// out[i] = sum over cluster ranks (in rank order) of part[i], i < K.
-__device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* out, int K, int cs) {
+__device__ __forceinline__ float2 df_of(double x);
+
+// out[i] = sum over cluster ranks (in rank order) of part[i], lo <= i < hi;
+// outdf (when not null) receives the sums as double-FP32 pairs.
+__device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* out, double* outdf, int lo, int hi,
+                                  int cs) {
     cl.sync();
-    for (int i = threadIdx.x; i < K; i += kThreads) {
+    for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
         double s = 0.0;
         for (int qq = 0; qq < cs; ++qq) s += cl.map_shared_rank(part, qq)[i];
         out[i] = s;
+        if (outdf) reinterpret_cast<float2*>(outdf)[i] = df_of(s);
     }
     __syncthreads();
 }
@@ -280,36 +305,54 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol)
     sh = s;
 }
 
+
+// Renormalised double-FP32 helpers (values as float2 {hi, lo}).
+__device__ __forceinline__ float2 df_of(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ float2 df_norm(float sh, float sl) {
+    const float h = __fadd_rn(sh, sl);
+    return make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
+}
+// a * s
+__device__ __forceinline__ float2 df_mul(float2 a, float2 s) {
+    const float p = __fmul_rn(a.x, s.x);
+    float e = fmaf(a.x, s.x, -p);
+    e = fmaf(a.x, s.y, e);
+    e = fmaf(a.y, s.x, e);
+    return df_norm(p, e);
+}
+// Warp sum of a double-FP32 accumulator (fixed butterfly order).
+__device__ __forceinline__ void df_warp_sum(float& sh, float& sl) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+        df_add(sh, sl, oh, ol);
+    }
+}
+
 // ---------------------------------------------------------------- Q stream
 //
-// Warp w of a CTA owns rows [wr0, wr1) of the CTA's slice and streams them in
-// row segments of at most kChunkB bytes through stages ring[w][0..kRing).
-// Chunk g (counted per warp across steps and problems, so the mbarrier phase
-// of stage g % kRing is (g / kRing) & 1) is segment u = (g - g0) % per_step of
-// the warp's rows, g0 being the problem's first chunk.
+// Warp w of a CTA owns rows [wr0, wr0 + per_step / nseg) of the CTA's slice
+// and streams them as a periodic sequence of row segments (position pos =
+// row-offset * nseg + segment) through its kRing stages, in order.  Stage
+// indices and mbarrier phases carry over from problem to problem.
 struct QStream {
-    const uint8_t* q;   // Q of the problem (bytes)
-    size_t row_stride;  // ldq * 8
-    int rowbytes;       // round_up(n, 2) * 8: what one row's copies cover
-    int segs;           // segments per row
-    int wr0, wr1;       // this warp's rows
-    int per_step;       // (wr1 - wr0) * segs
-    long long g0;       // first chunk of the problem
-    long long issued;   // chunks issued (valid in lane 0)
+    const uint8_t* q;   // Q of the problem
+    size_t stride;      // bytes per row of Q (ldq * 8)
+    int rowbytes;       // bytes a row's copies cover: round_up(n, 2) * 8
+    int nseg, segb;     // segments per row and bytes per segment (the last may be shorter)
+    int wr0, per_step;  // first row of this warp and segments per step
     uint8_t* ring;      // this warp's stages
-    uint64_t* full;     // this warp's barriers
+    uint64_t* full;     // their mbarriers
+    int cpos, ipos;     // stream positions of the next consume and the next issue
+    int cst, ist;       // their stages
+    int inflight;       // issued and not yet consumed
+    int issue_left;     // issues still allowed
+    uint32_t phase;     // parity each stage's next completion will have
 };
-
-__device__ __forceinline__ void qs_issue(QStream& Qs, long long g) {
-    const int u = (int)((g - Qs.g0) % Qs.per_step);
-    const int row = Qs.wr0 + u / Qs.segs, seg = u % Qs.segs;
-    const int off = seg * kChunkB;
-    const int bytes = min(kChunkB, Qs.rowbytes - off);
-    const int st = (int)(g % kRing);
-    tc::mbar_expect_tx(&Qs.full[st], (uint32_t)bytes);
-    tc::bulk_load(Qs.ring + (size_t)st * kChunkB, Qs.q + (size_t)row * Qs.row_stride + off, (uint32_t)bytes,
-                  &Qs.full[st]);
-}
 
 // Bounded wait on a stage; false after ~2 s (the copy source is ordinary
 // device memory, so this only guards against a broken launch).
@@ -323,55 +366,95 @@ __device__ __forceinline__ bool qs_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
-// Sets up this warp's stream for a problem and issues its first kRing chunks.
-__device__ __forceinline__ void qs_begin(QStream& Qs, const Smem& S, const double* Q, int ldq, int n, int r0,
-                                         int nr, long long g) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int per_warp = (nr + kWarps - 1) / kWarps;
-    Qs.q = reinterpret_cast<const uint8_t*>(Q);
-    Qs.row_stride = (size_t)ldq * 8;
-    Qs.rowbytes = (int)round_up(n, 2) * 8;
-    Qs.segs = (Qs.rowbytes + kChunkB - 1) / kChunkB;
-    Qs.wr0 = r0 + min(nr, warp * per_warp);
-    Qs.wr1 = r0 + min(nr, (warp + 1) * per_warp);
-    Qs.per_step = (Qs.wr1 - Qs.wr0) * Qs.segs;
-    Qs.g0 = g;
-    Qs.issued = g;
-    Qs.ring = S.ring + (size_t)warp * kRing * kChunkB;
-    Qs.full = S.full + warp * kRing;
-    if (Qs.per_step > 0 && lane == 0)
-        for (int i = 0; i < kRing; ++i) qs_issue(Qs, Qs.issued++);
-}
-
-// Waits (bounded) for the chunks still in flight at the end of a problem.
-__device__ __forceinline__ long long qs_end(QStream& Qs, long long consumed, bool& timeout) {
-    if (Qs.per_step > 0) {
-        for (long long g = consumed; g < consumed + kRing; ++g)
-            if (!qs_wait(&Qs.full[g % kRing], (uint32_t)((g / kRing) & 1))) timeout = true;
+// Issues chunks while a stage is free and issues are allowed (the whole warp
+// keeps the bookkeeping; lane 0 issues).
+__device__ __forceinline__ void qs_fill(QStream& s) {
+    while (s.inflight < kRing && s.issue_left > 0) {
+        if ((threadIdx.x & 31) == 0) {
+            const int row = s.wr0 + s.ipos / s.nseg, seg = s.ipos % s.nseg;
+            const int off = seg * s.segb;
+            const int bytes = min(s.segb, s.rowbytes - off);
+            tc::mbar_expect_tx(&s.full[s.ist], (uint32_t)bytes);
+            tc::bulk_load(s.ring + (size_t)s.ist * kChunkB, s.q + (size_t)row * s.stride + off, (uint32_t)bytes,
+                          &s.full[s.ist]);
+        }
+        s.ipos = s.ipos + 1 == s.per_step ? 0 : s.ipos + 1;
+        s.ist = s.ist + 1 == kRing ? 0 : s.ist + 1;
+        ++s.inflight;
+        --s.issue_left;
     }
-    __syncwarp();
-    return Qs.per_step > 0 ? consumed + kRing : consumed;
 }
 
-// w[row - r0] = Q[row, :] . v for this warp's rows, consuming one step of the
-// stream and re-issuing every stage it frees.  DF: Q entries and v are
-// (hi, lo) float pairs and the products run in double-FP32; else FP64.
+__device__ __forceinline__ bool qs_wait_front(QStream& s) {
+    const bool ok = qs_wait(&s.full[s.cst], (s.phase >> s.cst) & 1u);
+    s.phase ^= 1u << s.cst;
+    return ok;
+}
+
+__device__ __forceinline__ void qs_pop(QStream& s) {
+    s.cpos = s.cpos + 1 == s.per_step ? 0 : s.cpos + 1;
+    s.cst = s.cst + 1 == kRing ? 0 : s.cst + 1;
+    --s.inflight;
+}
+
+// Waits for the chunks in flight and discards them; they are issued again
+// from the same stream position later.  The warp's stages are then free.
+__device__ __forceinline__ bool qs_drain(QStream& s) {
+    bool ok = true;
+    const int keep = s.cpos;
+    while (s.inflight > 0) {
+        ok = qs_wait_front(s) && ok;
+        qs_pop(s);
+    }
+    s.cpos = s.ipos = keep;
+    s.issue_left = 0;
+    __syncwarp();
+    return ok;
+}
+
+// Sets up the warp's stream for a problem and issues its first chunks.
+__device__ __forceinline__ void qs_setup(QStream& s, const double* Q, int ldq, int n, int r0, int nr) {
+    const int warp = threadIdx.x >> 5;
+    const int per_warp = (nr + kWarps - 1) / kWarps;
+    const int a = min(nr, warp * per_warp), b = min(nr, (warp + 1) * per_warp);
+    s.q = reinterpret_cast<const uint8_t*>(Q);
+    s.stride = (size_t)ldq * 8;
+    s.rowbytes = (int)round_up(n, 2) * 8;
+    s.nseg = (s.rowbytes + kChunkB - 1) / kChunkB;
+    s.segb = (int)round_up((s.rowbytes + s.nseg - 1) / s.nseg, 16);
+    s.wr0 = r0 + a;
+    s.per_step = (b - a) * s.nseg;
+    s.cpos = s.ipos = 0;
+    s.issue_left = min(kRing, s.per_step);
+    qs_fill(s);
+}
+
+// Re-issues the first chunks of the next step (after a drain).
+__device__ __forceinline__ void qs_prime(QStream& s) {
+    s.issue_left = min(kRing, s.per_step);
+    qs_fill(s);
+}
+
+// One step of the stream: w[row - r0] = Q[row, :] . v for the warp's rows.
+// With prefetch the warp keeps issuing into the next step.
 template <bool DF>
-__device__ __forceinline__ long long qs_matvec(QStream& Qs, long long g, int n, int r0, const double* vfull,
-                                               double* w, bool& timeout) {
+__device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const double* vfull, double* w,
+                                          bool prefetch) {
     const int lane = threadIdx.x & 31;
+    bool ok = true;
+    s.issue_left = s.per_step - s.inflight + (prefetch ? min(kRing, s.per_step) : 0);
+    qs_fill(s);
     float sh = 0.f, sl = 0.f;
     double acc = 0.0;
-    for (int u = 0; u < Qs.per_step; ++u, ++g) {
-        const int st = (int)(g % kRing);
-        if (!qs_wait(&Qs.full[st], (uint32_t)((g / kRing) & 1))) timeout = true;
-        const int row = Qs.wr0 + u / Qs.segs, seg = u % Qs.segs;
-        const int col0 = seg * (kChunkB / 8);
-        const int bytes = min(kChunkB, Qs.rowbytes - seg * kChunkB);
-        const uint8_t* stage = Qs.ring + (size_t)st * kChunkB;
+    for (int u = 0; u < s.per_step; ++u) {
+        ok = qs_wait_front(s) && ok;
+        const int row = s.wr0 + s.cpos / s.nseg, seg = s.cpos % s.nseg;
+        const int col0 = seg * (s.segb / 8);
+        const int bytes = min(s.segb, s.rowbytes - seg * s.segb);
+        const uint8_t* stage = s.ring + (size_t)s.cst * kChunkB;
         for (int t = lane; t < bytes / 16; t += 32) {
             const int c = col0 + 2 * t;
-            if (DF) {
+            if constexpr (DF) {
                 const float4 x = reinterpret_cast<const float4*>(stage)[t];
                 const float4 vv = reinterpret_cast<const float4*>(vfull)[c >> 1];
                 df_madd(sh, sl, x.x, x.y, vv.x, vv.y);
@@ -384,16 +467,12 @@ __device__ __forceinline__ long long qs_matvec(QStream& Qs, long long g, int n, 
             }
         }
         __syncwarp();
-        if (lane == 0) qs_issue(Qs, Qs.issued++);   // the stage is free: next chunk in the periodic stream
-        if (seg == Qs.segs - 1) {
-            if (DF) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
-                    const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
-                    df_add(sh, sl, oh, ol);
-                }
-                if (lane == 0) w[row - r0] = (double)sh + (double)sl;
+        qs_pop(s);
+        qs_fill(s);   // the stage is free: next chunk of the periodic stream
+        if (seg == s.nseg - 1) {
+            if constexpr (DF) {
+                df_warp_sum(sh, sl);
+                if (lane == 0) reinterpret_cast<float2*>(w)[row - r0] = df_norm(sh, sl);
                 sh = sl = 0.f;
             } else {
                 acc = warp_sum(acc);
@@ -402,164 +481,246 @@ __device__ __forceinline__ long long qs_matvec(QStream& Qs, long long g, int n, 
             }
         }
     }
-    return g;
+    return ok;
 }
 
-// part[i] = sum over this CTA's rows of B[i][row] * w[row], i <= j (warp per i).
+// ------------------------------------------------------------ Gram-Schmidt
+//
 // B is written by this kernel (new Lanczos vectors), so it must never be read
 // through the non-coherent read-only path: no __restrict__ on it.
-// With with_norm, part[j+1] also receives the partial sum of w[row]^2.
-__device__ __forceinline__ void cgs_dots(const double* B, int ldq, int r0, int nr, int j,
-                                         const double* w, double* part, bool with_norm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (with_norm && warp == (j + 1) % kWarps) {
-        double s0 = 0.0;
-        for (int rr = lane; rr < nr; rr += 32) s0 = fma(w[rr], w[rr], s0);
-        s0 = warp_sum(s0);
-        if (lane == 0) part[j + 1] = s0;
-    }
-    for (int i = warp; i <= j; i += kWarps) {
-        const double* bi = B + (int64_t)i * ldq + r0;
-        double s0 = 0.0, s1 = 0.0;
-        int rr = lane;
-        for (; rr + 32 < nr; rr += 64) {
-            s0 = fma(bi[rr], w[rr], s0);
-            s1 = fma(bi[rr + 32], w[rr + 32], s1);
-        }
-        if (rr < nr) s0 = fma(bi[rr], w[rr], s0);
-        const double s = warp_sum(s0 + s1);
-        if (lane == 0) part[i] = s;
-    }
-}
 
-// w[row] -= sum_{i <= j} B[i][row] * c[i] (thread per row).
-__device__ __forceinline__ void cgs_update(const double* B, int ldq, int r0, int nr, int j,
-                                           const double* c, double* w) {
-    for (int rr = threadIdx.x; rr < nr; rr += kThreads) {
-        const double* b = B + r0 + rr;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int i = 0;
-        for (; i + 3 <= j; i += 4) {
-            s0 = fma(b[(int64_t)i * ldq], c[i], s0);
-            s1 = fma(b[(int64_t)(i + 1) * ldq], c[i + 1], s1);
-            s2 = fma(b[(int64_t)(i + 2) * ldq], c[i + 2], s2);
-            s3 = fma(b[(int64_t)(i + 3) * ldq], c[i + 3], s3);
-        }
-        for (; i <= j; ++i) s0 = fma(b[(int64_t)i * ldq], c[i], s0);
-        w[rr] -= (s0 + s1) + (s2 + s3);
-    }
-}
-
-// One eigenproblem (part pj) solved by the calling cluster.  DF: Q is stored
-// as double-FP32 pairs and the matrix-vector product runs in double-FP32.
+// part[i] = sum over this CTA's rows of B[i][row] * w[row] for ia <= i <= ib
+// (one warp per i, two vectors at a time); with_norm also sets part[ib + 1] =
+// sum of w[row]^2.
 template <bool DF>
-__device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q,
-                              double* smraw, int& s_flag, long long& qchunk) {
+__device__ void cgs_dots(const double* B, int ldq, int r0, int nr, int ia, int ib, const double* w, double* part,
+                         bool with_norm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (DF) {
+        const float2* w2 = reinterpret_cast<const float2*>(w);
+        if (with_norm && warp == (ib + 1) % kWarps) {
+            float sh = 0.f, sl = 0.f;
+            for (int rr = lane; rr < nr; rr += 32) {
+                const float2 x = w2[rr];
+                df_madd(sh, sl, x.x, x.y, x.x, x.y);
+            }
+            df_warp_sum(sh, sl);
+            if (lane == 0) part[ib + 1] = (double)sh + (double)sl;
+        }
+        for (int i = ia + warp; i <= ib; i += 2 * kWarps) {
+            const int i2 = i + kWarps;
+            const bool two = i2 <= ib;
+            const float2* b1 = reinterpret_cast<const float2*>(B) + (int64_t)i * ldq + r0;
+            const float2* b2 = reinterpret_cast<const float2*>(B) + (int64_t)(two ? i2 : i) * ldq + r0;
+            float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+            for (int rr = lane; rr < nr; rr += 32) {
+                const float2 x = w2[rr];
+                const float2 a1 = b1[rr];
+                const float2 a2 = b2[rr];
+                df_madd(h1, l1, a1.x, a1.y, x.x, x.y);
+                df_madd(h2, l2, a2.x, a2.y, x.x, x.y);
+            }
+            df_warp_sum(h1, l1);
+            df_warp_sum(h2, l2);
+            if (lane == 0) {
+                part[i] = (double)h1 + (double)l1;
+                if (two) part[i2] = (double)h2 + (double)l2;
+            }
+        }
+    } else {
+        if (with_norm && warp == (ib + 1) % kWarps) {
+            double s0 = 0.0;
+            for (int rr = lane; rr < nr; rr += 32) s0 = fma(w[rr], w[rr], s0);
+            s0 = warp_sum(s0);
+            if (lane == 0) part[ib + 1] = s0;
+        }
+        for (int i = ia + warp; i <= ib; i += kWarps) {
+            const double* bi = B + (int64_t)i * ldq + r0;
+            double s0 = 0.0, s1 = 0.0;
+            int rr = lane;
+            for (; rr + 32 < nr; rr += 64) {
+                s0 = fma(bi[rr], w[rr], s0);
+                s1 = fma(bi[rr + 32], w[rr + 32], s1);
+            }
+            if (rr < nr) s0 = fma(bi[rr], w[rr], s0);
+            const double s = warp_sum(s0 + s1);
+            if (lane == 0) part[i] = s;
+        }
+    }
+}
+
+// w[row] -= sum_{ia <= i <= ib} B[i][row] * c[i] (thread per row); c as FP64
+// (cf) and as double-FP32 pairs (cd).
+template <bool DF>
+__device__ void cgs_update(const double* B, int ldq, int r0, int nr, int ia, int ib, const double* cf,
+                           const double* cd, double* w) {
+    if constexpr (DF) {
+        const float2* c2 = reinterpret_cast<const float2*>(cd);
+        float2* w2 = reinterpret_cast<float2*>(w);
+        for (int rr = threadIdx.x; rr < nr; rr += kThreads) {
+            const float2* b = reinterpret_cast<const float2*>(B) + r0 + rr;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+            int i = ia;
+            for (; i + 1 <= ib; i += 2) {
+                const float2 x0 = b[(int64_t)i * ldq], x1 = b[(int64_t)(i + 1) * ldq];
+                const float2 k0 = c2[i], k1 = c2[i + 1];
+                df_madd(h0, l0, x0.x, x0.y, k0.x, k0.y);
+                df_madd(h1, l1, x1.x, x1.y, k1.x, k1.y);
+            }
+            if (i <= ib) {
+                const float2 x0 = b[(int64_t)i * ldq];
+                const float2 k0 = c2[i];
+                df_madd(h0, l0, x0.x, x0.y, k0.x, k0.y);
+            }
+            df_add(h0, l0, h1, l1);
+            const float2 wv = w2[rr];
+            float sh = wv.x, sl = wv.y;
+            df_add(sh, sl, -h0, -l0);
+            w2[rr] = df_norm(sh, sl);
+        }
+    } else {
+        for (int rr = threadIdx.x; rr < nr; rr += kThreads) {
+            const double* b = B + r0 + rr;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int i = ia;
+            for (; i + 3 <= ib; i += 4) {
+                s0 = fma(b[(int64_t)i * ldq], cf[i], s0);
+                s1 = fma(b[(int64_t)(i + 1) * ldq], cf[i + 1], s1);
+                s2 = fma(b[(int64_t)(i + 2) * ldq], cf[i + 2], s2);
+                s3 = fma(b[(int64_t)(i + 3) * ldq], cf[i + 3], s3);
+            }
+            for (; i <= ib; ++i) s0 = fma(b[(int64_t)i * ldq], cf[i], s0);
+            w[rr] -= (s0 + s1) + (s2 + s3);
+        }
+    }
+}
+
+// ------------------------------------------------------------ one problem
+
+// One eigenproblem (part pj) solved by the calling cluster.
+template <bool DF>
+__device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q, const Smem& S,
+                              int& s_flag, QStream& Qs) {
     const ProbDesc P = A.desc[pj];
     const int n = P.n, ldq = P.ldq, r = A.r;
     const int R = (n + cs - 1) / cs;
     const int r0 = min(n, q * R), r1 = min(n, r0 + R), nr = r1 - r0;
-    const double* __restrict__ Q = A.qarena + P.q_off;
+    const double* Q = A.qarena + P.q_off;
     double* B = A.barena + P.b_off;
     const int kmax = min(A.mmax, n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int L = A.mmax + 1;
     // per-problem global scratch: the final tridiagonal T_k (diagonal, off-diagonal)
     double* scr = A.scratch + (size_t)pj * lanczos_scratch_per_problem(A.mmax, r);
-
-    Smem S = carve(smraw, A.max_n, cs, A.mmax, r);
     double* part[2] = {S.part0, S.part1};
     int pb = 0;
-    // start streaming this CTA's rows of Q right away
-    QStream Qs;
-    qs_begin(Qs, S, Q, ldq, n, r0, nr, qchunk);
-    long long g = qchunk;
-    bool qtimeout = false;
-    if (tid == 0) S.red[40] = 0.0;   // set to 1 by any thread whose stage wait timed out
+    bool qok = true;
+
+    // start streaming this warp's rows of Q right away
+    qs_setup(Qs, Q, ldq, n, r0, nr);
 
     // ---- start vector: pseudo-random, unit norm
     double loc = 0.0;
     for (int i = tid; i < nr; i += kThreads) {
         const double v = start_entry(r0 + i);
-        S.vloc[i] = v;
+        S.wloc[i] = v;
         loc += v * v;
     }
     {
         const double s = block_sum(loc, S.red);
         if (tid == 0) part[pb][0] = s;
-        cluster_allreduce(cl, part[pb], S.cfull, 1, cs);
+        cluster_allreduce(cl, part[pb], S.cfull, nullptr, 0, 1, cs);
         pb ^= 1;
-        const double inv = 1.0 / sqrt(S.cfull[0]);
+        if (tid == 0) S.red[kWarps + 3] = 1.0 / sqrt(S.cfull[0]);
+        __syncthreads();
+        const double inv = S.red[kWarps + 3];
         for (int i = tid; i < nr; i += kThreads) {
-            S.vloc[i] *= inv;
-            B[r0 + i] = S.vloc[i];
+            const double v = S.wloc[i] * inv;
+            if constexpr (DF) {
+                const float2 d = df_of(v);
+                reinterpret_cast<float2*>(S.vloc)[i] = d;
+                reinterpret_cast<float2*>(B)[r0 + i] = d;
+            } else {
+                S.vloc[i] = v;
+                B[r0 + i] = v;
+            }
         }
+    }
+    if (tid == 0) {
+        S.vfull[n] = 0.0;   // guard entries read by the paired loads when n is odd
+        S.vfull[n + 1] = 0.0;
+        S.red[40] = 0.0;    // tnorm
     }
 
     const int kmin = min(kmax, max(2 * r, 8));
     int next_check = kmin;
-    double tnorm = 0.0, prev_worst = -1.0;
+    double prev_worst = -1.0;
     int k = 0, prev_k = 0;
     bool converged = false, have_vectors = false;
 
-    if (tid == 0) S.vfull[n] = 0.0;   // guard entry read by the paired loads when n is odd
     for (int j = 0; j < kmax; ++j) {
-        // ---- gather v_j from all ranks
+        // ---- gather v_j from all ranks (8-byte entries, copied as they are)
         cl.sync();
         for (int i = tid; i < n; i += kThreads) {
             const int src = i / R;
-            const double v = cl.map_shared_rank(S.vloc, src)[i - src * R];
-            if (DF) {
-                const float h = (float)v;
-                reinterpret_cast<float2*>(S.vfull)[i] = make_float2(h, (float)(v - (double)h));
-            } else {
-                S.vfull[i] = v;
-            }
+            S.vfull[i] = cl.map_shared_rank(S.vloc, src)[i - src * R];
         }
         __syncthreads();
 
-        // ---- w = Q v_j on this CTA's rows (streamed)
-        g = qs_matvec<DF>(Qs, g, n, r0, S.vfull, S.wloc, qtimeout);
+        // ---- w = Q v_j on this CTA's rows (streamed); no prefetch into a step
+        // that starts with a predicted check
+        qok = qs_matvec<DF>(Qs, n, r0, S.vfull, S.wloc, j + 1 < next_check && j + 1 < kmax) && qok;
         __syncthreads();
 
-        // ---- two passes of classical Gram-Schmidt against v_0..v_j; the
-        // second pass also reduces ||w_1||^2, and ||w_2||^2 = ||w_1||^2 - ||c_2||^2.
-        double alpha_j = 0.0;
-        for (int pass = 0; pass < 2; ++pass) {
-            cgs_dots(B, ldq, r0, nr, j, S.wloc, part[pb], pass == 1);
-            __syncthreads();
-            cluster_allreduce(cl, part[pb], S.cfull, j + 1 + pass, cs);
-            pb ^= 1;
-            cgs_update(B, ldq, r0, nr, j, S.cfull, S.wloc);
-            alpha_j += S.cfull[j];
-            if (pass == 1 && tid == 0) {
-                double c2 = 0.0;
-                for (int i = 0; i <= j; ++i) c2 = fma(S.cfull[i], S.cfull[i], c2);
-                S.red[kWarps] = sqrt(fmax(S.cfull[j + 1] - c2, 0.0));
+        // ---- local pass against v_{j-1}, v_j, then a full pass against
+        // v_0..v_j that also reduces ||w_1||^2 (||w_2||^2 = ||w_1||^2 - ||c_2||^2)
+        const int ia = j > 0 ? j - 1 : 0;
+        cgs_dots<DF>(B, ldq, r0, nr, ia, j, S.wloc, part[pb], false);
+        __syncthreads();
+        cluster_allreduce(cl, part[pb], S.cfull, S.cdf, ia, j + 1, cs);
+        pb ^= 1;
+        const double a1 = S.cfull[j];
+        cgs_update<DF>(B, ldq, r0, nr, ia, j, S.cfull, S.cdf, S.wloc);
+        __syncthreads();
+        cgs_dots<DF>(B, ldq, r0, nr, 0, j, S.wloc, part[pb], true);
+        __syncthreads();
+        cluster_allreduce(cl, part[pb], S.cfull, S.cdf, 0, j + 2, cs);
+        pb ^= 1;
+        cgs_update<DF>(B, ldq, r0, nr, 0, j, S.cfull, S.cdf, S.wloc);
+        if (warp == 0) {
+            double c2 = 0.0;
+            for (int i = lane; i <= j; i += 32) c2 = fma(S.cfull[i], S.cfull[i], c2);
+            c2 = warp_sum(c2);
+            if (lane == 0) {
+                const double alpha_j = a1 + S.cfull[j];
+                const double beta_j = sqrt(fmax(S.cfull[j + 1] - c2, 0.0));
+                const double tnorm = fmax(S.red[40], fabs(alpha_j) + 2.0 * beta_j);
+                S.alpha[j] = alpha_j;
+                S.beta[j] = beta_j;
+                S.beta2[j] = beta_j * beta_j;
+                S.red[40] = tnorm;
+                S.red[41] = (beta_j <= 1e-12 * tnorm || j + 1 == n) ? 1.0 : 0.0;
+                S.red[42] = beta_j > 0.0 ? 1.0 / beta_j : 0.0;
             }
-            __syncthreads();
         }
-        const double beta_j = S.red[kWarps];
-        if (tid == 0) {
-            S.alpha[j] = alpha_j;
-            S.beta[j] = beta_j;
-            S.beta2[j] = beta_j * beta_j;
-        }
-        tnorm = fmax(tnorm, fabs(alpha_j) + 2.0 * beta_j);
+        __syncthreads();
+        const double beta_j = S.beta[j];
+        const double tnorm = S.red[40];
         k = j + 1;
-        __syncthreads();
-
-        const bool breakdown = beta_j <= 1e-12 * tnorm || k == n;
+        const bool breakdown = S.red[41] != 0.0;
         const bool do_check = breakdown || k == kmax || k >= next_check;
         if (do_check && k >= r) {
+            // the stage rings hold the check's workspace from here on
+            qok = qs_drain(Qs) && qok;
+            __syncthreads();
             // Ritz values and residuals.  Eigenvalue i belongs to CTA i % cs and,
-            // there, to warp m % 4, lane m / 4 (m = i / cs): every FP64 warp
-            // instruction occupies an SMSP's FP64 unit for tens of cycles, so the
-            // r bisections run on as many SMSPs of the cluster as possible.  Each
-            // owner finds theta_i (bisection on Sturm counts, warm-bracketed by the
-            // previous check), the eigenvector x_i of T_k (inverse iteration) and
-            // the residual beta_j |x_i[k-1]|; all CTAs then read every theta and
-            // residual through DSMEM and take the same decision.
+            // there, to warp i / cs: every FP64 warp instruction occupies an
+            // SMSP's FP64 unit for tens of cycles, so the r bisections run on as
+            // many SMSPs of the cluster as possible.  Each owner finds theta_i
+            // (bisection on Sturm counts, warm-bracketed by the previous check),
+            // the eigenvector x_i of T_k (inverse iteration) and the residual
+            // beta_j |x_i[k-1]|; all CTAs then read every theta and residual
+            // through DSMEM and take the same decision.
             const int mine = (r - q + cs - 1) / cs;  // eigenvalues owned by this CTA
             if (warp < mine) {
                 double gl = DBL_MAX, gu = -DBL_MAX;
@@ -576,6 +737,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 gl -= pad;
                 gu += pad;
                 const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+                double* bd = S.band + (size_t)warp * 3 * L;
                 for (int m = warp; m < mine; m += kWarps) {   // one warp per eigenvalue
                     const int i = q + cs * m;
                     double lo = gl, hi = gu;
@@ -592,7 +754,6 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                     }
                     const double th = kth_largest(S.alpha, S.beta2, k, i, lo, hi);
                     if (lane == 0) {
-                        double* bd = S.band + (size_t)m * 3 * L;
                         double* x = S.xv + (size_t)i * L;
                         tri_inverse_iteration(S.alpha, S.beta, k, th, pert, bd, bd + L, bd + 2 * L, x);
                         S.theta[i] = th;
@@ -640,27 +801,38 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             prev_worst = worst;
             prev_k = k;
             next_check = k + gap;
+            if (!breakdown) qs_prime(Qs);   // the stages are Q stages again
         }
         if (breakdown) break;  // k < r: fewer Ritz values than wanted
 
         // ---- v_{j+1} = w / beta_j
-        const double inv = 1.0 / beta_j;
-        for (int rr = tid; rr < nr; rr += kThreads) {
-            const double v = S.wloc[rr] * inv;
-            S.vloc[rr] = v;
-            B[(int64_t)(j + 1) * ldq + r0 + rr] = v;
+        if constexpr (DF) {
+            const float2 binv = df_of(S.red[42]);
+            for (int rr = tid; rr < nr; rr += kThreads) {
+                const float2 v = df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
+                reinterpret_cast<float2*>(S.vloc)[rr] = v;
+                reinterpret_cast<float2*>(B)[(int64_t)(j + 1) * ldq + r0 + rr] = v;
+            }
+        } else {
+            const double binv = S.red[42];
+            for (int rr = tid; rr < nr; rr += kThreads) {
+                const double v = S.wloc[rr] * binv;
+                S.vloc[rr] = v;
+                B[(int64_t)(j + 1) * ldq + r0 + rr] = v;
+            }
         }
         __syncthreads();
     }
 
     // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
-    qchunk = qs_end(Qs, g, qtimeout);
-    if (qtimeout) S.red[40] = 1.0;
+    qok = qs_drain(Qs) && qok;
+    if (!qok) S.red[43] = 1.0;   // zero since the last problem; every writer stores 1
     __syncthreads();
     cl.sync();
     bool any_timeout = false;
-    for (int qq = 0; qq < cs; ++qq) any_timeout |= cl.map_shared_rank(S.red, qq)[40] != 0.0;
+    for (int qq = 0; qq < cs; ++qq) any_timeout |= cl.map_shared_rank(S.red, qq)[43] == 1.0;
     cl.sync();   // every CTA has read the flags before S.red is reused
+    if (tid == 0) S.red[43] = 0.0;
     int status = kDevOk;
     if (k < r || !have_vectors) {
         status = kDevRank;
@@ -713,16 +885,47 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             S.xv[(size_t)i * L + t] = src[(size_t)i * L + t];
         }
     }
+    cl.sync();   // rank 0's vectors have been copied before any CTA rewrites its own
+    if constexpr (DF) {
+        // s_i as double-FP32 pairs, in place
+        for (int e = tid; e < r * k; e += kThreads) {
+            const int i = e / k, t = e % k;
+            double* p = S.xv + (size_t)i * L + t;
+            *reinterpret_cast<float2*>(p) = df_of(*p);
+        }
+    }
     __syncthreads();
 
     // Ritz vectors y_i = V_k s_i for this CTA's rows; per-column |max| for the sign rule.
     double* V = A.varena + P.v_off;
     for (int rr = tid; rr < nr; rr += kThreads) {
-        for (int i = 0; i < r; ++i) {
-            const double* si = S.xv + (size_t)i * L;
-            double s = 0.0;
-            for (int t = 0; t < k; ++t) s = fma(B[(int64_t)t * ldq + r0 + rr], si[t], s);
-            V[(int64_t)(r0 + rr) * r + i] = s;
+        if constexpr (DF) {
+            const float2* b = reinterpret_cast<const float2*>(B) + r0 + rr;
+            for (int ig = 0; ig < r; ig += 8) {
+                float h[8], l[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) h[u] = l[u] = 0.f;
+                for (int t = 0; t < k; ++t) {
+                    const float2 x = b[(int64_t)t * ldq];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (ig + u < r) {
+                            const float2 sv = reinterpret_cast<const float2*>(S.xv + (size_t)(ig + u) * L)[t];
+                            df_madd(h[u], l[u], x.x, x.y, sv.x, sv.y);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (ig + u < r) V[(int64_t)(r0 + rr) * r + ig + u] = (double)h[u] + (double)l[u];
+            }
+        } else {
+            for (int i = 0; i < r; ++i) {
+                const double* si = S.xv + (size_t)i * L;
+                double s = 0.0;
+                for (int t = 0; t < k; ++t) s = fma(B[(int64_t)t * ldq + r0 + rr], si[t], s);
+                V[(int64_t)(r0 + rr) * r + i] = s;
+            }
         }
     }
     __syncthreads();
@@ -794,22 +997,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     const int q = (int)cl.block_rank();
     extern __shared__ __align__(16) double smraw[];
     __shared__ int s_flag, s_next;
-    {
-        const Smem S = carve(smraw, A.max_n, cs, A.mmax, A.r);
-        if (threadIdx.x == 0) {
-            for (int i = 0; i < kWarps * kRing; ++i) tc::mbar_init(&S.full[i], 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
+    const Smem S = carve(smraw, A.max_n, cs, A.mmax, A.r);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWarps * kRing; ++i) tc::mbar_init(&S.full[i], 1);
+        S.red[43] = 0.0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    long long qchunk = 0;   // Q-stream chunks this warp has consumed (all problems)
+    __syncthreads();
+    QStream Qs;
+    Qs.ring = S.ring + (size_t)(threadIdx.x >> 5) * kRing * kChunkB;
+    Qs.full = S.full + (threadIdx.x >> 5) * kRing;
+    Qs.cst = Qs.ist = 0;
+    Qs.inflight = 0;
+    Qs.phase = 0;
     for (;;) {
         if (q == 0 && threadIdx.x == 0) s_next = atomicAdd(A.counter, 1);
         cl.sync();
         const int next = q == 0 ? s_next : *cl.map_shared_rank(&s_next, 0);
         cl.sync();  // every CTA has read the index before rank 0 takes another
         if (next >= A.p) break;
-        solve_problem<DF>(A, A.order[next], cl, cs, q, smraw, s_flag, qchunk);
+        solve_problem<DF>(A, A.order[next], cl, cs, q, S, s_flag, Qs);
     }
 }
 
@@ -821,7 +1028,15 @@ size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
 
 template <bool DF>
 static cudaError_t launch_lanczos_t(const LanczosArgs& a, int cs, cudaStream_t st) {
-    const size_t smem = smem_doubles(a.max_n, cs, a.mmax, a.r) * sizeof(double);
+    const size_t need = smem_doubles(a.max_n, cs, a.mmax, a.r) * sizeof(double);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // Few CTAs in all (a single landmark problem, say): one CTA per SM, so a
+    // cluster spreads over as many SMs as it has CTAs.  Many: two per SM, so
+    // one CTA's reductions and checks overlap the other's Q stream.
+    const size_t one_per_sm = 120 * 1024;
+    const size_t smem = (size_t)a.p * cs <= (size_t)sms && need < one_per_sm ? one_per_sm : need;
     cudaError_t e = cudaFuncSetAttribute(k_lanczos<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (cs > 8) {
