@@ -253,8 +253,9 @@ int mds_server_destroy(mds_server srv);
  *   stage_ms[3] batched Lanczos eigen-solve (top-r eigenpairs)
  *   stage_ms[4] Gower projection / Procrustes alignment and output
  * eig_flops / eig_qbytes: algorithmic FP64 flops of the eigen-solve
- * (2 n^2 per matrix-vector product, 8 n (j+1) per step for two Gram-Schmidt
- * passes, 2 n k r for the Ritz vectors) and bytes of Q read (8 n^2 per step),
+ * (2 n^2 per matrix-vector product, 8 n for the local Gram-Schmidt pass and
+ * 4 n (j+1) for the full one at step j, 2 n k r for the Ritz vectors) and bytes of Q read per step (8 n^2
+ * for FP64 problems, 4 n^2 otherwise, where Q is stored in FP32),
  * summed over the problems of the call with their actual step counts. */
 typedef struct {
     double stage_ms[5];

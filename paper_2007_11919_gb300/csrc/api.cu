@@ -127,6 +127,7 @@ int check_ws(const Opts& o, size_t need) {
 struct Batch {
     std::vector<ProbDesc> desc;
     int p = 0, max_n = 0, max_tiles = 0, mmax = 0, r = 0;
+    int q_bytes = 8;                   // bytes per entry of Q as the eigen-solver reads it
     size_t q_el = 0, rp_el = 0, rm_el = 0, b_el = 0, v_el = 0;
     ProbDesc* d_desc = nullptr;
     double *q = nullptr, *rp = nullptr, *rm = nullptr, *grand = nullptr, *b = nullptr,
@@ -221,10 +222,12 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
                                  B.q, B.rp, o.st));
     }
     tmark(1, o.st);
-    // FP64 precision keeps an IEEE FP64 product; the other precisions, whose Q
-    // carries FP32-level distance rounding anyway, use the double-FP32 product.
-    const int q_df = o.prec != MDS_PREC_F64;
-    CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, q_df, o.st));
+    // FP64 precision keeps Q and the products in IEEE FP64.  The other
+    // precisions, whose Q carries FP32-level distance rounding anyway, store Q
+    // in FP32 and run the products and vector work in double-FP32.
+    const int q_f32 = o.prec != MDS_PREC_F64;
+    B.q_bytes = q_f32 ? 4 : 8;
+    CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, q_f32, o.st));
     LanczosArgs a;
     a.desc = B.d_desc;
     a.p = B.p;
@@ -236,7 +239,7 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.steps = B.steps;
     a.scratch = B.scr;
     a.order = B.d_order;
-    a.q_df = q_df;
+    a.q_f32 = q_f32;
     a.counter = B.counter;
     a.r = B.r;
     a.mmax = B.mmax;
@@ -270,8 +273,8 @@ int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr =
         for (int j = 0; j < B->p; ++j) {
             const double n = B->desc[j].n, k = steps[j];
             g_last.eig_steps += steps[j];
-            g_last.eig_flops += 2.0 * n * n * k + 4.0 * n * k * (k + 1) + 2.0 * n * k * B->r;
-            g_last.eig_qbytes += 8.0 * n * n * k;
+            g_last.eig_flops += 2.0 * n * n * k + 8.0 * n * k + 2.0 * n * k * (k + 1) + 2.0 * n * k * B->r;
+            g_last.eig_qbytes += (double)B->q_bytes * n * n * k;
         }
     }
     if (g_timing)

@@ -127,10 +127,10 @@ cudaError_t launch_load_dist(const double* D2, const ProbDesc* desc, double* qar
                              double* rparena, int n, int tiles, cudaStream_t st);
 
 // Double centering in place: Q = -1/2 (Delta - m 1^T - 1 m^T + g) per problem,
-// computed in FP64; stored as FP64, or (q_df) as the float pair
-// (hi = fl32(q), lo = fl32(q - hi)) in the same 8 bytes.
+// computed in FP64; stored as FP64, or (q_f32) as FP32 at the start of each
+// row's storage (row stride 2 * ldq floats, zero-padded to a multiple of 4).
 cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double* qarena,
-                                  const double* rparena, double* rmarena, double* grand, int q_df,
+                                  const double* rparena, double* rmarena, double* grand, int q_f32,
                                   cudaStream_t st);
 
 struct LanczosArgs {
@@ -144,7 +144,7 @@ struct LanczosArgs {
     int* steps;         // p
     double* scratch;    // p x lanczos_scratch_per_problem(mmax, r) doubles
     const int* order;   // p problem indices, the order in which clusters take them
-    int q_df;           // Q stored as double-FP32 (hi, lo) float pairs, product in double-FP32
+    int q_f32;          // Q stored as FP32 (row stride 2 * ldq floats), vectors in double-FP32
     int* counter;       // queue head, zero before the launch
     int r;
     int mmax;
@@ -165,7 +165,7 @@ constexpr size_t kMaxSmem = 220 * 1024;
 // W and X1 are written in double (w64/x1_64) and float (w32/x1_32) when the
 // pointers are not null.
 cudaError_t launch_interp_model(const double* V, const double* lam, const double* Qdiag_src,
-                                int ldq, int q_df, int l, int r, double* w64, float* w32,
+                                int ldq, int q_f32, int l, int r, double* w64, float* w32,
                                 double* x1_64, float* x1_32, double* bias, double* var_out,
                                 cudaStream_t st);
 

@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(256) k_rowmean(const ProbDesc* __restrict__ de
     }
 }
 
-template <bool DF>
+// Q = -1/2 P Delta P in place, row a of part blockIdx.y.  F32: the row is
+// rewritten as n floats at the start of its own storage (zero-padded to a
+// multiple of 4), chunk by chunk: a chunk's floats overlap only doubles of
+// chunks already read, and the whole chunk is read before any of it is written.
+template <bool F32>
 __global__ void __launch_bounds__(256) k_center(const ProbDesc* __restrict__ desc,
                                                 double* __restrict__ qarena,
                                                 const double* __restrict__ rmarena,
@@ -196,14 +200,17 @@ __global__ void __launch_bounds__(256) k_center(const ProbDesc* __restrict__ des
     const double g = grand[blockIdx.y];
     const double ma = rm[a];
     double* Q = qarena + P.q_off + (int64_t)a * P.ldq;
-    for (int b = threadIdx.x; b < P.n; b += 256) {
-        const double qv = -0.5 * (Q[b] - ma - rm[b] + g);
-        if (DF) {
-            const float h = (float)qv;
-            reinterpret_cast<float2*>(Q)[b] = make_float2(h, (float)(qv - (double)h));
-        } else {
-            Q[b] = qv;
+    if (F32) {
+        float* Qf = reinterpret_cast<float*>(Q);
+        const int n4 = (int)round_up(P.n, 4);
+        for (int c0 = 0; c0 < n4; c0 += 256) {
+            const int b = c0 + (int)threadIdx.x;
+            const float qv = b < P.n ? (float)(-0.5 * (Q[b] - ma - rm[b] + g)) : 0.f;
+            __syncthreads();
+            if (b < n4) Qf[b] = qv;
         }
+    } else {
+        for (int b = threadIdx.x; b < P.n; b += 256) Q[b] = -0.5 * (Q[b] - ma - rm[b] + g);
     }
 }
 
@@ -310,11 +317,11 @@ cudaError_t launch_load_dist(const double* D2, const ProbDesc* desc, double* qar
 }
 
 cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double* qarena,
-                                  const double* rparena, double* rmarena, double* grand, int q_df,
+                                  const double* rparena, double* rmarena, double* grand, int q_f32,
                                   cudaStream_t st) {
     if (p <= 0) return cudaSuccess;
     k_rowmean<<<p, 256, 0, st>>>(desc, rparena, rmarena, grand);
-    if (q_df) k_center<true><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
+    if (q_f32) k_center<true><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
     else k_center<false><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
     note_launch(2);
     return cudaGetLastError();

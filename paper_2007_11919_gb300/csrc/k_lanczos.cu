@@ -20,10 +20,11 @@
 //   Gram-Schmidt) and the Ritz vectors are y_i = V_k s_i.
 //
 // Arithmetic: the scalars (alpha, beta, Gram-Schmidt coefficients) and the
-// tridiagonal work are FP64.  The O(n^2) matrix-vector product and the O(n k)
-// vector work are FP64 for FP64 problems and double-FP32 otherwise (a value is
-// an unevaluated pair of floats, ~48 significant bits): GB300 issues FP64 at
-// 1/64 of its FP32 rate.  Q, the basis and the working vectors take 8 bytes
+// tridiagonal work are FP64.  For FP64 problems Q and every vector are FP64.
+// Otherwise Q (double-centred in FP64 from FP32 distances) is stored in FP32
+// and the products and all O(n k) vector work run in double-FP32 (a value is
+// an unevaluated pair of floats, ~48 significant bits), because GB300 issues
+// FP64 at 1/64 of its FP32 rate; the basis and working vectors take 8 bytes
 // per entry either way.
 //
 // Layout: Q_j row-major (ld = ldq).  The cluster's CTAs own contiguous row
@@ -62,7 +63,7 @@ struct Smem {
     double* xv;      // (in the ring) r x (mmax + 1): eigenvectors x_i of T_k
     double* band;    // (in the ring) per eigenvalue-owning warp 3 x (mmax + 1): U bands
     uint64_t* full;  // kWarps * kRing stage mbarriers
-    double* vfull;   // max_n + 2 entries: the full current Lanczos vector
+    double* vfull;   // max_n + 4 entries: the full current Lanczos vector
     double* vloc;    // rmax : this CTA's slice of v_j
     double* wloc;    // rmax : this CTA's slice of w
     double* part0;   // mmax + 2 : partial sums published to the cluster
@@ -90,7 +91,7 @@ __host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
 
 __host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
-    return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 2, 2) + 2 * round_up(rmax, 2) +
+    return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 4, 4) + 2 * round_up(rmax, 2) +
            4 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8;
 }
 
@@ -103,7 +104,7 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     s.band = p + (size_t)r * (mmax + 1);
     p += ring_doubles(cs, mmax, r);
     s.full = reinterpret_cast<uint64_t*>(p); p += kWarps * kRing;
-    s.vfull = p; p += round_up(max_n + 2, 2);
+    s.vfull = p; p += round_up(max_n + 4, 4);
     s.vloc = p; p += round_up(rmax, 2);
     s.wloc = p; p += round_up(rmax, 2);
     s.part0 = p; p += mmax + 2;
@@ -297,6 +298,19 @@ __device__ __forceinline__ void df_madd(float& sh, float& sl, float qh, float ql
     sh = s;
 }
 
+// sh + sl += q * (vh + vl) for an FP32 entry q (the product q * vh is split
+// exactly by the FMA; q * vl only needs FP32).
+__device__ __forceinline__ void df_madd1(float& sh, float& sl, float q, float vh, float vl) {
+    const float p = __fmul_rn(q, vh);
+    float e = fmaf(q, vh, -p);
+    e = fmaf(q, vl, e);
+    const float s = __fadd_rn(sh, p);
+    const float z = __fsub_rn(s, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+    sh = s;
+}
+
 __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
     const float s = __fadd_rn(sh, oh);
     const float z = __fsub_rn(s, sh);
@@ -342,7 +356,7 @@ __device__ __forceinline__ void df_warp_sum(float& sh, float& sl) {
 struct QStream {
     const uint8_t* q;   // Q of the problem
     size_t stride;      // bytes per row of Q (ldq * 8)
-    int rowbytes;       // bytes a row's copies cover: round_up(n, 2) * 8
+    int rowbytes;       // bytes a row's copies cover: FP32 round_up(n, 4) * 4, FP64 round_up(n, 2) * 8
     int nseg, segb;     // segments per row and bytes per segment (the last may be shorter)
     int wr0, per_step;  // first row of this warp and segments per step
     uint8_t* ring;      // this warp's stages
@@ -413,13 +427,14 @@ __device__ __forceinline__ bool qs_drain(QStream& s) {
 }
 
 // Sets up the warp's stream for a problem and issues its first chunks.
+template <bool DF>
 __device__ __forceinline__ void qs_setup(QStream& s, const double* Q, int ldq, int n, int r0, int nr) {
     const int warp = threadIdx.x >> 5;
     const int per_warp = (nr + kWarps - 1) / kWarps;
     const int a = min(nr, warp * per_warp), b = min(nr, (warp + 1) * per_warp);
     s.q = reinterpret_cast<const uint8_t*>(Q);
     s.stride = (size_t)ldq * 8;
-    s.rowbytes = (int)round_up(n, 2) * 8;
+    s.rowbytes = DF ? (int)round_up(n, 4) * 4 : (int)round_up(n, 2) * 8;
     s.nseg = (s.rowbytes + kChunkB - 1) / kChunkB;
     s.segb = (int)round_up((s.rowbytes + s.nseg - 1) / s.nseg, 16);
     s.wr0 = r0 + a;
@@ -444,22 +459,31 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
     bool ok = true;
     s.issue_left = s.per_step - s.inflight + (prefetch ? min(kRing, s.per_step) : 0);
     qs_fill(s);
-    float sh = 0.f, sl = 0.f;
+    // two accumulators per lane (alternate entries) for instruction-level parallelism
+    float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
     double acc = 0.0;
     for (int u = 0; u < s.per_step; ++u) {
         ok = qs_wait_front(s) && ok;
         const int row = s.wr0 + s.cpos / s.nseg, seg = s.cpos % s.nseg;
-        const int col0 = seg * (s.segb / 8);
         const int bytes = min(s.segb, s.rowbytes - seg * s.segb);
         const uint8_t* stage = s.ring + (size_t)s.cst * kChunkB;
-        for (int t = lane; t < bytes / 16; t += 32) {
-            const int c = col0 + 2 * t;
-            if constexpr (DF) {
+        if constexpr (DF) {
+            // FP32 Q: 4 entries per 16 bytes; the row's padding entries are zero
+            // and so are the vector's guard entries
+            const int col0 = seg * (s.segb / 4);
+            for (int t = lane; t < bytes / 16; t += 32) {
                 const float4 x = reinterpret_cast<const float4*>(stage)[t];
-                const float4 vv = reinterpret_cast<const float4*>(vfull)[c >> 1];
-                df_madd(sh, sl, x.x, x.y, vv.x, vv.y);
-                if (c + 1 < n) df_madd(sh, sl, x.z, x.w, vv.z, vv.w);
-            } else {
+                const float4 va = reinterpret_cast<const float4*>(vfull)[(col0 >> 1) + 2 * t];
+                const float4 vb = reinterpret_cast<const float4*>(vfull)[(col0 >> 1) + 2 * t + 1];
+                df_madd1(sh, sl, x.x, va.x, va.y);
+                df_madd1(th, tl, x.y, va.z, va.w);
+                df_madd1(sh, sl, x.z, vb.x, vb.y);
+                df_madd1(th, tl, x.w, vb.z, vb.w);
+            }
+        } else {
+            const int col0 = seg * (s.segb / 8);
+            for (int t = lane; t < bytes / 16; t += 32) {
+                const int c = col0 + 2 * t;
                 const double2 x = reinterpret_cast<const double2*>(stage)[t];
                 const double2 vv = reinterpret_cast<const double2*>(vfull)[c >> 1];
                 acc = fma(x.x, vv.x, acc);
@@ -471,9 +495,10 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
         qs_fill(s);   // the stage is free: next chunk of the periodic stream
         if (seg == s.nseg - 1) {
             if constexpr (DF) {
+                df_add(sh, sl, th, tl);
                 df_warp_sum(sh, sl);
                 if (lane == 0) reinterpret_cast<float2*>(w)[row - r0] = df_norm(sh, sl);
-                sh = sl = 0.f;
+                sh = sl = th = tl = 0.f;
             } else {
                 acc = warp_sum(acc);
                 if (lane == 0) w[row - r0] = acc;
@@ -617,7 +642,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     bool qok = true;
 
     // start streaming this warp's rows of Q right away
-    qs_setup(Qs, Q, ldq, n, r0, nr);
+    qs_setup<DF>(Qs, Q, ldq, n, r0, nr);
 
     // ---- start vector: pseudo-random, unit norm
     double loc = 0.0;
@@ -647,8 +672,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         }
     }
     if (tid == 0) {
-        S.vfull[n] = 0.0;   // guard entries read by the paired loads when n is odd
-        S.vfull[n + 1] = 0.0;
+        for (int i = n; i < (int)round_up(n, 4); ++i) S.vfull[i] = 0.0;   // guard entries of the padded loads
         S.red[40] = 0.0;    // tnorm
     }
 
@@ -1068,7 +1092,7 @@ static cudaError_t launch_lanczos_t(const LanczosArgs& a, int cs, cudaStream_t s
 cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
     if (a.p <= 0) return cudaSuccess;
     const int cs = cluster < 1 ? 1 : (cluster > 16 ? 16 : cluster);
-    return a.q_df ? launch_lanczos_t<true>(a, cs, st) : launch_lanczos_t<false>(a, cs, st);
+    return a.q_f32 ? launch_lanczos_t<true>(a, cs, st) : launch_lanczos_t<false>(a, cs, st);
 }
 
 }  // namespace gbmds

@@ -18,7 +18,7 @@ namespace {
 __global__ void __launch_bounds__(256) k_interp_model(const double* __restrict__ V,
                                                       const double* __restrict__ lam,
                                                       const double* __restrict__ Q, int ldq,
-                                                      int q_df, int l, int r, double* w64, float* w32,
+                                                      int q_f32, int l, int r, double* w64, float* w32,
                                                       double* x1_64, float* x1_32,
                                                       double* __restrict__ bias,
                                                       double* var_out) {
@@ -38,9 +38,8 @@ __global__ void __launch_bounds__(256) k_interp_model(const double* __restrict__
         double s = 0.0;
         for (int a = lane; a < l; a += 32) {
             double qaa;
-            if (q_df) {
-                const float2 h = reinterpret_cast<const float2*>(Q)[(int64_t)a * ldq + a];
-                qaa = (double)h.x + (double)h.y;
+            if (q_f32) {
+                qaa = (double)reinterpret_cast<const float*>(Q)[(int64_t)a * 2 * ldq + a];
             } else {
                 qaa = Q[(int64_t)a * ldq + a];
             }
@@ -177,9 +176,9 @@ __global__ void k_classical_out(const double* __restrict__ V, const double* __re
 }  // namespace
 
 cudaError_t launch_interp_model(const double* V, const double* lam, const double* Q, int ldq,
-                                int q_df, int l, int r, double* w64, float* w32, double* x1_64,
+                                int q_f32, int l, int r, double* w64, float* w32, double* x1_64,
                                 float* x1_32, double* bias, double* var_out, cudaStream_t st) {
-    k_interp_model<<<1, 256, 0, st>>>(V, lam, Q, ldq, q_df, l, r, w64, w32, x1_64, x1_32, bias, var_out);
+    k_interp_model<<<1, 256, 0, st>>>(V, lam, Q, ldq, q_f32, l, r, w64, w32, x1_64, x1_32, bias, var_out);
     note_launch(1);
     return cudaGetLastError();
 }
