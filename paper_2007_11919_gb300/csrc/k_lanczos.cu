@@ -62,6 +62,7 @@ struct Smem {
     uint8_t* ring;   // per-warp Q stages while streaming; the check workspace otherwise
     double* xv;      // (in the ring) r x (mmax + 1): eigenvectors x_i of T_k
     double* band;    // (in the ring) per eigenvalue-owning warp 3 x (mmax + 1): U bands
+    double* tri;     // (in the ring) 3 x (mmax + 1): scaled alpha, beta, beta^2 as double-FP32
     uint64_t* full;  // kWarps * kRing stage mbarriers
     double* vfull;   // max_n + 4 entries: the full current Lanczos vector
     double* vloc;    // rmax : this CTA's slice of v_j
@@ -84,7 +85,7 @@ __host__ __device__ inline int owned_max(int r, int cs) { return (r + cs - 1) / 
 // Doubles of the ring region: the Q stages or the check workspace, whichever is larger.
 __host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
     const int own = owned_max(r, cs) < kWarps ? owned_max(r, cs) : kWarps;
-    const size_t check = (size_t)(r + 3 * own) * (mmax + 1);
+    const size_t check = (size_t)(r + 3 * own + 3) * (mmax + 1);
     const size_t q = kRingBytes / 8;
     return (size_t)round_up((int64_t)(q > check ? q : check), 16);
 }
@@ -102,6 +103,10 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     s.ring = reinterpret_cast<uint8_t*>(p);
     s.xv = p;
     s.band = p + (size_t)r * (mmax + 1);
+    {
+        const int own = owned_max(r, cs) < kWarps ? owned_max(r, cs) : kWarps;
+        s.tri = s.band + (size_t)3 * own * (mmax + 1);
+    }
     p += ring_doubles(cs, mmax, r);
     s.full = reinterpret_cast<uint64_t*>(p); p += kWarps * kRing;
     s.vfull = p; p += round_up(max_n + 4, 4);
@@ -119,165 +124,6 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     s.red = p; p += 64;
     s.sgn = p; p += 4 * kMaxR;
     return s;
-}
-
-// Sum of one value per thread over the CTA, in a fixed order.  Result valid
-// in thread 0.  Contains __syncthreads.
-__device__ double block_sum(double v, double* red) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < kWarps; ++i) s += red[i];
-    return s;
-}
-
-__device__ __forceinline__ float2 df_of(double x);
-
-// out[i] = sum over cluster ranks (in rank order) of part[i], lo <= i < hi;
-// outdf (when not null) receives the sums as double-FP32 pairs.
-__device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* out, double* outdf, int lo, int hi,
-                                  int cs) {
-    cl.sync();
-    for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
-        double s = 0.0;
-        for (int qq = 0; qq < cs; ++qq) s += cl.map_shared_rank(part, qq)[i];
-        out[i] = s;
-        if (outdf) reinterpret_cast<float2*>(outdf)[i] = df_of(s);
-    }
-    __syncthreads();
-}
-
-// Number of eigenvalues of T (alpha, beta^2) smaller than x: the sign changes
-// of the Sturm sequence p_0 = 1, p_t = det(T_t - x I) =
-// (alpha_{t-1} - x) p_{t-1} - beta_{t-2}^2 p_{t-2} (a sign change between
-// p_{t-1} and p_t is a negative pivot of T - x I = L D L^T).  No division: the
-// pair (p_{t-1}, p_t) is rescaled by exact powers of two to stay in range, and
-// an exact zero counts as a sign change (a tiny negative pivot).
-__device__ int sturm_count(const double* al, const double* b2, int k, double x) {
-    double pm = 1.0, p = al[0] - x;
-    if (p == 0.0) p = -1e-300;
-    int c = p < 0.0;
-    for (int t = 1; t < k; ++t) {
-        double pn = fma(al[t] - x, p, -b2[t - 1] * pm);
-        if (pn == 0.0) pn = -p * 1e-300;
-        c += (pn < 0.0) != (p < 0.0);
-        pm = p;
-        p = pn;
-        const double ap = fabs(p);
-        if (ap > 0x1p+500) {
-            p *= 0x1p-500;
-            pm *= 0x1p-500;
-        } else if (ap < 0x1p-500 && fabs(pm) < 0x1p-500) {
-            p *= 0x1p+500;
-            pm *= 0x1p+500;
-        }
-    }
-    return c;
-}
-
-// The i-th largest eigenvalue of T on [lo, hi] (count(lo) <= k-1-i < count(hi))
-// by 32-way multisection: each lane of the calling warp counts at its own probe,
-// so every FP64 warp instruction (which occupies the SMSP's FP64 unit for the
-// whole warp whatever the mask) does 32 useful Sturm steps.  ~11 rounds.
-__device__ double kth_largest(const double* al, const double* b2, int k, int i, double lo, double hi) {
-    const int lane = threadIdx.x & 31;
-    const int target = k - 1 - i;
-    for (int round = 0; round < 16; ++round) {
-        const double step = (hi - lo) * (1.0 / 33.0);
-        const double x = fmin(fma((double)(lane + 1), step, lo), hi);
-        const unsigned ball = __ballot_sync(0xffffffffu, sturm_count(al, b2, k, x) > target);
-        const int first = ball ? __ffs(ball) - 1 : 32;
-        const double xf = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
-        const double xp = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
-        if (first < 32) hi = xf;
-        if (first > 0) lo = xp;
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) break;
-    }
-    return 0.5 * (lo + hi);
-}
-
-// 1/x by Newton-Raphson iteration y <- y (2 - x y) from the FP32 reciprocal:
-// 24 -> 48 -> 96 correct bits (limited by FP64), in four FP64 instructions.
-__device__ __forceinline__ double rcp_newton(double x) {
-    const float xf = (float)x;
-    if (!(fabsf(xf) > 1e-30f && fabsf(xf) < 1e30f)) return 1.0 / x;
-    double y = (double)__frcp_rn(xf);
-    y = y * fma(-x, y, 2.0);
-    y = y * fma(-x, y, 2.0);
-    return y;
-}
-
-// Inverse iteration for the eigenvector of T for eigenvalue th (unit 2-norm),
-// all in shared memory.  Each iteration factors T - th I = P L U by Gaussian
-// elimination with partial pivoting (U has the bands 1/u0, u1, u2) while it
-// applies the same row operations to the right-hand side x, then solves with
-// U from the bottom up: one division per row.  Two iterations from a fixed
-// positive start vector (th is accurate to a few ulps).
-__device__ void tri_inverse_iteration(const double* al, const double* be, int k, double th,
-                                      double pert, double* u0i, double* u1, double* u2,
-                                      double* x) {
-    for (int t = 0; t < k; ++t) x[t] = 1.0 + 0.25 * (double)((t * 7919) % 13) / 13.0;
-    for (int it = 0; it < 2; ++it) {
-        // working row t: entries (w0, w1) in columns t, t+1 and right-hand side yw
-        double w0 = al[0] - th, w1 = k > 1 ? be[0] : 0.0, yw = x[0];
-        for (int t = 0; t < k - 1; ++t) {
-            const double l0 = be[t];                           // row t+1, column t
-            const double l1 = al[t + 1] - th;                  // row t+1, column t+1
-            const double l2 = t + 2 < k ? be[t + 1] : 0.0;     // row t+1, column t+2
-            const double yl = x[t + 1];
-            if (fabs(w0) >= fabs(l0)) {                        // pivot on the working row
-                if (w0 == 0.0) w0 = pert;
-                const double inv = rcp_newton(w0);
-                const double f = l0 * inv;
-                u0i[t] = inv;
-                u1[t] = w1;
-                u2[t] = 0.0;
-                x[t] = yw;
-                w0 = l1 - f * w1;
-                w1 = l2;
-                yw = yl - f * yw;
-            } else {                                           // pivot on row t+1
-                const double inv = rcp_newton(l0);
-                const double f = w0 * inv;
-                u0i[t] = inv;
-                u1[t] = l1;
-                u2[t] = l2;
-                x[t] = yl;
-                w0 = w1 - f * l1;
-                w1 = -f * l2;
-                yw = yw - f * yl;
-            }
-        }
-        if (w0 == 0.0) w0 = pert;
-        u0i[k - 1] = rcp_newton(w0);
-        x[k - 1] = yw * u0i[k - 1];
-        if (k > 1) x[k - 2] = (x[k - 2] - u1[k - 2] * x[k - 1]) * u0i[k - 2];
-        for (int t = k - 3; t >= 0; --t) x[t] = (x[t] - u1[t] * x[t + 1] - u2[t] * x[t + 2]) * u0i[t];
-        double mx = 0.0;
-        for (int t = 0; t < k; ++t) mx = fmax(mx, fabs(x[t]));
-        if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
-        const double imx = 1.0 / mx;
-        double ss = 0.0;
-        for (int t = 0; t < k; ++t) {
-            x[t] *= imx;
-            ss += x[t] * x[t];
-        }
-        const double inv = 1.0 / sqrt(ss);
-        for (int t = 0; t < k; ++t) x[t] *= inv;
-    }
-}
-
-__device__ __forceinline__ double start_entry(int row) {
-    // splitmix64 of the row index -> uniform in [-1, 1)
-    uint64_t z = (uint64_t)row * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
 // Double-FP32 arithmetic (Dekker 1971; Knuth's TwoSum): a value is an
@@ -345,6 +191,188 @@ __device__ __forceinline__ void df_warp_sum(float& sh, float& sl) {
         const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
         df_add(sh, sl, oh, ol);
     }
+}
+
+// Sum of one value per thread over the CTA, in a fixed order.  Result valid
+// in thread 0.  Contains __syncthreads.
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kWarps; ++i) s += red[i];
+    return s;
+}
+
+// out[i] = sum over cluster ranks (in rank order) of part[i], lo <= i < hi;
+// outdf (when not null) receives the sums as double-FP32 pairs.
+__device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* out, double* outdf, int lo, int hi,
+                                  int cs) {
+    cl.sync();
+    for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
+        double s = 0.0;
+        for (int qq = 0; qq < cs; ++qq) s += cl.map_shared_rank(part, qq)[i];
+        out[i] = s;
+        if (outdf) reinterpret_cast<float2*>(outdf)[i] = df_of(s);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------- tridiagonal eigen-work
+//
+// The checks work on T_k scaled by an exact power of two to norm ~1 (counts
+// and eigenvectors do not change), in double-FP32 arithmetic: every FP64
+// warp instruction occupies an SMSP's FP64 unit for tens of cycles on GB300,
+// while these recurrences are short dependent chains of FP32 operations.
+
+// x - y, x * y and 1 / x for renormalised double-FP32 values.
+__device__ __forceinline__ float2 df_sub2(float2 x, float2 y) {
+    const float s = __fsub_rn(x.x, y.x);
+    const float z = __fsub_rn(s, x.x);
+    float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s, z)), __fsub_rn(-y.x, z));   // TwoSum error
+    e = __fadd_rn(e, __fsub_rn(x.y, y.y));
+    return df_norm(s, e);
+}
+__device__ __forceinline__ float2 df_mul2(float2 x, float2 y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = fmaf(x.x, y.x, -p);
+    e = fmaf(x.x, y.y, e);
+    e = fmaf(x.y, y.x, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ float2 df_rcp2(float2 x) {
+    const float y0 = __frcp_rn(x.x);
+    const float2 r = df_sub2(make_float2(1.f, 0.f), df_mul2(x, make_float2(y0, 0.f)));   // 1 - x y0
+    return df_norm(y0, __fmul_rn(y0, r.x));                                           // y0 (1 + r)
+}
+__device__ __forceinline__ float2 df_scale(float2 x, float s) { return make_float2(x.x * s, x.y * s); }
+
+// Number of eigenvalues of T (a, b2 = beta^2, scaled) smaller than x: the sign
+// changes of the Sturm sequence p_0 = 1, p_t = det(T_t - x I) =
+// (a_{t-1} - x) p_{t-1} - b2_{t-2} p_{t-2} (a sign change between p_{t-1} and
+// p_t is a negative pivot of T - x I = L D L^T).  No division: the pair
+// (p_{t-1}, p_t) is rescaled by exact powers of two to stay in range, and an
+// exact zero counts as a sign change (a tiny negative pivot).
+__device__ int sturm_count_df(const float2* a, const float2* b2, int k, float2 x) {
+    float2 pm = make_float2(1.f, 0.f), p = df_sub2(a[0], x);
+    if (p.x == 0.f) p = make_float2(-0x1p-100f, 0.f);
+    int c = p.x < 0.f;
+    for (int t = 1; t < k; ++t) {
+        float2 pn = df_sub2(df_mul2(df_sub2(a[t], x), p), df_mul2(b2[t - 1], pm));
+        if (pn.x == 0.f) pn = make_float2(-p.x * 0x1p-40f, 0.f);
+        c += (pn.x < 0.f) != (p.x < 0.f);
+        pm = p;
+        p = pn;
+        const float ap = fabsf(p.x);
+        if (ap > 0x1p+60f) {
+            p = df_scale(p, 0x1p-60f);
+            pm = df_scale(pm, 0x1p-60f);
+        } else if (ap < 0x1p-60f && fabsf(pm.x) < 0x1p-60f) {
+            p = df_scale(p, 0x1p+60f);
+            pm = df_scale(pm, 0x1p+60f);
+        }
+    }
+    return c;
+}
+
+// The i-th largest eigenvalue of T on [lo, hi] (count(lo) <= k-1-i < count(hi))
+// by 32-way multisection: each lane of the calling warp counts at its own
+// probe.  lo, hi and the result are unscaled FP64; the counts run on the
+// scaled arrays at x * scale.  Stops at ~2^-44 relative width.
+__device__ double kth_largest_df(const float2* a, const float2* b2, int k, int i, double lo, double hi,
+                                 double scale) {
+    const int lane = threadIdx.x & 31;
+    const int target = k - 1 - i;
+    for (int round = 0; round < 16; ++round) {
+        const double step = (hi - lo) * (1.0 / 33.0);
+        const double x = fmin(fma((double)(lane + 1), step, lo), hi);
+        const unsigned ball = __ballot_sync(0xffffffffu, sturm_count_df(a, b2, k, df_of(x * scale)) > target);
+        const int first = ball ? __ffs(ball) - 1 : 32;
+        const double xf = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
+        const double xp = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+        if (first < 32) hi = xf;
+        if (first > 0) lo = xp;
+        if (hi - lo <= 0x1p-44 * fmax(fabs(lo), fabs(hi))) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Inverse iteration for the eigenvector of T (a, b scaled) for eigenvalue th
+// (scaled), by lane 0 of a warp, in shared memory: each iteration factors
+// T - th I = P L U by Gaussian elimination with partial pivoting (U has the
+// bands 1/u0, u1, u2) while it applies the same row operations to the
+// right-hand side x, then solves with U from the bottom up.  Two iterations
+// from a fixed positive start vector; x leaves with unit 2-norm.
+__device__ void tri_inverse_iteration_df(const float2* a, const float2* b, int k, float2 th, float2 pert,
+                                         float2* u0i, float2* u1, float2* u2, float2* x) {
+    for (int t = 0; t < k; ++t) x[t] = make_float2(1.f + 0.25f * (float)((t * 7919) % 13) / 13.f, 0.f);
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int it = 0; it < 2; ++it) {
+        // working row t: entries (w0, w1) in columns t, t+1 and right-hand side yw
+        float2 w0 = df_sub2(a[0], th), w1 = k > 1 ? b[0] : zero, yw = x[0];
+        for (int t = 0; t < k - 1; ++t) {
+            const float2 l0 = b[t];                            // row t+1, column t
+            const float2 l1 = df_sub2(a[t + 1], th);           // row t+1, column t+1
+            const float2 l2 = t + 2 < k ? b[t + 1] : zero;     // row t+1, column t+2
+            const float2 yl = x[t + 1];
+            if (fabsf(w0.x) >= fabsf(l0.x)) {                  // pivot on the working row
+                if (w0.x == 0.f) w0 = pert;
+                const float2 inv = df_rcp2(w0);
+                const float2 f = df_mul2(l0, inv);
+                u0i[t] = inv;
+                u1[t] = w1;
+                u2[t] = zero;
+                x[t] = yw;
+                w0 = df_sub2(l1, df_mul2(f, w1));
+                w1 = l2;
+                yw = df_sub2(yl, df_mul2(f, yw));
+            } else {                                           // pivot on row t+1
+                const float2 inv = df_rcp2(l0);
+                const float2 f = df_mul2(w0, inv);
+                u0i[t] = inv;
+                u1[t] = l1;
+                u2[t] = l2;
+                x[t] = yl;
+                w0 = df_sub2(w1, df_mul2(f, l1));
+                w1 = df_mul2(make_float2(-f.x, -f.y), l2);
+                yw = df_sub2(yw, df_mul2(f, yl));
+            }
+        }
+        if (w0.x == 0.f) w0 = pert;
+        u0i[k - 1] = df_rcp2(w0);
+        x[k - 1] = df_mul2(yw, u0i[k - 1]);
+        if (k > 1) x[k - 2] = df_mul2(df_sub2(x[k - 2], df_mul2(u1[k - 2], x[k - 1])), u0i[k - 2]);
+        for (int t = k - 3; t >= 0; --t)
+            x[t] = df_mul2(df_sub2(df_sub2(x[t], df_mul2(u1[t], x[t + 1])), df_mul2(u2[t], x[t + 2])), u0i[t]);
+        // scale by a power of two (largest entry ~1), then to unit norm
+        float mx = 0.f;
+        for (int t = 0; t < k; ++t) mx = fmaxf(mx, fabsf(x[t].x));
+        if (!(mx > 0.f) || !isfinite(mx)) mx = 1.f;
+        int ex;
+        frexpf(mx, &ex);
+        const float sc = ldexpf(1.f, -ex);
+        float sh = 0.f, sl = 0.f;
+        for (int t = 0; t < k; ++t) {
+            x[t] = df_scale(x[t], sc);
+            df_madd(sh, sl, x[t].x, x[t].y, x[t].x, x[t].y);
+        }
+        const float2 inv = df_of(1.0 / sqrt((double)sh + (double)sl));
+        for (int t = 0; t < k; ++t) x[t] = df_mul2(x[t], inv);
+    }
+}
+
+// Entry `row` of the fixed pseudo-random start vector (splitmix64 of the row
+// index, mapped to [-1, 1)).
+__device__ __forceinline__ double start_entry(int row) {
+    // splitmix64 of the row index -> uniform in [-1, 1)
+    uint64_t z = (uint64_t)row * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
 // ---------------------------------------------------------------- Q stream
@@ -746,6 +774,20 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             // beta_j |x_i[k-1]|; all CTAs then read every theta and residual
             // through DSMEM and take the same decision.
             const int mine = (r - q + cs - 1) / cs;  // eigenvalues owned by this CTA
+            // T_k scaled by a power of two to norm ~1, as double-FP32 arrays
+            int ex;
+            frexp(tnorm, &ex);
+            const double scale = ldexp(1.0, -ex);
+            float2* adf = reinterpret_cast<float2*>(S.tri);
+            float2* bdf = adf + L;
+            float2* b2df = bdf + L;
+            if (mine > 0)
+                for (int t = tid; t < k; t += kThreads) {
+                    adf[t] = df_of(S.alpha[t] * scale);
+                    bdf[t] = df_of(S.beta[t] * scale);
+                    b2df[t] = df_of(S.beta2[t] * (scale * scale));
+                }
+            __syncthreads();
             if (warp < mine) {
                 double gl = DBL_MAX, gu = -DBL_MAX;
                 for (int t = lane; t < k; t += 32) {
@@ -760,8 +802,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const double pad = 2.0 * DBL_EPSILON * fmax(fabs(gl), fabs(gu)) * k + DBL_MIN;
                 gl -= pad;
                 gu += pad;
-                const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-                double* bd = S.band + (size_t)warp * 3 * L;
+                const float2 pert = df_of(0x1p-44 * fmax(tnorm * scale, 0.5));
+                float2* bd = reinterpret_cast<float2*>(S.band + (size_t)warp * 3 * L);
                 for (int m = warp; m < mine; m += kWarps) {   // one warp per eigenvalue
                     const int i = q + cs * m;
                     double lo = gl, hi = gu;
@@ -769,20 +811,23 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                         // lane 0 tests the lower end, lane 1 the upper end of the warm bracket
                         const int target = k - 1 - i;
                         const double t0 = S.theta[i];
-                        const double t1 = t0 + 4.0 * S.resid[i] + 64.0 * DBL_EPSILON * fabs(t0);
+                        const double t1 = t0 + 4.0 * S.resid[i] + 0x1p-38 * fabs(t0);   // above the counts' resolution
                         const double xt = lane == 0 ? t0 : t1;
-                        const int c = sturm_count(S.alpha, S.beta2, k, xt);
+                        const int c = sturm_count_df(adf, b2df, k, df_of(xt * scale));
                         const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
                         if (t0 > gl && c0 <= target) lo = t0;
                         if (t1 < gu && t1 > lo && c1 > target) hi = t1;
                     }
-                    const double th = kth_largest(S.alpha, S.beta2, k, i, lo, hi);
+                    const double th = kth_largest_df(adf, b2df, k, i, lo, hi, scale);
+                    double* x = S.xv + (size_t)i * L;
+                    float2* xf = reinterpret_cast<float2*>(x);
                     if (lane == 0) {
-                        double* x = S.xv + (size_t)i * L;
-                        tri_inverse_iteration(S.alpha, S.beta, k, th, pert, bd, bd + L, bd + 2 * L, x);
+                        tri_inverse_iteration_df(adf, bdf, k, df_of(th * scale), pert, bd, bd + L, bd + 2 * L, xf);
                         S.theta[i] = th;
-                        S.resid[i] = beta_j * fabs(x[k - 1]);
+                        S.resid[i] = beta_j * fabs((double)xf[k - 1].x + (double)xf[k - 1].y);
                     }
+                    __syncwarp();
+                    for (int t = lane; t < k; t += 32) x[t] = (double)xf[t].x + (double)xf[t].y;   // in place
                     __syncwarp();
                 }
             }
