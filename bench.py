@@ -72,6 +72,7 @@ def parse():
                     help="requests per serving run (the serving leg of every line; per step for --workload serve)")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of measured capacity")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (for launch lists)")
     ap.add_argument("--n", type=int, default=0,
                     help="points per GPU (default: the workload's full size; smaller sizes are for profiling)")
     return ap.parse_args()
@@ -501,7 +502,8 @@ def ours(args):
         err = O.aligned_rel_error(Xh.double().numpy()[rows], Xo)
         cpu = {"value": npts / dt, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle", "sample": sample}
 
-    serve = serve_leg(dev, seed, args.serve_requests, 50, args.serve_load, args.serve_slots) if rank == 0 else None
+    serve = (serve_leg(dev, seed, args.serve_requests, 50, args.serve_load, args.serve_slots)
+             if rank == 0 and not args.no_serve else None)
 
     if rank == 0:
         peaks_note = None
