@@ -49,9 +49,10 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic per launch of the dominant kernel from an ncu capture, valid
 # only while the kernel source is unchanged (sha256 of the .cu file).
 NCU_TRAFFIC = {
-    # small-case captures scaled to a full launch by algorithmic bytes / rows
-    # (profiles/k_lanczos_dc_f32_n100000.md, profiles/k_gower_tc_interp_bf16_n1000000.md)
-    "k_lanczos.cu": {"sha": "13b1ea186f3151ae", "bytes_per_launch": 50.8e9},
+    # ncu DRAM bytes of a smaller case scaled to a full launch by rows
+    # (profiles/k_gower_tck_image_fp8_n814255.md, profiles/k_gower_tc_interp_bf16_n1000000.md);
+    # k_lanczos has no full-size figure (its small case is L2-resident)
+    "k_gower_tck.cu": {"sha": "1757ed87459cdf6c", "bytes_per_launch": 1.375e9},
     "k_gower_tc.cu": {"sha": "36af15e74c95328c", "bytes_per_launch": 452e6},
 }
 
