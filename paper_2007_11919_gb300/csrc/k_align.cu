@@ -13,83 +13,109 @@
 namespace gbmds {
 namespace {
 
-// One warp per part; lane i owns row i of the r x r matrices.
-__global__ void __launch_bounds__(32) k_procrustes(const ProbDesc* __restrict__ desc,
-                                                   const double* __restrict__ varena,
-                                                   const double* __restrict__ lam, int r, int c,
-                                                   double* __restrict__ Tt) {
+// One CTA per part.  The one-sided Jacobi sweeps rotate disjoint column pairs
+// concurrently, one warp per pair, in round-robin order (r - 1 rounds of r / 2
+// pairs per sweep, the circle method); lane i owns row i.  FP64 throughout.
+constexpr int kProcThreads = 512;   // 16 warps: r / 2 <= 16 pairs per round
+
+__device__ __forceinline__ void round_robin_pair(int round, int k, int n, int& p, int& q) {
+    int x, y;
+    if (k == 0) {
+        x = round;
+        y = n - 1;
+    } else {
+        x = (round + k) % (n - 1);
+        y = (round - k + (n - 1)) % (n - 1);
+    }
+    p = x < y ? x : y;
+    q = x < y ? y : x;
+}
+
+__global__ void __launch_bounds__(kProcThreads) k_procrustes(const ProbDesc* __restrict__ desc,
+                                                             const double* __restrict__ varena,
+                                                             const double* __restrict__ lam, int r, int c,
+                                                             double* __restrict__ Tt) {
     __shared__ double G[kMaxR][kMaxR + 1];
     __shared__ double Wm[kMaxR][kMaxR + 1];
     __shared__ double abar[kMaxR], bbar[kMaxR], sq0[kMaxR], sqj[kMaxR];
+    __shared__ int s_rot;
     const int j = blockIdx.x;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double* T = Tt + (size_t)j * (r * r + r);
     double* t = T + r * r;
     if (j == 0) {
-        for (int e = lane; e < r * r; e += 32) T[e] = (e / r == e % r) ? 1.0 : 0.0;
-        if (lane < r) t[lane] = 0.0;
+        for (int e = tid; e < r * r; e += kProcThreads) T[e] = (e / r == e % r) ? 1.0 : 0.0;
+        if (tid < r) t[tid] = 0.0;
         return;
     }
     const double* V0 = varena + desc[0].v_off;
     const double* Vj = varena + desc[j].v_off;
-    if (lane < r) {
-        sq0[lane] = sqrt(lam[lane]);
-        sqj[lane] = sqrt(lam[(size_t)j * r + lane]);
+    if (tid < r) {
+        sq0[tid] = sqrt(lam[tid]);
+        sqj[tid] = sqrt(lam[(size_t)j * r + tid]);
     }
-    __syncwarp();
-    if (lane < r) {
+    __syncthreads();
+    if (tid < r) {
         double sa = 0.0, sb = 0.0;
         for (int a = 0; a < c; ++a) {
-            sa += V0[(int64_t)a * r + lane] * sq0[lane];
-            sb += Vj[(int64_t)a * r + lane] * sqj[lane];
+            sa += V0[(int64_t)a * r + tid] * sq0[tid];
+            sb += Vj[(int64_t)a * r + tid] * sqj[tid];
         }
-        abar[lane] = sa / c;
-        bbar[lane] = sb / c;
+        abar[tid] = sa / c;
+        bbar[tid] = sb / c;
     }
-    __syncwarp();
-    // C[i][m] = sum_a (B_ai - bbar_i)(A_am - abar_m); lane i builds row i
-    if (lane < r) {
-        for (int m = 0; m < r; ++m) {
-            double s = 0.0;
-            for (int a = 0; a < c; ++a) {
-                const double b = Vj[(int64_t)a * r + lane] * sqj[lane] - bbar[lane];
-                const double av = V0[(int64_t)a * r + m] * sq0[m] - abar[m];
-                s += b * av;
-            }
-            G[lane][m] = s;
+    __syncthreads();
+    // C[i][m] = sum_a (B_ai - bbar_i)(A_am - abar_m), one thread per entry
+    for (int e = tid; e < r * r; e += kProcThreads) {
+        const int i = e / r, m = e % r;
+        double s = 0.0;
+        for (int a = 0; a < c; ++a) {
+            const double b = Vj[(int64_t)a * r + i] * sqj[i] - bbar[i];
+            const double av = V0[(int64_t)a * r + m] * sq0[m] - abar[m];
+            s += b * av;
         }
-        for (int m = 0; m < r; ++m) Wm[lane][m] = (lane == m) ? 1.0 : 0.0;
+        G[i][m] = s;
+        Wm[i][m] = (i == m) ? 1.0 : 0.0;
     }
-    __syncwarp();
+    __syncthreads();
     // one-sided Jacobi: rotate column pairs of G (and W) until orthogonal
+    const int rr = r + (r & 1);   // column r is a dummy when r is odd
     for (int sweep = 0; sweep < 40; ++sweep) {
-        int rotated = 0;
-        for (int p = 0; p < r - 1; ++p) {
-            for (int q = p + 1; q < r; ++q) {
-                const double gp = lane < r ? G[lane][p] : 0.0;
-                const double gq = lane < r ? G[lane][q] : 0.0;
-                const double al = warp_sum(gp * gp);
-                const double be = warp_sum(gq * gq);
-                const double ga = warp_sum(gp * gq);
-                if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
-                    ++rotated;
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double cs = 1.0 / sqrt(1.0 + tt * tt);
-                    const double sn = cs * tt;
-                    if (lane < r) {
-                        G[lane][p] = cs * gp - sn * gq;
-                        G[lane][q] = sn * gp + cs * gq;
-                        const double wp = Wm[lane][p], wq = Wm[lane][q];
-                        Wm[lane][p] = cs * wp - sn * wq;
-                        Wm[lane][q] = sn * wp + cs * wq;
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < rr - 1; ++round) {
+            if (warp < rr / 2) {
+                int p, q;
+                round_robin_pair(round, warp, rr, p, q);
+                if (q < r) {
+                    const double gp = lane < r ? G[lane][p] : 0.0;
+                    const double gq = lane < r ? G[lane][q] : 0.0;
+                    const double al = warp_sum(gp * gp);
+                    const double be = warp_sum(gq * gq);
+                    const double ga = warp_sum(gp * gq);
+                    if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
+                        const double zeta = (be - al) / (2.0 * ga);
+                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double cs = 1.0 / sqrt(1.0 + tt * tt);
+                        const double sn = cs * tt;
+                        if (lane < r) {
+                            G[lane][p] = cs * gp - sn * gq;
+                            G[lane][q] = sn * gp + cs * gq;
+                            const double wp = Wm[lane][p], wq = Wm[lane][q];
+                            Wm[lane][p] = cs * wp - sn * wq;
+                            Wm[lane][q] = sn * wp + cs * wq;
+                        }
+                        if (lane == 0) s_rot = 1;
                     }
                 }
-                __syncwarp();
             }
+            __syncthreads();
         }
-        if (rotated == 0) break;
+        const bool again = s_rot != 0;
+        __syncthreads();   // every thread has read the flag before it is reset
+        if (!again) break;
     }
+    if (warp != 0) return;
     // U columns = G columns / sigma; complete null directions by Gram-Schmidt
     double smax = 0.0;
     for (int m = 0; m < r; ++m) {
@@ -182,7 +208,7 @@ __global__ void k_lambda_bar(const ProbDesc* __restrict__ desc, int p,
 
 cudaError_t launch_dc_procrustes(const ProbDesc* desc, int p, const double* varena,
                                  const double* lam, int r, int c, double* Tt, cudaStream_t st) {
-    k_procrustes<<<p, 32, 0, st>>>(desc, varena, lam, r, c, Tt);
+    k_procrustes<<<p, kProcThreads, 0, st>>>(desc, varena, lam, r, c, Tt);
     note_launch(1);
     return cudaGetLastError();
 }

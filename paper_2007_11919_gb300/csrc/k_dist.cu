@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace gbmds {
 
@@ -33,8 +34,10 @@ __global__ void __launch_bounds__(256) k_rownorm(const T* __restrict__ Y, int64_
 // ------------------------------------------------------- distance tiles
 // One CTA = one 64 x 64 tile (rows a0.., columns b0..) of Delta_j for problem
 // blockIdx.y.  256 threads, 4 x 4 outputs each; K staged through shared memory
-// 16 at a time.  Writes Delta as FP64 (row-major, ld = ldq) and the tile's row
-// sums into rp[tb * n + a] (summed later in a fixed order).
+// 16 at a time.  Writes Delta as FP64 (row-major, ld = ldq) or, accumulating
+// in FP32, as FP32 at the start of each row's storage (row stride 2 * ldq
+// floats), and the tile's row sums into rp[tb * n + a] (summed later in a
+// fixed order).
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
@@ -101,29 +104,59 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
 
     double* Q = qarena + P.q_off;
     double* rp = rparena + P.rp_off;
+    A nb[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) nb[jj] = b0 + tx * 4 + jj < n ? (A)nrm[rowB[tx * 4 + jj]] : A(0);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int a = a0 + ty * 4 + i;
-        double rs = 0.0;
-        if (a < n) {
-            const A na = (A)nrm[rowA[ty * 4 + i]];
+        if constexpr (sizeof(A) == 8) {
+            double rs = 0.0;
+            if (a < n) {
+                const A na = (A)nrm[rowA[ty * 4 + i]];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int b = b0 + tx * 4 + jj;
-                if (b < n) {
-                    const A nb = (A)nrm[rowB[tx * 4 + jj]];
-                    A dist = na + nb - A(2) * acc[i][jj];
-                    dist = dist > A(0) ? dist : A(0);
-                    if (a == b) dist = A(0);
-                    Q[(int64_t)a * P.ldq + b] = (double)dist;
-                    rs += (double)dist;
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int b = b0 + tx * 4 + jj;
+                    if (b < n) {
+                        A dist = na + nb[jj] - A(2) * acc[i][jj];
+                        dist = dist > A(0) ? dist : A(0);
+                        if (a == b) dist = A(0);
+                        Q[(int64_t)a * P.ldq + b] = dist;
+                        rs += dist;
+                    }
                 }
             }
-        }
-        // sum over the 16 column-threads of this row (same warp, lanes xor 1..8)
+            // sum over the 16 column-threads of this row (same warp, lanes xor 1..8)
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-        if (tx == 0 && a < n) rp[(int64_t)tb * n + a] = rs;
+            for (int o = 8; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            if (tx == 0 && a < n) rp[(int64_t)tb * n + a] = rs;
+        } else {
+            // FP32: Delta as floats at the start of each row's storage (row
+            // stride 2 * ldq floats); tile row sums in double-FP32
+            float* Qf = reinterpret_cast<float*>(Q);
+            float rh = 0.f, rl = 0.f;
+            if (a < n) {
+                const float na = (float)nrm[rowA[ty * 4 + i]];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int b = b0 + tx * 4 + jj;
+                    if (b < n) {
+                        float dist = na + nb[jj] - 2.f * acc[i][jj];
+                        dist = dist > 0.f ? dist : 0.f;
+                        if (a == b) dist = 0.f;
+                        Qf[(int64_t)a * 2 * P.ldq + b] = dist;
+                        df_add(rh, rl, dist, 0.f);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, rh, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, rl, o);
+                df_add(rh, rl, oh, ol);
+            }
+            if (tx == 0 && a < n) rp[(int64_t)tb * n + a] = (double)rh + (double)rl;
+        }
     }
 }
 
@@ -157,6 +190,9 @@ __global__ void __launch_bounds__(256) k_load_dist(const double* __restrict__ D2
 
 // ------------------------------------------------------------ centering
 
+// Row means m_a (FP64, from the tile row sums in a fixed order) and the
+// grand mean g.  F32: m is stored as double-FP32 pairs for k_center.
+template <bool F32>
 __global__ void __launch_bounds__(256) k_rowmean(const ProbDesc* __restrict__ desc,
                                                  const double* __restrict__ rparena,
                                                  double* __restrict__ rmarena,
@@ -171,7 +207,8 @@ __global__ void __launch_bounds__(256) k_rowmean(const ProbDesc* __restrict__ de
         double s = 0.0;
         for (int tb = 0; tb < P.tiles; ++tb) s += rp[(int64_t)tb * n + a];
         const double m = s / n;
-        rm[a] = m;
+        if (F32) reinterpret_cast<float2*>(rm)[a] = df_of(m);
+        else rm[a] = m;
         loc += m;
     }
     loc = warp_sum(loc);
@@ -198,18 +235,29 @@ __global__ void __launch_bounds__(256) k_center(const ProbDesc* __restrict__ des
     if (a >= P.n) return;
     const double* rm = rmarena + P.rm_off;
     const double g = grand[blockIdx.y];
-    const double ma = rm[a];
     double* Q = qarena + P.q_off + (int64_t)a * P.ldq;
     if (F32) {
+        // Delta (floats, in place) -> Q = -1/2 (Delta - (m_a - g) - m_b) in
+        // double-FP32, rounded once to FP32; padding entries set to zero
         float* Qf = reinterpret_cast<float*>(Q);
+        const float2* md = reinterpret_cast<const float2*>(rm);
+        const float2 ma = md[a];
+        const float2 cag = df_sub2(ma, df_of(g));
         const int n4 = (int)round_up(P.n, 4);
-        for (int c0 = 0; c0 < n4; c0 += 256) {
-            const int b = c0 + (int)threadIdx.x;
-            const float qv = b < P.n ? (float)(-0.5 * (Q[b] - ma - rm[b] + g)) : 0.f;
-            __syncthreads();
-            if (b < n4) Qf[b] = qv;
+        for (int b = threadIdx.x; b < n4; b += 256) {
+            float qv = 0.f;
+            if (b < P.n) {
+                const float2 mb = md[b];
+                float ch = cag.x, cl = cag.y;
+                df_add(ch, cl, mb.x, mb.y);          // c = m_a - g + m_b
+                float dh = Qf[b], dl = 0.f;
+                df_add(dh, dl, -ch, -cl);            // Delta - c
+                qv = -0.5f * __fadd_rn(dh, dl);
+            }
+            Qf[b] = qv;
         }
     } else {
+        const double ma = rm[a];
         for (int b = threadIdx.x; b < P.n; b += 256) Q[b] = -0.5 * (Q[b] - ma - rm[b] + g);
     }
 }
@@ -320,7 +368,8 @@ cudaError_t launch_center_batched(const ProbDesc* desc, int p, int max_n, double
                                   const double* rparena, double* rmarena, double* grand, int q_f32,
                                   cudaStream_t st) {
     if (p <= 0) return cudaSuccess;
-    k_rowmean<<<p, 256, 0, st>>>(desc, rparena, rmarena, grand);
+    if (q_f32) k_rowmean<true><<<p, 256, 0, st>>>(desc, rparena, rmarena, grand);
+    else k_rowmean<false><<<p, 256, 0, st>>>(desc, rparena, rmarena, grand);
     if (q_f32) k_center<true><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
     else k_center<false><<<dim3((unsigned)max_n, (unsigned)p), 256, 0, st>>>(desc, qarena, rmarena, grand);
     note_launch(2);

@@ -276,44 +276,84 @@ __device__ __forceinline__ uint8_t e4m3(float v) {
     return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
 
-// Rows of byte data -> the kernel's A operand and exact squared norms.
+// E4M3 encodings of 16 h and of g for a nibble h or g (exact: at most four
+// significant bits), filled once per block.
+__device__ __forceinline__ void fill_nibble_tables(uint8_t* hi16, uint8_t* lo) {
+    if (threadIdx.x < 16) {
+        hi16[threadIdx.x] = e4m3((float)(threadIdx.x * 16));
+        lo[threadIdx.x] = e4m3((float)threadIdx.x);
+    }
+}
+
+// Rows of byte data -> the kernel's A operand and exact squared norms, one
+// warp per row (16 bytes per lane and step when d is a multiple of 16).
 // kBf16: n x ldb BF16 (ldb = d rounded up to 8, zero tail).
 // kFp8:  n x 2 dh bytes [16 h | g] (dh = d rounded up to 16, zero tails).
 template <int MODE>
-__global__ void k_encode_u8(const uint8_t* __restrict__ Y, int64_t n, int d, void* __restrict__ out,
-                            float* __restrict__ nrm) {
-    const int64_t i = blockIdx.x;
+__global__ void __launch_bounds__(256) k_encode_u8(const uint8_t* __restrict__ Y, int64_t n, int d,
+                                                   void* __restrict__ out, float* __restrict__ nrm) {
+    __shared__ uint8_t t_hi[16], t_lo[16];
+    fill_nibble_tables(t_hi, t_lo);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (i >= n) return;
     const uint8_t* y = Y + i * d;
+    const bool vec = (d & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(out) & 15) == 0;
     uint32_t ss = 0;
     if (MODE == kTckBf16) {
         const int ld = round_up(d, 8);
         __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + i * ld;
-        for (int k = threadIdx.x; k < ld; k += blockDim.x) {
-            const uint32_t v = k < d ? y[k] : 0u;
-            ss += v * v;
-            o[k] = __float2bfloat16_rn((float)v);
+        if (vec) {
+            for (int k = 16 * lane; k < d; k += 512) {
+                const uint4 v = *reinterpret_cast<const uint4*>(y + k);
+                const uint8_t* b = reinterpret_cast<const uint8_t*>(&v);
+                __align__(16) __nv_bfloat16 w[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    ss += (uint32_t)b[u] * b[u];
+                    w[u] = __float2bfloat16_rn((float)b[u]);
+                }
+                reinterpret_cast<uint4*>(o + k)[0] = reinterpret_cast<const uint4*>(w)[0];
+                reinterpret_cast<uint4*>(o + k)[1] = reinterpret_cast<const uint4*>(w)[1];
+            }
+        } else {
+            for (int k = lane; k < ld; k += 32) {
+                const uint32_t v = k < d ? y[k] : 0u;
+                ss += v * v;
+                o[k] = __float2bfloat16_rn((float)v);
+            }
         }
     } else {
         const int dh = round_up(d, 16);
         uint8_t* o = static_cast<uint8_t*>(out) + i * 2 * dh;
-        for (int k = threadIdx.x; k < dh; k += blockDim.x) {
-            const uint32_t v = k < d ? y[k] : 0u;
-            ss += v * v;
-            o[k] = e4m3((float)(v & 0xF0u));
-            o[dh + k] = e4m3((float)(v & 0x0Fu));
+        if (vec) {
+            for (int k = 16 * lane; k < d; k += 512) {
+                const uint4 v = *reinterpret_cast<const uint4*>(y + k);
+                const uint8_t* b = reinterpret_cast<const uint8_t*>(&v);
+                __align__(16) uint8_t h[16], g[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    ss += (uint32_t)b[u] * b[u];
+                    h[u] = t_hi[b[u] >> 4];
+                    g[u] = t_lo[b[u] & 15];
+                }
+                *reinterpret_cast<uint4*>(o + k) = *reinterpret_cast<const uint4*>(h);
+                *reinterpret_cast<uint4*>(o + dh + k) = *reinterpret_cast<const uint4*>(g);
+            }
+        } else {
+            for (int k = lane; k < dh; k += 32) {
+                const uint32_t v = k < d ? y[k] : 0u;
+                ss += v * v;
+                o[k] = t_hi[v >> 4];
+                o[dh + k] = t_lo[v & 15];
+            }
         }
     }
-    // block reduction of the integer norm (exact: at most d * 65025)
-    __shared__ uint32_t red[32];
+    // exact: at most d * 65025
     for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-        nrm[i] = (float)tot;
-    }
+    if (lane == 0) nrm[i] = (float)ss;
 }
 
 // Landmark rows idx[j] of byte data -> B operands (kFp8: B1 = [16h | g] and
@@ -417,8 +457,9 @@ size_t tck_landmark_bytes(int mode, int l, int d) {
 
 cudaError_t launch_encode_u8(int mode, const uint8_t* Y, int64_t n, int d, void* out, float* nrm, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (mode == kTckBf16) k_encode_u8<kTckBf16><<<(unsigned)n, 128, 0, st>>>(Y, n, d, out, nrm);
-    else k_encode_u8<kTckFp8><<<(unsigned)n, 128, 0, st>>>(Y, n, d, out, nrm);
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    if (mode == kTckBf16) k_encode_u8<kTckBf16><<<blocks, 256, 0, st>>>(Y, n, d, out, nrm);
+    else k_encode_u8<kTckFp8><<<blocks, 256, 0, st>>>(Y, n, d, out, nrm);
     note_launch(1);
     return cudaGetLastError();
 }

@@ -45,6 +45,7 @@
 #include <limits.h>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -126,73 +127,6 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     return s;
 }
 
-// Double-FP32 arithmetic (Dekker 1971; Knuth's TwoSum): a value is an
-// unevaluated sum hi + lo of two floats (about 48 significant bits).  The
-// products run on the FP32 pipe, whose rate on GB300 is ~57x the FP64 rate.
-// __fmul_rn / __fadd_rn / __fsub_rn keep the compiler from contracting the
-// error-free transforms into FMAs.
-__device__ __forceinline__ void df_madd(float& sh, float& sl, float qh, float ql, float vh,
-                                        float vl) {
-    const float p = __fmul_rn(qh, vh);
-    float e = fmaf(qh, vh, -p);          // exact rounding error of qh * vh
-    e = fmaf(qh, vl, e);
-    e = fmaf(ql, vh, e);
-    const float s = __fadd_rn(sh, p);    // TwoSum(sh, p) = s + t exactly
-    const float z = __fsub_rn(s, sh);
-    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
-    sl = __fadd_rn(sl, __fadd_rn(t, e));
-    sh = s;
-}
-
-// sh + sl += q * (vh + vl) for an FP32 entry q (the product q * vh is split
-// exactly by the FMA; q * vl only needs FP32).
-__device__ __forceinline__ void df_madd1(float& sh, float& sl, float q, float vh, float vl) {
-    const float p = __fmul_rn(q, vh);
-    float e = fmaf(q, vh, -p);
-    e = fmaf(q, vl, e);
-    const float s = __fadd_rn(sh, p);
-    const float z = __fsub_rn(s, sh);
-    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
-    sl = __fadd_rn(sl, __fadd_rn(t, e));
-    sh = s;
-}
-
-__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
-    const float s = __fadd_rn(sh, oh);
-    const float z = __fsub_rn(s, sh);
-    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(oh, z));
-    sl = __fadd_rn(sl, __fadd_rn(t, ol));
-    sh = s;
-}
-
-
-// Renormalised double-FP32 helpers (values as float2 {hi, lo}).
-__device__ __forceinline__ float2 df_of(double x) {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-}
-__device__ __forceinline__ float2 df_norm(float sh, float sl) {
-    const float h = __fadd_rn(sh, sl);
-    return make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
-}
-// a * s
-__device__ __forceinline__ float2 df_mul(float2 a, float2 s) {
-    const float p = __fmul_rn(a.x, s.x);
-    float e = fmaf(a.x, s.x, -p);
-    e = fmaf(a.x, s.y, e);
-    e = fmaf(a.y, s.x, e);
-    return df_norm(p, e);
-}
-// Warp sum of a double-FP32 accumulator (fixed butterfly order).
-__device__ __forceinline__ void df_warp_sum(float& sh, float& sl) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
-        df_add(sh, sl, oh, ol);
-    }
-}
-
 // Sum of one value per thread over the CTA, in a fixed order.  Result valid
 // in thread 0.  Contains __syncthreads.
 __device__ double block_sum(double v, double* red) {
@@ -227,28 +161,6 @@ __device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* o
 // and eigenvectors do not change), in double-FP32 arithmetic: every FP64
 // warp instruction occupies an SMSP's FP64 unit for tens of cycles on GB300,
 // while these recurrences are short dependent chains of FP32 operations.
-
-// x - y, x * y and 1 / x for renormalised double-FP32 values.
-__device__ __forceinline__ float2 df_sub2(float2 x, float2 y) {
-    const float s = __fsub_rn(x.x, y.x);
-    const float z = __fsub_rn(s, x.x);
-    float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s, z)), __fsub_rn(-y.x, z));   // TwoSum error
-    e = __fadd_rn(e, __fsub_rn(x.y, y.y));
-    return df_norm(s, e);
-}
-__device__ __forceinline__ float2 df_mul2(float2 x, float2 y) {
-    const float p = __fmul_rn(x.x, y.x);
-    float e = fmaf(x.x, y.x, -p);
-    e = fmaf(x.x, y.y, e);
-    e = fmaf(x.y, y.x, e);
-    return df_norm(p, e);
-}
-__device__ __forceinline__ float2 df_rcp2(float2 x) {
-    const float y0 = __frcp_rn(x.x);
-    const float2 r = df_sub2(make_float2(1.f, 0.f), df_mul2(x, make_float2(y0, 0.f)));   // 1 - x y0
-    return df_norm(y0, __fmul_rn(y0, r.x));                                           // y0 (1 + r)
-}
-__device__ __forceinline__ float2 df_scale(float2 x, float s) { return make_float2(x.x * s, x.y * s); }
 
 // Number of eigenvalues of T (a, b2 = beta^2, scaled) smaller than x: the sign
 // changes of the Sturm sequence p_0 = 1, p_t = det(T_t - x I) =
