@@ -378,14 +378,14 @@ def ours(args):
         part = aux
         anc = torch.from_numpy(part.anchors).to(dev)
         own = torch.from_numpy(part.own).to(dev)
-        import ctypes
-        ptr = np.ascontiguousarray(part.ptr)
-        wsb = L.mds_divide_conquer_workspace_size(w.n, w.d, part.p, ptr.ctypes.data_as(ctypes.c_void_p), w.c,
-                                                  w.r, M.PREC[w.prec])
-        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        # the whole divide-and-conquer call as one autotuned, graph-captured plan
+        plan = M.DcPlan(w.n, w.d, Yd.dtype, part.ptr, w.c, w.r, w.prec, tune=args.cluster == 0,
+                        cluster=args.cluster, device=dev)
+        Xbuf = torch.zeros((w.n, w.r), dtype=torch.float64 if w.prec == "f64" else torch.float32, device=dev)
+        vbuf = torch.empty(w.r, dtype=torch.float64, device=dev)
 
         def step(Yin=Yd, a=anc, o=own):
-            return G.mds_divide_conquer(Yin, a, part.ptr, o, w.r, w.prec, workspace=ws, cluster=args.cluster)
+            return plan.execute(Yin, a, o, X=Xbuf, var=vbuf)
     else:
         idx = torch.from_numpy(aux).to(dev)
         wsb = L.mds_interpolate_workspace_size(w.n, w.d, w.l, w.r, M.PREC[w.prec])
@@ -475,9 +475,11 @@ def ours(args):
         anc_h = torch.from_numpy(aux).pin_memory()
         own_h = None
         h2d = Yh.numel() * Yh.element_size() + anc_h.numel() * 8
-    Ybuf = torch.empty_like(Yd)
-    abuf = torch.empty(anc_h.shape, dtype=torch.int64, device=dev)
-    obuf = torch.empty(own_h.shape, dtype=torch.int64, device=dev) if own_h is not None else None
+    # the step's own device buffers receive the host copies (a plan keeps its
+    # captured graph for the same buffers)
+    Ybuf = Yd
+    abuf = anc if is_dc(args.workload) else idx
+    obuf = own if is_dc(args.workload) else None
     e2e_ms = []
     d2h = w.n * w.r * 4 + w.r * 8
     for _ in range(args.steps):
@@ -515,7 +517,9 @@ def ours(args):
                          "parts": (part.p if is_dc(args.workload) else None),
                          "c": (w.c if is_dc(args.workload) else None),
                          "l": (w.l if not is_dc(args.workload) else None),
-                         "eigensolve": "f64 Lanczos", "cluster": stats[-1]["cluster"],
+                         "eigensolve": "Lanczos (FP64 scalars, double-FP32 vectors)", "cluster": stats[-1]["cluster"],
+                         "plan": (dict(plan.info(), graph=True, autotuned=args.cluster == 0)
+                                  if is_dc(args.workload) else None),
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
               "procrustes_rel_err_vs_oracle": err,
               "stage_ms": {k: statistics.mean(s["stage_ms"][k] for s in stats) for k in stats[0]["stage_ms"]},

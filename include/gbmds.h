@@ -183,6 +183,33 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
                        const mds_opts* opts, void* X, double* var);
 
 /* ------------------------------------------------------------------ */
+/* Divide-and-conquer plans (Section 3.2 repeated on new data of fixed shape).
+ * A plan fixes n, d, dtype, the part layout (part_ptr, c), r and the
+ * precision; it allocates its own workspace once (opts->workspace must be
+ * NULL), keeps the part descriptors on the device, and on execute runs the
+ * whole launch sequence of mds_divide_conquer -- every part in one persistent
+ * eigen-solver launch -- as one CUDA graph, captured at the first execute and
+ * again whenever a buffer pointer or the stream changes.
+ *   tune  nonzero (and opts->cluster 0): the first execute is an autotuner:
+ *         it runs the complete computation once per eligible cluster size
+ *         (CTAs per eigenproblem, 1..8, shared memory permitting), times each
+ *         with CUDA events on these buffers, and keeps the fastest; those
+ *         runs write valid outputs.  Otherwise the cluster size is
+ *         opts->cluster or the library's heuristic.
+ *   execute: buffers as for mds_divide_conquer (Y, part_own, anchors, X, var
+ *         device pointers), stream NULL = opts->stream.  Waits for the graph
+ *         and returns the status of the run.
+ *   info: cluster size in use, nodes of the captured graph, and per cluster
+ *         size 0..16 the autotuner's time in ms (0 = not tried). */
+typedef struct mds_dc_plan_s* mds_dc_plan;
+int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr, int c, int r,
+                       const mds_opts* opts, int tune, mds_dc_plan* out);
+int mds_dc_plan_execute(mds_dc_plan plan, const void* Y, const int64_t* part_own, const int64_t* anchors,
+                        void* X, double* var, void* stream);
+int mds_dc_plan_info(mds_dc_plan plan, int* cluster, int64_t* graph_nodes, double* trial_ms);
+void mds_dc_plan_destroy(mds_dc_plan plan);
+
+/* ------------------------------------------------------------------ */
 /* Serving: continuous batching of embed requests (Section 3.1, Eq. (2),
  * applied to points that arrive after the landmark configurations were built;
  * the paper embeds its new points in fixed blocks and has no request loop).

@@ -57,8 +57,16 @@ thread_local cudaEvent_t g_ev[6] = {};
 thread_local bool g_ev_made = false;
 thread_local int g_cluster = 0;
 
+// While a plan captures its launch sequence, stage marks go to the plan's
+// events as event-record nodes of the graph.
+thread_local cudaEvent_t* g_capture_ev = nullptr;
+
 // Marks the start (stage = -1) or the end of a pipeline stage on the stream.
 void tmark(int stage, cudaStream_t st) {
+    if (g_capture_ev) {
+        cudaEventRecordWithFlags(g_capture_ev[stage + 1], st, cudaEventRecordExternal);
+        return;
+    }
     if (!g_timing) return;
     if (!g_ev_made) {
         for (auto& e : g_ev) cudaEventCreate(&e);
@@ -71,7 +79,7 @@ void begin_call(cudaStream_t st) {
     g_launches = 0;
     g_cluster = 0;
     g_last = mds_stats{};
-    if (g_timing)
+    if (g_timing || g_capture_ev)
         for (int i = 0; i <= 5; ++i) tmark(i - 1, st);  // all stages empty by default
 }
 
@@ -213,9 +221,12 @@ int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
 // Uploads descriptors, forms Q_j for every problem (squared distances +
 // double centering) and runs the batched eigen-solver.
 int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
-                  const int64_t* anchors, const int64_t* own, int acc_f64, const Opts& o) {
-    CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
-    CK(cudaMemcpyAsync(B.d_order, B.order.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
+                  const int64_t* anchors, const int64_t* own, int acc_f64, const Opts& o,
+                  bool upload = true) {
+    if (upload) {
+        CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
+        CK(cudaMemcpyAsync(B.d_order, B.order.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
+    }
     CK(cudaMemsetAsync(B.counter, 0, sizeof(int), o.st));
     if (Y) {
         CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64,
@@ -254,6 +265,8 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
 }
 
 // Waits for the stream and folds the device status words into one code.
+int batch_status(const Batch& B, const int* hs, const int* steps, int flag, int kerr);
+
 int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr = nullptr) {
     tmark(4, o.st);
     std::vector<int> hs(B ? B->p : 0), steps(B ? B->p : 0);
@@ -266,31 +279,17 @@ int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr =
     if (d_flag) CK(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, o.st));
     CK(cudaStreamSynchronize(o.st));
     CK(cudaGetLastError());
-    g_last.launches = g_launches;
-    g_last.cluster = g_cluster;
-    if (B) {
-        g_last.problems = B->p;
-        for (int j = 0; j < B->p; ++j) {
-            const double n = B->desc[j].n, k = steps[j];
-            g_last.eig_steps += steps[j];
-            g_last.eig_flops += 2.0 * n * n * k + 8.0 * n * k + 2.0 * n * k * (k + 1) + 2.0 * n * k * B->r;
-            g_last.eig_qbytes += (double)B->q_bytes * n * n * k;
-        }
-    }
     if (g_timing)
         for (int i = 0; i < 5; ++i) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]);
             g_last.stage_ms[i] = ms;
         }
+    if (B) return batch_status(*B, hs.data(), steps.data(), flag, kerr);
+    g_last.launches = g_launches;
+    g_last.cluster = g_cluster;
     if (flag) return MDS_ERR_ARG;
-    if (kerr) return kerr;
-    int worst = MDS_OK;
-    for (int s : hs) {
-        if (s == MDS_ERR_RANK) return MDS_ERR_RANK;
-        if (s != MDS_OK) worst = s;
-    }
-    return worst;
+    return kerr;
 }
 
 bool valid_dt(int dt) { return dt == MDS_IN_F64 || dt == MDS_IN_F32 || dt == MDS_IN_U8; }
@@ -394,6 +393,52 @@ int prep_data(const void* Y, int dt, int64_t n, int d, int prec, double* nrm, vo
         *dteff = dt;
     }
     return MDS_OK;
+}
+
+// The whole divide-and-conquer launch sequence on o.st, without waiting:
+// index checks, norms, every part's distance tiles, centering and eigenpairs
+// (one persistent launch), Procrustes, alignment and lambda-bar.  The
+// workspace W is carved; upload = false when its part descriptors are
+// already on the device.
+int dc_enqueue(DcWs& W, const void* Y, int dt, int64_t n, int d, int p, const int64_t* part_ptr,
+               const int64_t* part_own, const int64_t* anchors, int c, int r, const Opts& o, void* X,
+               double* var, bool upload) {
+    const int f64 = o.prec == MDS_PREC_F64;
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(launch_check_idx(anchors, c, n, W.flag, o.st));
+    CK(launch_check_idx(part_own, part_ptr[p], n, W.flag, o.st));
+    const void* Ye;
+    int dte;
+    int s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte);
+    if (s) return s;
+    tmark(0, o.st);
+    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, o, upload))) return s;
+    CK(launch_dc_procrustes(W.B.d_desc, p, W.B.v, W.B.lam, r, c, W.Tt, o.st));
+    CK(launch_dc_align(W.B.d_desc, p, W.B.max_n, W.B.v, W.B.lam, W.Tt, r, anchors, part_own, f64, X, o.st));
+    CK(launch_dc_lambda_bar(W.B.d_desc, p, W.B.lam, r, var, o.st));
+    tmark(4, o.st);
+    return MDS_OK;
+}
+
+// Stats of a finished batch from host copies of its status words.
+int batch_status(const Batch& B, const int* hs, const int* steps, int flag, int kerr) {
+    g_last.launches = g_launches;
+    g_last.cluster = g_cluster;
+    g_last.problems = B.p;
+    for (int j = 0; j < B.p; ++j) {
+        const double n = B.desc[j].n, k = steps[j];
+        g_last.eig_steps += steps[j];
+        g_last.eig_flops += 2.0 * n * n * k + 8.0 * n * k + 2.0 * n * k * (k + 1) + 2.0 * n * k * B.r;
+        g_last.eig_qbytes += (double)B.q_bytes * n * n * k;
+    }
+    if (flag) return MDS_ERR_ARG;
+    if (kerr) return kerr;
+    int worst = MDS_OK;
+    for (int j = 0; j < B.p; ++j) {
+        if (hs[j] == MDS_ERR_RANK) return MDS_ERR_RANK;
+        if (hs[j] != MDS_OK) worst = hs[j];
+    }
+    return worst;
 }
 
 }  // namespace
@@ -837,19 +882,230 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
     if ((s = check_ws(o, need))) return s;
     if (dc_layout(W, o.ws, n, d, p, part_ptr, c, r, o.prec, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
-    const int f64 = o.prec == MDS_PREC_F64;
-    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
-    CK(launch_check_idx(anchors, c, n, W.flag, o.st));
-    CK(launch_check_idx(part_own, part_ptr[p], n, W.flag, o.st));
-    const void* Ye;
-    int dte;
-    if ((s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
-    tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, o))) return s;
-    CK(launch_dc_procrustes(W.B.d_desc, p, W.B.v, W.B.lam, r, c, W.Tt, o.st));
-    CK(launch_dc_align(W.B.d_desc, p, W.B.max_n, W.B.v, W.B.lam, W.Tt, r, anchors, part_own, f64, X, o.st));
-    CK(launch_dc_lambda_bar(W.B.d_desc, p, W.B.lam, r, var, o.st));
+    if ((s = dc_enqueue(W, Y, dt, n, d, p, part_ptr, part_own, anchors, c, r, o, X, var, true))) return s;
     return finish(&W.B, W.flag, o);
+}
+
+
+// ------------------------------------------------- divide-and-conquer plans
+
+}  // extern "C"
+
+struct mds_dc_plan_s {
+    int device = 0;
+    int64_t n = 0;
+    int d = 0, dt = 0, p = 0, c = 0, r = 0;
+    std::vector<int64_t> ptr;
+    Opts o{};
+    void* ws = nullptr;
+    DcWs W;
+    bool tune = false, tuned = false;
+    int cs = 0;
+    double trial_ms[17] = {};   // autotuner: call time per cluster size (0 = not tried)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+    int64_t launches = 0;
+    const void* cY = nullptr;   // buffers the graph was captured with
+    const int64_t* cown = nullptr;
+    const int64_t* canc = nullptr;
+    void* cX = nullptr;
+    double* cvar = nullptr;
+    cudaStream_t cst = nullptr;
+    int* hbuf = nullptr;        // page-locked: status[p], steps[p], flag
+    cudaEvent_t ev[6] = {};
+};
+
+namespace {
+
+void plan_drop_graph(mds_dc_plan P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    P->exec = nullptr;
+    P->graph = nullptr;
+}
+
+// One direct (uncaptured) run with cluster size cs, timed on the stream.
+int plan_trial(mds_dc_plan P, int cs, const void* Y, const int64_t* own, const int64_t* anc, void* X,
+               double* var, cudaStream_t st, double* ms) {
+    Opts o = P->o;
+    o.st = st;
+    o.cluster = cs;
+    begin_call(st);
+    CK(cudaEventRecord(P->ev[0], st));
+    int s = dc_enqueue(P->W, Y, P->dt, P->n, P->d, P->p, P->ptr.data(), own, anc, P->c, P->r, o, X, var, false);
+    if (s) return s;
+    CK(cudaEventRecord(P->ev[5], st));
+    const int p = P->p;
+    CK(cudaMemcpyAsync(P->hbuf, P->W.B.status, sizeof(int) * p, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(P->hbuf + p, P->W.B.steps, sizeof(int) * p, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(P->hbuf + 2 * p, P->W.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    float f = 0.f;
+    cudaEventElapsedTime(&f, P->ev[0], P->ev[5]);
+    *ms = f;
+    return batch_status(P->W.B, P->hbuf, P->hbuf + p, P->hbuf[2 * p], 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr, int c, int r,
+                       const mds_opts* opts, int tune, mds_dc_plan* out) {
+    if (!out) return MDS_ERR_ARG;
+    *out = nullptr;
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (opts->workspace || opts->workspace_bytes) return MDS_ERR_ARG;   // the plan owns its workspace
+    if (!part_ptr || !valid_dt(dt) || n < 2 || d <= 0 || p <= 0 || r <= 0 || r > kMaxR || c < r + 1 || c > n ||
+        part_ptr[0] != 0)
+        return MDS_ERR_ARG;
+    for (int j = 0; j < p; ++j) {
+        const int64_t own = part_ptr[j + 1] - part_ptr[j];
+        if (own < 0 || own + c > kMaxEigN || own + c <= r) return MDS_ERR_ARG;
+    }
+    if (o.prec == MDS_PREC_FP8 || o.prec == MDS_PREC_BF16) return MDS_ERR_UNSUPPORTED;
+    mds_dc_plan P = new (std::nothrow) mds_dc_plan_s();
+    if (!P) return MDS_ERR_NOMEM;
+    P->n = n;
+    P->d = d;
+    P->dt = dt;
+    P->p = p;
+    P->c = c;
+    P->r = r;
+    P->ptr.assign(part_ptr, part_ptr + p + 1);
+    P->tune = tune != 0 && o.cluster == 0;
+    P->cs = o.cluster;
+    cudaGetDevice(&P->device);
+    const size_t need = dc_layout(P->W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
+    bool ok = cudaMalloc(&P->ws, need) == cudaSuccess &&
+              cudaHostAlloc((void**)&P->hbuf, sizeof(int) * (2 * p + 1), cudaHostAllocDefault) == cudaSuccess;
+    for (auto& e : P->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        mds_dc_plan_destroy(P);
+        return MDS_ERR_NOMEM;
+    }
+    dc_layout(P->W, (char*)P->ws, n, d, p, part_ptr, c, r, o.prec, o.mmax);
+    o.ws = (char*)P->ws;
+    o.wsb = need;
+    P->o = o;
+    // part descriptors and queue order stay on the device for the plan's life
+    if (cudaMemcpy(P->W.B.d_desc, P->W.B.desc.data(), sizeof(ProbDesc) * p, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->W.B.d_order, P->W.B.order.data(), sizeof(int) * p, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        mds_dc_plan_destroy(P);
+        return MDS_ERR_CUDA;
+    }
+    *out = P;
+    return MDS_OK;
+}
+
+int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, const int64_t* anchors, void* X,
+                        double* var, void* stream) {
+    if (!P || !Y || !X || !var || !anchors || (P->ptr[P->p] > 0 && !part_own)) return MDS_ERR_ARG;
+    cudaStream_t st = stream ? (cudaStream_t)stream : P->o.st;
+    const Batch& B = P->W.B;
+    if (P->cs == 0 && P->tune) {
+        // autotuner: every cluster size that fits, timed on these buffers
+        // (each trial is a complete, correct run); the fastest one is kept
+        double best = 0.0;
+        for (int cs = 1; cs <= 16; ++cs) {
+            if (lanczos_smem_bytes(B.max_n, cs, B.mmax, B.r) > kMaxSmem || cs > std::max(1, B.max_n / 64)) continue;
+            if (cs > 8 && B.p > 1) continue;   // portable cluster sizes for batches
+            double ms = 0.0;
+            int s = plan_trial(P, cs, Y, part_own, anchors, X, var, st, &ms);   // warm-up
+            if (s == MDS_OK) s = plan_trial(P, cs, Y, part_own, anchors, X, var, st, &ms);
+            if (s != MDS_OK) {
+                if (s == MDS_ERR_ARG || s == MDS_ERR_RANK) return s;   // the data, not the cluster size
+                continue;
+            }
+            P->trial_ms[cs] = ms;
+            if (P->cs == 0 || ms < best) {
+                best = ms;
+                P->cs = cs;
+            }
+        }
+        P->tuned = true;
+        if (P->cs == 0) return MDS_ERR_CUDA;
+    }
+    if (P->cs == 0) P->cs = pick_cluster(0, B.p, B.max_n, B.mmax, B.r);
+    if (!P->exec || Y != P->cY || part_own != P->cown || anchors != P->canc || X != P->cX || var != P->cvar ||
+        st != P->cst) {
+        plan_drop_graph(P);
+        Opts o = P->o;
+        o.st = st;
+        o.cluster = P->cs;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MDS_ERR_CUDA;
+        g_capture_ev = P->ev;
+        begin_call(st);
+        int s = dc_enqueue(P->W, Y, P->dt, P->n, P->d, P->p, P->ptr.data(), part_own, anchors, P->c, P->r, o, X,
+                           var, false);
+        const int p = P->p;
+        if (s == MDS_OK &&
+            (cudaMemcpyAsync(P->hbuf, B.status, sizeof(int) * p, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaMemcpyAsync(P->hbuf + p, B.steps, sizeof(int) * p, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaMemcpyAsync(P->hbuf + 2 * p, P->W.flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess))
+            s = MDS_ERR_CUDA;
+        g_capture_ev = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st, &P->graph);
+        if (s == MDS_OK && ce != cudaSuccess) s = MDS_ERR_CUDA;
+        if (s == MDS_OK && cudaGraphInstantiate(&P->exec, P->graph, 0) != cudaSuccess) s = MDS_ERR_CUDA;
+        if (s != MDS_OK) {
+            cudaGetLastError();
+            plan_drop_graph(P);
+            return s;
+        }
+        cudaGraphGetNodes(P->graph, nullptr, &P->nodes);
+        P->launches = g_launches;
+        P->cY = Y;
+        P->cown = part_own;
+        P->canc = anchors;
+        P->cX = X;
+        P->cvar = var;
+        P->cst = st;
+    }
+    g_last = mds_stats{};
+    CK(cudaGraphLaunch(P->exec, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    g_launches = P->launches;
+    g_cluster = P->cs;
+    if (g_timing)
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]);
+            g_last.stage_ms[i] = ms;
+        }
+    return batch_status(B, P->hbuf, P->hbuf + P->p, P->hbuf[2 * P->p], 0);
+}
+
+int mds_dc_plan_info(mds_dc_plan P, int* cluster, int64_t* graph_nodes, double* trial_ms) {
+    if (!P) return MDS_ERR_ARG;
+    if (cluster) *cluster = P->cs;
+    if (graph_nodes) *graph_nodes = (int64_t)P->nodes;
+    if (trial_ms)
+        for (int i = 0; i <= 16; ++i) trial_ms[i] = P->trial_ms[i];
+    return MDS_OK;
+}
+
+void mds_dc_plan_destroy(mds_dc_plan P) {
+    if (!P) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(P->device);
+    if (P->cst) cudaStreamSynchronize(P->cst);
+    plan_drop_graph(P);
+    if (P->ws) cudaFree(P->ws);
+    if (P->hbuf) cudaFreeHost(P->hbuf);
+    for (auto& e : P->ev)
+        if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    cudaSetDevice(cur);
+    delete P;
 }
 
 }  // extern "C"

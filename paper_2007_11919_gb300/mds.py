@@ -375,3 +375,60 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class DcPlan:
+    """Divide-and-conquer plan (mds_dc_plan_*): fixed shapes, own workspace,
+    the whole launch sequence replayed as one CUDA graph; ``tune=True`` makes
+    the first ``execute`` pick the eigen-solver cluster size by timing."""
+
+    def __init__(self, n, d, dtype, part_ptr, c, r, prec="f32", tune=True, cluster=0, device="cuda"):
+        L = _lib()
+        for name, res, args in [
+            ("mds_dc_plan_create", _I, [_I64, _I, _I, _I, _P, _I, _I, _P, _I, _P]),
+            ("mds_dc_plan_execute", _I, [_P, _P, _P, _P, _P, _P, _P]),
+            ("mds_dc_plan_info", _I, [_P, _P, _P, _P]),
+            ("mds_dc_plan_destroy", None, [_P]),
+        ]:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        self.device = torch.device(device)
+        self.ptr = np.ascontiguousarray(np.asarray(part_ptr, dtype=np.int64))
+        self.p = len(self.ptr) - 1
+        self.n, self.d, self.r, self.prec = n, d, r, prec
+        o = MdsOpts(prec=PREC[prec], cluster=cluster, flags=0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.mds_dc_plan_create(n, d, DTYPE[dtype], self.p, self.ptr.ctypes.data_as(ctypes.c_void_p), c, r,
+                                        ctypes.byref(o), 1 if tune else 0, ctypes.byref(h)), "mds_dc_plan_create")
+        self.handle = h
+
+    def execute(self, Y, anchors, part_own, X=None, var=None, stream=None):
+        _data(Y)
+        if X is None:
+            X = torch.zeros((self.n, self.r), dtype=_xdtype(self.prec), device=Y.device)
+        if var is None:
+            var = torch.empty(self.r, dtype=torch.float64, device=Y.device)
+        st = stream if stream is not None else torch.cuda.current_stream(Y.device)
+        _check(_lib().mds_dc_plan_execute(self.handle, _ptr(Y), _ptr(part_own), _ptr(anchors), _ptr(X), _ptr(var),
+                                          ctypes.c_void_p(st.cuda_stream)), "mds_dc_plan_execute")
+        return X, var
+
+    def info(self):
+        cs, nodes = ctypes.c_int(), ctypes.c_int64()
+        trials = (ctypes.c_double * 17)()
+        _check(_lib().mds_dc_plan_info(self.handle, ctypes.byref(cs), ctypes.byref(nodes), trials), "mds_dc_plan_info")
+        return {"cluster": cs.value, "graph_nodes": nodes.value,
+                "trial_ms": {i: trials[i] for i in range(17) if trials[i] > 0}}
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _lib().mds_dc_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

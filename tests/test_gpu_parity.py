@@ -369,3 +369,42 @@ def test_image_fp8_full_size_sampled(gb):
     ref = np.concatenate([X1, Xs])
     assert O.aligned_rel_error(both, ref) < TOL["bf16"]
     assert rel(host(var), lam / w.l) < LAM_TOL["f32"]
+
+
+# ------------------------------------------------------ divide-and-conquer plans
+
+
+def test_dc_plan_autotuned_graph(gb):
+    """The plan's autotuned, graph-replayed run equals a direct call with the
+    cluster size it chose, bit for bit, and the oracle within tolerance; a
+    changed output buffer is captured again."""
+    from paper_2007_11919_gb300.mds import DcPlan
+    Y = W.gaussian_dominant(12_000, 100, 5, seed=4, dtype=np.float32)
+    part = W.partitions_uneven(12_000, 20, 800, 1200, seed=4)
+    Yd, anc, own = dev(Y), dev(part.anchors), dev(part.own)
+    plan = DcPlan(12_000, 100, torch.float32, part.ptr, 20, 10, "f32", tune=True)
+    X1, v1 = plan.execute(Yd, anc, own)
+    info = plan.info()
+    assert 1 <= info["cluster"] <= 8 and info["graph_nodes"] >= 8 and len(info["trial_ms"]) >= 2
+    X2, v2 = plan.execute(Yd, anc, own)                       # graph replay, same buffers
+    assert torch.equal(X1, X2) and torch.equal(v1, v2)
+    Xd, vd = gb.mds_divide_conquer(Yd, anc, part.ptr, own, 10, "f32", cluster=info["cluster"])
+    assert torch.equal(X2, Xd) and torch.equal(v2, vd)
+    X3 = torch.zeros_like(X1)
+    plan.execute(Yd, anc, own, X=X3)                          # new buffer: captured again
+    assert torch.equal(X3, Xd)
+    Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 10)
+    assert O.aligned_rel_error(host(X2), Xo) < TOL["f32"]
+    plan.close()
+
+
+def test_dc_plan_fixed_cluster_f64(gb):
+    from paper_2007_11919_gb300.mds import DcPlan
+    Y = W.gaussian_dominant(3000, 10, 3, seed=3)
+    part = W.partitions_uneven(3000, 10, 300, 420, seed=3)
+    plan = DcPlan(3000, 10, torch.float64, part.ptr, 10, 3, "f64", tune=False, cluster=3)
+    X, var = plan.execute(dev(Y), dev(part.anchors), dev(part.own))
+    assert plan.info()["cluster"] == 3
+    Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 3)
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+    assert rel(host(var), lo) < LAM_TOL["f64"]

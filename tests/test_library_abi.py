@@ -117,3 +117,21 @@ def test_server_argument_checks_without_gpu(lib):
     st = ctypes.c_int()
     assert L.mds_server_wait(None, 1, 1.0, ctypes.byref(st), None) == 1
     assert L.mds_server_destroy(None) == 1
+
+
+def test_dc_plan_argument_checks_without_gpu(lib):
+    from paper_2007_11919_gb300.mds import MdsOpts
+    lib.mds_dc_plan_create.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.mds_dc_plan_create.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    o = MdsOpts(prec=1)
+    ptr = np.array([0, 100, 200], dtype=np.int64)
+    pp = ptr.ctypes.data_as(ctypes.c_void_p)
+    # c must exceed r; the plan owns its workspace; BF16 / FP8 D&C not built
+    assert lib.mds_dc_plan_create(220, 3, 1, 2, pp, 3, 3, ctypes.byref(o), 1, ctypes.byref(h)) == 1
+    ow = MdsOpts(prec=1, workspace=ctypes.c_void_p(256), workspace_bytes=1024)
+    assert lib.mds_dc_plan_create(220, 3, 1, 2, pp, 10, 3, ctypes.byref(ow), 1, ctypes.byref(h)) == 1
+    ob = MdsOpts(prec=2)
+    assert lib.mds_dc_plan_create(220, 3, 1, 2, pp, 10, 3, ctypes.byref(ob), 1, ctypes.byref(h)) == 7
+    assert lib.mds_dc_plan_create(220, 3, 1, 2, pp, 10, 3, ctypes.byref(o), 1, None) == 1
