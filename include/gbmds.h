@@ -197,8 +197,10 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
  *         runs write valid outputs.  Otherwise the cluster size is
  *         opts->cluster or the library's heuristic.
  *   execute: buffers as for mds_divide_conquer (Y, part_own, anchors, X, var
- *         device pointers), stream NULL = opts->stream.  Waits for the graph
- *         and returns the status of the run.
+ *         device pointers).  The graph runs on a stream the plan owns (stream
+ *         capture needs one), ordered after the work already queued on
+ *         `stream` (NULL = opts->stream); execute waits for it and returns
+ *         the status of the run.
  *   info: cluster size in use, nodes of the captured graph, and per cluster
  *         size 0..16 the autotuner's time in ms (0 = not tried). */
 typedef struct mds_dc_plan_s* mds_dc_plan;

@@ -911,7 +911,8 @@ struct mds_dc_plan_s {
     const int64_t* canc = nullptr;
     void* cX = nullptr;
     double* cvar = nullptr;
-    cudaStream_t cst = nullptr;
+    cudaStream_t pst = nullptr; // the plan's own stream (stream capture needs one)
+    cudaEvent_t join = nullptr; // orders it after the caller's stream
     int* hbuf = nullptr;        // page-locked: status[p], steps[p], flag
     cudaEvent_t ev[6] = {};
 };
@@ -984,6 +985,8 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
     bool ok = cudaMalloc(&P->ws, need) == cudaSuccess &&
               cudaHostAlloc((void**)&P->hbuf, sizeof(int) * (2 * p + 1), cudaHostAllocDefault) == cudaSuccess;
     for (auto& e : P->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&P->pst, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         mds_dc_plan_destroy(P);
@@ -1007,7 +1010,11 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
 int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, const int64_t* anchors, void* X,
                         double* var, void* stream) {
     if (!P || !Y || !X || !var || !anchors || (P->ptr[P->p] > 0 && !part_own)) return MDS_ERR_ARG;
-    cudaStream_t st = stream ? (cudaStream_t)stream : P->o.st;
+    // work runs on the plan's stream, after what the caller queued on theirs
+    const cudaStream_t ust = stream ? (cudaStream_t)stream : P->o.st;
+    const cudaStream_t st = P->pst;
+    CK(cudaEventRecord(P->join, ust));
+    CK(cudaStreamWaitEvent(st, P->join, 0));
     const Batch& B = P->W.B;
     if (P->cs == 0 && P->tune) {
         // autotuner: every cluster size that fits, timed on these buffers
@@ -1033,8 +1040,7 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         if (P->cs == 0) return MDS_ERR_CUDA;
     }
     if (P->cs == 0) P->cs = pick_cluster(0, B.p, B.max_n, B.mmax, B.r);
-    if (!P->exec || Y != P->cY || part_own != P->cown || anchors != P->canc || X != P->cX || var != P->cvar ||
-        st != P->cst) {
+    if (!P->exec || Y != P->cY || part_own != P->cown || anchors != P->canc || X != P->cX || var != P->cvar) {
         plan_drop_graph(P);
         Opts o = P->o;
         o.st = st;
@@ -1066,7 +1072,6 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         P->canc = anchors;
         P->cX = X;
         P->cvar = var;
-        P->cst = st;
     }
     g_last = mds_stats{};
     CK(cudaGraphLaunch(P->exec, st));
@@ -1097,8 +1102,10 @@ void mds_dc_plan_destroy(mds_dc_plan P) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(P->device);
-    if (P->cst) cudaStreamSynchronize(P->cst);
+    if (P->pst) cudaStreamSynchronize(P->pst);
     plan_drop_graph(P);
+    if (P->pst) cudaStreamDestroy(P->pst);
+    if (P->join) cudaEventDestroy(P->join);
     if (P->ws) cudaFree(P->ws);
     if (P->hbuf) cudaFreeHost(P->hbuf);
     for (auto& e : P->ev)
