@@ -218,17 +218,42 @@ int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
         if (e_ != cudaSuccess) return MDS_ERR_CUDA; \
     } while (0)
 
+// Tensor-core part Gram of byte rows (divide-and-conquer with BF16 or FP8
+// distances): the encoded member rows, their norms and the work units.
+struct GramOp {
+    int mode = -1;                 // kTckBf16 / kTckFp8, or -1: SIMT distance tiles
+    int64_t slots = 0;             // operand rows (parts at 4-aligned offsets)
+    std::vector<int> h_moff;       // per part: first operand row
+    std::vector<int4> h_units;     // (part, row0, col0, moff)
+    int* moff = nullptr;
+    int4* units = nullptr;
+    void* ops = nullptr;
+    float* nrm = nullptr;
+    int* kerr = nullptr;
+};
+
 // Uploads descriptors, forms Q_j for every problem (squared distances +
 // double centering) and runs the batched eigen-solver.
 int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
                   const int64_t* anchors, const int64_t* own, int acc_f64, const Opts& o,
-                  bool upload = true) {
+                  bool upload = true, const GramOp* gram = nullptr) {
     if (upload) {
         CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
         CK(cudaMemcpyAsync(B.d_order, B.order.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
+        if (gram && gram->mode >= 0) {
+            CK(cudaMemcpyAsync(gram->moff, gram->h_moff.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
+            CK(cudaMemcpyAsync(gram->units, gram->h_units.data(), sizeof(int4) * gram->h_units.size(),
+                               cudaMemcpyHostToDevice, o.st));
+        }
     }
     CK(cudaMemsetAsync(B.counter, 0, sizeof(int), o.st));
-    if (Y) {
+    if (gram && gram->mode >= 0) {
+        CK(cudaMemsetAsync(gram->kerr, 0, sizeof(int), o.st));
+        CK(launch_encode_parts_u8(gram->mode, (const uint8_t*)Y, d, anchors, own, B.d_desc, gram->moff, B.p,
+                                  gram->slots, gram->ops, gram->nrm, o.st));
+        CK(launch_gram_tck(gram->mode, gram->ops, gram->slots, d, gram->nrm, gram->units,
+                           (int)gram->h_units.size(), B.d_desc, B.q, B.rp, gram->kerr, o.st));
+    } else if (Y) {
         CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64,
                                  B.q, B.rp, o.st));
     }
@@ -359,6 +384,7 @@ struct DcWs {
     void* Yq;
     Batch B;
     double* Tt;
+    GramOp G;
 };
 
 size_t dc_layout(DcWs& W, char* base, int64_t n, int d, int p, const int64_t* part_ptr, int c,
@@ -376,6 +402,27 @@ size_t dc_layout(DcWs& W, char* base, int64_t n, int d, int p, const int64_t* pa
     plan_batch(W.B, sizes, offs, c, r, mmax, n);
     carve_batch(W.B, A);
     W.Tt = A.take<double>((size_t)p * (r * r + r));
+    // BF16 / FP8 (byte rows): tensor-core part Gram
+    W.G = GramOp();
+    if (prec == MDS_PREC_BF16 || prec == MDS_PREC_FP8) {
+        GramOp& G = W.G;
+        G.mode = prec == MDS_PREC_FP8 ? kTckFp8 : kTckBf16;
+        G.h_moff.resize(p);
+        int64_t slots = 0;
+        for (int j = 0; j < p; ++j) {
+            G.h_moff[j] = (int)slots;
+            const int nj = sizes[j];
+            slots += round_up(nj, 4);
+            for (int r0 = 0; r0 < nj; r0 += 128)
+                for (int c0 = 0; c0 < nj; c0 += 256) G.h_units.push_back(make_int4(j, r0, c0, G.h_moff[j]));
+        }
+        G.slots = slots;
+        G.kerr = A.take<int>(1);
+        G.moff = A.take<int>(p);
+        G.units = A.take<int4>(G.h_units.size());
+        G.nrm = A.take<float>((size_t)slots + 256);
+        G.ops = A.take<char>(gram_operand_bytes(G.mode, slots, d));
+    }
     return A.off;
 }
 
@@ -407,12 +454,12 @@ int dc_enqueue(DcWs& W, const void* Y, int dt, int64_t n, int d, int p, const in
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(launch_check_idx(anchors, c, n, W.flag, o.st));
     CK(launch_check_idx(part_own, part_ptr[p], n, W.flag, o.st));
-    const void* Ye;
-    int dte;
-    int s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte);
-    if (s) return s;
+    const void* Ye = Y;
+    int dte = dt;
+    int s = MDS_OK;
+    if (W.G.mode < 0 && (s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
     tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, o, upload))) return s;
+    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, o, upload, &W.G))) return s;
     CK(launch_dc_procrustes(W.B.d_desc, p, W.B.v, W.B.lam, r, c, W.Tt, o.st));
     CK(launch_dc_align(W.B.d_desc, p, W.B.max_n, W.B.v, W.B.lam, W.Tt, r, anchors, part_own, f64, X, o.st));
     CK(launch_dc_lambda_bar(W.B.d_desc, p, W.B.lam, r, var, o.st));
@@ -876,14 +923,14 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
         if (own < 0 || own + c > kMaxEigN || own + c <= r) return MDS_ERR_ARG;
     }
     if (part_ptr[p] > 0 && !part_own) return MDS_ERR_ARG;
-    if (o.prec == MDS_PREC_FP8 || o.prec == MDS_PREC_BF16) return MDS_ERR_UNSUPPORTED;
+    if ((o.prec == MDS_PREC_FP8 || o.prec == MDS_PREC_BF16) && dt != MDS_IN_U8) return MDS_ERR_UNSUPPORTED;
     DcWs W;
     const size_t need = dc_layout(W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (dc_layout(W, o.ws, n, d, p, part_ptr, c, r, o.prec, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     if ((s = dc_enqueue(W, Y, dt, n, d, p, part_ptr, part_own, anchors, c, r, o, X, var, true))) return s;
-    return finish(&W.B, W.flag, o);
+    return finish(&W.B, W.flag, o, W.G.mode >= 0 ? W.G.kerr : nullptr);
 }
 
 
@@ -941,12 +988,15 @@ int plan_trial(mds_dc_plan P, int cs, const void* Y, const int64_t* own, const i
     CK(cudaMemcpyAsync(P->hbuf, P->W.B.status, sizeof(int) * p, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(P->hbuf + p, P->W.B.steps, sizeof(int) * p, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(P->hbuf + 2 * p, P->W.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    P->hbuf[2 * p + 1] = 0;
+    if (P->W.G.mode >= 0)
+        CK(cudaMemcpyAsync(P->hbuf + 2 * p + 1, P->W.G.kerr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     float f = 0.f;
     cudaEventElapsedTime(&f, P->ev[0], P->ev[5]);
     *ms = f;
-    return batch_status(P->W.B, P->hbuf, P->hbuf + p, P->hbuf[2 * p], 0);
+    return batch_status(P->W.B, P->hbuf, P->hbuf + p, P->hbuf[2 * p], P->hbuf[2 * p + 1]);
 }
 
 }  // namespace
@@ -968,7 +1018,7 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
         const int64_t own = part_ptr[j + 1] - part_ptr[j];
         if (own < 0 || own + c > kMaxEigN || own + c <= r) return MDS_ERR_ARG;
     }
-    if (o.prec == MDS_PREC_FP8 || o.prec == MDS_PREC_BF16) return MDS_ERR_UNSUPPORTED;
+    if ((o.prec == MDS_PREC_FP8 || o.prec == MDS_PREC_BF16) && dt != MDS_IN_U8) return MDS_ERR_UNSUPPORTED;
     mds_dc_plan P = new (std::nothrow) mds_dc_plan_s();
     if (!P) return MDS_ERR_NOMEM;
     P->n = n;
@@ -983,7 +1033,7 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
     cudaGetDevice(&P->device);
     const size_t need = dc_layout(P->W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
     bool ok = cudaMalloc(&P->ws, need) == cudaSuccess &&
-              cudaHostAlloc((void**)&P->hbuf, sizeof(int) * (2 * p + 1), cudaHostAllocDefault) == cudaSuccess;
+              cudaHostAlloc((void**)&P->hbuf, sizeof(int) * (2 * p + 2), cudaHostAllocDefault) == cudaSuccess;
     for (auto& e : P->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming) == cudaSuccess &&
          cudaStreamCreateWithFlags(&P->pst, cudaStreamNonBlocking) == cudaSuccess;
@@ -997,8 +1047,13 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
     o.wsb = need;
     P->o = o;
     // part descriptors and queue order stay on the device for the plan's life
+    const GramOp& G = P->W.G;
     if (cudaMemcpy(P->W.B.d_desc, P->W.B.desc.data(), sizeof(ProbDesc) * p, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(P->W.B.d_order, P->W.B.order.data(), sizeof(int) * p, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(P->W.B.d_order, P->W.B.order.data(), sizeof(int) * p, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (G.mode >= 0 &&
+         (cudaMemcpy(G.moff, G.h_moff.data(), sizeof(int) * p, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(G.units, G.h_units.data(), sizeof(int4) * G.h_units.size(), cudaMemcpyHostToDevice) !=
+              cudaSuccess))) {
         cudaGetLastError();
         mds_dc_plan_destroy(P);
         return MDS_ERR_CUDA;
@@ -1054,7 +1109,9 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         if (s == MDS_OK &&
             (cudaMemcpyAsync(P->hbuf, B.status, sizeof(int) * p, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
              cudaMemcpyAsync(P->hbuf + p, B.steps, sizeof(int) * p, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-             cudaMemcpyAsync(P->hbuf + 2 * p, P->W.flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess))
+             cudaMemcpyAsync(P->hbuf + 2 * p, P->W.flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             (P->W.G.mode >= 0 && cudaMemcpyAsync(P->hbuf + 2 * p + 1, P->W.G.kerr, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, st) != cudaSuccess)))
             s = MDS_ERR_CUDA;
         g_capture_ev = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(st, &P->graph);
@@ -1085,7 +1142,7 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
             cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]);
             g_last.stage_ms[i] = ms;
         }
-    return batch_status(B, P->hbuf, P->hbuf + P->p, P->hbuf[2 * P->p], 0);
+    return batch_status(B, P->hbuf, P->hbuf + P->p, P->hbuf[2 * P->p], P->W.G.mode >= 0 ? P->hbuf[2 * P->p + 1] : 0);
 }
 
 int mds_dc_plan_info(mds_dc_plan P, int* cluster, int64_t* graph_nodes, double* trial_ms) {

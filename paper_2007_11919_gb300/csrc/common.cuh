@@ -248,6 +248,18 @@ cudaError_t launch_gower_tck(int mode, const void* A, int64_t m, int d, const fl
                              const float* nrm_l, const float* Wp, const double* bias, int r, float* X, int* err,
                              cudaStream_t st);
 
+// Divide-and-conquer part Gram of byte rows on the tensor cores
+// (k_gower_tck.cu): members of part j encoded at operand rows moff[j] ..
+// (moff ascending, multiples of 4, slots = total rows incl. padding); units
+// are (part, row0, col0, moff) work items of 128 rows x 256 columns.
+size_t gram_operand_bytes(int mode, int64_t member_slots, int d);
+cudaError_t launch_encode_parts_u8(int mode, const uint8_t* Y, int d, const int64_t* anchors, const int64_t* own,
+                                   const ProbDesc* desc, const int* moff, int p, int64_t slots, void* ops,
+                                   float* nrm, cudaStream_t st);
+cudaError_t launch_gram_tck(int mode, const void* ops, int64_t slots, int d, const float* nrm, const int4* units,
+                            int nunits, const ProbDesc* desc, double* qarena, double* rparena, int* err,
+                            cudaStream_t st);
+
 // Host side (api.cu): queue an embedding against a model without waiting.
 int embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, char* ws, cudaStream_t st, void* X,
                   int** kerr_out);

@@ -29,6 +29,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "tc_common.cuh"
 
 namespace gbmds {
@@ -270,6 +271,197 @@ __global__ void __launch_bounds__(kThreadsK, 1)
     }
 }
 
+// ------------------------------------------------------------ part Gram
+//
+// Divide-and-conquer (Section 3.2) for byte rows: Delta_j of every part j
+// from the same operands.  Part j's members (its c connecting points, then
+// its own points) are encoded as rows moff_j .. moff_j + n_j - 1 of one
+// operand matrix (moff_j a multiple of 4).  A work unit is (part, 128-row
+// tile, 256-column chunk); the accumulator S = Y_tile Y_chunk^T gives
+// Delta = ||y_a||^2 + ||y_b||^2 - 2 S (clamped at 0, diagonal 0), stored as
+// FP32 at the start of row a's storage in the Q arena (row stride 2 * ldq
+// floats), with double-FP32 row sums per 64-column tile into
+// rp[tile * n_j + a].  Rows or columns past n_j belong to the next part and
+// are masked.
+
+struct GramArgs {
+    int units;
+    const int4* unit;           // (part, row0, col0, moff)
+    const ProbDesc* desc;
+    const float* nrm;           // member norms (moff-indexed; zero padding)
+    double* qarena;
+    double* rparena;
+    int nkb;
+    int* err;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreadsK, 1)
+    k_gram_tck(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b1,
+               const __grid_constant__ CUtensorMap tm_b2, GramArgs a) {
+    using Cfg = KCfg<MODE>;
+    using Smem = KSmem<MODE>;
+    constexpr int NST = Cfg::kStages;
+    constexpr int NB = Cfg::kNB;
+    extern __shared__ __align__(1024) uint8_t tck_smraw[];
+    Smem& S = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(tck_smraw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abort = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&S.wfull[s], 1);
+            mbar_init(&S.wempty[s], 128);
+            mbar_init(&S.acc_full[s], 1);
+            mbar_init(&S.acc_empty[s], 128);
+        }
+        mbar_init(&S.mma_done, 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem_base)),
+                     "r"(kTmemColsK)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem_base;
+    constexpr uint32_t stage_tx = kABytes + NB * kBBytes;
+    constexpr int xstep = MODE == kTckBf16 ? 64 : 128;
+
+    if (warp == 0) {
+        // ---------------- TMA producer: operand K slices and the chunk's norms
+        if (lane == 0) {
+            long long g = 0, kb = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < a.units && ok && !*abort; u += gridDim.x, ++g) {
+                const int4 w = a.unit[u];
+                const int ws = (int)(g & 1);
+                if (g >= 2 && !(ok = mbar_wait(&S.wempty[ws], (uint32_t)(((g >> 1) - 1) & 1), abort, a.err))) break;
+                mbar_expect_tx(&S.wfull[ws], (uint32_t)(kChunkK * 4));
+                bulk_load(S.nl[ws], a.nrm + w.w + w.z, (uint32_t)(kChunkK * 4), &S.wfull[ws]);
+                for (int k = 0; k < a.nkb; ++k, ++kb) {
+                    const int s = (int)(kb % NST);
+                    const long long use = kb / NST;
+                    if (use > 0 && !(ok = mbar_wait(&S.empty[s], (uint32_t)((use - 1) & 1), abort, a.err))) break;
+                    mbar_expect_tx(&S.full[s], stage_tx);
+                    tma_load_2d(S.a[s], &tm_a, k * xstep, w.w + w.y, &S.full[s]);
+                    tma_load_2d(S.b[s][0], &tm_b1, k * xstep, w.w + w.z, &S.full[s]);
+                    if (NB == 2) tma_load_2d(S.b[s][NB - 1], &tm_b2, k * xstep, w.w + w.z, &S.full[s]);
+                }
+            }
+            for (long long q = kb - NST < 0 ? 0 : kb - NST; q < kb; ++q)
+                mbar_drain(&S.full[q % NST], (uint32_t)((q / NST) & 1), a.err);
+            for (long long q = g - 2 < 0 ? 0 : g - 2; q < g; ++q)
+                mbar_drain(&S.wfull[q & 1], (uint32_t)((q >> 1) & 1), a.err);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            long long g = 0, kb = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < a.units && ok && !*abort; u += gridDim.x, ++g) {
+                const int as = (int)(g & 1);
+                if (g >= 2 && !(ok = mbar_wait(&S.acc_empty[as], (uint32_t)(((g >> 1) - 1) & 1), abort, a.err))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(as * kChunkK);
+                for (int k = 0; k < a.nkb; ++k, ++kb) {
+                    const int s = (int)(kb % NST);
+                    if (!(ok = mbar_wait(&S.full[s], (uint32_t)((kb / NST) & 1), abort, a.err))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = umma_desc(smem_u32(S.a[s]) + kk * 32);
+                        const uint64_t b1 = umma_desc(smem_u32(S.b[s][0]) + kk * 32);
+                        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+                        if (MODE == kTckBf16) {
+                            umma_bf16(d, ad, b1, Cfg::kIdesc, acc);
+                        } else {
+                            const uint64_t b2 = umma_desc(smem_u32(S.b[s][NB - 1]) + kk * 32);
+                            umma_f8(d, ad, b1, Cfg::kIdesc, acc);
+                            umma_f8(d, ad, b2, Cfg::kIdesc, 1u);
+                        }
+                    }
+                    umma_commit(&S.empty[s]);
+                }
+                if (ok) umma_commit(&S.acc_full[as]);
+            }
+            umma_commit(&S.mma_done);
+            mbar_drain(&S.mma_done, 0, a.err);
+        }
+    } else {
+        // ---------------- epilogue: warps 2-5, one tile row per thread
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        long long g = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < a.units && ok && !*abort; u += gridDim.x, ++g) {
+            const int4 w = a.unit[u];
+            const ProbDesc P = a.desc[w.x];
+            const int n = P.n;
+            const int ra = w.y + row;                       // part-local row
+            const float ny = ra < n ? a.nrm[w.w + ra] : 0.f;
+            float* Qrow = reinterpret_cast<float*>(a.qarena + P.q_off) + (int64_t)ra * 2 * P.ldq;
+            double* rp = a.rparena + P.rp_off;
+            const int as = (int)(g & 1);
+            const uint32_t par = (uint32_t)((g >> 1) & 1);
+            if (!(ok = mbar_wait(&S.acc_full[as], par, abort, a.err) && mbar_wait(&S.wfull[as], par, abort, a.err)))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float* ns = S.nl[as];
+            float rh = 0.f, rl = 0.f;
+#pragma unroll 1
+            for (int cb = 0; cb < kChunkK; cb += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(as * kChunkK + cb), v);
+                const int b0 = w.z + cb;                     // part-local column of v[0]
+                if (ra < n && b0 < n) {
+                    float dv[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        float dist = fmaxf(fmaf(-2.f, v[e], ny + ns[cb + e]), 0.f);
+                        if (b0 + e == ra || b0 + e >= n) dist = 0.f;
+                        dv[e] = dist;
+                        df_add(rh, rl, dist, 0.f);
+                    }
+                    if (b0 + 32 <= n) {
+#pragma unroll
+                        for (int q4 = 0; q4 < 8; ++q4)
+                            reinterpret_cast<float4*>(Qrow + b0)[q4] =
+                                make_float4(dv[4 * q4], dv[4 * q4 + 1], dv[4 * q4 + 2], dv[4 * q4 + 3]);
+                    } else {
+                        for (int e = 0; e < n - b0; ++e) Qrow[b0 + e] = dv[e];
+                    }
+                }
+                if ((cb & 63) == 32) {                       // a 64-column tile is complete
+                    const int tb = (w.z + cb) >> 6;
+                    if (ra < n && tb * 64 < n) rp[(int64_t)tb * n + ra] = (double)rh + (double)rl;
+                    rh = rl = 0.f;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&S.acc_empty[as]);
+            mbar_arrive(&S.wempty[as]);
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemColsK)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------ operand encodings
 
 __device__ __forceinline__ uint8_t e4m3(float v) {
@@ -406,6 +598,60 @@ __global__ void k_encode_landmarks_u8(const uint8_t* __restrict__ Y, int64_t ny,
     }
 }
 
+// Members of every part -> operand rows moff_j + a (kFp8: A = [16h | g] and
+// B2 = [g | 16h]; kBf16: BF16 rows) and exact norms; one warp per member.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_encode_parts_u8(const uint8_t* __restrict__ Y, int d,
+                                                         const int64_t* __restrict__ anchors,
+                                                         const int64_t* __restrict__ own,
+                                                         const ProbDesc* __restrict__ desc,
+                                                         const int* __restrict__ moff, int p, int64_t total,
+                                                         void* __restrict__ A, void* __restrict__ B2,
+                                                         float* __restrict__ nrm) {
+    __shared__ uint8_t t_hi[16], t_lo[16];
+    fill_nibble_tables(t_hi, t_lo);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // member slot (moff space)
+    if (m >= total) return;
+    // the part whose slots contain m (moff ascending)
+    int lo = 0, hi = p - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (moff[mid] <= m) lo = mid;
+        else hi = mid - 1;
+    }
+    const ProbDesc P = desc[lo];
+    const int a = (int)(m - moff[lo]);
+    const bool real = a < P.n;
+    const uint8_t* y = Y + (real ? member_row(P, anchors, own, a) : 0) * d;
+    uint32_t ss = 0;
+    if (MODE == kTckBf16) {
+        const int ld = round_up(d, 8);
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(A) + m * ld;
+        for (int k = lane; k < ld; k += 32) {
+            const uint32_t v = real && k < d ? y[k] : 0u;
+            ss += v * v;
+            o[k] = __float2bfloat16_rn((float)v);
+        }
+    } else {
+        const int dh = round_up(d, 16);
+        uint8_t* o = static_cast<uint8_t*>(A) + m * 2 * dh;
+        uint8_t* o2 = static_cast<uint8_t*>(B2) + m * 2 * dh;
+        for (int k = lane; k < dh; k += 32) {
+            const uint32_t v = real && k < d ? y[k] : 0u;
+            ss += v * v;
+            const uint8_t h = t_hi[v >> 4], g = t_lo[v & 15];
+            o[k] = h;
+            o[dh + k] = g;
+            o2[k] = g;
+            o2[dh + k] = h;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
+    if (lane == 0) nrm[m] = (float)ss;
+}
+
 __global__ void k_pad_w_rows(const float* __restrict__ W, int l, int r, int rp, int lpad, float* __restrict__ Wp) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)lpad * rp) return;
@@ -479,6 +725,73 @@ cudaError_t launch_pad_w_rows(const float* W, int l, int r, float* Wp, cudaStrea
     const int rp = gower_tc_rp(r), lpad = tck_lpad(l);
     const int64_t total = (int64_t)lpad * rp;
     k_pad_w_rows<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(W, l, r, rp, lpad, Wp);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+size_t gram_operand_bytes(int mode, int64_t member_slots, int d) {
+    return (mode == kTckFp8 ? 2 : 1) * tck_operand_bytes(mode, member_slots, d);
+}
+
+cudaError_t launch_encode_parts_u8(int mode, const uint8_t* Y, int d, const int64_t* anchors, const int64_t* own,
+                                   const ProbDesc* desc, const int* moff, int p, int64_t slots, void* ops,
+                                   float* nrm, cudaStream_t st) {
+    if (slots <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((slots + 7) / 8);
+    void* b2 = static_cast<uint8_t*>(ops) + tck_operand_bytes(mode, slots, d);
+    if (mode == kTckBf16)
+        k_encode_parts_u8<kTckBf16><<<blocks, 256, 0, st>>>(Y, d, anchors, own, desc, moff, p, slots, ops, b2, nrm);
+    else
+        k_encode_parts_u8<kTckFp8><<<blocks, 256, 0, st>>>(Y, d, anchors, own, desc, moff, p, slots, ops, b2, nrm);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tck(int mode, const void* ops, int64_t slots, int d, const float* nrm, const int4* units,
+                            int nunits, const ProbDesc* desc, double* qarena, double* rparena, int* err,
+                            cudaStream_t st) {
+    if (nunits <= 0) return cudaSuccess;
+    CUtensorMap ma, mb1, mb2;
+    int64_t cols;
+    bool ok;
+    if (mode == kTckBf16) {
+        cols = round_up(d, 8);
+        ok = make_map_k(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ops, slots, cols, kRowsK) &&
+             make_map_k(&mb1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ops, slots, cols, kChunkK);
+        mb2 = mb1;
+    } else {
+        cols = 2 * round_up(d, 16);
+        const uint8_t* b2 = static_cast<const uint8_t*>(ops) + (size_t)slots * cols;
+        ok = make_map_k(&ma, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, ops, slots, cols, kRowsK) &&
+             make_map_k(&mb1, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, ops, slots, cols, kChunkK) &&
+             make_map_k(&mb2, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, b2, slots, cols, kChunkK);
+    }
+    if (!ok) return cudaErrorInvalidValue;
+    GramArgs a;
+    a.units = nunits;
+    a.unit = units;
+    a.desc = desc;
+    a.nrm = nrm;
+    a.qarena = qarena;
+    a.rparena = rparena;
+    a.nkb = (int)((cols * (mode == kTckBf16 ? 2 : 1) + 127) / 128);
+    a.err = err;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nunits < sms ? nunits : sms;
+    cudaError_t e;
+    if (mode == kTckBf16) {
+        const size_t smem = sizeof(KSmem<kTckBf16>) + 1024;
+        e = cudaFuncSetAttribute(k_gram_tck<kTckBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gram_tck<kTckBf16><<<grid, kThreadsK, smem, st>>>(ma, mb1, mb2, a);
+    } else {
+        const size_t smem = sizeof(KSmem<kTckFp8>) + 1024;
+        e = cudaFuncSetAttribute(k_gram_tck<kTckFp8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gram_tck<kTckFp8><<<grid, kThreadsK, smem, st>>>(ma, mb1, mb2, a);
+    }
     note_launch(1);
     return cudaGetLastError();
 }

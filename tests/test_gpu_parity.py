@@ -408,3 +408,33 @@ def test_dc_plan_fixed_cluster_f64(gb):
     Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 3)
     assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
     assert rel(host(var), lo) < LAM_TOL["f64"]
+
+
+@pytest.mark.parametrize("prec", ["fp8", "bf16"])
+@pytest.mark.parametrize("n,d,c,lo,hi", [(6000, 784, 50, 900, 1100), (3000, 37, 12, 300, 420)])
+def test_dc_u8_tensor_core_gram(gb, prec, n, d, c, lo, hi):
+    """Divide-and-conquer of byte rows with the part Gram on tcgen05 (exact
+    BF16 or E4M3 nibble operands): against the oracle, and against the FP32
+    distance-tile path on the same data."""
+    Y = W.image_like(n, d, seed=d)
+    part = W.partitions_uneven(n, c, lo, hi, seed=d)
+    r = 10 if d > 100 else 4
+    X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), r, prec)
+    Xf, vf = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), r, "f32")
+    assert O.aligned_rel_error(host(X), host(Xf)) < 1e-5
+    Xo, lo_, _ = O.divide_conquer_mds(Y.astype(np.float64), part.anchors, part.ptr, part.own, r)
+    assert O.aligned_rel_error(host(X), Xo) < TOL["bf16"]
+    assert rel(host(var), lo_) < LAM_TOL["f32"]
+
+
+def test_dc_plan_fp8(gb):
+    from paper_2007_11919_gb300.mds import DcPlan
+    Y = W.image_like(5000, 784, seed=2)
+    part = W.partitions_equal(5000, 1000, 50, seed=2)
+    plan = DcPlan(5000, 784, torch.uint8, part.ptr, 50, 10, "fp8", tune=True)
+    Yd, anc, own = dev(Y), dev(part.anchors), dev(part.own)
+    X, var = plan.execute(Yd, anc, own)
+    Xd, vd = gb.mds_divide_conquer(Yd, anc, part.ptr, own, 10, "fp8", cluster=plan.info()["cluster"])
+    assert torch.equal(X, Xd) and torch.equal(var, vd)
+    Xo, lo_, _ = O.divide_conquer_mds(Y.astype(np.float64), part.anchors, part.ptr, part.own, 10)
+    assert O.aligned_rel_error(host(X), Xo) < TOL["bf16"]

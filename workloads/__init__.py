@@ -223,8 +223,8 @@ SERVE_SIZES = (1, 50_000)
 IMAGE_FP8 = Workload("image_fp8_n814255_d784_l2000_r10", "interp", 814_255, 784, 10, "fp8", l=2000,
                      c=50)
 # The same image-like set by divide-and-conquer: parts of l = 2000 points with
-# c = 50 shared connecting points (Section 3.2 layout), FP32 distances.
-IMAGE_DC = Workload("image_dc_f32_n814255_d784_parts2000_c50_r10", "dc", 814_255, 784, 10, "f32", l=2000,
+# c = 50 shared connecting points (Section 3.2 layout), FP8 nibble distance tiles.
+IMAGE_DC = Workload("image_dc_fp8_n814255_d784_parts2000_c50_r10", "dc", 814_255, 784, 10, "fp8", l=2000,
                     c=50)
 
 
