@@ -143,6 +143,8 @@ struct Batch {
     int *status = nullptr, *steps = nullptr;
     std::vector<int> order;            // problems, largest first (eigen-solver queue order)
     int *d_order = nullptr, *counter = nullptr;
+    double* tscr = nullptr;            // single-problem team exchange buffers
+    unsigned* tbar = nullptr;          // team barrier words
 };
 
 void plan_batch(Batch& B, const std::vector<int>& sizes, const std::vector<int64_t>& own_off,
@@ -195,6 +197,10 @@ void carve_batch(Batch& B, Arena& A) {
     B.steps = A.take<int>(B.p);
     B.d_order = A.take<int>(B.p);
     B.counter = A.take<int>(1);
+    if (B.p == 1) {
+        B.tscr = A.take<double>(lanczos_team_scratch_doubles(B.max_n, B.mmax, B.r));
+        B.tbar = A.take<unsigned>(4);
+    }
 }
 
 int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
@@ -282,9 +288,13 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.tol = o.tol;
     a.rank_tol = o.rank_tol;
     a.max_n = B.max_n;
+    a.team = 1;
+    a.tscr = B.tscr;
+    a.tbar = B.tbar;
+    if (B.tbar) CK(cudaMemsetAsync(B.tbar, 0, 4 * sizeof(unsigned), o.st));
     tmark(2, o.st);
     g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r);
-    CK(launch_lanczos(a, g_cluster, o.st));
+    CK(launch_lanczos(a, g_cluster, o.st, o.cluster == 0));
     tmark(3, o.st);
     return MDS_OK;
 }

@@ -151,11 +151,16 @@ struct LanczosArgs {
     double tol;
     double rank_tol;
     int max_n;
+    int team;           // clusters sharing one problem (1 = the cluster alone)
+    double* tscr;       // team exchange buffers (lanczos_team_scratch_doubles)
+    unsigned* tbar;     // team barrier words [arrivals, generation, abort], zero before the launch
 };
+constexpr int kMaxTeam = 32;   // clusters per team
+size_t lanczos_team_scratch_doubles(int max_n, int mmax, int r);
 __host__ __device__ inline size_t lanczos_scratch_per_problem(int mmax, int r) {
     return (size_t)(r * 7 + 2) * (mmax + 1) + 8;
 }
-cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st);
+cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st, bool allow_team);
 // Shared memory one CTA of the eigen-solver needs for a cluster of cs CTAs.
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r);
 constexpr size_t kMaxSmem = 220 * 1024;

@@ -276,6 +276,83 @@ __device__ void tri_inverse_iteration_df(const float2* a, const float2* b, int k
     }
 }
 
+// ------------------------------------------------------------------- teams
+//
+// A problem is solved by a team of G clusters of cs CTAs; G = 1 is the
+// cluster alone (every batched problem).  A single large problem (a landmark
+// set) uses G > 1 clusters of one cooperative launch: inside a cluster the
+// exchanges go through DSMEM as before, across clusters through global memory
+// behind a grid barrier (L2-only loads of the exchange buffers, bounded
+// waits).  All CTAs of a team take the same decisions from the same sums.
+struct Team {
+    int G, g, T, qt;    // clusters, this cluster, CTAs in all, this CTA's rank
+    double* v;          // n: the current Lanczos vector (G > 1)
+    double* part;       // 2 x G x (mmax + 2): cluster partial sums, double-buffered
+    double* theta;      // kMaxR
+    double* resid;      // kMaxR
+    double* xv;         // r x (mmax + 1)
+    double* sgn;        // T x kMaxR x 3
+    unsigned* bar;      // grid barrier: arrivals, generation
+    int* abort;         // set when a barrier wait or a stage wait timed out
+};
+
+// Grid barrier of the team (every CTA's thread 0 arrives; the last one opens
+// the next generation).  False after a timeout anywhere in the team.
+__device__ bool team_sync(const Team& tm) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = tm.bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(tm.bar, 1u) == (unsigned)(tm.T - 1)) {
+            atomicExch(tm.bar, 0u);
+            __threadfence();
+            atomicAdd(tm.bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = tc::global_ns();
+            while (*gen == g0) {
+                if (*(volatile int*)tm.abort) {
+                    ok = 0;
+                    break;
+                }
+                if (tc::global_ns() - t0 > tc::kWaitNs) {
+                    atomicExch(tm.abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum over the team of part[i], lo <= i < hi, into out (and outdf as
+// double-FP32 pairs): cluster sums through DSMEM, then (G > 1) the clusters'
+// sums in cluster order through the team buffers of parity pb.
+__device__ void team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int cs, int mmax, int pb, double* part,
+                               double* out, double* outdf, int lo, int hi) {
+    cluster_allreduce(cl, part, out, tm.G > 1 ? nullptr : outdf, lo, hi, cs);
+    if (tm.G == 1) return;
+    const int stride = mmax + 2;
+    double* gp = tm.part + (size_t)pb * tm.G * stride;
+    if (q == 0)
+        for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) gp[(size_t)tm.g * stride + i] = out[i];
+    team_sync(tm);
+    for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
+        double sum = 0.0;
+        for (int h = 0; h < tm.G; ++h) sum += __ldcg(gp + (size_t)h * stride + i);
+        out[i] = sum;
+        if (outdf) reinterpret_cast<float2*>(outdf)[i] = df_of(sum);
+    }
+    __syncthreads();
+}
+
 // Entry `row` of the fixed pseudo-random start vector (splitmix64 of the row
 // index, mapped to [-1, 1)).
 __device__ __forceinline__ double start_entry(int row) {
@@ -565,11 +642,12 @@ __device__ void cgs_update(const double* B, int ldq, int r0, int nr, int ia, int
 // One eigenproblem (part pj) solved by the calling cluster.
 template <bool DF>
 __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q, const Smem& S,
-                              int& s_flag, QStream& Qs) {
+                              int& s_flag, QStream& Qs, const Team& tm) {
     const ProbDesc P = A.desc[pj];
     const int n = P.n, ldq = P.ldq, r = A.r;
-    const int R = (n + cs - 1) / cs;
-    const int r0 = min(n, q * R), r1 = min(n, r0 + R), nr = r1 - r0;
+    const int T = tm.T, qt = tm.qt;   // CTAs of the team and this CTA's rank (cs, q when G = 1)
+    const int R = (n + T - 1) / T;
+    const int r0 = min(n, qt * R), r1 = min(n, r0 + R), nr = r1 - r0;
     const double* Q = A.qarena + P.q_off;
     double* B = A.barena + P.b_off;
     const int kmax = min(A.mmax, n);
@@ -594,7 +672,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     {
         const double s = block_sum(loc, S.red);
         if (tid == 0) part[pb][0] = s;
-        cluster_allreduce(cl, part[pb], S.cfull, nullptr, 0, 1, cs);
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, nullptr, 0, 1);
         pb ^= 1;
         if (tid == 0) S.red[kWarps + 3] = 1.0 / sqrt(S.cfull[0]);
         __syncthreads();
@@ -609,6 +687,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 S.vloc[i] = v;
                 B[r0 + i] = v;
             }
+            if (tm.G > 1) tm.v[r0 + i] = S.vloc[i];
         }
     }
     if (tid == 0) {
@@ -624,10 +703,15 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
 
     for (int j = 0; j < kmax; ++j) {
         // ---- gather v_j from all ranks (8-byte entries, copied as they are)
-        cl.sync();
-        for (int i = tid; i < n; i += kThreads) {
-            const int src = i / R;
-            S.vfull[i] = cl.map_shared_rank(S.vloc, src)[i - src * R];
+        if (tm.G > 1) {
+            team_sync(tm);
+            for (int i = tid; i < n; i += kThreads) S.vfull[i] = __ldcg(tm.v + i);
+        } else {
+            cl.sync();
+            for (int i = tid; i < n; i += kThreads) {
+                const int src = i / R;
+                S.vfull[i] = cl.map_shared_rank(S.vloc, src)[i - src * R];
+            }
         }
         __syncthreads();
 
@@ -641,14 +725,14 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         const int ia = j > 0 ? j - 1 : 0;
         cgs_dots<DF>(B, ldq, r0, nr, ia, j, S.wloc, part[pb], false);
         __syncthreads();
-        cluster_allreduce(cl, part[pb], S.cfull, S.cdf, ia, j + 1, cs);
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1);
         pb ^= 1;
         const double a1 = S.cfull[j];
         cgs_update<DF>(B, ldq, r0, nr, ia, j, S.cfull, S.cdf, S.wloc);
         __syncthreads();
         cgs_dots<DF>(B, ldq, r0, nr, 0, j, S.wloc, part[pb], true);
         __syncthreads();
-        cluster_allreduce(cl, part[pb], S.cfull, S.cdf, 0, j + 2, cs);
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, 0, j + 2);
         pb ^= 1;
         cgs_update<DF>(B, ldq, r0, nr, 0, j, S.cfull, S.cdf, S.wloc);
         if (warp == 0) {
@@ -685,7 +769,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             // the eigenvector x_i of T_k (inverse iteration) and the residual
             // beta_j |x_i[k-1]|; all CTAs then read every theta and residual
             // through DSMEM and take the same decision.
-            const int mine = (r - q + cs - 1) / cs;  // eigenvalues owned by this CTA
+            const int mine = (r - qt + T - 1) / T;  // eigenvalues owned by this CTA
             // T_k scaled by a power of two to norm ~1, as double-FP32 arrays
             int ex;
             frexp(tnorm, &ex);
@@ -717,7 +801,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const float2 pert = df_of(0x1p-44 * fmax(tnorm * scale, 0.5));
                 float2* bd = reinterpret_cast<float2*>(S.band + (size_t)warp * 3 * L);
                 for (int m = warp; m < mine; m += kWarps) {   // one warp per eigenvalue
-                    const int i = q + cs * m;
+                    const int i = qt + T * m;
                     double lo = gl, hi = gu;
                     if (have_vectors) {
                         // lane 0 tests the lower end, lane 1 the upper end of the warm bracket
@@ -743,12 +827,27 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                     __syncwarp();
                 }
             }
-            cl.sync();
-            for (int i = tid; i < r; i += kThreads) {
-                const int owner = i % cs;
-                if (owner != q) {
-                    S.theta[i] = cl.map_shared_rank(S.theta, owner)[i];
-                    S.resid[i] = cl.map_shared_rank(S.resid, owner)[i];
+            if (tm.G > 1) {
+                // owners publish theta and residuals; every CTA reads them all
+                __syncthreads();
+                for (int i = tid; i < r; i += kThreads)
+                    if (i % T == qt) {
+                        tm.theta[i] = S.theta[i];
+                        tm.resid[i] = S.resid[i];
+                    }
+                team_sync(tm);
+                for (int i = tid; i < r; i += kThreads) {
+                    S.theta[i] = __ldcg(tm.theta + i);
+                    S.resid[i] = __ldcg(tm.resid + i);
+                }
+            } else {
+                cl.sync();
+                for (int i = tid; i < r; i += kThreads) {
+                    const int owner = i % cs;
+                    if (owner != q) {
+                        S.theta[i] = cl.map_shared_rank(S.theta, owner)[i];
+                        S.resid[i] = cl.map_shared_rank(S.resid, owner)[i];
+                    }
                 }
             }
             __syncthreads();
@@ -763,7 +862,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 S.red[kWarps + 1] = worst;
                 s_flag = ok ? 1 : 0;
             }
-            cl.sync();  // owners keep theta/resid until every CTA has read them
+            if (tm.G > 1) __syncthreads();
+            else cl.sync();  // owners keep theta/resid until every CTA has read them
             have_vectors = true;
             if (s_flag & 1) {
                 converged = true;
@@ -793,6 +893,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const float2 v = df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
                 reinterpret_cast<float2*>(S.vloc)[rr] = v;
                 reinterpret_cast<float2*>(B)[(int64_t)(j + 1) * ldq + r0 + rr] = v;
+                if (tm.G > 1) reinterpret_cast<float2*>(tm.v)[r0 + rr] = v;
             }
         } else {
             const double binv = S.red[42];
@@ -800,6 +901,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const double v = S.wloc[rr] * binv;
                 S.vloc[rr] = v;
                 B[(int64_t)(j + 1) * ldq + r0 + rr] = v;
+                if (tm.G > 1) tm.v[r0 + rr] = v;
             }
         }
         __syncthreads();
@@ -807,13 +909,19 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
 
     // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
     qok = qs_drain(Qs) && qok;
-    if (!qok) S.red[43] = 1.0;   // zero since the last problem; every writer stores 1
-    __syncthreads();
-    cl.sync();
     bool any_timeout = false;
-    for (int qq = 0; qq < cs; ++qq) any_timeout |= cl.map_shared_rank(S.red, qq)[43] == 1.0;
-    cl.sync();   // every CTA has read the flags before S.red is reused
-    if (tid == 0) S.red[43] = 0.0;
+    if (tm.G > 1) {
+        if (!qok) atomicExch(tm.abort, 1);
+        team_sync(tm);
+        any_timeout = *(volatile int*)tm.abort != 0;
+    } else {
+        if (!qok) S.red[43] = 1.0;   // zero since the last problem; every writer stores 1
+        __syncthreads();
+        cl.sync();
+        for (int qq = 0; qq < cs; ++qq) any_timeout |= cl.map_shared_rank(S.red, qq)[43] == 1.0;
+        cl.sync();   // every CTA has read the flags before S.red is reused
+        if (tid == 0) S.red[43] = 0.0;
+    }
     int status = kDevOk;
     if (k < r || !have_vectors) {
         status = kDevRank;
@@ -822,51 +930,89 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         if (!(S.theta[r - 1] > 0.0) || !(S.theta[r - 1] > A.rank_tol * S.theta[0])) status = kDevRank;
     }
     if (any_timeout) status = kDevTimeout;
-    if (q == 0 && status != kDevRank) {
-        // rank 0 collects the eigenvectors of T_k computed by the other CTAs
-        for (int e = tid; e < r * k; e += kThreads) {
-            const int i = e / k, t = e % k;
-            if (i % cs != 0) S.xv[(size_t)i * L + t] = cl.map_shared_rank(S.xv, i % cs)[(size_t)i * L + t];
-        }
-        __syncthreads();
-    }
-    if (q == 0 && status != kDevRank && warp == 0) {
-        // modified Gram-Schmidt across the r inverse-iteration vectors (shared memory)
+    // rank 0 of the team collects the eigenvectors of T_k from their owners,
+    // orthonormalises them (modified Gram-Schmidt, warp 0, shared memory) and
+    // every other CTA copies the result
+    auto mgs = [&]() {
         for (int i = 0; i < r; ++i) {
             double* xi = S.xv + (size_t)i * L;
             for (int m = 0; m < i; ++m) {
                 const double* xm = S.xv + (size_t)m * L;
-                double s = 0.0;
-                for (int t = lane; t < k; t += 32) s += xi[t] * xm[t];
-                s = warp_sum(s);
-                for (int t = lane; t < k; t += 32) xi[t] -= s * xm[t];
+                double sm = 0.0;
+                for (int t = lane; t < k; t += 32) sm += xi[t] * xm[t];
+                sm = warp_sum(sm);
+                for (int t = lane; t < k; t += 32) xi[t] -= sm * xm[t];
                 __syncwarp();
             }
-            double s = 0.0;
-            for (int t = lane; t < k; t += 32) s += xi[t] * xi[t];
-            s = warp_sum(s);
-            const double inv = 1.0 / sqrt(s);
+            double sm = 0.0;
+            for (int t = lane; t < k; t += 32) sm += xi[t] * xi[t];
+            sm = warp_sum(sm);
+            const double inv = 1.0 / sqrt(sm);
             for (int t = lane; t < k; t += 32) xi[t] *= inv;
             __syncwarp();
         }
-    }
-    cl.sync();
-    if (status == kDevRank) {
-        if (q == 0 && tid == 0) {
-            A.status[pj] = status;
-            A.steps[pj] = k;
+    };
+    if (tm.G > 1) {
+        if (status != kDevRank)
+            for (int e = tid; e < r * k; e += kThreads) {
+                const int i = e / k, t = e % k;
+                if (i % T == qt) tm.xv[(size_t)i * L + t] = S.xv[(size_t)i * L + t];
+            }
+        team_sync(tm);
+        if (qt == 0 && status != kDevRank) {
+            for (int e = tid; e < r * k; e += kThreads) {
+                const int i = e / k, t = e % k;
+                S.xv[(size_t)i * L + t] = __ldcg(tm.xv + (size_t)i * L + t);
+            }
+            __syncthreads();
+            if (warp == 0) mgs();
+            __syncthreads();
+            for (int e = tid; e < r * k; e += kThreads) {
+                const int i = e / k, t = e % k;
+                tm.xv[(size_t)i * L + t] = S.xv[(size_t)i * L + t];
+            }
         }
-        return;
-    }
-    // the other CTAs copy the eigenvectors of T_k from rank 0 (DSMEM)
-    if (q != 0) {
-        const double* src = cl.map_shared_rank(S.xv, 0);
-        for (int e = tid; e < r * k; e += kThreads) {
-            const int i = e / k, t = e % k;
-            S.xv[(size_t)i * L + t] = src[(size_t)i * L + t];
+        team_sync(tm);
+        if (status == kDevRank) {
+            if (qt == 0 && tid == 0) {
+                A.status[pj] = status;
+                A.steps[pj] = k;
+            }
+            return;
         }
+        if (qt != 0)
+            for (int e = tid; e < r * k; e += kThreads) {
+                const int i = e / k, t = e % k;
+                S.xv[(size_t)i * L + t] = __ldcg(tm.xv + (size_t)i * L + t);
+            }
+        __syncthreads();
+    } else {
+        if (q == 0 && status != kDevRank) {
+            for (int e = tid; e < r * k; e += kThreads) {
+                const int i = e / k, t = e % k;
+                if (i % cs != 0) S.xv[(size_t)i * L + t] = cl.map_shared_rank(S.xv, i % cs)[(size_t)i * L + t];
+            }
+            __syncthreads();
+        }
+        if (q == 0 && status != kDevRank && warp == 0) mgs();
+        cl.sync();
+        if (status == kDevRank) {
+            if (q == 0 && tid == 0) {
+                A.status[pj] = status;
+                A.steps[pj] = k;
+            }
+            return;
+        }
+        // the other CTAs copy the eigenvectors of T_k from rank 0 (DSMEM)
+        if (q != 0) {
+            const double* src = cl.map_shared_rank(S.xv, 0);
+            for (int e = tid; e < r * k; e += kThreads) {
+                const int i = e / k, t = e % k;
+                S.xv[(size_t)i * L + t] = src[(size_t)i * L + t];
+            }
+        }
+        cl.sync();   // rank 0's vectors have been copied before any CTA rewrites its own
     }
-    cl.sync();   // rank 0's vectors have been copied before any CTA rewrites its own
     if constexpr (DF) {
         // s_i as double-FP32 pairs, in place
         for (int e = tid; e < r * k; e += kThreads) {
@@ -939,29 +1085,49 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             S.sgn[3 * i + 2] = bestv;
         }
     }
-    cl.sync();
     double* flip = S.sgn + 3 * kMaxR;  // kMaxR slots after the (|max|, row, value) triples
-    if (tid < r) {
-        double best = -1.0, bestv = 0.0, brow = 1e300;
-        for (int qq = 0; qq < cs; ++qq) {
-            const double* o = cl.map_shared_rank(S.sgn, qq) + 3 * tid;
-            if (o[0] > best || (o[0] == best && o[1] < brow)) {
-                best = o[0];
-                brow = o[1];
-                bestv = o[2];
+    if (tm.G > 1) {
+        __syncthreads();
+        for (int e = tid; e < 3 * r; e += kThreads) tm.sgn[(size_t)qt * 3 * kMaxR + e] = S.sgn[e];
+        team_sync(tm);
+        if (tid < r) {
+            double best = -1.0, bestv = 0.0, brow = 1e300;
+            for (int qq = 0; qq < T; ++qq) {
+                const double* o = tm.sgn + (size_t)qq * 3 * kMaxR + 3 * tid;
+                const double o0 = __ldcg(o), o1 = __ldcg(o + 1), o2 = __ldcg(o + 2);
+                if (o0 > best || (o0 == best && o1 < brow)) {
+                    best = o0;
+                    brow = o1;
+                    bestv = o2;
+                }
             }
+            flip[tid] = bestv < 0.0 ? -1.0 : 1.0;
         }
-        flip[tid] = bestv < 0.0 ? -1.0 : 1.0;
+        __syncthreads();
+    } else {
+        cl.sync();
+        if (tid < r) {
+            double best = -1.0, bestv = 0.0, brow = 1e300;
+            for (int qq = 0; qq < cs; ++qq) {
+                const double* o = cl.map_shared_rank(S.sgn, qq) + 3 * tid;
+                if (o[0] > best || (o[0] == best && o[1] < brow)) {
+                    best = o[0];
+                    brow = o[1];
+                    bestv = o[2];
+                }
+            }
+            flip[tid] = bestv < 0.0 ? -1.0 : 1.0;
+        }
+        cl.sync();  // peers are done reading S.sgn before any CTA exits
     }
-    cl.sync();  // peers are done reading S.sgn before any CTA exits
     for (int rr = tid; rr < nr; rr += kThreads)
         for (int i = 0; i < r; ++i) V[(int64_t)(r0 + rr) * r + i] *= flip[i];
-    if (q == 0 && tid == 0) {
+    if (qt == 0 && tid == 0) {
         for (int i = 0; i < r; ++i) A.lam[(size_t)pj * r + i] = S.theta[i];
         A.status[pj] = status;
         A.steps[pj] = k;
     }
-    if (q == 0)
+    if (qt == 0)
         for (int t = tid; t < k; t += kThreads) {
             scr[t] = S.alpha[t];
             scr[L + t] = S.beta[t];
@@ -991,13 +1157,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     Qs.cst = Qs.ist = 0;
     Qs.inflight = 0;
     Qs.phase = 0;
+    Team tm;
+    tm.G = A.team > 1 ? A.team : 1;
+    tm.g = (int)blockIdx.x / cs;
+    tm.T = tm.G * cs;
+    tm.qt = tm.G > 1 ? (int)blockIdx.x : q;
+    {
+        double* t = A.tscr;
+        tm.v = t;
+        t += round_up(A.max_n, 4);
+        tm.part = t;
+        t += (size_t)2 * tm.G * (A.mmax + 2);
+        tm.theta = t;
+        t += kMaxR;
+        tm.resid = t;
+        t += kMaxR;
+        tm.xv = t;
+        t += (size_t)A.r * (A.mmax + 1);
+        tm.sgn = t;
+        tm.bar = A.tbar;
+        tm.abort = reinterpret_cast<int*>(A.tbar + 2);
+    }
+    if (tm.G > 1) {   // one problem for the whole team
+        solve_problem<DF>(A, A.order[0], cl, cs, q, S, s_flag, Qs, tm);
+        return;
+    }
     for (;;) {
         if (q == 0 && threadIdx.x == 0) s_next = atomicAdd(A.counter, 1);
         cl.sync();
         const int next = q == 0 ? s_next : *cl.map_shared_rank(&s_next, 0);
         cl.sync();  // every CTA has read the index before rank 0 takes another
         if (next >= A.p) break;
-        solve_problem<DF>(A, A.order[next], cl, cs, q, S, s_flag, Qs);
+        solve_problem<DF>(A, A.order[next], cl, cs, q, S, s_flag, Qs, tm);
     }
 }
 
@@ -1005,6 +1196,53 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
 
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
     return smem_doubles(max_n, cs, mmax, r) * sizeof(double) + kMaxR * sizeof(double);
+}
+
+size_t lanczos_team_scratch_doubles(int max_n, int mmax, int r) {
+    return (size_t)round_up(max_n, 4) + (size_t)2 * kMaxTeam * (mmax + 2) + 2 * kMaxR + (size_t)r * (mmax + 1) +
+           (size_t)kMaxTeam * 8 * 3 * kMaxR;
+}
+
+// A single problem spread over G clusters of 8 CTAs (one CTA per SM) in one
+// cooperative launch.  Returns cudaErrorNotSupported when the problem is too
+// small or the launch form is not available (the caller then uses one cluster).
+template <bool DF>
+static cudaError_t launch_lanczos_team(LanczosArgs a, cudaStream_t st) {
+    constexpr int cs = 8;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int G = std::min(std::min(sms / cs, kMaxTeam), a.max_n / (cs * 16));   // at least 16 rows per CTA
+    if (G < 2) return cudaErrorNotSupported;
+    const size_t need = smem_doubles(a.max_n, cs, a.mmax, a.r) * sizeof(double);
+    const size_t smem = need < 120 * 1024 ? 120 * 1024 : need;   // one CTA per SM
+    cudaError_t e = cudaFuncSetAttribute(k_lanczos<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(G * cs));
+    int resident = 0;
+    e = cudaOccupancyMaxActiveClusters(&resident, k_lanczos<DF>, &cfg);
+    if (e != cudaSuccess) return e;
+    G = std::min(G, resident);
+    if (G < 2) return cudaErrorNotSupported;
+    cfg.gridDim = dim3((unsigned)(G * cs));
+    cfg.numAttrs = 2;
+    a.team = G;
+    e = cudaLaunchKernelEx(&cfg, k_lanczos<DF>, a);
+    if (e == cudaSuccess) note_launch(1);
+    return e;
 }
 
 template <bool DF>
@@ -1046,10 +1284,17 @@ static cudaError_t launch_lanczos_t(const LanczosArgs& a, int cs, cudaStream_t s
     return cudaLaunchKernelEx(&cfg, k_lanczos<DF>, a);
 }
 
-cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st) {
+cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st, bool allow_team) {
     if (a.p <= 0) return cudaSuccess;
+    if (allow_team && a.p == 1 && a.tscr) {
+        const cudaError_t e = a.q_f32 ? launch_lanczos_team<true>(a, st) : launch_lanczos_team<false>(a, st);
+        if (e == cudaSuccess) return e;
+        cudaGetLastError();   // not available: one cluster below
+    }
+    LanczosArgs b = a;
+    b.team = 1;
     const int cs = cluster < 1 ? 1 : (cluster > 16 ? 16 : cluster);
-    return a.q_f32 ? launch_lanczos_t<true>(a, cs, st) : launch_lanczos_t<false>(a, cs, st);
+    return b.q_f32 ? launch_lanczos_t<true>(b, cs, st) : launch_lanczos_t<false>(b, cs, st);
 }
 
 }  // namespace gbmds
