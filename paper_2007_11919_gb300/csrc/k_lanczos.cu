@@ -79,6 +79,7 @@ struct Smem {
     double* resid;   // kMaxR
     double* red;     // 64 : scratch
     double* sgn;     // 4 * kMaxR : (|max|, row, signed) per eigenvector, then sign flips
+    double* ttmp;    // teams only: kMaxTeam x (mmax + 2), the clusters' partial sums
 };
 
 __host__ __device__ inline int owned_max(int r, int cs) { return (r + cs - 1) / cs; }
@@ -91,13 +92,14 @@ __host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
     return (size_t)round_up((int64_t)(q > check ? q : check), 16);
 }
 
-__host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r) {
+__host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r, bool team = false) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
     return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 4, 4) + 2 * round_up(rmax, 2) +
-           4 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8;
+           4 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8 +
+           (team ? (size_t)kMaxTeam * (mmax + 2) : 0);
 }
 
-__device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
+__device__ Smem carve(double* base, int max_n, int cs, int mmax, int r, bool team = false) {
     Smem s;
     const int rmax = (max_n + cs - 1) / cs;
     double* p = base;
@@ -124,6 +126,7 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r) {
     s.resid = p; p += kMaxR;
     s.red = p; p += 64;
     s.sgn = p; p += 4 * kMaxR;
+    s.ttmp = team ? p : nullptr;
     return s;
 }
 
@@ -296,59 +299,60 @@ struct Team {
     int* abort;         // set when a barrier wait or a stage wait timed out
 };
 
-// Grid barrier of the team (every CTA's thread 0 arrives; the last one opens
-// the next generation).  False after a timeout anywhere in the team.
-__device__ bool team_sync(const Team& tm) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
+// Grid barrier of the team: a cluster barrier, then thread 0 of each
+// cluster's rank 0 arrives on the team counter (the last arrival opens the
+// next generation) and waits, then a second cluster barrier releases the
+// cluster.  Writes before the barrier are fenced; a timed-out wait sets the
+// team's abort word, after which every barrier returns at once.
+__device__ void team_sync(cg::cluster_group& cl, const Team& tm) {
+    __threadfence();
+    cl.sync();
+    if (cl.block_rank() == 0 && threadIdx.x == 0) {
         volatile unsigned* gen = tm.bar + 1;
         const unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(tm.bar, 1u) == (unsigned)(tm.T - 1)) {
+        if (atomicAdd(tm.bar, 1u) == (unsigned)(tm.G - 1)) {
             atomicExch(tm.bar, 0u);
             __threadfence();
             atomicAdd(tm.bar + 1, 1u);
         } else {
             const unsigned long long t0 = tc::global_ns();
             while (*gen == g0) {
-                if (*(volatile int*)tm.abort) {
-                    ok = 0;
-                    break;
-                }
+                if (*(volatile int*)tm.abort) break;
                 if (tc::global_ns() - t0 > tc::kWaitNs) {
                     atomicExch(tm.abort, 1);
-                    ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
-        s_ok = ok;
     }
-    __syncthreads();
-    return s_ok != 0;
+    cl.sync();
 }
 
 // Sum over the team of part[i], lo <= i < hi, into out (and outdf as
 // double-FP32 pairs): cluster sums through DSMEM, then (G > 1) the clusters'
 // sums in cluster order through the team buffers of parity pb.
+// tmp: shared scratch of at least G x (hi - lo) doubles (the idle Q-stage ring).
 __device__ void team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int cs, int mmax, int pb, double* part,
-                               double* out, double* outdf, int lo, int hi) {
+                               double* out, double* outdf, int lo, int hi, double* tmp) {
     cluster_allreduce(cl, part, out, tm.G > 1 ? nullptr : outdf, lo, hi, cs);
     if (tm.G == 1) return;
-    const int stride = mmax + 2;
+    const int stride = mmax + 2, K = hi - lo;
     double* gp = tm.part + (size_t)pb * tm.G * stride;
     if (q == 0)
         for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) gp[(size_t)tm.g * stride + i] = out[i];
-    team_sync(tm);
-    for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
+    team_sync(cl, tm);
+    // every cluster's sums in one pass of independent loads, then the sum in cluster order
+    for (int e = threadIdx.x; e < tm.G * K; e += kThreads) {
+        const int h = e / K, i = e % K;
+        tmp[e] = __ldcg(gp + (size_t)h * stride + lo + i);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += kThreads) {
         double sum = 0.0;
-        for (int h = 0; h < tm.G; ++h) sum += __ldcg(gp + (size_t)h * stride + i);
-        out[i] = sum;
-        if (outdf) reinterpret_cast<float2*>(outdf)[i] = df_of(sum);
+        for (int h = 0; h < tm.G; ++h) sum += tmp[h * K + i];
+        out[lo + i] = sum;
+        if (outdf) reinterpret_cast<float2*>(outdf)[lo + i] = df_of(sum);
     }
     __syncthreads();
 }
@@ -672,7 +676,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     {
         const double s = block_sum(loc, S.red);
         if (tid == 0) part[pb][0] = s;
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, nullptr, 0, 1);
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, nullptr, 0, 1, S.ttmp);
         pb ^= 1;
         if (tid == 0) S.red[kWarps + 3] = 1.0 / sqrt(S.cfull[0]);
         __syncthreads();
@@ -704,7 +708,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     for (int j = 0; j < kmax; ++j) {
         // ---- gather v_j from all ranks (8-byte entries, copied as they are)
         if (tm.G > 1) {
-            team_sync(tm);
+            team_sync(cl, tm);
             for (int i = tid; i < n; i += kThreads) S.vfull[i] = __ldcg(tm.v + i);
         } else {
             cl.sync();
@@ -725,14 +729,14 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         const int ia = j > 0 ? j - 1 : 0;
         cgs_dots<DF>(B, ldq, r0, nr, ia, j, S.wloc, part[pb], false);
         __syncthreads();
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1);
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1, S.ttmp);
         pb ^= 1;
         const double a1 = S.cfull[j];
         cgs_update<DF>(B, ldq, r0, nr, ia, j, S.cfull, S.cdf, S.wloc);
         __syncthreads();
         cgs_dots<DF>(B, ldq, r0, nr, 0, j, S.wloc, part[pb], true);
         __syncthreads();
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, 0, j + 2);
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, 0, j + 2, S.ttmp);
         pb ^= 1;
         cgs_update<DF>(B, ldq, r0, nr, 0, j, S.cfull, S.cdf, S.wloc);
         if (warp == 0) {
@@ -835,7 +839,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                         tm.theta[i] = S.theta[i];
                         tm.resid[i] = S.resid[i];
                     }
-                team_sync(tm);
+                team_sync(cl, tm);
                 for (int i = tid; i < r; i += kThreads) {
                     S.theta[i] = __ldcg(tm.theta + i);
                     S.resid[i] = __ldcg(tm.resid + i);
@@ -912,7 +916,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     bool any_timeout = false;
     if (tm.G > 1) {
         if (!qok) atomicExch(tm.abort, 1);
-        team_sync(tm);
+        team_sync(cl, tm);
         any_timeout = *(volatile int*)tm.abort != 0;
     } else {
         if (!qok) S.red[43] = 1.0;   // zero since the last problem; every writer stores 1
@@ -958,7 +962,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const int i = e / k, t = e % k;
                 if (i % T == qt) tm.xv[(size_t)i * L + t] = S.xv[(size_t)i * L + t];
             }
-        team_sync(tm);
+        team_sync(cl, tm);
         if (qt == 0 && status != kDevRank) {
             for (int e = tid; e < r * k; e += kThreads) {
                 const int i = e / k, t = e % k;
@@ -972,7 +976,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 tm.xv[(size_t)i * L + t] = S.xv[(size_t)i * L + t];
             }
         }
-        team_sync(tm);
+        team_sync(cl, tm);
         if (status == kDevRank) {
             if (qt == 0 && tid == 0) {
                 A.status[pj] = status;
@@ -1089,7 +1093,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     if (tm.G > 1) {
         __syncthreads();
         for (int e = tid; e < 3 * r; e += kThreads) tm.sgn[(size_t)qt * 3 * kMaxR + e] = S.sgn[e];
-        team_sync(tm);
+        team_sync(cl, tm);
         if (tid < r) {
             double best = -1.0, bestv = 0.0, brow = 1e300;
             for (int qq = 0; qq < T; ++qq) {
@@ -1144,7 +1148,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     const int q = (int)cl.block_rank();
     extern __shared__ __align__(16) double smraw[];
     __shared__ int s_flag, s_next;
-    const Smem S = carve(smraw, A.max_n, cs, A.mmax, A.r);
+    const Smem S = carve(smraw, A.max_n, cs, A.mmax, A.r, A.team > 1);
     if (threadIdx.x == 0) {
         for (int i = 0; i < kWarps * kRing; ++i) tc::mbar_init(&S.full[i], 1);
         S.red[43] = 0.0;
@@ -1214,7 +1218,8 @@ static cudaError_t launch_lanczos_team(LanczosArgs a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int G = std::min(std::min(sms / cs, kMaxTeam), a.max_n / (cs * 16));   // at least 16 rows per CTA
     if (G < 2) return cudaErrorNotSupported;
-    const size_t need = smem_doubles(a.max_n, cs, a.mmax, a.r) * sizeof(double);
+    const size_t need = smem_doubles(a.max_n, cs, a.mmax, a.r, true) * sizeof(double);
+    if (need > kMaxSmem) return cudaErrorNotSupported;
     const size_t smem = need < 120 * 1024 ? 120 * 1024 : need;   // one CTA per SM
     cudaError_t e = cudaFuncSetAttribute(k_lanczos<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
