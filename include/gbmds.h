@@ -192,7 +192,7 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
  * again whenever a buffer pointer or the stream changes.
  *   tune  nonzero (and opts->cluster 0): the first execute is an autotuner:
  *         it runs the complete computation once per eligible cluster size
- *         (CTAs per eigenproblem, 1..8, shared memory permitting), times each
+ *         (CTAs per eigenproblem, 1..16, shared memory permitting), times each
  *         with CUDA events on these buffers, and keeps the fastest; those
  *         runs write valid outputs.  Otherwise the cluster size is
  *         opts->cluster or the library's heuristic.

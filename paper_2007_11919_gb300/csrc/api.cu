@@ -1087,10 +1087,12 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         double best = 0.0;
         for (int cs = 1; cs <= 16; ++cs) {
             if (lanczos_smem_bytes(B.max_n, cs, B.mmax, B.r) > kMaxSmem || cs > std::max(1, B.max_n / 64)) continue;
-            if (cs > 8 && B.p > 1) continue;   // portable cluster sizes for batches
             double ms = 0.0;
-            int s = plan_trial(P, cs, Y, part_own, anchors, X, var, st, &ms);   // warm-up
-            if (s == MDS_OK) s = plan_trial(P, cs, Y, part_own, anchors, X, var, st, &ms);
+            int s = plan_trial(P, cs, Y, part_own, anchors, X, var, st, &ms);
+            if (s == MDS_OK && P->trial_ms[0] == 0.0) {   // the first run also warms the device up
+                P->trial_ms[0] = ms;
+                s = plan_trial(P, cs, Y, part_own, anchors, X, var, st, &ms);
+            }
             if (s != MDS_OK) {
                 if (s == MDS_ERR_ARG || s == MDS_ERR_RANK) return s;   // the data, not the cluster size
                 continue;
@@ -1102,6 +1104,7 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
             }
         }
         P->tuned = true;
+        P->trial_ms[0] = 0.0;
         if (P->cs == 0) return MDS_ERR_CUDA;
     }
     if (P->cs == 0) P->cs = pick_cluster(0, B.p, B.max_n, B.mmax, B.r);

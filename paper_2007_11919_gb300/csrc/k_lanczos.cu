@@ -55,9 +55,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRing = 2;           // stages per warp
-constexpr int kChunkB = 4096;      // bytes per stage (at most one row segment of Q)
-constexpr size_t kRingBytes = (size_t)kWarps * kRing * kChunkB;
+constexpr int kRing = 4;           // stage barriers per warp (stages in use: as many as fit)
+constexpr int kChunkB = 4096;      // longest row segment of Q
+constexpr int kWarpRingB = 8192;   // stage bytes per warp
+constexpr size_t kRingBytes = (size_t)kWarps * kWarpRingB;
 
 struct Smem {
     uint8_t* ring;   // per-warp Q stages while streaming; the check workspace otherwise
@@ -375,8 +376,9 @@ __device__ __forceinline__ double start_entry(int row) {
 // row-offset * nseg + segment) through its kRing stages, in order.  Stage
 // indices and mbarrier phases carry over from problem to problem.
 struct QStream {
+    int nst, stride;    // stages in use and their spacing (bytes) for this problem
     const uint8_t* q;   // Q of the problem
-    size_t stride;      // bytes per row of Q (ldq * 8)
+    size_t rstride;     // bytes per row of Q (ldq * 8)
     int rowbytes;       // bytes a row's copies cover: FP32 round_up(n, 4) * 4, FP64 round_up(n, 2) * 8
     int nseg, segb;     // segments per row and bytes per segment (the last may be shorter)
     int wr0, per_step;  // first row of this warp and segments per step
@@ -404,17 +406,17 @@ __device__ __forceinline__ bool qs_wait(uint64_t* bar, uint32_t parity) {
 // Issues chunks while a stage is free and issues are allowed (the whole warp
 // keeps the bookkeeping; lane 0 issues).
 __device__ __forceinline__ void qs_fill(QStream& s) {
-    while (s.inflight < kRing && s.issue_left > 0) {
+    while (s.inflight < s.nst && s.issue_left > 0) {
         if ((threadIdx.x & 31) == 0) {
             const int row = s.wr0 + s.ipos / s.nseg, seg = s.ipos % s.nseg;
             const int off = seg * s.segb;
             const int bytes = min(s.segb, s.rowbytes - off);
             tc::mbar_expect_tx(&s.full[s.ist], (uint32_t)bytes);
-            tc::bulk_load(s.ring + (size_t)s.ist * kChunkB, s.q + (size_t)row * s.stride + off, (uint32_t)bytes,
+            tc::bulk_load(s.ring + (size_t)s.ist * s.stride, s.q + (size_t)row * s.rstride + off, (uint32_t)bytes,
                           &s.full[s.ist]);
         }
         s.ipos = s.ipos + 1 == s.per_step ? 0 : s.ipos + 1;
-        s.ist = s.ist + 1 == kRing ? 0 : s.ist + 1;
+        s.ist = s.ist + 1 == s.nst ? 0 : s.ist + 1;
         ++s.inflight;
         --s.issue_left;
     }
@@ -428,7 +430,7 @@ __device__ __forceinline__ bool qs_wait_front(QStream& s) {
 
 __device__ __forceinline__ void qs_pop(QStream& s) {
     s.cpos = s.cpos + 1 == s.per_step ? 0 : s.cpos + 1;
-    s.cst = s.cst + 1 == kRing ? 0 : s.cst + 1;
+    s.cst = s.cst + 1 == s.nst ? 0 : s.cst + 1;
     --s.inflight;
 }
 
@@ -454,20 +456,26 @@ __device__ __forceinline__ void qs_setup(QStream& s, const double* Q, int ldq, i
     const int per_warp = (nr + kWarps - 1) / kWarps;
     const int a = min(nr, warp * per_warp), b = min(nr, (warp + 1) * per_warp);
     s.q = reinterpret_cast<const uint8_t*>(Q);
-    s.stride = (size_t)ldq * 8;
+    s.rstride = (size_t)ldq * 8;
     s.rowbytes = DF ? (int)round_up(n, 4) * 4 : (int)round_up(n, 2) * 8;
     s.nseg = (s.rowbytes + kChunkB - 1) / kChunkB;
     s.segb = (int)round_up((s.rowbytes + s.nseg - 1) / s.nseg, 16);
     s.wr0 = r0 + a;
     s.per_step = (b - a) * s.nseg;
     s.cpos = s.ipos = 0;
-    s.issue_left = min(kRing, s.per_step);
+    // as many stages of this problem's segment size as the warp's ring holds
+    // (the stream is drained between problems, so the stages restart at 0;
+    // each stage's barrier keeps its own phase bit)
+    s.stride = (int)round_up(s.segb, 128);
+    s.nst = min(kRing, kWarpRingB / s.stride);
+    s.cst = s.ist = 0;
+    s.issue_left = min(s.nst, s.per_step);
     qs_fill(s);
 }
 
 // Re-issues the first chunks of the next step (after a drain).
 __device__ __forceinline__ void qs_prime(QStream& s) {
-    s.issue_left = min(kRing, s.per_step);
+    s.issue_left = min(s.nst, s.per_step);
     qs_fill(s);
 }
 
@@ -478,7 +486,7 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
                                           bool prefetch) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
-    s.issue_left = s.per_step - s.inflight + (prefetch ? min(kRing, s.per_step) : 0);
+    s.issue_left = s.per_step - s.inflight + (prefetch ? min(s.nst, s.per_step) : 0);
     qs_fill(s);
     // two accumulators per lane (alternate entries) for instruction-level parallelism
     float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
@@ -487,7 +495,7 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
         ok = qs_wait_front(s) && ok;
         const int row = s.wr0 + s.cpos / s.nseg, seg = s.cpos % s.nseg;
         const int bytes = min(s.segb, s.rowbytes - seg * s.segb);
-        const uint8_t* stage = s.ring + (size_t)s.cst * kChunkB;
+        const uint8_t* stage = s.ring + (size_t)s.cst * s.stride;
         if constexpr (DF) {
             // FP32 Q: 4 entries per 16 bytes; the row's padding entries are zero
             // and so are the vector's guard entries
@@ -1156,8 +1164,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     }
     __syncthreads();
     QStream Qs;
-    Qs.ring = S.ring + (size_t)(threadIdx.x >> 5) * kRing * kChunkB;
+    Qs.ring = S.ring + (size_t)(threadIdx.x >> 5) * kWarpRingB;
     Qs.full = S.full + (threadIdx.x >> 5) * kRing;
+    Qs.nst = 1;
+    Qs.stride = kWarpRingB;
     Qs.cst = Qs.ist = 0;
     Qs.inflight = 0;
     Qs.phase = 0;
