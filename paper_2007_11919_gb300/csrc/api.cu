@@ -38,7 +38,7 @@ int model_kind(int prec, int dt, int d, int r) {
 // kinds, to tck_lpad(l) rows).
 size_t model_W_bytes(int kind, int prec, int l, int r) {
     if (kind != kKindRows) return (size_t)tck_lpad(l) * gower_tc_rp(r) * 4;
-    if (prec == MDS_PREC_BF16) return (size_t)l * gower_tc_rp(r) * 4;
+    if (prec == MDS_PREC_BF16) return (size_t)gower_tc_lpad(l) * gower_tc_rp(r) * 4;
     return (size_t)l * r * (prec == MDS_PREC_F64 ? 8 : 4);
 }
 
@@ -48,7 +48,9 @@ size_t model_L_bytes(int kind, int prec, int l, int d) {
     return (size_t)l * d * (prec == MDS_PREC_F64 ? 8 : 4);
 }
 
-size_t model_nlf_count(int kind, int l) { return kind != kKindRows ? (size_t)tck_lpad(l) : (size_t)round_up(l, 4); }
+size_t model_nlf_count(int kind, int l) {
+    return kind != kKindRows ? (size_t)tck_lpad(l) : (size_t)gower_tc_lpad(l);
+}
 
 // ---- per-thread instrumentation (mds_set_timing / mds_last_stats)
 bool g_timing = false;
@@ -708,7 +710,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
                             o.st));
     } else if (o.prec == MDS_PREC_BF16) {
         // tensor-core distance tiles fused with the Gower projection
-        CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * round_up(l, 4), o.st));
+        CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * model_nlf_count(kind, l), o.st));
         CK(launch_gather_split(Ye, n, d, landmark_idx, l, W.L, W.nrm, W.nrm_lf, o.st));
         CK(launch_pad_w((const float*)W.W, l, r, W.Wpad, o.st));
         CK(launch_gower_tc(Ye, n, d, W.nrm, W.L, W.nrm_lf, l, W.Wpad, W.bias, r, (float*)X,
@@ -814,7 +816,7 @@ void mds_model_free(mds_model m) {
     delete m;
 }
 
-static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '3'};
+static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '4'};
 
 int mds_model_save(mds_model m, const char* path) {
     if (!m || !path) return MDS_ERR_ARG;

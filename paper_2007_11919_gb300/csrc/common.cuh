@@ -211,6 +211,8 @@ cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* 
 // Padded width (4, 8, 12 or 16) of W rows for the tensor-core kernel, and the
 // padding of an l x r W into l x RP (zero columns).
 int gower_tc_rp(int r);
+// W (l x r) -> gower_tc_lpad(l) x gower_tc_rp(r) with zeros (the kernel reads whole chunks).
+int gower_tc_lpad(int l);
 cudaError_t launch_pad_w(const float* W, int l, int r, float* Wp, cudaStream_t st);
 // Landmark rows of split planes into split planes, norms as float.
 cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int64_t* idx, int l,

@@ -34,7 +34,7 @@ constexpr int kChunk = 128;         // landmarks per chunk (MMA N)
 constexpr int kAtomK = 64;          // BF16 elements per 128-byte swizzle atom
 constexpr int kMaxAtoms = 2;        // K up to 128 (d <= 128 padded to 8)
 constexpr int kTcMaxR = 16;
-constexpr int kThreadsTc = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kThreadsTc = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quadrant)
 constexpr uint32_t kTmemCols = 256; // two accumulators of kChunk FP32 columns
 
 constexpr uint32_t kPlaneBytes = kRows * 128;                 // one atom of one plane: 16 KB
@@ -46,6 +46,7 @@ struct TcSmem {
     uint8_t l[2][kTileBytes];        // landmark chunk ring
     float w[2][kChunk * kTcMaxR];    // W rows of the chunk (padded width RP)
     float nl[2][kChunk];             // landmark norms of the chunk
+    float xs[kRows][kTcMaxR];        // the second column half's partial projections
     uint64_t y_full, y_empty;
     uint64_t l_full[2], l_empty[2];
     uint64_t acc_full[2], acc_empty[2];
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             mbar_init(&S.l_full[s], 1);
             mbar_init(&S.l_empty[s], 1);
             mbar_init(&S.acc_full[s], 1);
-            mbar_init(&S.acc_empty[s], 128);
+            mbar_init(&S.acc_empty[s], 256);
         }
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -130,9 +131,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                                     !mbar_wait(&S.acc_empty[s], (uint32_t)((use - 1) & 1), abort, a.err)))
                         break;
                     const int j0 = c * kChunk;
-                    const int nc = min(kChunk, a.l - j0);
-                    const uint32_t wbytes = (uint32_t)(nc * RP * 4);
-                    const uint32_t nbytes = (uint32_t)(((nc + 3) & ~3) * 4);
+                    const uint32_t wbytes = (uint32_t)(kChunk * RP * 4);   // W, norms zero-padded
+                    const uint32_t nbytes = (uint32_t)(kChunk * 4);
                     mbar_expect_tx(&S.l_full[s], tile_tx + wbytes + nbytes);
                     for (int at = 0; at < a.natoms; ++at) {
                         tma_load_2d(S.l[s] + (0 * kMaxAtoms + at) * kPlaneBytes, &tm_lhi, at * kAtomK, j0, &S.l_full[s]);
@@ -189,74 +189,72 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             mbar_drain(&S.mma_done, 0, a.err);
         }
     } else {
-        // ---------------- epilogue: warps 2-5, one accumulator row per thread.
-        // The chunk's W rows and norms come from shared memory, loaded with the
-        // landmark tiles; the producer refills the stage only after this epilogue
-        // has arrived on acc_empty.
+        // ---------------- epilogue: warps 2-9, one accumulator row per thread;
+        // warps 2-5 take columns 0-63 of every chunk, warps 6-9 columns 64-127
+        // (two warps per TMEM lane quadrant).  The chunk's W rows and norms come
+        // from shared memory (zero-padded past l); the producer refills the
+        // stage only after all eight warps have arrived on acc_empty.  The r-wide
+        // projection runs as packed f32x2 FMAs.
         const int quad = warp & 3;                 // TMEM lane quadrant this warp may read
+        const int half = (warp - 2) >> 2;          // column half of the chunk
         const int row = quad * 32 + lane;
         const int r = a.r;
+        // Every epilogue warp runs the same tiles and chunks whatever happens
+        // (an aborted wait only skips the work), so the eight warps always meet
+        // at the named barrier.
         long long gc = 0;
-        for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int64_t gi = t * kRows + row;
             const float ny = gi < a.m ? (float)a.nrm_y[gi] : 0.f;
-            float x[RP];
+            uint64_t xp[RP / 2];                   // pairs (x[2o], x[2o+1])
 #pragma unroll
-            for (int o = 0; o < RP; ++o) x[o] = 0.f;
-            bool ok = true;
+            for (int o = 0; o < RP / 2; ++o) xp[o] = 0ull;
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 const int s = (int)(gc & 1);
-                ok = mbar_wait(&S.acc_full[s], (uint32_t)((gc >> 1) & 1), abort, a.err);
-                if (!ok) break;
+                // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
+                const bool got = __all_sync(0xffffffffu, mbar_wait(&S.acc_full[s], (uint32_t)((gc >> 1) & 1), abort, a.err));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int nc = min(kChunk, a.l - c * kChunk);
-                const float* ws = S.w[s];
-                const float* ns = S.nl[s];
+                const float* ws = S.w[s] + half * (kChunk / 2) * RP;
+                const float* ns = S.nl[s] + half * (kChunk / 2);
 #pragma unroll 1
-                for (int cb = 0; cb < kChunk; cb += 32) {
+                for (int cb = 0; cb < (got ? kChunk / 2 : 0); cb += 32) {
                     float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kChunk + cb), v);
-                    if (cb + 32 <= nc) {
+                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kChunk + half * (kChunk / 2) + cb), v);
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const float a2 = fmaxf(fmaf(-2.f, v[e], ny + ns[cb + e]), 0.f);
-                            const float4* w4 = reinterpret_cast<const float4*>(ws + (cb + e) * RP);
+                    for (int e = 0; e < 32; ++e) {
+                        const float a2 = fmaxf(fmaf(-2.f, v[e], ny + ns[cb + e]), 0.f);
+                        uint64_t a2p;
+                        asm("mov.b64 %0, {%1, %1};" : "=l"(a2p) : "f"(a2));
+                        const uint4* w4 = reinterpret_cast<const uint4*>(ws + (cb + e) * RP);
 #pragma unroll
-                            for (int q4 = 0; q4 < RP / 4; ++q4) {
-                                const float4 w = w4[q4];
-                                x[4 * q4 + 0] = fmaf(a2, w.x, x[4 * q4 + 0]);
-                                x[4 * q4 + 1] = fmaf(a2, w.y, x[4 * q4 + 1]);
-                                x[4 * q4 + 2] = fmaf(a2, w.z, x[4 * q4 + 2]);
-                                x[4 * q4 + 3] = fmaf(a2, w.w, x[4 * q4 + 3]);
-                            }
-                        }
-                    } else if (cb < nc) {
-                        for (int e = 0; e < nc - cb; ++e) {
-                            float ve = v[0];
-#pragma unroll
-                            for (int u = 1; u < 32; ++u) ve = u == e ? v[u] : ve;
-                            const float a2 = fmaxf(fmaf(-2.f, ve, ny + ns[cb + e]), 0.f);
-                            const float4* w4 = reinterpret_cast<const float4*>(ws + (cb + e) * RP);
-#pragma unroll
-                            for (int q4 = 0; q4 < RP / 4; ++q4) {
-                                const float4 w = w4[q4];
-                                x[4 * q4 + 0] = fmaf(a2, w.x, x[4 * q4 + 0]);
-                                x[4 * q4 + 1] = fmaf(a2, w.y, x[4 * q4 + 1]);
-                                x[4 * q4 + 2] = fmaf(a2, w.z, x[4 * q4 + 2]);
-                                x[4 * q4 + 3] = fmaf(a2, w.w, x[4 * q4 + 3]);
-                            }
+                        for (int q4 = 0; q4 < RP / 4; ++q4) {
+                            const uint4 w = w4[q4];
+                            uint64_t w01, w23;
+                            asm("mov.b64 %0, {%1, %2};" : "=l"(w01) : "r"(w.x), "r"(w.y));
+                            asm("mov.b64 %0, {%1, %2};" : "=l"(w23) : "r"(w.z), "r"(w.w));
+                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(xp[2 * q4]) : "l"(a2p), "l"(w01));
+                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(xp[2 * q4 + 1]) : "l"(a2p), "l"(w23));
                         }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(&S.acc_empty[s]);
             }
-            if (!ok) break;
-            if (gi < a.m) {
+            float x[RP];
+#pragma unroll
+            for (int o = 0; o < RP / 2; ++o)
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(x[2 * o]), "=f"(x[2 * o + 1]) : "l"(xp[o]));
+            // the second half hands its partial sums to the first (named barrier of the 8 warps)
+            if (half == 1)
+#pragma unroll
+                for (int o = 0; o < RP; ++o) S.xs[row][o] = x[o];
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (half == 0 && gi < a.m) {
 #pragma unroll
                 for (int o = 0; o < RP; ++o)
-                    if (o < r) a.X[gi * r + o] = x[o] + (float)a.bias[o];
+                    if (o < r) a.X[gi * r + o] = x[o] + S.xs[row][o] + (float)a.bias[o];
             }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
         }
     }
 
@@ -297,11 +295,12 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int cols_pad) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-__global__ void k_pad_w(const float* __restrict__ W, int l, int r, int rp, float* __restrict__ Wp) {
+// W (l x r) -> rows padded to a multiple of kChunk, columns to RP, zeros.
+__global__ void k_pad_w(const float* __restrict__ W, int l, int r, int rp, int lpad, float* __restrict__ Wp) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= l * rp) return;
+    if (e >= lpad * rp) return;
     const int j = e / rp, o = e % rp;
-    Wp[e] = o < r ? W[j * r + o] : 0.f;
+    Wp[e] = (j < l && o < r) ? W[j * r + o] : 0.f;
 }
 
 }  // namespace
@@ -323,9 +322,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+int gower_tc_lpad(int l) { return (int)round_up(l, kChunk); }
+
 cudaError_t launch_pad_w(const float* W, int l, int r, float* Wp, cudaStream_t st) {
     const int rp = gower_tc_rp(r);
-    k_pad_w<<<(l * rp + 255) / 256, 256, 0, st>>>(W, l, r, rp, Wp);
+    const int lpad = gower_tc_lpad(l);
+    k_pad_w<<<(lpad * rp + 255) / 256, 256, 0, st>>>(W, l, r, rp, lpad, Wp);
     note_launch(1);
     return cudaGetLastError();
 }
