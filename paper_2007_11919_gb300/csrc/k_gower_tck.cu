@@ -227,8 +227,9 @@ __global__ void __launch_bounds__(kThreadsK, 1)
             for (int c = 0; c < a.nchunks; ++c, ++g) {
                 const int as = (int)(g & 1);
                 const uint32_t par = (uint32_t)((g >> 1) & 1);
-                if (!(ok = mbar_wait(&S.acc_full[as], par, abort, a.err) && mbar_wait(&S.wfull[as], par, abort, a.err)))
-                    break;
+                ok = __all_sync(0xffffffffu, mbar_wait(&S.acc_full[as], par, abort, a.err) &&
+                                                 mbar_wait(&S.wfull[as], par, abort, a.err));   // warp-uniform
+                if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const float* ws = S.w[as];
                 const float* ns = S.nl[as];
@@ -413,8 +414,9 @@ __global__ void __launch_bounds__(kThreadsK, 1)
             double* rp = a.rparena + P.rp_off;
             const int as = (int)(g & 1);
             const uint32_t par = (uint32_t)((g >> 1) & 1);
-            if (!(ok = mbar_wait(&S.acc_full[as], par, abort, a.err) && mbar_wait(&S.wfull[as], par, abort, a.err)))
-                break;
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.acc_full[as], par, abort, a.err) &&
+                                             mbar_wait(&S.wfull[as], par, abort, a.err));   // warp-uniform
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float* ns = S.nl[as];
             float rh = 0.f, rl = 0.f;
