@@ -34,11 +34,12 @@ int model_kind(int prec, int dt, int d, int r) {
     return kKindRows;
 }
 
-// Tensor-core models keep W padded to the kernel's width (and, for byte-row
-// kinds, to tck_lpad(l) rows).
+// Tensor-core models keep W in the form their kernel reads: padded to the
+// kernel's width and tck_lpad(l) rows for byte-row kinds, the BF16 W^T image
+// for BF16 split rows.
 size_t model_W_bytes(int kind, int prec, int l, int r) {
     if (kind != kKindRows) return (size_t)tck_lpad(l) * gower_tc_rp(r) * 4;
-    if (prec == MDS_PREC_BF16) return (size_t)gower_tc_lpad(l) * gower_tc_rp(r) * 4;
+    if (prec == MDS_PREC_BF16) return gower_tc_w_bytes(l);
     return (size_t)l * r * (prec == MDS_PREC_F64 ? 8 : 4);
 }
 
@@ -537,7 +538,7 @@ int gbmds::embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, ch
     if (s) return s;
     for (int i = 0; i < 4; ++i) tmark(i, st);   // stage 0 = preparation, stage 4 = projection
     if (m->prec == MDS_PREC_BF16) {
-        CK(launch_gower_tc(Ye, rows, m->d, nrm, m->L, m->nrm_lf, m->l, (const float*)m->W, m->bias,
+        CK(launch_gower_tc(Ye, rows, m->d, nrm, m->L, m->nrm_lf, m->l, m->W, m->bias,
                            m->r, (float*)X, kerr, st));
         return MDS_OK;
     }
@@ -689,7 +690,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     int dtl = dte;
     const double* nrml = W.nrm;
     if (o.prec == MDS_PREC_BF16 || o.prec == MDS_PREC_FP8) {
-        CK(launch_rownorm(Y, dt, n, d, 0, W.nrm_raw, o.st));
+        CK(launch_rownorm_idx(Y, dt, n, d, landmark_idx, l, 0, W.nrm_raw, o.st));
         Yl = Y;
         dtl = dt;
         nrml = W.nrm_raw;
@@ -712,7 +713,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
         // tensor-core distance tiles fused with the Gower projection
         CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * model_nlf_count(kind, l), o.st));
         CK(launch_gather_split(Ye, n, d, landmark_idx, l, W.L, W.nrm, W.nrm_lf, o.st));
-        CK(launch_pad_w((const float*)W.W, l, r, W.Wpad, o.st));
+        CK(launch_w_image((const float*)W.W, l, r, W.Wpad, o.st));
         CK(launch_gower_tc(Ye, n, d, W.nrm, W.L, W.nrm_lf, l, W.Wpad, W.bias, r, (float*)X,
                            W.kerr, o.st));
     } else {
@@ -816,7 +817,7 @@ void mds_model_free(mds_model m) {
     delete m;
 }
 
-static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '4'};
+static const char kMagic[8] = {'G', 'B', 'M', 'D', 'S', 'M', '0', '5'};
 
 int mds_model_save(mds_model m, const char* path) {
     if (!m || !path) return MDS_ERR_ARG;

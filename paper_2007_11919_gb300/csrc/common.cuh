@@ -113,6 +113,10 @@ __host__ __device__ inline int split_ld(int d) { return (int)round_up(d, 8); }
 // accumulated in A (float or double).
 cudaError_t launch_rownorm(const void* Y, int dt, int64_t n, int d, int acc_f64, double* nrm,
                            cudaStream_t st);
+// The same for rows idx[0..count-1] of an ny x d matrix only, each written at
+// nrm[idx[i]] (the other entries of nrm are left as they are).
+cudaError_t launch_rownorm_idx(const void* Y, int dt, int64_t ny, int d, const int64_t* idx, int64_t count,
+                               int acc_f64, double* nrm, cudaStream_t st);
 
 // Delta_j tiles for every problem of a batch, written as FP64 into the Q arena,
 // plus per-tile row sums.  acc_f64 selects FP64 (else FP32) dot products.
@@ -202,18 +206,21 @@ cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq,
 
 // Tensor-core Gower projection for BF16 split data (tcgen05 + TMA): X (m x r,
 // float) = A^2 W + b with A^2 from the split planes of Y (m rows) and of the l
-// landmarks.  Requires gower_tc_supported(d, r).  *err receives
+// landmarks (norms nrm_l zero-padded to gower_tc_lpad(l)), W as the image
+// launch_w_image writes.  Requires gower_tc_supported(d, r).  *err receives
 // MDS_ERR_TIMEOUT if a bounded wait gives up.
 bool gower_tc_supported(int d, int r);
 cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
-                            const void* Lsplit, const float* nrm_l, int l, const float* W,
+                            const void* Lsplit, const float* nrm_l, int l, const void* Wimg,
                             const double* bias, int r, float* X, int* err, cudaStream_t st);
-// Padded width (4, 8, 12 or 16) of W rows for the tensor-core kernel, and the
-// padding of an l x r W into l x RP (zero columns).
+// Padded width (4, 8, 12 or 16) of W rows for the byte-row kernel.
 int gower_tc_rp(int r);
-// W (l x r) -> gower_tc_lpad(l) x gower_tc_rp(r) with zeros (the kernel reads whole chunks).
+// Landmarks rounded up to whole 128-landmark chunks.
 int gower_tc_lpad(int l);
-cudaError_t launch_pad_w(const float* W, int l, int r, float* Wp, cudaStream_t st);
+// W (l x r, float, r <= 16) -> the BF16 hi/lo W^T image k_gower_tc's projection
+// MMA reads (gower_tc_w_bytes(l) bytes, zero past l and r).
+size_t gower_tc_w_bytes(int l);
+cudaError_t launch_w_image(const float* W, int l, int r, void* img, cudaStream_t st);
 // Landmark rows of split planes into split planes, norms as float.
 cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int64_t* idx, int l,
                                 void* Lsplit, const double* nrm, float* nrm_l, cudaStream_t st);

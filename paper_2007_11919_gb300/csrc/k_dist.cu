@@ -15,12 +15,19 @@ namespace {
 
 // ------------------------------------------------------------------ norms
 
+// Squared norms of rows 0..n-1, or, with idx, of rows idx[0..n-1] (each
+// clamped to 0..ny-1) written at their own positions nrm[idx[i]].
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_rownorm(const T* __restrict__ Y, int64_t n, int d,
-                                                 double* __restrict__ nrm) {
+                                                 double* __restrict__ nrm,
+                                                 const int64_t* __restrict__ idx, int64_t ny) {
     const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= n) return;
+    if (idx) {
+        row = idx[row];
+        row = row < 0 ? 0 : (row >= ny ? ny - 1 : row);
+    }
     const T* y = Y + row * (int64_t)d;
     A s = 0;
     for (int k = lane; k < d; k += 32) {
@@ -298,6 +305,42 @@ __global__ void __launch_bounds__(256) k_quant_bf16(const T* __restrict__ Y, int
     if (lane == 0) nrm[row] = (double)s;
 }
 
+// The same split for FP32 rows with d a multiple of 4 and a 16-byte aligned
+// base: float4 loads (streamed, the rows are read once), 8-byte stores of four
+// BF16 values.  split_ld(d) - d is then 0 or 4, one zero group.
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(256) k_quant_bf16_f4(const float* __restrict__ Y, int64_t n, int d,
+                                                       __nv_bfloat16* __restrict__ Yq,
+                                                       double* __restrict__ nrm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const int ld = split_ld(d);
+    const float4* y4 = reinterpret_cast<const float4*>(Y + row * d);
+    uint2* hi = reinterpret_cast<uint2*>(Yq + row * ld);
+    uint2* lo = reinterpret_cast<uint2*>(Yq + n * (int64_t)ld + row * ld);
+    float s = 0.f;
+    for (int k4 = lane; k4 < ld / 4; k4 += 32) {
+        const float4 v = k4 < d / 4 ? __ldcs(y4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float y[4] = {v.x, v.y, v.z, v.w};
+        __nv_bfloat16 h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = __float2bfloat16_rn(y[e]);
+            const float hf = __bfloat162float(h[e]);
+            l[e] = __float2bfloat16_rn(y[e] - hf);
+            s += hf * hf + 2.f * hf * __bfloat162float(l[e]);
+        }
+        hi[k4] = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+        lo[k4] = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+    }
+    s = warp_sum(s);
+    if (lane == 0) nrm[row] = (double)s;
+}
+
 template <typename Ld, typename A>
 __global__ void __launch_bounds__(256) k_gather(Ld Y, int d,
                                                 const int64_t* __restrict__ idx, int l,
@@ -314,21 +357,31 @@ __global__ void __launch_bounds__(256) k_gather(Ld Y, int d,
 
 }  // namespace
 
-cudaError_t launch_rownorm(const void* Y, int dt, int64_t n, int d, int acc_f64, double* nrm,
-                           cudaStream_t st) {
+static cudaError_t rownorm_any(const void* Y, int dt, int64_t n, int d, int acc_f64, double* nrm,
+                               const int64_t* idx, int64_t ny, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     dim3 grid((unsigned)((n + 7) / 8)), block(256);
     if (acc_f64) {
-        if (dt == MDS_IN_F64) k_rownorm<double, double><<<grid, block, 0, st>>>((const double*)Y, n, d, nrm);
-        else if (dt == MDS_IN_F32) k_rownorm<float, double><<<grid, block, 0, st>>>((const float*)Y, n, d, nrm);
-        else k_rownorm<uint8_t, double><<<grid, block, 0, st>>>((const uint8_t*)Y, n, d, nrm);
+        if (dt == MDS_IN_F64) k_rownorm<double, double><<<grid, block, 0, st>>>((const double*)Y, n, d, nrm, idx, ny);
+        else if (dt == MDS_IN_F32) k_rownorm<float, double><<<grid, block, 0, st>>>((const float*)Y, n, d, nrm, idx, ny);
+        else k_rownorm<uint8_t, double><<<grid, block, 0, st>>>((const uint8_t*)Y, n, d, nrm, idx, ny);
     } else {
-        if (dt == MDS_IN_F64) k_rownorm<double, float><<<grid, block, 0, st>>>((const double*)Y, n, d, nrm);
-        else if (dt == MDS_IN_F32) k_rownorm<float, float><<<grid, block, 0, st>>>((const float*)Y, n, d, nrm);
-        else k_rownorm<uint8_t, float><<<grid, block, 0, st>>>((const uint8_t*)Y, n, d, nrm);
+        if (dt == MDS_IN_F64) k_rownorm<double, float><<<grid, block, 0, st>>>((const double*)Y, n, d, nrm, idx, ny);
+        else if (dt == MDS_IN_F32) k_rownorm<float, float><<<grid, block, 0, st>>>((const float*)Y, n, d, nrm, idx, ny);
+        else k_rownorm<uint8_t, float><<<grid, block, 0, st>>>((const uint8_t*)Y, n, d, nrm, idx, ny);
     }
     note_launch(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_rownorm(const void* Y, int dt, int64_t n, int d, int acc_f64, double* nrm,
+                           cudaStream_t st) {
+    return rownorm_any(Y, dt, n, d, acc_f64, nrm, nullptr, n, st);
+}
+
+cudaError_t launch_rownorm_idx(const void* Y, int dt, int64_t ny, int d, const int64_t* idx, int64_t count,
+                               int acc_f64, double* nrm, cudaStream_t st) {
+    return rownorm_any(Y, dt, count, d, acc_f64, nrm, idx, ny, st);
 }
 
 cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nrm,
@@ -418,6 +471,8 @@ cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq,
     if (n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((n + 7) / 8));
     if (dt == MDS_IN_F64) k_quant_bf16<double><<<grid, 256, 0, st>>>((const double*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
+    else if (dt == MDS_IN_F32 && d % 4 == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0)
+        k_quant_bf16_f4<<<grid, 256, 0, st>>>((const float*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
     else if (dt == MDS_IN_F32) k_quant_bf16<float><<<grid, 256, 0, st>>>((const float*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
     else k_quant_bf16<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
     note_launch(1);

@@ -3,21 +3,34 @@
 // For a tile of 128 new points and every chunk of 128 landmarks:
 //   S = Y L^T          (tcgen05.mma, BF16 operands, FP32 accumulation in TMEM)
 //   A^2 = ||y||^2 + ||l||^2 - 2 S, clamped at 0       (epilogue, FP32)
-//   X  += A^2 W         (W = -1/2 V Lambda^{-1/2}, r <= 16 columns, FP32 FMAs)
+//   X  += A^2 W         (tcgen05.mma again: A^2 from TMEM, W^T from shared memory)
 // and finally X += b.  A^2 never leaves the chip.
 //
 // Precision: each value is split into BF16 planes hi = bf16(y), lo = bf16(y - hi)
 // and y . l is accumulated from the three products hi.hi + hi.lo + lo.hi
 // (about 16 significant bits per operand; the dropped lo.lo term is ~2^-18
-// relative).  The norms come from the same split.
+// relative).  The norms come from the same split.  The projection splits A^2
+// and W the same way: A^2_hi [W_hi | W_lo] (one MMA of N = 32, two 16-column
+// halves) plus A^2_lo W_hi (N = 16, into the first half), FP32 accumulation in
+// TMEM; X is the sum of the two halves.
 //
 // Structure: persistent CTAs (one per SM) walk 128-row tiles.  Warp 0 issues
-// TMA loads (Y tile once per tile, landmark chunks through a 2-stage ring),
-// warp 1 allocates TMEM (2 x 128 FP32 columns) and one thread issues the MMAs
-// into alternating accumulators, warps 2-5 read the accumulators back
-// (tcgen05.ld, one row per thread) and do the epilogue.  mbarriers order the
-// roles; every wait is bounded and reports a timeout through *err instead of
-// hanging.
+// TMA loads (Y tile once per tile, landmark chunks through a 2-stage ring that
+// is refilled as soon as the MMAs have read a stage), warp 10 copies each
+// chunk's W^T image and landmark norms into a 2-stage ring of its own, warp 1
+// allocates TMEM (3 x 128 FP32 accumulator columns plus a 32-column X
+// accumulator) and one thread issues the MMAs, warps 2-9 read an accumulator
+// back (tcgen05.ld, one row per thread, two warps per lane quadrant, one per
+// 64-column half), form A^2 and write it back in place as packed BF16 hi/lo
+// pairs (tcgen05.st), which the projection MMA then reads as its A operand.
+// mbarriers order the roles; every wait is bounded and reports a timeout
+// through *err instead of hanging.
+//
+// Three accumulators, because tcgen05.commit tracks every MMA the thread has
+// issued before it: the commit that frees accumulator g (after chunk g's
+// projection, issued behind chunk g + 1's distance MMAs) fires only once chunk
+// g + 1's distances are done, so the distance MMAs of chunk g + 2 must not
+// need it if the tensor pipe is to stay fed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -30,26 +43,31 @@ namespace {
 using namespace tc;
 
 constexpr int kRows = 128;          // points per tile (MMA M)
-constexpr int kChunk = 128;         // landmarks per chunk (MMA N)
+constexpr int kChunk = 128;         // landmarks per chunk (MMA N, projection K)
 constexpr int kAtomK = 64;          // BF16 elements per 128-byte swizzle atom
 constexpr int kMaxAtoms = 2;        // K up to 128 (d <= 128 padded to 8)
-constexpr int kTcMaxR = 16;
-constexpr int kThreadsTc = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quadrant)
-constexpr uint32_t kTmemCols = 256; // two accumulators of kChunk FP32 columns
+constexpr int kTcMaxR = 16;         // X columns of the projection (r <= 16, columns r..15 zero)
+constexpr int kThreadsTc = 352;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue, warp 10 W copies
+constexpr int kAcc = 3;             // distance accumulators of kChunk FP32 columns
+constexpr uint32_t kTmemCols = 512; // the accumulators + the X accumulator (two 16-column halves)
+constexpr uint32_t kXCol = kAcc * kChunk;
 
 constexpr uint32_t kPlaneBytes = kRows * 128;                 // one atom of one plane: 16 KB
 constexpr uint32_t kTileBytes = 2 * kMaxAtoms * kPlaneBytes;  // hi + lo, all atoms: 64 KB
+constexpr uint32_t kWAtomBytes = 2 * kTcMaxR * 128;           // rows W_hi^T, W_lo^T x 64 landmarks: 4 KB
+constexpr uint32_t kWImgBytes = 2 * kWAtomBytes;              // two 64-landmark atoms: 8 KB per chunk
 
 struct TcSmem {
     // operand tiles first (1024-byte aligned for the 128-byte swizzle)
     uint8_t y[kTileBytes];           // [plane hi/lo][atom][128 rows x 128 B]
     uint8_t l[2][kTileBytes];        // landmark chunk ring
-    float w[2][kChunk * kTcMaxR];    // W rows of the chunk (padded width RP)
+    uint8_t w[2][kWImgBytes];        // W^T of the chunk, BF16 hi/lo rows, swizzled
     float nl[2][kChunk];             // landmark norms of the chunk
-    float xs[kRows][kTcMaxR];        // the second column half's partial projections
     uint64_t y_full, y_empty;
     uint64_t l_full[2], l_empty[2];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t acc_full[kAcc], acc_empty[kAcc], a2_full[kAcc];
+    uint64_t w_full[2], w_empty[2];
+    uint64_t x_full, x_empty;
     uint64_t mma_done;
     uint32_t tmem_base;
     int abort;
@@ -62,14 +80,13 @@ struct TcArgs {
     int ksteps;           // MMA K-steps of 16 (ceil(d_pad / 16))
     int r;
     const double* nrm_y;  // m
-    const float* nrm_l;   // l, zero-padded to a multiple of 4
-    const float* W;       // l x RP (columns r..RP-1 zero)
+    const float* nrm_l;   // l, zero-padded to a multiple of kChunk
+    const uint8_t* Wimg;  // W^T images, kWImgBytes per chunk (launch_w_image)
     const double* bias;   // r
     float* X;             // m x r
     int* err;
 };
 
-template <int RP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_gower_tc(const __grid_constant__ CUtensorMap tm_yhi, const __grid_constant__ CUtensorMap tm_ylo,
                const __grid_constant__ CUtensorMap tm_lhi, const __grid_constant__ CUtensorMap tm_llo,
@@ -86,11 +103,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         mbar_init(&S.y_full, 1);
         mbar_init(&S.y_empty, 1);
         mbar_init(&S.mma_done, 1);
+        mbar_init(&S.x_full, 1);
+        mbar_init(&S.x_empty, 128);
         for (int s = 0; s < 2; ++s) {
             mbar_init(&S.l_full[s], 1);
             mbar_init(&S.l_empty[s], 1);
+            mbar_init(&S.w_full[s], 1);
+            mbar_init(&S.w_empty[s], 1);
+        }
+        for (int s = 0; s < kAcc; ++s) {
             mbar_init(&S.acc_full[s], 1);
-            mbar_init(&S.acc_empty[s], 256);
+            mbar_init(&S.acc_empty[s], 1);
+            mbar_init(&S.a2_full[s], 256);
         }
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -109,7 +133,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const uint32_t tile_tx = 2u * a.natoms * kPlaneBytes;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: Y tiles and landmark operand chunks
         if (lane == 0) {
             long long gc = 0;  // chunks issued
             int ti = 0;        // tiles issued by this CTA
@@ -125,21 +149,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                     const int s = (int)(gc & 1);
                     const long long use = gc >> 1;
                     // stage s is free when the MMAs of its previous chunk are done
-                    // (l_empty) and the epilogue has read that chunk's W and norms
-                    // (acc_empty of the same use)
-                    if (use > 0 && (!mbar_wait(&S.l_empty[s], (uint32_t)((use - 1) & 1), abort, a.err) ||
-                                    !mbar_wait(&S.acc_empty[s], (uint32_t)((use - 1) & 1), abort, a.err)))
-                        break;
+                    if (use > 0 && !mbar_wait(&S.l_empty[s], (uint32_t)((use - 1) & 1), abort, a.err)) break;
                     const int j0 = c * kChunk;
-                    const uint32_t wbytes = (uint32_t)(kChunk * RP * 4);   // W, norms zero-padded
-                    const uint32_t nbytes = (uint32_t)(kChunk * 4);
-                    mbar_expect_tx(&S.l_full[s], tile_tx + wbytes + nbytes);
+                    mbar_expect_tx(&S.l_full[s], tile_tx);
                     for (int at = 0; at < a.natoms; ++at) {
                         tma_load_2d(S.l[s] + (0 * kMaxAtoms + at) * kPlaneBytes, &tm_lhi, at * kAtomK, j0, &S.l_full[s]);
                         tma_load_2d(S.l[s] + (1 * kMaxAtoms + at) * kPlaneBytes, &tm_llo, at * kAtomK, j0, &S.l_full[s]);
                     }
-                    bulk_load(S.w[s], a.W + (int64_t)j0 * RP, wbytes, &S.l_full[s]);
-                    bulk_load(S.nl[s], a.nrm_l + j0, nbytes, &S.l_full[s]);
                 }
             }
             // drain: wait (bounded) for the copies this thread issued that may
@@ -149,112 +165,179 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                 mbar_drain(&S.l_full[g & 1], (uint32_t)((g >> 1) & 1), a.err);
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer.  Chunk g: the distance MMAs into
+        // accumulator g % 3; then, once the epilogue has turned chunk g - 1
+        // into A^2, that chunk's projection MMAs into the X accumulator (so the
+        // tensor pipe has the next distance tile queued while A^2 is formed).
         if (lane == 0) {
             const uint32_t idesc = umma_idesc(kRows, kChunk);
-            long long gc = 0;
+            const uint32_t idesc_x2 = umma_idesc(kRows, 2 * kTcMaxR);
+            const uint32_t idesc_x1 = umma_idesc(kRows, kTcMaxR);
+            // Shared-memory descriptors of every operand buffer, built once; a
+            // K-step adds its byte offset / 16 to the start-address field (the
+            // single issuing thread is on the critical path, so the loops below
+            // do no more than that per MMA).
+            const uint32_t ybase = smem_u32(S.y);
+            const uint64_t dYh = umma_desc(ybase), dYl = umma_desc(ybase + kMaxAtoms * kPlaneBytes);
+            const uint64_t dLh0 = umma_desc(smem_u32(S.l[0])), dLl0 = umma_desc(smem_u32(S.l[0]) + kMaxAtoms * kPlaneBytes);
+            const uint64_t dLh1 = umma_desc(smem_u32(S.l[1])), dLl1 = umma_desc(smem_u32(S.l[1]) + kMaxAtoms * kPlaneBytes);
+            const uint64_t dW0 = umma_desc(smem_u32(S.w[0])), dW1 = umma_desc(smem_u32(S.w[1]));
+            const int ksteps = a.ksteps;
+            // projection MMAs of chunk g (chunk c of the CTA's tile number tix)
+            auto project = [&](long long g, int c, int tix) -> bool {
+                const int q = (int)(g % kAcc), s = (int)(g & 1);
+                if (!mbar_wait(&S.a2_full[q], (uint32_t)((g / kAcc) & 1), abort, a.err) ||
+                    !mbar_wait(&S.w_full[s], (uint32_t)((g >> 1) & 1), abort, a.err))
+                    return false;
+                // the X accumulator of the previous tile has been read
+                if (c == 0 && tix > 0 && !mbar_wait(&S.x_empty, (uint32_t)((tix - 1) & 1), abort, a.err))
+                    return false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a2 = tmem + (uint32_t)(q * kChunk);
+                const uint64_t dw = s ? dW1 : dW0;
+                const uint32_t first = c > 0 ? 1u : 0u;
+#pragma unroll
+                for (int k = 0; k < kChunk / 16; ++k) {
+                    const int h = k >> 2, kk = k & 3;  // 64-landmark half, K-step within it
+                    const uint32_t ahi = a2 + (uint32_t)(h * 64 + kk * 8), alo = ahi + 32;
+                    // rows 0-15 of the atom are W_hi^T, rows 16-31 W_lo^T
+                    const uint64_t b = dw + (uint64_t)((h * kWAtomBytes + kk * 32) >> 4);
+                    umma_bf16_ta(tmem + kXCol, ahi, b, idesc_x2, k > 0 ? 1u : first);
+                    umma_bf16_ta(tmem + kXCol, alo, b, idesc_x1, 1);
+                }
+                umma_commit(&S.acc_empty[q]);              // accumulator and A^2 free
+                umma_commit(&S.w_empty[s]);                // W stage free
+                if (c == nchunks - 1) umma_commit(&S.x_full);
+                return true;
+            };
+            long long gc = 0, pend = -1;
+            int pend_c = 0, pend_t = 0;
             int ti = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++ti) {
-                if (!mbar_wait(&S.y_full, ti & 1, abort, a.err)) break;
-                bool ok = true;
-                for (int c = 0; c < nchunks && ok; ++c, ++gc) {
-                    const int s = (int)(gc & 1);
-                    const long long use = gc >> 1;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++ti) {
+                if (!mbar_wait(&S.y_full, ti & 1, abort, a.err)) {
+                    ok = false;
+                    break;
+                }
+                for (int c = 0; c < nchunks; ++c, ++gc) {
+                    const int s = (int)(gc & 1), q = (int)(gc % kAcc);
+                    const long long use = gc >> 1, qu = gc / kAcc;
                     ok = mbar_wait(&S.l_full[s], (uint32_t)(use & 1), abort, a.err);
-                    if (ok && use > 0) ok = mbar_wait(&S.acc_empty[s], (uint32_t)((use - 1) & 1), abort, a.err);
+                    if (ok && qu > 0) ok = mbar_wait(&S.acc_empty[q], (uint32_t)((qu - 1) & 1), abort, a.err);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d = tmem + (uint32_t)(s * kChunk);
-                    uint32_t acc = 0;
-                    for (int k = 0; k < a.ksteps; ++k) {
-                        const int at = k / (kAtomK / 16), kk = k % (kAtomK / 16);
-                        const uint32_t off = (uint32_t)(at * kPlaneBytes + kk * 32);
-                        const uint64_t ahi = umma_desc(smem_u32(S.y) + off);
-                        const uint64_t alo = umma_desc(smem_u32(S.y) + kMaxAtoms * kPlaneBytes + off);
-                        const uint64_t bhi = umma_desc(smem_u32(S.l[s]) + off);
-                        const uint64_t blo = umma_desc(smem_u32(S.l[s]) + kMaxAtoms * kPlaneBytes + off);
-                        umma_bf16(d, ahi, bhi, idesc, acc);
-                        acc = 1;
-                        umma_bf16(d, ahi, blo, idesc, 1);
-                        umma_bf16(d, alo, bhi, idesc, 1);
+                    const uint32_t d = tmem + (uint32_t)(q * kChunk);
+                    const uint64_t dLh = s ? dLh1 : dLh0, dLl = s ? dLl1 : dLl0;
+#pragma unroll
+                    for (int k = 0; k < kMaxAtoms * kAtomK / 16; ++k) {
+                        if (k < ksteps) {
+                            const int at = k / (kAtomK / 16), kk = k % (kAtomK / 16);
+                            const uint64_t o = (uint64_t)((at * kPlaneBytes + kk * 32) >> 4);
+                            umma_bf16(d, dYh + o, dLh + o, idesc, k > 0 ? 1u : 0u);
+                            umma_bf16(d, dYh + o, dLl + o, idesc, 1);
+                            umma_bf16(d, dYl + o, dLh + o, idesc, 1);
+                        }
                     }
                     umma_commit(&S.l_empty[s]);    // landmark stage free when these MMAs finish
-                    umma_commit(&S.acc_full[s]);   // accumulator ready for the epilogue
+                    umma_commit(&S.acc_full[q]);   // accumulator ready for the epilogue
+                    if (c == nchunks - 1) umma_commit(&S.y_empty);  // Y tile free after its last MMA
+                    if (pend >= 0 && !(ok = project(pend, pend_c, pend_t))) break;
+                    pend = gc;
+                    pend_c = c;
+                    pend_t = ti;
                 }
-                if (!ok) break;
-                umma_commit(&S.y_empty);           // Y tile free after the tile's last MMA
             }
+            if (ok && pend >= 0 && !*abort) project(pend, pend_c, pend_t);
             // every MMA this thread issued has completed before TMEM is released
             umma_commit(&S.mma_done);
             mbar_drain(&S.mma_done, 0, a.err);
         }
+    } else if (warp == 10) {
+        // ---------------- W^T images and landmark norms of each chunk
+        if (lane == 0) {
+            const uint32_t nbytes = (uint32_t)(kChunk * 4);
+            long long gc = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
+                for (int c = 0; c < nchunks; ++c, ++gc) {
+                    const int s = (int)(gc & 1);
+                    const long long use = gc >> 1;
+                    // stage s is free when the projection of its previous chunk is done
+                    if (use > 0 && !mbar_wait(&S.w_empty[s], (uint32_t)((use - 1) & 1), abort, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&S.w_full[s], kWImgBytes + nbytes);
+                    bulk_load(S.w[s], a.Wimg + (int64_t)c * kWImgBytes, kWImgBytes, &S.w_full[s]);
+                    bulk_load(S.nl[s], a.nrm_l + c * kChunk, nbytes, &S.w_full[s]);
+                }
+            }
+            for (long long g = gc - 2 < 0 ? 0 : gc - 2; g < gc; ++g)
+                mbar_drain(&S.w_full[g & 1], (uint32_t)((g >> 1) & 1), a.err);
+        }
     } else {
         // ---------------- epilogue: warps 2-9, one accumulator row per thread;
         // warps 2-5 take columns 0-63 of every chunk, warps 6-9 columns 64-127
-        // (two warps per TMEM lane quadrant).  The chunk's W rows and norms come
-        // from shared memory (zero-padded past l); the producer refills the
-        // stage only after all eight warps have arrived on acc_empty.  The r-wide
-        // projection runs as packed f32x2 FMAs.
+        // (two warps per TMEM lane quadrant).  Each thread reads its 64 FP32
+        // values, forms A^2 and stores the BF16 hi words over the first 32 of
+        // those columns and the lo words over the last 32, the layout the
+        // projection MMA reads A from.  Every epilogue warp runs the same tiles
+        // and chunks whatever happens (an aborted wait only skips the work).
         const int quad = warp & 3;                 // TMEM lane quadrant this warp may read
         const int half = (warp - 2) >> 2;          // column half of the chunk
         const int row = quad * 32 + lane;
+        const uint32_t lanes = (uint32_t)(quad * 32) << 16;
         const int r = a.r;
-        // Every epilogue warp runs the same tiles and chunks whatever happens
-        // (an aborted wait only skips the work), so the eight warps always meet
-        // at the named barrier.
         long long gc = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int ti = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
             const int64_t gi = t * kRows + row;
             const float ny = gi < a.m ? (float)a.nrm_y[gi] : 0.f;
-            uint64_t xp[RP / 2];                   // pairs (x[2o], x[2o+1])
-#pragma unroll
-            for (int o = 0; o < RP / 2; ++o) xp[o] = 0ull;
             for (int c = 0; c < nchunks; ++c, ++gc) {
-                const int s = (int)(gc & 1);
-                // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
-                const bool got = __all_sync(0xffffffffu, mbar_wait(&S.acc_full[s], (uint32_t)((gc >> 1) & 1), abort, a.err));
+                const int s = (int)(gc & 1), q = (int)(gc % kAcc);
+                // warp-uniform: tcgen05.ld / st are .sync.aligned warp instructions
+                const bool got = __all_sync(0xffffffffu,
+                                            mbar_wait(&S.acc_full[q], (uint32_t)((gc / kAcc) & 1), abort, a.err) &&
+                                                mbar_wait(&S.w_full[s], (uint32_t)((gc >> 1) & 1), abort, a.err));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const float* ws = S.w[s] + half * (kChunk / 2) * RP;
-                const float* ns = S.nl[s] + half * (kChunk / 2);
-#pragma unroll 1
-                for (int cb = 0; cb < (got ? kChunk / 2 : 0); cb += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kChunk + half * (kChunk / 2) + cb), v);
+                if (got) {
+                    const uint32_t col = tmem + lanes + (uint32_t)(q * kChunk + half * 64);
+                    const float* ns = S.nl[s] + half * 64;
+                    float v[2][32];
+                    tmem_ld32(col, v[0]);
+                    tmem_ld32(col + 32, v[1]);
+                    uint32_t hi[32], lo[32];
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const float a2 = fmaxf(fmaf(-2.f, v[e], ny + ns[cb + e]), 0.f);
-                        uint64_t a2p;
-                        asm("mov.b64 %0, {%1, %1};" : "=l"(a2p) : "f"(a2));
-                        const uint4* w4 = reinterpret_cast<const uint4*>(ws + (cb + e) * RP);
-#pragma unroll
-                        for (int q4 = 0; q4 < RP / 4; ++q4) {
-                            const uint4 w = w4[q4];
-                            uint64_t w01, w23;
-                            asm("mov.b64 %0, {%1, %2};" : "=l"(w01) : "r"(w.x), "r"(w.y));
-                            asm("mov.b64 %0, {%1, %2};" : "=l"(w23) : "r"(w.z), "r"(w.w));
-                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(xp[2 * q4]) : "l"(a2p), "l"(w01));
-                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(xp[2 * q4 + 1]) : "l"(a2p), "l"(w23));
-                        }
+                    for (int i = 0; i < 32; ++i) {
+                        const int e = 2 * i;
+                        const float a0 = fmaxf(fmaf(-2.f, v[e >> 5][e & 31], ny + ns[e]), 0.f);
+                        const float a1 = fmaxf(fmaf(-2.f, v[(e + 1) >> 5][(e + 1) & 31], ny + ns[e + 1]), 0.f);
+                        hi[i] = bf16x2_rn(a0, a1);
+                        const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
+                        lo[i] = bf16x2_rn(a0 - h0, a1 - h1);
                     }
+                    tmem_st32(col, hi);
+                    tmem_st32(col + 32, lo);
+                    tmem_wait_st();
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                mbar_arrive(&S.acc_empty[s]);
+                mbar_arrive(&S.a2_full[q]);
             }
-            float x[RP];
+            // the tile's X (r <= 16 columns, the sum of the accumulator's two
+            // halves) from the X accumulator: warps 2-5
+            if (half == 0) {
+                const bool got = __all_sync(0xffffffffu, mbar_wait(&S.x_full, (uint32_t)(ti & 1), abort, a.err));
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float x[2 * kTcMaxR];
+                if (got) tmem_ld32(tmem + lanes + kXCol, x);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&S.x_empty);
+                if (got && gi < a.m) {
 #pragma unroll
-            for (int o = 0; o < RP / 2; ++o)
-                asm("mov.b64 {%0, %1}, %2;" : "=f"(x[2 * o]), "=f"(x[2 * o + 1]) : "l"(xp[o]));
-            // the second half hands its partial sums to the first (named barrier of the 8 warps)
-            if (half == 1)
-#pragma unroll
-                for (int o = 0; o < RP; ++o) S.xs[row][o] = x[o];
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            if (half == 0 && gi < a.m) {
-#pragma unroll
-                for (int o = 0; o < RP; ++o)
-                    if (o < r) a.X[gi * r + o] = x[o] + S.xs[row][o] + (float)a.bias[o];
+                    for (int o = 0; o < kTcMaxR; ++o)
+                        if (o < r) a.X[gi * r + o] = (x[o] + x[kTcMaxR + o]) + (float)a.bias[o];
+                }
             }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
         }
     }
 
@@ -295,12 +378,24 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int cols_pad) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// W (l x r) -> rows padded to a multiple of kChunk, columns to RP, zeros.
-__global__ void k_pad_w(const float* __restrict__ W, int l, int r, int rp, int lpad, float* __restrict__ Wp) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= lpad * rp) return;
-    const int j = e / rp, o = e % rp;
-    Wp[e] = (j < l && o < r) ? W[j * r + o] : 0.f;
+// W (l x r, float) -> per chunk of kChunk landmarks the shared-memory image
+// of W^T that the projection MMAs read as their B operand: [64-landmark
+// atom][32 rows: o = 0..15 of hi = bf16(w), then o = 0..15 of lo = bf16(w - hi)]
+// [128 bytes], zeros for j >= l or o >= r, each row's 16-byte granules stored
+// 128-byte swizzled (granule g of row R at position g ^ (R & 7)).
+__global__ void k_w_image(const float* __restrict__ W, int l, int r, int nchunks, uint16_t* __restrict__ img) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nchunks * (kWImgBytes / 2)) return;
+    const int k = (int)(e % kAtomK), R = (int)((e / kAtomK) % (2 * kTcMaxR));
+    const int at = (int)((e / (kAtomK * 2 * kTcMaxR)) % 2), c = (int)(e / (kWImgBytes / 2));
+    const int o = R % kTcMaxR, plane = R / kTcMaxR;
+    const int j = c * kChunk + at * kAtomK + k;
+    const float w = (j < l && o < r) ? W[(int64_t)j * r + o] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+    const __nv_bfloat16 v = plane == 0 ? h : __float2bfloat16_rn(w - __bfloat162float(h));
+    const int64_t byte = (int64_t)c * kWImgBytes + at * (int64_t)kWAtomBytes + R * 128 +
+                         (((k >> 3) ^ (R & 7)) << 4) + (k & 7) * 2;
+    img[byte / 2] = __bfloat16_as_ushort(v);
 }
 
 }  // namespace
@@ -324,10 +419,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 int gower_tc_lpad(int l) { return (int)round_up(l, kChunk); }
 
-cudaError_t launch_pad_w(const float* W, int l, int r, float* Wp, cudaStream_t st) {
-    const int rp = gower_tc_rp(r);
-    const int lpad = gower_tc_lpad(l);
-    k_pad_w<<<(lpad * rp + 255) / 256, 256, 0, st>>>(W, l, r, rp, lpad, Wp);
+size_t gower_tc_w_bytes(int l) { return (size_t)(gower_tc_lpad(l) / kChunk) * kWImgBytes; }
+
+cudaError_t launch_w_image(const float* W, int l, int r, void* img, cudaStream_t st) {
+    const int nchunks = gower_tc_lpad(l) / kChunk;
+    const int64_t total = (int64_t)nchunks * (kWImgBytes / 2);
+    k_w_image<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(W, l, r, nchunks, (uint16_t*)img);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -345,18 +442,8 @@ bool gower_tc_supported(int d, int r) { return d >= 1 && split_ld(d) <= kMaxAtom
 
 int gower_tc_rp(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : (r <= 12 ? 12 : 16)); }
 
-template <int RP>
-static cudaError_t launch_rp(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
-                             const CUtensorMap& b1, const TcArgs& a, int grid, size_t smem,
-                             cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_gower_tc<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gower_tc<RP><<<grid, kThreadsTc, smem, st>>>(a0, a1, b0, b1, a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
-                            const void* Lsplit, const float* nrm_l, int l, const float* W,
+                            const void* Lsplit, const float* nrm_l, int l, const void* Wimg,
                             const double* bias, int r, float* X, int* err, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     if (!gower_tc_supported(d, r) || l < 1) return cudaErrorInvalidValue;
@@ -375,7 +462,7 @@ cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* 
     a.r = r;
     a.nrm_y = nrm_y;
     a.nrm_l = nrm_l;
-    a.W = W;
+    a.Wimg = (const uint8_t*)Wimg;
     a.bias = bias;
     a.X = X;
     a.err = err;
@@ -386,12 +473,10 @@ cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* 
     const int64_t ntiles = (m + kRows - 1) / kRows;
     const int grid = (int)(ntiles < sms ? ntiles : sms);
     note_launch(1);
-    switch (gower_tc_rp(r)) {
-        case 4: return launch_rp<4>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
-        case 8: return launch_rp<8>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
-        case 12: return launch_rp<12>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
-        default: return launch_rp<16>(m_yhi, m_ylo, m_lhi, m_llo, a, grid, smem, st);
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_gower_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gower_tc<<<grid, kThreadsTc, smem, st>>>(m_yhi, m_ylo, m_lhi, m_llo, a);
+    return cudaGetLastError();
 }
 
 }  // namespace gbmds
