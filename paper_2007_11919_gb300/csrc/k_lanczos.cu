@@ -54,6 +54,7 @@ namespace gbmds {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kMaxCluster = 16;    // largest cluster the launcher forms
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 4;           // stage barriers per warp (stages in use: as many as fit)
 constexpr int kChunkB = 4096;      // longest row segment of Q
@@ -146,17 +147,50 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // out[i] = sum over cluster ranks (in rank order) of part[i], lo <= i < hi;
-// outdf (when not null) receives the sums as double-FP32 pairs.
+// outdf (when not null) receives the sums as double-FP32 pairs.  Each thread
+// issues its loads from all ranks before it adds any of them, so the remote
+// latencies overlap instead of adding up.
 __device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* out, double* outdf, int lo, int hi,
                                   int cs) {
     cl.sync();
     for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
         double s = 0.0;
-        for (int qq = 0; qq < cs; ++qq) s += cl.map_shared_rank(part, qq)[i];
+        for (int q0 = 0; q0 < cs; q0 += 4) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = q0 + u < cs ? cl.map_shared_rank(part, q0 + u)[i] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += v[u];
+        }
         out[i] = s;
         if (outdf) reinterpret_cast<float2*>(outdf)[i] = df_of(s);
     }
     __syncthreads();
+}
+
+// put(i, get(i)) for 0 <= i < n, kUnroll independent loads in flight per
+// thread before their stores.
+constexpr int kUnroll = 4;
+template <class G, class P>
+__device__ __forceinline__ void copy_unrolled(int n, G get, P put) {
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kThreads) {
+        double t[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            t[u] = i < n ? get(i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i < n) put(i, t[u]);
+        }
+    }
+}
+
+template <class G>
+__device__ __forceinline__ void gather_unrolled(double* dst, int n, G get) {
+    copy_unrolled(n, get, [&](int i, double v) { dst[i] = v; });
 }
 
 // ------------------------------------------------- tridiagonal eigen-work
@@ -344,10 +378,10 @@ __device__ void team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int
         for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) gp[(size_t)tm.g * stride + i] = out[i];
     team_sync(cl, tm);
     // every cluster's sums in one pass of independent loads, then the sum in cluster order
-    for (int e = threadIdx.x; e < tm.G * K; e += kThreads) {
+    gather_unrolled(tmp, tm.G * K, [&](int e) {
         const int h = e / K, i = e % K;
-        tmp[e] = __ldcg(gp + (size_t)h * stride + lo + i);
-    }
+        return __ldcg(gp + (size_t)h * stride + lo + i);
+    });
     __syncthreads();
     for (int i = threadIdx.x; i < K; i += kThreads) {
         double sum = 0.0;
@@ -717,13 +751,13 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         // ---- gather v_j from all ranks (8-byte entries, copied as they are)
         if (tm.G > 1) {
             team_sync(cl, tm);
-            for (int i = tid; i < n; i += kThreads) S.vfull[i] = __ldcg(tm.v + i);
+            gather_unrolled(S.vfull, n, [&](int i) { return __ldcg(tm.v + i); });
         } else {
             cl.sync();
-            for (int i = tid; i < n; i += kThreads) {
+            gather_unrolled(S.vfull, n, [&](int i) {
                 const int src = i / R;
-                S.vfull[i] = cl.map_shared_rank(S.vloc, src)[i - src * R];
-            }
+                return cl.map_shared_rank(S.vloc, src)[i - src * R];
+            });
         }
         __syncthreads();
 
@@ -972,10 +1006,9 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             }
         team_sync(cl, tm);
         if (qt == 0 && status != kDevRank) {
-            for (int e = tid; e < r * k; e += kThreads) {
-                const int i = e / k, t = e % k;
-                S.xv[(size_t)i * L + t] = __ldcg(tm.xv + (size_t)i * L + t);
-            }
+            copy_unrolled(
+                r * k, [&](int e) { return __ldcg(tm.xv + (size_t)(e / k) * L + e % k); },
+                [&](int e, double v) { S.xv[(size_t)(e / k) * L + e % k] = v; });
             __syncthreads();
             if (warp == 0) mgs();
             __syncthreads();
@@ -993,17 +1026,20 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             return;
         }
         if (qt != 0)
-            for (int e = tid; e < r * k; e += kThreads) {
-                const int i = e / k, t = e % k;
-                S.xv[(size_t)i * L + t] = __ldcg(tm.xv + (size_t)i * L + t);
-            }
+            copy_unrolled(
+                r * k, [&](int e) { return __ldcg(tm.xv + (size_t)(e / k) * L + e % k); },
+                [&](int e, double v) { S.xv[(size_t)(e / k) * L + e % k] = v; });
         __syncthreads();
     } else {
         if (q == 0 && status != kDevRank) {
-            for (int e = tid; e < r * k; e += kThreads) {
-                const int i = e / k, t = e % k;
-                if (i % cs != 0) S.xv[(size_t)i * L + t] = cl.map_shared_rank(S.xv, i % cs)[(size_t)i * L + t];
-            }
+            copy_unrolled(
+                r * k,
+                [&](int e) {
+                    const int i = e / k;
+                    const size_t o = (size_t)i * L + e % k;
+                    return i % cs != 0 ? cl.map_shared_rank(S.xv, i % cs)[o] : S.xv[o];
+                },
+                [&](int e, double v) { S.xv[(size_t)(e / k) * L + e % k] = v; });
             __syncthreads();
         }
         if (q == 0 && status != kDevRank && warp == 0) mgs();
@@ -1018,10 +1054,9 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         // the other CTAs copy the eigenvectors of T_k from rank 0 (DSMEM)
         if (q != 0) {
             const double* src = cl.map_shared_rank(S.xv, 0);
-            for (int e = tid; e < r * k; e += kThreads) {
-                const int i = e / k, t = e % k;
-                S.xv[(size_t)i * L + t] = src[(size_t)i * L + t];
-            }
+            copy_unrolled(
+                r * k, [&](int e) { return src[(size_t)(e / k) * L + e % k]; },
+                [&](int e, double v) { S.xv[(size_t)(e / k) * L + e % k] = v; });
         }
         cl.sync();   // rank 0's vectors have been copied before any CTA rewrites its own
     }
