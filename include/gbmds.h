@@ -121,6 +121,26 @@ size_t mds_interpolate_workspace_size(int64_t n, int d, int l, int r, int prec);
 int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
                     int r, const mds_opts* opts, void* X, double* var, mds_model* out_model);
 
+/* Interpolation MDS (Section 3.1) of rows that live in host memory: the same
+ * result as mds_interpolate on a device copy of Y (bitwise), computed while Y
+ * crosses the link.  Y (n x d, dtype dt), landmark_idx (l int64), X (n x r:
+ * float, or double for MDS_PREC_F64) and var (r) are HOST pointers; the
+ * caller keeps them alive until the call returns.  The landmark rows are
+ * gathered on the host and their eigenproblem starts at once; meanwhile the
+ * rows are copied in chunks of chunk_rows (0 = 65,536) on a second stream,
+ * each chunk is turned into the projection operands as it lands, projected
+ * once the model is ready, and its rows of X are copied back on a third
+ * stream.  Y and X should be page-locked (pinned) for the copies to overlap
+ * the computation; pageable memory works but serialises them.  The
+ * workspace (opts->workspace, mds_interpolate_host_workspace_size bytes)
+ * holds a device copy of Y and X besides mds_interpolate's workspace.
+ * Errors: MDS_ERR_ARG also for a landmark index outside [0, n) (checked on
+ * the host before any work); statuses as mds_interpolate. */
+size_t mds_interpolate_host_workspace_size(int64_t n, int d, int l, int r, int prec, int dt);
+int mds_interpolate_host(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
+                         int r, int64_t chunk_rows, const mds_opts* opts, void* X, double* var,
+                         mds_model* out_model);
+
 /* Gower's formula, Eq. (2), for m new rows Ynew (m x d, dtype dt) against a
  * stored model; X is m x r.  opts->prec must equal the model's precision.
  * Equal inputs give bitwise-equal outputs regardless of what else is batched

@@ -538,7 +538,7 @@ int gbmds::embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, ch
     if (s) return s;
     for (int i = 0; i < 4; ++i) tmark(i, st);   // stage 0 = preparation, stage 4 = projection
     if (m->prec == MDS_PREC_BF16) {
-        CK(launch_gower_tc(Ye, rows, m->d, nrm, m->L, m->nrm_lf, m->l, m->W, m->bias,
+        CK(launch_gower_tc(Ye, rows, rows, m->d, nrm, m->L, m->nrm_lf, m->l, m->W, m->bias,
                            m->r, (float*)X, kerr, st));
         return MDS_OK;
     }
@@ -655,6 +655,52 @@ size_t mds_interpolate_workspace_size(int64_t n, int d, int l, int r, int prec) 
     return need + 256;
 }
 
+// Copies the interpolation model of a finished call out of its workspace into
+// a device-resident handle for mds_embed_new.
+static int make_model(InterpWs& W, int kind, const Opts& o, int l, int d, int r, mds_model* out_model) {
+    const int f64 = o.prec == MDS_PREC_F64;
+    // device-resident model for mds_embed_new
+    mds_model m = new (std::nothrow) mds_model_s();
+    if (!m) return MDS_ERR_NOMEM;
+    const size_t es = f64 ? 8 : 4;
+    m->l = l;
+    m->d = d;
+    m->r = r;
+    m->prec = o.prec;
+    m->kind = kind;
+    cudaGetDevice(&m->device);
+    const size_t szL = model_L_bytes(kind, o.prec, l, d);
+    const size_t szW = model_W_bytes(kind, o.prec, l, r);
+    const size_t nlf = model_nlf_count(kind, l);
+    bool ok = cudaMalloc(&m->L, szL) == cudaSuccess &&
+              cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
+              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * nlf) == cudaSuccess &&
+              cudaMalloc(&m->W, szW) == cudaSuccess &&
+              cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
+              cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
+              cudaMalloc((void**)&m->lam, sizeof(double) * r) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        mds_model_free(m);
+        return MDS_ERR_NOMEM;
+    }
+    ok = cudaMemcpyAsync(m->L, W.L, szL, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->nrm_l, W.nrm_l, sizeof(double) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * nlf, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->W, (kind != kKindRows || o.prec == MDS_PREC_BF16) ? (void*)W.Wpad : W.W, szW,
+                         cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->bias, W.bias, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->X1, W.X1, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaMemcpyAsync(m->lam, W.B.lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
+         cudaStreamSynchronize(o.st) == cudaSuccess;
+    if (!ok) {
+        mds_model_free(m);
+        return MDS_ERR_CUDA;
+    }
+    *out_model = m;
+    return MDS_OK;
+}
+
 int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
                     int r, const mds_opts* opts, void* X, double* var, mds_model* out_model) {
     Opts o;
@@ -714,7 +760,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
         CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * model_nlf_count(kind, l), o.st));
         CK(launch_gather_split(Ye, n, d, landmark_idx, l, W.L, W.nrm, W.nrm_lf, o.st));
         CK(launch_w_image((const float*)W.W, l, r, W.Wpad, o.st));
-        CK(launch_gower_tc(Ye, n, d, W.nrm, W.L, W.nrm_lf, l, W.Wpad, W.bias, r, (float*)X,
+        CK(launch_gower_tc(Ye, n, n, d, W.nrm, W.L, W.nrm_lf, l, W.Wpad, W.bias, r, (float*)X,
                            W.kerr, o.st));
     } else {
         CK(launch_gather_rows(Ye, dte, n, d, landmark_idx, l, f64, W.L, W.nrm, W.nrm_l, o.st));
@@ -723,47 +769,180 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     CK(launch_scatter_rows(W.X1, landmark_idx, l, r, n, f64, X, o.st));
     s = finish(&W.B, W.flag, o, W.kerr);
     if (s != MDS_OK || !out_model) return s;
+    return make_model(W, kind, o, l, d, r, out_model);
+}
 
-    // device-resident model for mds_embed_new
-    mds_model m = new (std::nothrow) mds_model_s();
-    if (!m) return MDS_ERR_NOMEM;
-    const size_t es = f64 ? 8 : 4;
-    m->l = l;
-    m->d = d;
-    m->r = r;
-    m->prec = o.prec;
-    m->kind = kind;
-    cudaGetDevice(&m->device);
-    const size_t szL = model_L_bytes(kind, o.prec, l, d);
-    const size_t szW = model_W_bytes(kind, o.prec, l, r);
-    const size_t nlf = model_nlf_count(kind, l);
-    bool ok = cudaMalloc(&m->L, szL) == cudaSuccess &&
-              cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
-              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * nlf) == cudaSuccess &&
-              cudaMalloc(&m->W, szW) == cudaSuccess &&
-              cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
-              cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
-              cudaMalloc((void**)&m->lam, sizeof(double) * r) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();
-        mds_model_free(m);
-        return MDS_ERR_NOMEM;
+// ------------------------------------------ interpolation from host memory
+
+struct InterpHostWs {
+    InterpWs W;
+    void* Yd;          // n x d of the input type: the rows as they arrive
+    void* Xd;          // n x r (float, or double for FP64)
+    void* Ylm;         // l x d: the landmark rows
+    int64_t* idx;      // l: landmark indices (for the landmark rows of X)
+    int64_t* iota;     // l
+    double* nrm_lm;    // l: norms of the landmark rows for the landmark problem
+    double* nrm_lms;   // l: BF16 split norms of the landmark rows
+    void* Yq_lm;       // BF16 split planes of the landmark rows
+    double* var;       // r
+};
+
+static size_t in_size(int dt) { return dt == MDS_IN_F64 ? 8 : (dt == MDS_IN_F32 ? 4 : 1); }
+
+size_t interp_host_layout(InterpHostWs& H, char* base, int64_t n, int d, int l, int r, int prec, int kind,
+                          int dt, int mmax) {
+    Arena A{base, interp_layout(H.W, base, n, d, l, r, prec, kind, mmax)};
+    const size_t es = in_size(dt), ex = prec == MDS_PREC_F64 ? 8 : 4;
+    H.Yd = A.take<char>((size_t)n * d * es);
+    H.Xd = A.take<char>((size_t)n * r * ex);
+    H.Ylm = A.take<char>((size_t)l * d * es);
+    H.idx = A.take<int64_t>(l);
+    H.iota = A.take<int64_t>(l);
+    H.nrm_lm = A.take<double>(l);
+    H.nrm_lms = A.take<double>(l);
+    H.Yq_lm = A.take<uint16_t>((size_t)2 * l * split_ld(d));
+    H.var = A.take<double>(r);
+    return A.off;
+}
+
+constexpr int64_t kHostChunkRows = 65536;
+
+// Streams and events of one host-input call, released on every return path.
+struct HostPipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~HostPipe() {
+        if (h2d) cudaStreamSynchronize(h2d);
+        if (d2h) cudaStreamSynchronize(d2h);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (h2d) cudaStreamDestroy(h2d);
+        if (d2h) cudaStreamDestroy(d2h);
     }
-    ok = cudaMemcpyAsync(m->L, W.L, szL, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->nrm_l, W.nrm_l, sizeof(double) * l, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->nrm_lf, W.nrm_lf, sizeof(float) * nlf, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->W, (kind != kKindRows || o.prec == MDS_PREC_BF16) ? (void*)W.Wpad : W.W, szW,
-                         cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->bias, W.bias, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->X1, W.X1, (size_t)l * r * es, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaMemcpyAsync(m->lam, W.B.lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, o.st) == cudaSuccess &&
-         cudaStreamSynchronize(o.st) == cudaSuccess;
-    if (!ok) {
-        mds_model_free(m);
-        return MDS_ERR_CUDA;
+    cudaError_t make(int nev) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking);
+        for (int i = 0; i < nev && e == cudaSuccess; ++i) {
+            cudaEvent_t x;
+            e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+            if (e == cudaSuccess) ev.push_back(x);
+        }
+        return e;
     }
-    *out_model = m;
-    return MDS_OK;
+};
+
+size_t mds_interpolate_host_workspace_size(int64_t n, int d, int l, int r, int prec, int dt) {
+    if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0 || !valid_dt(dt)) return 0;
+    const int kind = model_kind(prec, dt, d, r);
+    if (kind < 0) return 0;
+    InterpHostWs H;
+    return interp_host_layout(H, nullptr, n, d, l, r, prec, kind, dt, kDefaultSteps) + 256;
+}
+
+int mds_interpolate_host(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l, int r,
+                         int64_t chunk_rows, const mds_opts* opts, void* X, double* var, mds_model* out_model) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (out_model) *out_model = nullptr;
+    if (!Y || !X || !var || !landmark_idx || !valid_dt(dt) || n < 2 || d <= 0 || l < 2 || l > n ||
+        l > kMaxEigN || r <= 0 || r > kMaxR || r >= l || chunk_rows < 0)
+        return MDS_ERR_ARG;
+    for (int i = 0; i < l; ++i)
+        if (landmark_idx[i] < 0 || landmark_idx[i] >= n) return MDS_ERR_ARG;
+    const int kind = model_kind(o.prec, dt, d, r);
+    if (kind < 0) return MDS_ERR_UNSUPPORTED;
+    InterpHostWs H;
+    const size_t need = interp_host_layout(H, nullptr, n, d, l, r, o.prec, kind, dt, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    if (interp_host_layout(H, o.ws, n, d, l, r, o.prec, kind, dt, o.mmax) != need) return MDS_ERR_WORKSPACE;
+    InterpWs& W = H.W;
+    const int f64 = o.prec == MDS_PREC_F64;
+    const size_t es = in_size(dt), ex = f64 ? 8 : 4;
+    const int64_t chunk = chunk_rows > 0 ? chunk_rows : kHostChunkRows;
+    const int nch = (int)((n + chunk - 1) / chunk);
+    const char* Yh = static_cast<const char*>(Y);
+    char* Xh = static_cast<char*>(X);
+    char* Yd = static_cast<char*>(H.Yd);
+    char* Xd = static_cast<char*>(H.Xd);
+
+    // the landmark rows, gathered on the host so that the landmark problem can
+    // start before the bulk of the rows has crossed the link
+    std::vector<char> lm((size_t)l * d * es);
+    for (int i = 0; i < l; ++i) memcpy(lm.data() + (size_t)i * d * es, Yh + (size_t)landmark_idx[i] * d * es, d * es);
+
+    HostPipe P;
+    CK(P.make(2 * nch + 1));
+    begin_call(o.st);
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
+    CK(cudaMemcpyAsync(H.Ylm, lm.data(), lm.size(), cudaMemcpyHostToDevice, o.st));
+    CK(cudaMemcpyAsync(H.idx, landmark_idx, sizeof(int64_t) * l, cudaMemcpyHostToDevice, o.st));
+    CK(launch_iota(H.iota, l, o.st));
+
+    // rows stream in on their own stream while the landmark problem runs: each
+    // chunk is copied and turned into the projection kernel's operands
+    for (int c = 0; c < nch; ++c) {
+        const int64_t row0 = (int64_t)c * chunk, rows = std::min(chunk, n - row0);
+        char* Yc = Yd + (size_t)row0 * d * es;
+        CK(cudaMemcpyAsync(Yc, Yh + (size_t)row0 * d * es, (size_t)rows * d * es, cudaMemcpyHostToDevice, P.h2d));
+        if (kind != kKindRows)
+            CK(launch_encode_u8(kind - 1, (const uint8_t*)Yc, rows, d,
+                                static_cast<char*>(W.Yq) + tck_operand_bytes(kind - 1, row0, d), W.nrm_f + row0,
+                                P.h2d));
+        else if (o.prec == MDS_PREC_BF16)
+            CK(launch_quant_bf16_rows(Yc, dt, rows, d, W.Yq, row0, n, W.nrm, P.h2d));
+        else
+            CK(launch_rownorm(Yc, dt, rows, d, f64, W.nrm + row0, P.h2d));
+        CK(cudaEventRecord(P.ev[2 * c], P.h2d));
+    }
+
+    // classical MDS of the landmarks (first subset of Section 3.1) from the
+    // unrounded landmark rows, then the Gower operator and its operands
+    CK(launch_rownorm(H.Ylm, dt, l, d, f64, H.nrm_lm, o.st));
+    tmark(0, o.st);
+    if ((s = run_eig_batch(W.B, H.Ylm, dt, d, H.nrm_lm, nullptr, H.iota, f64, o))) return s;
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, o.prec != MDS_PREC_F64, l, r,
+                           f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
+                           f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
+                           H.var, o.st));
+    if (kind != kKindRows) {
+        CK(launch_encode_landmarks_u8(kind - 1, (const uint8_t*)H.Ylm, l, d, H.iota, l, W.L, W.nrm_lf, o.st));
+        CK(launch_pad_w_rows((const float*)W.W, l, r, W.Wpad, o.st));
+    } else if (o.prec == MDS_PREC_BF16) {
+        CK(cudaMemsetAsync(W.nrm_lf, 0, sizeof(float) * model_nlf_count(kind, l), o.st));
+        CK(launch_quant_bf16(H.Ylm, dt, l, d, H.Yq_lm, H.nrm_lms, o.st));
+        CK(launch_gather_split(H.Yq_lm, l, d, H.iota, l, W.L, H.nrm_lms, W.nrm_lf, o.st));
+        CK(launch_w_image((const float*)W.W, l, r, W.Wpad, o.st));
+    } else {
+        CK(launch_gather_rows(H.Ylm, dt, l, d, H.iota, l, f64, W.L, H.nrm_lm, W.nrm_l, o.st));
+    }
+
+    // each chunk is projected once it has arrived, its landmark rows set to
+    // X_1, and its X copied out on a third stream
+    for (int c = 0; c < nch; ++c) {
+        const int64_t row0 = (int64_t)c * chunk, rows = std::min(chunk, n - row0);
+        char* Xc = Xd + (size_t)row0 * r * ex;
+        CK(cudaStreamWaitEvent(o.st, P.ev[2 * c], 0));
+        if (kind != kKindRows)
+            CK(launch_gower_tck(kind - 1, static_cast<char*>(W.Yq) + tck_operand_bytes(kind - 1, row0, d), rows, d,
+                                W.nrm_f + row0, W.L, l, W.nrm_lf, W.Wpad, W.bias, r, (float*)Xc, W.kerr, o.st));
+        else if (o.prec == MDS_PREC_BF16)
+            CK(launch_gower_tc(static_cast<uint16_t*>(W.Yq) + (size_t)row0 * split_ld(d), rows, n, d, W.nrm + row0,
+                               W.L, W.nrm_lf, l, W.Wpad, W.bias, r, (float*)Xc, W.kerr, o.st));
+        else
+            CK(launch_gower_proj(Yd + (size_t)row0 * d * es, dt, rows, d, W.nrm + row0, W.L, W.nrm_l, l, W.W,
+                                 W.bias, r, f64, Xc, o.st));
+        CK(launch_scatter_rows_range(W.X1, H.idx, l, r, row0, rows, f64, Xc, o.st));
+        CK(cudaEventRecord(P.ev[2 * c + 1], o.st));
+        CK(cudaStreamWaitEvent(P.d2h, P.ev[2 * c + 1], 0));
+        CK(cudaMemcpyAsync(Xh + (size_t)row0 * r * ex, Xc, (size_t)rows * r * ex, cudaMemcpyDeviceToHost, P.d2h));
+    }
+    CK(cudaMemcpyAsync(var, H.var, sizeof(double) * r, cudaMemcpyDeviceToHost, P.d2h));
+    CK(cudaEventRecord(P.ev[2 * nch], P.d2h));
+    CK(cudaStreamWaitEvent(o.st, P.ev[2 * nch], 0));
+    s = finish(&W.B, W.flag, o, W.kerr);
+    if (s != MDS_OK || !out_model) return s;
+    return make_model(W, kind, o, l, d, r, out_model);
 }
 
 size_t mds_embed_new_workspace_size(mds_model m, int64_t rows) {

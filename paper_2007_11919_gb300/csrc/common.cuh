@@ -203,14 +203,20 @@ cudaError_t launch_iota(int64_t* out, int64_t n, cudaStream_t st);
 // hi^2 + 2 hi lo (the products a split tensor-core dot product forms).
 cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
                               cudaStream_t st);
+// The same for `rows` rows that are rows row0.. of planes of nplane rows each
+// (hi plane at Yq, lo plane nplane * split_ld(d) elements later; norms at nrm[row0..]).
+cudaError_t launch_quant_bf16_rows(const void* Y, int dt, int64_t rows, int d, void* Yq, int64_t row0,
+                                   int64_t nplane, double* nrm, cudaStream_t st);
 
 // Tensor-core Gower projection for BF16 split data (tcgen05 + TMA): X (m x r,
 // float) = A^2 W + b with A^2 from the split planes of Y (m rows) and of the l
 // landmarks (norms nrm_l zero-padded to gower_tc_lpad(l)), W as the image
-// launch_w_image writes.  Requires gower_tc_supported(d, r).  *err receives
-// MDS_ERR_TIMEOUT if a bounded wait gives up.
+// launch_w_image writes.  The lo plane of Y starts ylo_rows * split_ld(d)
+// elements after Ysplit (ylo_rows = m for planes of exactly these rows).
+// Requires gower_tc_supported(d, r).  *err receives MDS_ERR_TIMEOUT if a
+// bounded wait gives up.
 bool gower_tc_supported(int d, int r);
-cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
+cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int64_t ylo_rows, int d, const double* nrm_y,
                             const void* Lsplit, const float* nrm_l, int l, const void* Wimg,
                             const double* bias, int r, float* X, int* err, cudaStream_t st);
 // Padded width (4, 8, 12 or 16) of W rows for the byte-row kernel.
@@ -228,6 +234,9 @@ cudaError_t launch_gather_split(const void* Ysplit, int64_t ny, int d, const int
 // X[idx[i]] = X1[i] (landmark rows of interpolation MDS).
 cudaError_t launch_scatter_rows(const void* X1, const int64_t* idx, int l, int r, int64_t nx,
                                 int out_f64, void* X, cudaStream_t st);
+// The same restricted to rows row0 .. row0 + rows - 1, X holding those rows only.
+cudaError_t launch_scatter_rows_range(const void* X1, const int64_t* idx, int l, int r, int64_t row0,
+                                      int64_t rows, int out_f64, void* X, cudaStream_t st);
 
 // Divide-and-conquer: Procrustes of every part against part 0, then the
 // aligned scatter and the averaged eigenvalues.

@@ -282,14 +282,14 @@ __global__ void k_iota(int64_t* __restrict__ out, int64_t n) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_quant_bf16(const T* __restrict__ Y, int64_t n, int d,
-                                                    __nv_bfloat16* __restrict__ Yq,
+                                                    __nv_bfloat16* __restrict__ Yq, int64_t row0, int64_t nplane,
                                                     double* __restrict__ nrm) {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= n) return;
     const int ld = split_ld(d);
-    __nv_bfloat16* hi = Yq + row * ld;
-    __nv_bfloat16* lo = hi + n * (int64_t)ld;
+    __nv_bfloat16* hi = Yq + (row0 + row) * ld;
+    __nv_bfloat16* lo = hi + nplane * (int64_t)ld;
     float s = 0.f;
     for (int k = lane; k < ld; k += 32) {
         const float y = k < d ? (float)Y[row * d + k] : 0.f;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_quant_bf16(const T* __restrict__ Y, int
         s += hf * hf + 2.f * hf * lf;
     }
     s = warp_sum(s);
-    if (lane == 0) nrm[row] = (double)s;
+    if (lane == 0) nrm[row0 + row] = (double)s;
 }
 
 // The same split for FP32 rows with d a multiple of 4 and a 16-byte aligned
@@ -313,15 +313,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b
 }
 
 __global__ void __launch_bounds__(256) k_quant_bf16_f4(const float* __restrict__ Y, int64_t n, int d,
-                                                       __nv_bfloat16* __restrict__ Yq,
+                                                       __nv_bfloat16* __restrict__ Yq, int64_t row0, int64_t nplane,
                                                        double* __restrict__ nrm) {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= n) return;
     const int ld = split_ld(d);
     const float4* y4 = reinterpret_cast<const float4*>(Y + row * d);
-    uint2* hi = reinterpret_cast<uint2*>(Yq + row * ld);
-    uint2* lo = reinterpret_cast<uint2*>(Yq + n * (int64_t)ld + row * ld);
+    uint2* hi = reinterpret_cast<uint2*>(Yq + (row0 + row) * ld);
+    uint2* lo = reinterpret_cast<uint2*>(Yq + nplane * (int64_t)ld + (row0 + row) * ld);
     float s = 0.f;
     for (int k4 = lane; k4 < ld / 4; k4 += 32) {
         const float4 v = k4 < d / 4 ? __ldcs(y4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) k_quant_bf16_f4(const float* __restrict__
         lo[k4] = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
     }
     s = warp_sum(s);
-    if (lane == 0) nrm[row] = (double)s;
+    if (lane == 0) nrm[row0 + row] = (double)s;
 }
 
 template <typename Ld, typename A>
@@ -466,17 +466,23 @@ cudaError_t launch_iota(int64_t* out, int64_t n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
-                              cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((n + 7) / 8));
-    if (dt == MDS_IN_F64) k_quant_bf16<double><<<grid, 256, 0, st>>>((const double*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
+cudaError_t launch_quant_bf16_rows(const void* Y, int dt, int64_t rows, int d, void* Yq, int64_t row0,
+                                   int64_t nplane, double* nrm, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((rows + 7) / 8));
+    __nv_bfloat16* q = (__nv_bfloat16*)Yq;
+    if (dt == MDS_IN_F64) k_quant_bf16<double><<<grid, 256, 0, st>>>((const double*)Y, rows, d, q, row0, nplane, nrm);
     else if (dt == MDS_IN_F32 && d % 4 == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0)
-        k_quant_bf16_f4<<<grid, 256, 0, st>>>((const float*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
-    else if (dt == MDS_IN_F32) k_quant_bf16<float><<<grid, 256, 0, st>>>((const float*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
-    else k_quant_bf16<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)Y, n, d, (__nv_bfloat16*)Yq, nrm);
+        k_quant_bf16_f4<<<grid, 256, 0, st>>>((const float*)Y, rows, d, q, row0, nplane, nrm);
+    else if (dt == MDS_IN_F32) k_quant_bf16<float><<<grid, 256, 0, st>>>((const float*)Y, rows, d, q, row0, nplane, nrm);
+    else k_quant_bf16<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)Y, rows, d, q, row0, nplane, nrm);
     note_launch(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_quant_bf16(const void* Y, int dt, int64_t n, int d, void* Yq, double* nrm,
+                              cudaStream_t st) {
+    return launch_quant_bf16_rows(Y, dt, n, d, Yq, 0, n, nrm, st);
 }
 
 }  // namespace gbmds

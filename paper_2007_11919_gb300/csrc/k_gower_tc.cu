@@ -442,7 +442,7 @@ bool gower_tc_supported(int d, int r) { return d >= 1 && split_ld(d) <= kMaxAtom
 
 int gower_tc_rp(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : (r <= 12 ? 12 : 16)); }
 
-cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* nrm_y,
+cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int64_t ylo_rows, int d, const double* nrm_y,
                             const void* Lsplit, const float* nrm_l, int l, const void* Wimg,
                             const double* bias, int r, float* X, int* err, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
@@ -451,7 +451,7 @@ cudaError_t launch_gower_tc(const void* Ysplit, int64_t m, int d, const double* 
     const __nv_bfloat16* yh = (const __nv_bfloat16*)Ysplit;
     const __nv_bfloat16* lh = (const __nv_bfloat16*)Lsplit;
     CUtensorMap m_yhi, m_ylo, m_lhi, m_llo;
-    if (!make_map(&m_yhi, yh, m, ld) || !make_map(&m_ylo, yh + m * ld, m, ld) ||
+    if (!make_map(&m_yhi, yh, m, ld) || !make_map(&m_ylo, yh + ylo_rows * ld, m, ld) ||
         !make_map(&m_lhi, lh, l, ld) || !make_map(&m_llo, lh + (int64_t)l * ld, l, ld))
         return cudaErrorInvalidValue;
     TcArgs a;

@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(256) k_gower(Ld Y, int64_t m, int d,
 
 template <typename A>
 __global__ void k_scatter(const A* __restrict__ X1, const int64_t* __restrict__ idx, int l, int r,
-                          int64_t nx, A* __restrict__ X) {
+                          int64_t row0, int64_t nx, A* __restrict__ X) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= l * r) return;
     const int i = e / r, c = e % r;
-    const int64_t g = idx[i];
+    const int64_t g = idx[i] - row0;
     if (g >= 0 && g < nx) X[g * r + c] = X1[e];
 }
 
@@ -218,8 +218,18 @@ cudaError_t launch_scatter_rows(const void* X1, const int64_t* idx, int l, int r
                                 int out_f64, void* X, cudaStream_t st) {
     const int tot = l * r;
     if (tot <= 0) return cudaSuccess;
-    if (out_f64) k_scatter<double><<<(tot + 255) / 256, 256, 0, st>>>((const double*)X1, idx, l, r, nx, (double*)X);
-    else k_scatter<float><<<(tot + 255) / 256, 256, 0, st>>>((const float*)X1, idx, l, r, nx, (float*)X);
+    if (out_f64) k_scatter<double><<<(tot + 255) / 256, 256, 0, st>>>((const double*)X1, idx, l, r, 0, nx, (double*)X);
+    else k_scatter<float><<<(tot + 255) / 256, 256, 0, st>>>((const float*)X1, idx, l, r, 0, nx, (float*)X);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows_range(const void* X1, const int64_t* idx, int l, int r, int64_t row0,
+                                      int64_t rows, int out_f64, void* X, cudaStream_t st) {
+    const int tot = l * r;
+    if (tot <= 0 || rows <= 0) return cudaSuccess;
+    if (out_f64) k_scatter<double><<<(tot + 255) / 256, 256, 0, st>>>((const double*)X1, idx, l, r, row0, rows, (double*)X);
+    else k_scatter<float><<<(tot + 255) / 256, 256, 0, st>>>((const float*)X1, idx, l, r, row0, rows, (float*)X);
     note_launch(1);
     return cudaGetLastError();
 }

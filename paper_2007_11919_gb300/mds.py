@@ -59,6 +59,8 @@ def _lib():
             "mds_classical_dist": (_I, [_P, _I64, _I, _P, _P, _P]),
             "mds_interpolate_workspace_size": (_SZ, [_I64, _I, _I, _I, _I]),
             "mds_interpolate": (_I, [_P, _I, _I64, _I, _P, _I, _I, _P, _P, _P, _P]),
+            "mds_interpolate_host_workspace_size": (_SZ, [_I64, _I, _I, _I, _I, _I]),
+            "mds_interpolate_host": (_I, [_P, _I, _I64, _I, _P, _I, _I, _I64, _P, _P, _P, _P]),
             "mds_embed_new_workspace_size": (_SZ, [_P, _I64]),
             "mds_embed_new": (_I, [_P, _P, _I, _I64, _P, _P]),
             "mds_model_info": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -194,6 +196,33 @@ def mds_interpolate(Y, landmark_idx, r, prec="f32", want_model=False, **kw):
     _check(L.mds_interpolate(_ptr(Y), dt, n, d, _ptr(idx), l, r, ctypes.byref(o), _ptr(X), _ptr(var),
                              ctypes.byref(h) if want_model else None), "mds_interpolate")
     return X, var, (Model(h.value, Y.device) if want_model else None)
+
+
+def mds_interpolate_host(Y, landmark_idx, r, prec="f32", want_model=False, chunk_rows=0, out=None,
+                         device=None, **kw):
+    """Interpolation MDS (Section 3.1) of host-resident rows: ``Y`` is a 2-D CPU
+    tensor (pin it for the copies to overlap the computation), the result X and
+    var are CPU tensors (X pinned unless ``out`` is given).  Bitwise equal to
+    ``mds_interpolate`` on a device copy of ``Y``."""
+    if not (isinstance(Y, torch.Tensor) and not Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()):
+        raise ValueError("data must be a contiguous 2-D CPU tensor")
+    if Y.dtype not in DTYPE:
+        raise ValueError(f"unsupported dtype {Y.dtype}")
+    dt = DTYPE[Y.dtype]
+    n, d = Y.shape
+    idx = torch.as_tensor(landmark_idx, dtype=torch.int64).cpu().contiguous()
+    l = idx.numel()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    L = _lib()
+    o, ws = _opts(dev, prec, L.mds_interpolate_host_workspace_size(n, d, l, r, PREC[prec], dt), **kw)
+    X = out if out is not None else torch.empty((n, r), dtype=_xdtype(prec), pin_memory=True)
+    if X.is_cuda or X.shape != (n, r) or X.dtype != _xdtype(prec) or not X.is_contiguous():
+        raise ValueError("out must be a contiguous CPU tensor of shape (n, r) and the result dtype")
+    var = torch.empty(r, dtype=torch.float64)
+    h = ctypes.c_void_p()
+    _check(L.mds_interpolate_host(_ptr(Y), dt, n, d, _ptr(idx), l, r, int(chunk_rows), ctypes.byref(o), _ptr(X),
+                                  _ptr(var), ctypes.byref(h) if want_model else None), "mds_interpolate_host")
+    return X, var, (Model(h.value, dev) if want_model else None)
 
 
 def mds_embed_new(model: Model, Ynew, prec=None, **kw):

@@ -438,3 +438,48 @@ def test_dc_plan_fp8(gb):
     assert torch.equal(X, Xd) and torch.equal(var, vd)
     Xo, lo_, _ = O.divide_conquer_mds(Y.astype(np.float64), part.anchors, part.ptr, part.own, 10)
     assert O.aligned_rel_error(host(X), Xo) < TOL["bf16"]
+
+
+# ------------------------------------------------ interpolation from host memory
+
+@pytest.mark.parametrize("prec,kind", [("bf16", "f32"), ("f32", "f32"), ("f64", "f64"), ("f32", "f64"),
+                                       ("fp8", "u8"), ("bf16", "u8")])
+@pytest.mark.parametrize("n,d,l,r,chunk", [(5000, 100, 300, 10, 1024), (2999, 37, 129, 3, 700),
+                                           (700, 20, 300, 5, 0)])
+def test_interp_host_equals_device(gb, prec, kind, n, d, l, r, chunk):
+    """mds_interpolate_host (host rows, chunked copies overlapping the landmark
+    eigenproblem and the projection) gives bitwise the result of
+    mds_interpolate on a device copy: same X (landmark rows included), same
+    variances, and a model that embeds identically; ragged last chunk, chunks
+    smaller than a tile, one chunk for all rows."""
+    if kind == "u8":
+        d = 784 if d == 100 else d
+        Y = W.image_like(n, d, seed=n + d)
+    else:
+        Y = W.gaussian_dominant(n, d, min(5, d), seed=n + d, dtype=np.float64 if kind == "f64" else np.float32)
+    idx = W.landmarks(n, l, seed=n + l)
+    Xd, vd, md = gb.mds_interpolate(dev(Y), dev(idx), r, prec, want_model=True)
+    Yh = torch.from_numpy(np.ascontiguousarray(Y)).pin_memory()
+    Xh, vh, mh = gb.mds_interpolate_host(Yh, torch.from_numpy(idx), r, prec, want_model=True, chunk_rows=chunk)
+    assert not Xh.is_cuda and Xh.shape == (n, r)
+    assert torch.equal(Xh, Xd.cpu())
+    assert torch.equal(vh, vd.cpu())
+    probe = dev(Y[:257])
+    assert torch.equal(gb.mds_embed_new(mh, probe), gb.mds_embed_new(md, probe))
+
+
+def test_interp_host_pageable_and_errors(gb):
+    """Pageable host rows give the same result (the copies just do not
+    overlap); a landmark index outside [0, n) is an argument error."""
+    n, d, l, r = 3000, 50, 200, 4
+    Y = W.gaussian_dominant(n, d, 5, seed=3, dtype=np.float32)
+    idx = W.landmarks(n, l, seed=4)
+    Xd, vd, _ = gb.mds_interpolate(dev(Y), dev(idx), r, "bf16")
+    Xh, vh, _ = gb.mds_interpolate_host(torch.from_numpy(Y), torch.from_numpy(idx), r, "bf16", chunk_rows=512)
+    assert torch.equal(Xh, Xd.cpu()) and torch.equal(vh, vd.cpu())
+    bad = idx.copy()
+    bad[3] = n
+    with pytest.raises(gb.MdsError):
+        gb.mds_interpolate_host(torch.from_numpy(Y), torch.from_numpy(bad), r, "bf16")
+    with pytest.raises(ValueError):
+        gb.mds_interpolate_host(dev(Y), torch.from_numpy(idx), r, "bf16")

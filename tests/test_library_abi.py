@@ -93,6 +93,30 @@ def test_workspace_sizes(lib):
         10_000, 100, 500, 10, 1)
 
 
+def test_host_interpolation_checks_without_gpu(lib):
+    """mds_interpolate_host checks its host-side arguments (landmark range,
+    chunk size, workspace) before any CUDA work."""
+    o = _opts(prec=1)
+    p = ctypes.c_void_p(8)
+    good = np.arange(0, 200, 2, dtype=np.int64)            # 100 landmarks of 1,000 rows
+    bad = good.copy()
+    bad[7] = 1000                                           # outside [0, n)
+    neg = good.copy()
+    neg[0] = -1
+    gp, bp, np_ = (a.ctypes.data_as(ctypes.c_void_p) for a in (good, bad, neg))
+    assert lib.mds_interpolate_host(p, 1, 1000, 8, bp, 100, 3, 0, ctypes.byref(o), p, p, None) == 1
+    assert lib.mds_interpolate_host(p, 1, 1000, 8, np_, 100, 3, 0, ctypes.byref(o), p, p, None) == 1
+    assert lib.mds_interpolate_host(p, 1, 1000, 8, gp, 100, 3, -5, ctypes.byref(o), p, p, None) == 1
+    assert lib.mds_interpolate_host(p, 1, 1000, 8, gp, 100, 100, 0, ctypes.byref(o), p, p, None) == 1
+    # valid arguments, no workspace: reported before anything touches the data
+    assert lib.mds_interpolate_host(p, 1, 1000, 8, gp, 100, 3, 0, ctypes.byref(o), p, p, None) == 8
+    # the host variant's workspace holds a device copy of Y and X on top
+    dev = lib.mds_interpolate_workspace_size(10_000, 100, 500, 10, 2)
+    host = lib.mds_interpolate_host_workspace_size(10_000, 100, 500, 10, 2, 1)
+    assert host >= dev + 10_000 * 100 * 4 + 10_000 * 10 * 4
+    assert lib.mds_interpolate_host_workspace_size(10_000, 100, 500, 10, 2, 9) == 0
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     import paper_2007_11919_gb300.mds as M
     monkeypatch.setattr(M, "_L", None)
