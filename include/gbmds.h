@@ -69,7 +69,8 @@ typedef struct {
     int32_t prec;            /* mds_precision */
     int32_t max_steps;       /* Lanczos step cap per eigenproblem; 0 = 256 */
     double eig_tol;          /* stop when every wanted Ritz residual
-                                <= eig_tol * lambda_1; 0 = 1e-10 */
+                                <= eig_tol * lambda_1; 0 = 1e-10 for
+                                MDS_PREC_F64 / F32, 1e-8 for BF16 / FP8 */
     double rank_tol;         /* MDS_ERR_RANK unless lambda_r > rank_tol * lambda_1;
                                 0 = 1e-12 */
     void* stream;            /* cudaStream_t; NULL = the legacy default stream */
@@ -127,7 +128,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
  * float, or double for MDS_PREC_F64) and var (r) are HOST pointers; the
  * caller keeps them alive until the call returns.  The landmark rows are
  * gathered on the host and their eigenproblem starts at once; meanwhile the
- * rows are copied in chunks of chunk_rows (0 = 65,536) on a second stream,
+ * rows are copied in chunks of chunk_rows (0 = about 96 MiB of rows) on a second stream,
  * each chunk is turned into the projection operands as it lands, projected
  * once the model is ready, and its rows of X are copied back on a third
  * stream.  Y and X should be page-locked (pinned) for the copies to overlap
