@@ -10,7 +10,7 @@ batched Lanczos eigen-solve, Procrustes alignment and the aligned scatter).
 Metric: points embedded per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dc|interp|serve]
+                    [--workload dc|interp|interp_f32|image|image_dc|serve]
 
 Every line also carries a short serving leg ("serve"): three resident BF16
 models (l, r) = (500, 2), (1000, 5), (2000, 10) over d=100 Gaussian data,
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["dc", "interp", "image", "image_dc", "serve"], default="dc")
+    ap.add_argument("--workload", choices=["dc", "interp", "interp_f32", "image", "image_dc", "serve"], default="dc")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-parts", type=int, default=4, help="parts in the bounded oracle sample")
@@ -226,7 +226,8 @@ def oracle_interp_sample(Y, idx, r, m):
 # ---------------------------------------------------------------- workloads
 
 
-WORKLOADS = {"dc": W.DC_F32, "interp": W.INTERP_BF16, "image": W.IMAGE_FP8, "image_dc": W.IMAGE_DC}
+WORKLOADS = {"dc": W.DC_F32, "interp": W.INTERP_BF16, "interp_f32": W.INTERP_F32, "image": W.IMAGE_FP8,
+             "image_dc": W.IMAGE_DC}
 
 
 def is_dc(name):
@@ -459,6 +460,15 @@ def ours(args):
             pk *= 2.0
             src_note += " x 2 (nominal FP8 / BF16 ratio)"
         byte_rows = Y.dtype == np.uint8
+        if w.prec in ("f32", "f64"):
+            # SIMT distance tiles and projection on the FP32 pipe: peak from the
+            # unit counts, 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+            pk = 152 * 128 * 2 * 2.07e9 / 1e12
+            achieved = flops / (kms * 1e-3) / 1e12
+            return {"kernel": "k_gower (SIMT distance tiles fused with the Gower projection)", "bound": "alu",
+                    "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.07 GHz", "launch_ms": kms,
+                    "flops_per_launch": flops, "traffic": None}
         kname = ("k_gower_tck (tcgen05 distance tiles of byte rows, K streamed, fused with the Gower projection)"
                  if byte_rows else "k_gower_tc (tcgen05 distance tiles and Gower projection, A^2 kept in TMEM)")
         achieved = flops / (kms * 1e-3) / 1e12

@@ -921,7 +921,9 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             if (prev_worst > 0.0 && worst > 0.0 && worst < prev_worst) {
                 const double rate = (log(prev_worst) - log(worst)) / (double)(k - prev_k);
                 const double need = (log(worst) - log(A.tol)) / rate;
-                gap = (int)fmin(16.0, fmax(2.0, ceil(need) + 1.0));
+                // one problem on the whole GPU: a check costs ~3 steps, so trust
+                // the extrapolation further; batched parts overshoot costlier
+                gap = (int)fmin(A.p == 1 ? 32.0 : 16.0, fmax(2.0, ceil(need) + 1.0));
             } else if (worst < 1e-6) {
                 gap = 4;
             }

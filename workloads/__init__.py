@@ -215,6 +215,11 @@ DC_F32 = Workload("dc_f32_n100000_d100_parts800-1200_c20_r10", "dc", 100_000, 10
                   c=20, own_lo=800, own_hi=1200)
 INTERP_BF16 = Workload("interp_bf16_n1000000_d100_l1000_r10", "interp", 1_000_000, 100, 10, "bf16",
                        l=1000)
+# The same interpolation problem on the plain FP32 path (SIMT distance tiles
+# and projection, one problem): the baseline the mixed-precision forms are
+# compared against.
+INTERP_F32 = Workload("interp_f32_n1000000_d100_l1000_r10", "interp", 1_000_000, 100, 10, "f32",
+                      l=1000)
 SERVE_BF16 = Workload("serve_bf16_d100_l500r2_l1000r5_l2000r10_req1-50000", "serve", 200_000, 100, 10,
                       "bf16", l=2000)
 # Resident models of the serving workload: (landmarks, r).
@@ -235,7 +240,7 @@ def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
         return gaussian_dominant(n, w.d, 3, seed, dtype=np.float64)
     if w.name == DC_F32.name:
         return gaussian_dominant(n, w.d, 5, seed, dtype=np.float32)
-    if w.name == INTERP_BF16.name:
+    if w.name in (INTERP_BF16.name, INTERP_F32.name):
         return gaussian_mixture(n, w.d, 4, 5.0, seed, dtype=np.float32)
     if w.name == SERVE_BF16.name:
         return gaussian_graded(n, w.d, seed)
