@@ -54,7 +54,6 @@ namespace gbmds {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxCluster = 16;    // largest cluster the launcher forms
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 4;           // stage barriers per warp (stages in use: as many as fit)
 constexpr int kChunkB = 4096;      // longest row segment of Q
@@ -74,6 +73,8 @@ struct Smem {
     double* part1;   // mmax + 2
     double* cfull;   // mmax + 2 : reduced coefficients
     double* cdf;     // mmax + 2 : the same as double-FP32 pairs
+    double* ecf;     // mmax + 2 : coefficients of the combined update (FP64)
+    double* edf;     // mmax + 2 : the same as double-FP32 pairs
     double* alpha;   // mmax + 1
     double* beta;    // mmax + 1
     double* beta2;   // mmax + 1
@@ -97,7 +98,7 @@ __host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
 __host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r, bool team = false) {
     const size_t rmax = (size_t)((max_n + cs - 1) / cs);
     return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 4, 4) + 2 * round_up(rmax, 2) +
-           4 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8 +
+           6 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8 +
            (team ? (size_t)kMaxTeam * (mmax + 2) : 0);
 }
 
@@ -121,6 +122,8 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r, bool tea
     s.part1 = p; p += mmax + 2;
     s.cfull = p; p += mmax + 2;
     s.cdf = p; p += mmax + 2;
+    s.ecf = p; p += mmax + 2;
+    s.edf = p; p += mmax + 2;
     s.alpha = p; p += mmax + 1;
     s.beta = p; p += mmax + 1;
     s.beta2 = p; p += mmax + 1;
@@ -388,6 +391,57 @@ __device__ void team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int
         for (int h = 0; h < tm.G; ++h) sum += tmp[h * K + i];
         out[lo + i] = sum;
         if (outdf) reinterpret_cast<float2*>(outdf)[lo + i] = df_of(sum);
+    }
+    __syncthreads();
+}
+
+// The first half of a team reduction whose exchange comes later: partial
+// sums part[lo..hi) of this CTA.  In a cluster alone the ranks read part[]
+// through DSMEM after the next cluster barrier, so nothing moves now; in a
+// team the cluster's sums (in rank order, through DSMEM) go to the team
+// buffer of parity pb.  tmp: shared scratch of hi doubles.
+__device__ void deferred_publish(cg::cluster_group& cl, const Team& tm, int q, int cs, int mmax, int pb,
+                                 double* part, double* tmp, int lo, int hi) {
+    if (tm.G == 1) return;
+    cluster_allreduce(cl, part, tmp, nullptr, lo, hi, cs);
+    double* gp = tm.part + (size_t)pb * tm.G * (mmax + 2);
+    if (q == 0)
+        for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) gp[(size_t)tm.g * (mmax + 2) + i] = tmp[i];
+}
+
+// The second half, after the exchange: out[lo..hi) (and outdf as double-FP32
+// pairs) = the team's sums of the partials published with parity pb, in the
+// same order on every CTA.  tmp: shared scratch of G x (hi - lo) doubles.
+__device__ void deferred_collect(cg::cluster_group& cl, const Team& tm, int cs, int mmax, int pb, double* part,
+                                 double* out, double* outdf, int lo, int hi, double* tmp) {
+    if (tm.G == 1) {
+        for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) {
+            double s = 0.0;
+            for (int q0 = 0; q0 < cs; q0 += 4) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = q0 + u < cs ? cl.map_shared_rank(part, q0 + u)[i] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) s += v[u];
+            }
+            out[i] = s;
+            reinterpret_cast<float2*>(outdf)[i] = df_of(s);
+        }
+        __syncthreads();
+        return;
+    }
+    const int stride = mmax + 2, K = hi - lo;
+    const double* gp = tm.part + (size_t)pb * tm.G * stride;
+    gather_unrolled(tmp, tm.G * K, [&](int e) {
+        const int h = e / K, i = e % K;
+        return __ldcg(gp + (size_t)h * stride + lo + i);
+    });
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += kThreads) {
+        double sum = 0.0;
+        for (int h = 0; h < tm.G; ++h) sum += tmp[h * K + i];
+        out[lo + i] = sum;
+        reinterpret_cast<float2*>(outdf)[lo + i] = df_of(sum);
     }
     __syncthreads();
 }
@@ -747,8 +801,18 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     int k = 0, prev_k = 0;
     bool converged = false, have_vectors = false;
 
-    for (int j = 0; j < kmax; ++j) {
-        // ---- gather v_j from all ranks (8-byte entries, copied as they are)
+    // Step j orthogonalises w = Q u_j against the two newest vectors (one
+    // exchange), giving w_1, and publishes w_1 with its partial dots against
+    // v_0..v_j and ||w_1||^2.  The exchange that opens step j+1 carries both,
+    // so every CTA completes the second pass on its own rows -- w_2 = w_1 -
+    // sum c'_i v_i, beta_j^2 = ||w_1||^2 - ||c'||^2, v_{j+1} = w_2 / beta_j --
+    // with no reduction of its own.  The matvec of step j+1 takes u_{j+1} =
+    // w_1 / beta_j as gathered; it differs from the stored v_{j+1} by
+    // |c'| / beta_j, the rounding-level loss of orthogonality the second pass
+    // removes from the basis.
+    for (int j = 0;; ++j) {
+        // ---- exchange: every rank's published vector and, from step 1 on,
+        // its deferred partial sums
         if (tm.G > 1) {
             team_sync(cl, tm);
             gather_unrolled(S.vfull, n, [&](int i) { return __ldcg(tm.v + i); });
@@ -759,50 +823,65 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 return cl.map_shared_rank(S.vloc, src)[i - src * R];
             });
         }
-        __syncthreads();
-
-        // ---- w = Q v_j on this CTA's rows (streamed); no prefetch into a step
-        // that starts with a predicted check
-        qok = qs_matvec<DF>(Qs, n, r0, S.vfull, S.wloc, j + 1 < next_check && j + 1 < kmax) && qok;
-        __syncthreads();
-
-        // ---- local pass against v_{j-1}, v_j, then a full pass against
-        // v_0..v_j that also reduces ||w_1||^2 (||w_2||^2 = ||w_1||^2 - ||c_2||^2)
-        const int ia = j > 0 ? j - 1 : 0;
-        cgs_dots<DF>(B, ldq, r0, nr, ia, j, S.wloc, part[pb], false);
-        __syncthreads();
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1, S.ttmp);
-        pb ^= 1;
-        const double a1 = S.cfull[j];
-        cgs_update<DF>(B, ldq, r0, nr, ia, j, S.cfull, S.cdf, S.wloc);
-        __syncthreads();
-        cgs_dots<DF>(B, ldq, r0, nr, 0, j, S.wloc, part[pb], true);
-        __syncthreads();
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, 0, j + 2, S.ttmp);
-        pb ^= 1;
-        cgs_update<DF>(B, ldq, r0, nr, 0, j, S.cfull, S.cdf, S.wloc);
-        if (warp == 0) {
-            double c2 = 0.0;
-            for (int i = lane; i <= j; i += 32) c2 = fma(S.cfull[i], S.cfull[i], c2);
-            c2 = warp_sum(c2);
-            if (lane == 0) {
-                const double alpha_j = a1 + S.cfull[j];
-                const double beta_j = sqrt(fmax(S.cfull[j + 1] - c2, 0.0));
-                const double tnorm = fmax(S.red[40], fabs(alpha_j) + 2.0 * beta_j);
-                S.alpha[j] = alpha_j;
-                S.beta[j] = beta_j;
-                S.beta2[j] = beta_j * beta_j;
-                S.red[40] = tnorm;
-                S.red[41] = (beta_j <= 1e-12 * tnorm || j + 1 == n) ? 1.0 : 0.0;
-                S.red[42] = beta_j > 0.0 ? 1.0 / beta_j : 0.0;
+        if (j > 0) {
+            deferred_collect(cl, tm, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, 0, j + 1, S.ttmp);
+            pb ^= 1;
+            // alpha_{j-1} and beta_{j-1} from the second pass
+            if (warp == 0) {
+                double c2 = 0.0;
+                for (int i = lane; i < j; i += 32) c2 = fma(S.cfull[i], S.cfull[i], c2);
+                c2 = warp_sum(c2);
+                if (lane == 0) {
+                    const double alpha = S.alpha[j - 1] + S.cfull[j - 1];
+                    const double beta = sqrt(fmax(S.cfull[j] - c2, 0.0));
+                    const double tn = fmax(S.red[40], fabs(alpha) + 2.0 * beta);
+                    S.alpha[j - 1] = alpha;
+                    S.beta[j - 1] = beta;
+                    S.beta2[j - 1] = beta * beta;
+                    S.red[40] = tn;
+                    S.red[41] = (beta <= 1e-12 * tn || j == n) ? 1.0 : 0.0;
+                    S.red[42] = beta > 0.0 ? 1.0 / beta : 0.0;
+                    S.red[47] = S.cfull[j - 1];   // d_{j-1}: see alpha_j below
+                }
+            }
+            // the second pass on this CTA's rows: w_2 (in wloc) ...
+            cgs_update<DF>(B, ldq, r0, nr, 0, j - 1, S.cfull, S.cdf, S.wloc);
+            __syncthreads();
+            // ... and what Q (u_j - v_j) = sum_i d_i Q v_i / beta_{j-1} adds to the
+            // next matvec along v_m, from the three-term relation
+            // Q v_i = beta_{i-1} v_{i-1} + alpha_i v_i + beta_i v_{i+1}:
+            // e_m = (d_{m+1} beta_m + d_m alpha_m + d_{m-1} beta_{m-1}) / beta_{j-1}.
+            // The update after the next matvec removes it (m <= j-2; the pass
+            // against v_{j-1}, v_j measures its own coefficients), so that the
+            // one-pass completion never sees components that grow step to step.
+            for (int m = tid; m <= j - 2; m += kThreads) {
+                double t = S.cfull[m] * S.alpha[m] + S.cfull[m + 1] * S.beta[m];
+                if (m >= 1) t += S.cfull[m - 1] * S.beta[m - 1];
+                t *= S.red[42];
+                S.ecf[m] = t;
+                reinterpret_cast<float2*>(S.edf)[m] = df_of(t);
+            }
+            // ... v_j = w_2 / beta_{j-1} into the basis, and u_j = w_1 / beta_{j-1}
+            // (the gathered vector) for the matvec
+            if constexpr (DF) {
+                const float2 binv = df_of(S.red[42]);
+                for (int rr = tid; rr < nr; rr += kThreads)
+                    reinterpret_cast<float2*>(B)[(int64_t)j * ldq + r0 + rr] =
+                        df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
+                for (int i = tid; i < n; i += kThreads)
+                    reinterpret_cast<float2*>(S.vfull)[i] = df_mul(reinterpret_cast<const float2*>(S.vfull)[i], binv);
+            } else {
+                const double binv = S.red[42];
+                for (int rr = tid; rr < nr; rr += kThreads) B[(int64_t)j * ldq + r0 + rr] = S.wloc[rr] * binv;
+                for (int i = tid; i < n; i += kThreads) S.vfull[i] *= binv;
             }
         }
         __syncthreads();
-        const double beta_j = S.beta[j];
+        k = j;
+        const double beta_j = j > 0 ? S.beta[j - 1] : 0.0;   // beta_{k-1}: the residual coefficient
         const double tnorm = S.red[40];
-        k = j + 1;
-        const bool breakdown = S.red[41] != 0.0;
-        const bool do_check = breakdown || k == kmax || k >= next_check;
+        const bool breakdown = j > 0 && S.red[41] != 0.0;
+        const bool do_check = j > 0 && (breakdown || k == kmax || k >= next_check);
         if (do_check && k >= r) {
             // the stage rings hold the check's workspace from here on
             qok = qs_drain(Qs) && qok;
@@ -932,27 +1011,44 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             next_check = k + gap;
             if (!breakdown) qs_prime(Qs);   // the stages are Q stages again
         }
-        if (breakdown) break;  // k < r: fewer Ritz values than wanted
+        if (breakdown || k == kmax) break;  // breakdown with k < r: fewer Ritz values than wanted
 
-        // ---- v_{j+1} = w / beta_j
-        if constexpr (DF) {
-            const float2 binv = df_of(S.red[42]);
-            for (int rr = tid; rr < nr; rr += kThreads) {
-                const float2 v = df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
-                reinterpret_cast<float2*>(S.vloc)[rr] = v;
-                reinterpret_cast<float2*>(B)[(int64_t)(j + 1) * ldq + r0 + rr] = v;
-                if (tm.G > 1) reinterpret_cast<float2*>(tm.v)[r0 + rr] = v;
+        // ---- w = Q u_j on this CTA's rows (streamed); no prefetch into a step
+        // that starts with a predicted check
+        qok = qs_matvec<DF>(Qs, n, r0, S.vfull, S.wloc, j + 1 < next_check && j + 1 < kmax) && qok;
+        __syncthreads();
+
+        // ---- pass against v_{j-1}, v_j: w_1 = w - c_{j-1} v_{j-1} - c_j v_j
+        const int ia = j > 0 ? j - 1 : 0;
+        cgs_dots<DF>(B, ldq, r0, nr, ia, j, S.wloc, part[pb], false);
+        __syncthreads();
+        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1, S.ttmp);
+        pb ^= 1;
+        // alpha_j = v_j . Q v_j; the matvec saw u_j = v_j + sum_i d_i v_i / beta_{j-1},
+        // whose extra part adds e_j = v_j . Q v_{j-1} d_{j-1} / beta_{j-1} = d_{j-1}
+        // to c_j; the second pass of this step adds its own coefficient later
+        if (tid == 0) S.alpha[j] = S.cfull[j] - (j > 0 ? S.red[47] : 0.0);
+        if (j >= 2) {
+            // one update with e_0..e_{j-2} and the measured c_{j-1}, c_j
+            if (tid < 2) {
+                S.ecf[j - 1 + tid] = S.cfull[j - 1 + tid];
+                S.edf[j - 1 + tid] = S.cdf[j - 1 + tid];
             }
+            __syncthreads();
+            cgs_update<DF>(B, ldq, r0, nr, 0, j, S.ecf, S.edf, S.wloc);
         } else {
-            const double binv = S.red[42];
-            for (int rr = tid; rr < nr; rr += kThreads) {
-                const double v = S.wloc[rr] * binv;
-                S.vloc[rr] = v;
-                B[(int64_t)(j + 1) * ldq + r0 + rr] = v;
-                if (tm.G > 1) tm.v[r0 + rr] = v;
-            }
+            cgs_update<DF>(B, ldq, r0, nr, ia, j, S.cfull, S.cdf, S.wloc);
         }
         __syncthreads();
+
+        // ---- publish w_1 and its partial dots against v_0..v_j with ||w_1||^2
+        cgs_dots<DF>(B, ldq, r0, nr, 0, j, S.wloc, part[pb], true);
+        __syncthreads();
+        deferred_publish(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, 0, j + 2);
+        for (int rr = tid; rr < nr; rr += kThreads) {
+            S.vloc[rr] = S.wloc[rr];
+            if (tm.G > 1) tm.v[r0 + rr] = S.wloc[rr];
+        }
     }
 
     // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
