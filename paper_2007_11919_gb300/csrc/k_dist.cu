@@ -40,11 +40,14 @@ __global__ void __launch_bounds__(256) k_rownorm(const T* __restrict__ Y, int64_
 
 // ------------------------------------------------------- distance tiles
 // One CTA = one 64 x 64 tile (rows a0.., columns b0..) of Delta_j for problem
-// blockIdx.y.  256 threads, 4 x 4 outputs each; K staged through shared memory
-// 16 at a time.  Writes Delta as FP64 (row-major, ld = ldq) or, accumulating
-// in FP32, as FP32 at the start of each row's storage (row stride 2 * ldq
-// floats), and the tile's row sums into rp[tb * n + a] (summed later in a
-// fixed order).
+// blockIdx.y, on or above the diagonal (tb >= ta): Delta is symmetric, so a
+// tile off the diagonal is written twice, as itself and as its transpose, from
+// the same values.  256 threads, 4 x 4 outputs each; K staged through shared
+// memory 16 at a time.  Writes Delta as FP64 (row-major, ld = ldq) or,
+// accumulating in FP32, as FP32 at the start of each row's storage (row stride
+// 2 * ldq floats), and each tile's row sums into rp[tb * n + a] (the mirrored
+// tile's into rp[ta * n + b], from the tile's column sums; all summed later in
+// a fixed order).
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
@@ -59,12 +62,20 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
     __shared__ __align__(16) A As[KC][LD];
     __shared__ __align__(16) A Bs[KC][LD];
     __shared__ int64_t rowA[kTile], rowB[kTile];
+    // column sums of the tile by row group: [ty][column] (double-FP32 pairs as
+    // float2 for FP32 accumulation)
+    __shared__ __align__(16) double csum[16][kTile];
 
     const ProbDesc P = desc[blockIdx.y];
     const int n = P.n;
-    const int t = blockIdx.x;
-    if (t >= P.tiles * P.tiles) return;
-    const int ta = t / P.tiles, tb = t % P.tiles;
+    int t = blockIdx.x;
+    if (t >= P.tiles * (P.tiles + 1) / 2) return;
+    int ta = 0;
+    while (t >= P.tiles - ta) {   // t -> (ta, tb), tb >= ta, row-major over the upper triangle
+        t -= P.tiles - ta;
+        ++ta;
+    }
+    const int tb = ta + t;
     const int a0 = ta * kTile, b0 = tb * kTile;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -163,6 +174,61 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
                 df_add(rh, rl, oh, ol);
             }
             if (tx == 0 && a < n) rp[(int64_t)tb * n + a] = (double)rh + (double)rl;
+        }
+    }
+    if (ta == tb) return;
+
+    // ---- the mirrored tile: Delta[b][a] = Delta[a][b], and the row sums of
+    // rows b over this tile's columns a (the tile's column sums: each thread's
+    // four rows, then the sixteen row groups in order)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        const int b = b0 + tx * 4 + jj;
+        if constexpr (sizeof(A) == 8) {
+            double cs = 0.0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int a = a0 + ty * 4 + i;
+                if (a < n && b < n) {
+                    A dist = (A)nrm[rowA[ty * 4 + i]] + nb[jj] - A(2) * acc[i][jj];
+                    dist = dist > A(0) ? dist : A(0);
+                    Q[(int64_t)b * P.ldq + a] = dist;
+                    cs += dist;
+                }
+            }
+            csum[ty][tx * 4 + jj] = cs;
+        } else {
+            float* Qf = reinterpret_cast<float*>(Q);
+            float ch = 0.f, cl = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int a = a0 + ty * 4 + i;
+                if (a < n && b < n) {
+                    float dist = (float)nrm[rowA[ty * 4 + i]] + nb[jj] - 2.f * acc[i][jj];
+                    dist = dist > 0.f ? dist : 0.f;
+                    Qf[(int64_t)b * 2 * P.ldq + a] = dist;
+                    df_add(ch, cl, dist, 0.f);
+                }
+            }
+            reinterpret_cast<float2*>(&csum[ty][0])[tx * 4 + jj] = make_float2(ch, cl);
+        }
+    }
+    __syncthreads();
+    if (tid < kTile) {
+        const int b = b0 + tid;
+        if (b < n) {
+            if constexpr (sizeof(A) == 8) {
+                double s = 0.0;
+                for (int g = 0; g < 16; ++g) s += csum[g][tid];
+                rp[(int64_t)ta * n + b] = s;
+            } else {
+                float sh = 0.f, sl = 0.f;
+                for (int g = 0; g < 16; ++g) {
+                    const float2 c = reinterpret_cast<const float2*>(&csum[g][0])[tid];
+                    df_add(sh, sl, c.x, c.y);
+                }
+                rp[(int64_t)ta * n + b] = (double)sh + (double)sl;
+            }
         }
     }
 }
@@ -389,7 +455,7 @@ cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nr
                                   const ProbDesc* desc, int p, int max_tiles, int acc_f64,
                                   double* qarena, double* rparena, cudaStream_t st) {
     if (p <= 0) return cudaSuccess;
-    dim3 grid((unsigned)(max_tiles * max_tiles), (unsigned)p), block(256);
+    dim3 grid((unsigned)(max_tiles * (max_tiles + 1) / 2), (unsigned)p), block(256);
     if (acc_f64) {
         if (dt == MDS_IN_F64)
             k_sqdist<double, double><<<grid, block, 0, st>>>((const double*)Y, d, nrm, anchors, own, desc, qarena, rparena);
