@@ -576,7 +576,12 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
     bool ok = true;
     s.issue_left = s.per_step - s.inflight + (prefetch ? min(s.nst, s.per_step) : 0);
     qs_fill(s);
-    // two accumulators per lane (alternate entries) for instruction-level parallelism
+    // FP32 Q: each lane keeps four FMA chains, q * v_hi and q * v_lo for
+    // alternate entries (~16 entries per chain and row); the chains meet in
+    // double-FP32 at the end of the row.  Rounding the chains' sums to FP32
+    // moves the Ritz values by ~1e-9 relative in a replay of the D&C problem
+    // (the FP32 storage of Q itself moves them more), and a step costs 2 FMAs
+    // per entry instead of a double-FP32 product and sum.
     float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
     double acc = 0.0;
     for (int u = 0; u < s.per_step; ++u) {
@@ -592,10 +597,14 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
                 const float4 x = reinterpret_cast<const float4*>(stage)[t];
                 const float4 va = reinterpret_cast<const float4*>(vfull)[(col0 >> 1) + 2 * t];
                 const float4 vb = reinterpret_cast<const float4*>(vfull)[(col0 >> 1) + 2 * t + 1];
-                df_madd1(sh, sl, x.x, va.x, va.y);
-                df_madd1(th, tl, x.y, va.z, va.w);
-                df_madd1(sh, sl, x.z, vb.x, vb.y);
-                df_madd1(th, tl, x.w, vb.z, vb.w);
+                sh = fmaf(x.x, va.x, sh);
+                sl = fmaf(x.x, va.y, sl);
+                th = fmaf(x.y, va.z, th);
+                tl = fmaf(x.y, va.w, tl);
+                sh = fmaf(x.z, vb.x, sh);
+                sl = fmaf(x.z, vb.y, sl);
+                th = fmaf(x.w, vb.z, th);
+                tl = fmaf(x.w, vb.w, tl);
             }
         } else {
             const int col0 = seg * (s.segb / 8);
@@ -612,9 +621,12 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
         qs_fill(s);   // the stage is free: next chunk of the periodic stream
         if (seg == s.nseg - 1) {
             if constexpr (DF) {
-                df_add(sh, sl, th, tl);
-                df_warp_sum(sh, sl);
-                if (lane == 0) reinterpret_cast<float2*>(w)[row - r0] = df_norm(sh, sl);
+                float h = sh, l = 0.f;
+                df_add(h, l, th, 0.f);
+                df_add(h, l, sl, 0.f);
+                df_add(h, l, tl, 0.f);
+                df_warp_sum(h, l);
+                if (lane == 0) reinterpret_cast<float2*>(w)[row - r0] = df_norm(h, l);
                 sh = sl = th = tl = 0.f;
             } else {
                 acc = warp_sum(acc);
