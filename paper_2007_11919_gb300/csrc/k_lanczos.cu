@@ -661,19 +661,24 @@ __device__ void cgs_dots(const double* B, int ldq, int r0, int nr, int ia, int i
             df_warp_sum(sh, sl);
             if (lane == 0) part[ib + 1] = (double)sh + (double)sl;
         }
+        // FP32 basis: per lane FMA chains b * w_hi and b * w_lo, met in double-FP32
         for (int i = ia + warp; i <= ib; i += 2 * kWarps) {
             const int i2 = i + kWarps;
             const bool two = i2 <= ib;
-            const float2* b1 = reinterpret_cast<const float2*>(B) + (int64_t)i * ldq + r0;
-            const float2* b2 = reinterpret_cast<const float2*>(B) + (int64_t)(two ? i2 : i) * ldq + r0;
-            float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+            const float* b1 = reinterpret_cast<const float*>(B) + (int64_t)i * ldq + r0;
+            const float* b2 = reinterpret_cast<const float*>(B) + (int64_t)(two ? i2 : i) * ldq + r0;
+            float c1h = 0.f, c1l = 0.f, c2h = 0.f, c2l = 0.f;
             for (int rr = lane; rr < nr; rr += 32) {
                 const float2 x = w2[rr];
-                const float2 a1 = b1[rr];
-                const float2 a2 = b2[rr];
-                df_madd(h1, l1, a1.x, a1.y, x.x, x.y);
-                df_madd(h2, l2, a2.x, a2.y, x.x, x.y);
+                const float a1 = b1[rr], a2 = b2[rr];
+                c1h = fmaf(a1, x.x, c1h);
+                c1l = fmaf(a1, x.y, c1l);
+                c2h = fmaf(a2, x.x, c2h);
+                c2l = fmaf(a2, x.y, c2l);
             }
+            float h1 = c1h, l1 = 0.f, h2 = c2h, l2 = 0.f;
+            df_add(h1, l1, c1l, 0.f);
+            df_add(h2, l2, c2l, 0.f);
             df_warp_sum(h1, l1);
             df_warp_sum(h2, l2);
             if (lane == 0) {
@@ -712,19 +717,19 @@ __device__ void cgs_update(const double* B, int ldq, int r0, int nr, int ia, int
         const float2* c2 = reinterpret_cast<const float2*>(cd);
         float2* w2 = reinterpret_cast<float2*>(w);
         for (int rr = threadIdx.x; rr < nr; rr += kThreads) {
-            const float2* b = reinterpret_cast<const float2*>(B) + r0 + rr;
+            const float* b = reinterpret_cast<const float*>(B) + r0 + rr;   // FP32 basis
             float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             int i = ia;
             for (; i + 1 <= ib; i += 2) {
-                const float2 x0 = b[(int64_t)i * ldq], x1 = b[(int64_t)(i + 1) * ldq];
+                const float x0 = b[(int64_t)i * ldq], x1 = b[(int64_t)(i + 1) * ldq];
                 const float2 k0 = c2[i], k1 = c2[i + 1];
-                df_madd(h0, l0, x0.x, x0.y, k0.x, k0.y);
-                df_madd(h1, l1, x1.x, x1.y, k1.x, k1.y);
+                df_madd1(h0, l0, x0, k0.x, k0.y);
+                df_madd1(h1, l1, x1, k1.x, k1.y);
             }
             if (i <= ib) {
-                const float2 x0 = b[(int64_t)i * ldq];
+                const float x0 = b[(int64_t)i * ldq];
                 const float2 k0 = c2[i];
-                df_madd(h0, l0, x0.x, x0.y, k0.x, k0.y);
+                df_madd1(h0, l0, x0, k0.x, k0.y);
             }
             df_add(h0, l0, h1, l1);
             const float2 wv = w2[rr];
@@ -792,9 +797,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         for (int i = tid; i < nr; i += kThreads) {
             const double v = S.wloc[i] * inv;
             if constexpr (DF) {
-                const float2 d = df_of(v);
-                reinterpret_cast<float2*>(S.vloc)[i] = d;
-                reinterpret_cast<float2*>(B)[r0 + i] = d;
+                // the basis holds FP32; the gathered v_0 is that same value
+                const float f = (float)v;
+                reinterpret_cast<float2*>(S.vloc)[i] = make_float2(f, 0.f);
+                reinterpret_cast<float*>(B)[r0 + i] = f;
             } else {
                 S.vloc[i] = v;
                 B[r0 + i] = v;
@@ -877,9 +883,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             // (the gathered vector) for the matvec
             if constexpr (DF) {
                 const float2 binv = df_of(S.red[42]);
-                for (int rr = tid; rr < nr; rr += kThreads)
-                    reinterpret_cast<float2*>(B)[(int64_t)j * ldq + r0 + rr] =
-                        df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
+                for (int rr = tid; rr < nr; rr += kThreads) {
+                    const float2 v = df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
+                    reinterpret_cast<float*>(B)[(int64_t)j * ldq + r0 + rr] = __fadd_rn(v.x, v.y);
+                }
                 for (int i = tid; i < n; i += kThreads)
                     reinterpret_cast<float2*>(S.vfull)[i] = df_mul(reinterpret_cast<const float2*>(S.vfull)[i], binv);
             } else {
@@ -1184,18 +1191,18 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     double* V = A.varena + P.v_off;
     for (int rr = tid; rr < nr; rr += kThreads) {
         if constexpr (DF) {
-            const float2* b = reinterpret_cast<const float2*>(B) + r0 + rr;
+            const float* b = reinterpret_cast<const float*>(B) + r0 + rr;   // FP32 basis
             for (int ig = 0; ig < r; ig += 8) {
                 float h[8], l[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) h[u] = l[u] = 0.f;
                 for (int t = 0; t < k; ++t) {
-                    const float2 x = b[(int64_t)t * ldq];
+                    const float x = b[(int64_t)t * ldq];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         if (ig + u < r) {
                             const float2 sv = reinterpret_cast<const float2*>(S.xv + (size_t)(ig + u) * L)[t];
-                            df_madd(h[u], l[u], x.x, x.y, sv.x, sv.y);
+                            df_madd1(h[u], l[u], x, sv.x, sv.y);
                         }
                     }
                 }
