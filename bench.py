@@ -555,7 +555,7 @@ def ours(args):
                          "parts": (part.p if is_dc(args.workload) else None),
                          "c": (w.c if is_dc(args.workload) else None),
                          "l": (w.l if not is_dc(args.workload) else None),
-                         "eigensolve": "Lanczos (FP64 scalars, double-FP32 vectors)", "cluster": stats[-1]["cluster"],
+                         "eigensolve": "Lanczos (FP64 scalars, double-FP32 working vectors, FP32 basis)", "cluster": stats[-1]["cluster"],
                          "plan": (dict(plan.info(), graph=True, autotuned=args.cluster == 0)
                                   if is_dc(args.workload) else None),
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},

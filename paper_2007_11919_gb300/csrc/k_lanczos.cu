@@ -8,7 +8,8 @@
 //   Krylov basis v_0, v_1, ... of Q from a fixed pseudo-random start vector;
 //   w = Q v_j, a local Gram-Schmidt pass against v_{j-1} and v_j (the
 //   three-term recurrence, with computed coefficients) and a full classical
-//   Gram-Schmidt pass against v_0..v_j; alpha_j = v_j . Q v_j, beta_j = ||w||,
+//   Gram-Schmidt pass against v_0..v_j, completed after the next step's
+//   exchange (see the step loop); alpha_j = v_j . Q v_j, beta_j = ||w||,
 //   v_{j+1} = w / beta_j.  The Rayleigh quotient T_k = V_k^T Q V_k is the
 //   tridiagonal of the alphas and betas.  Every few steps the r largest
 //   eigenvalues theta_i of T_k are found by Sturm-count multisection and their
@@ -21,11 +22,12 @@
 //
 // Arithmetic: the scalars (alpha, beta, Gram-Schmidt coefficients) and the
 // tridiagonal work are FP64.  For FP64 problems Q and every vector are FP64.
-// Otherwise Q (double-centred in FP64 from FP32 distances) is stored in FP32
-// and the products and all O(n k) vector work run in double-FP32 (a value is
-// an unevaluated pair of floats, ~48 significant bits), because GB300 issues
-// FP64 at 1/64 of its FP32 rate; the basis and working vectors take 8 bytes
-// per entry either way.
+// Otherwise Q (double-centred in FP64 from FP32 distances) is stored in FP32,
+// the basis vectors in FP32 and the working vectors in double-FP32 (a value
+// is an unevaluated pair of floats, ~48 significant bits), because GB300
+// issues FP64 at 1/64 of its FP32 rate; the matvec and the Gram-Schmidt dots
+// run as FP32 FMA chains that meet in double-FP32, the updates in
+// double-FP32.
 //
 // Layout: Q_j row-major (ld = ldq).  The cluster's CTAs own contiguous row
 // slices; each CTA's slice of the current Lanczos vector lives in its shared
