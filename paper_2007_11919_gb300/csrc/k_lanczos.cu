@@ -176,14 +176,14 @@ __device__ void cluster_allreduce(cg::cluster_group& cl, double* part, double* o
 // put(i, get(i)) for 0 <= i < n, kUnroll independent loads in flight per
 // thread before their stores.
 constexpr int kUnroll = 4;
-template <class G, class P>
+template <class G, class P, class T = double>
 __device__ __forceinline__ void copy_unrolled(int n, G get, P put) {
     for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kThreads) {
-        double t[kUnroll];
+        T t[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int i = i0 + u * kThreads;
-            t[u] = i < n ? get(i) : 0.0;
+            t[u] = i < n ? get(i) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
@@ -193,9 +193,21 @@ __device__ __forceinline__ void copy_unrolled(int n, G get, P put) {
     }
 }
 
-template <class G>
-__device__ __forceinline__ void gather_unrolled(double* dst, int n, G get) {
-    copy_unrolled(n, get, [&](int i, double v) { dst[i] = v; });
+template <class T, class G>
+__device__ __forceinline__ void gather_unrolled(T* dst, int n, G get) {
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kThreads) {
+        T t[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            t[u] = i < n ? get(i) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i < n) dst[i] = t[u];
+        }
+    }
 }
 
 // ------------------------------------------------- tridiagonal eigen-work
@@ -578,12 +590,11 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
     bool ok = true;
     s.issue_left = s.per_step - s.inflight + (prefetch ? min(s.nst, s.per_step) : 0);
     qs_fill(s);
-    // FP32 Q: each lane keeps four FMA chains, q * v_hi and q * v_lo for
-    // alternate entries (~16 entries per chain and row); the chains meet in
-    // double-FP32 at the end of the row.  Rounding the chains' sums to FP32
-    // moves the Ritz values by ~1e-9 relative in a replay of the D&C problem
-    // (the FP32 storage of Q itself moves them more), and a step costs 2 FMAs
-    // per entry instead of a double-FP32 product and sum.
+    // FP32 Q and FP32 v: each lane keeps four FMA chains (one per entry of a
+    // float4, ~8 entries per chain and row) that meet in double-FP32 at the
+    // end of the row.  Rounding v and the chains' sums to FP32 moves the Ritz
+    // values by ~1e-9 relative in a replay of the D&C problem (the FP32
+    // storage of Q itself moves them more), for one FMA per entry.
     float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
     double acc = 0.0;
     for (int u = 0; u < s.per_step; ++u) {
@@ -595,18 +606,14 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
             // FP32 Q: 4 entries per 16 bytes; the row's padding entries are zero
             // and so are the vector's guard entries
             const int col0 = seg * (s.segb / 4);
+            const float4* v4 = reinterpret_cast<const float4*>(vfull) + (col0 >> 2);
             for (int t = lane; t < bytes / 16; t += 32) {
                 const float4 x = reinterpret_cast<const float4*>(stage)[t];
-                const float4 va = reinterpret_cast<const float4*>(vfull)[(col0 >> 1) + 2 * t];
-                const float4 vb = reinterpret_cast<const float4*>(vfull)[(col0 >> 1) + 2 * t + 1];
-                sh = fmaf(x.x, va.x, sh);
-                sl = fmaf(x.x, va.y, sl);
-                th = fmaf(x.y, va.z, th);
-                tl = fmaf(x.y, va.w, tl);
-                sh = fmaf(x.z, vb.x, sh);
-                sl = fmaf(x.z, vb.y, sl);
-                th = fmaf(x.w, vb.z, th);
-                tl = fmaf(x.w, vb.w, tl);
+                const float4 v = v4[t];
+                sh = fmaf(x.x, v.x, sh);
+                sl = fmaf(x.y, v.y, sl);
+                th = fmaf(x.z, v.z, th);
+                tl = fmaf(x.w, v.w, tl);
             }
         } else {
             const int col0 = seg * (s.segb / 8);
@@ -801,17 +808,23 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             if constexpr (DF) {
                 // the basis holds FP32; the gathered v_0 is that same value
                 const float f = (float)v;
-                reinterpret_cast<float2*>(S.vloc)[i] = make_float2(f, 0.f);
+                reinterpret_cast<float*>(S.vloc)[i] = f;   // the published vector is FP32
                 reinterpret_cast<float*>(B)[r0 + i] = f;
             } else {
                 S.vloc[i] = v;
                 B[r0 + i] = v;
             }
-            if (tm.G > 1) tm.v[r0 + i] = S.vloc[i];
+            if (tm.G > 1) {
+                if constexpr (DF) reinterpret_cast<float*>(tm.v)[r0 + i] = reinterpret_cast<const float*>(S.vloc)[i];
+                else tm.v[r0 + i] = S.vloc[i];
+            }
         }
     }
     if (tid == 0) {
-        for (int i = n; i < (int)round_up(n, 4); ++i) S.vfull[i] = 0.0;   // guard entries of the padded loads
+        for (int i = n; i < (int)round_up(n, 4); ++i) {   // guard entries of the padded loads
+            if constexpr (DF) reinterpret_cast<float*>(S.vfull)[i] = 0.f;
+            else S.vfull[i] = 0.0;
+        }
         S.red[40] = 0.0;    // tnorm
     }
 
@@ -835,13 +848,23 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         // its deferred partial sums
         if (tm.G > 1) {
             team_sync(cl, tm);
-            gather_unrolled(S.vfull, n, [&](int i) { return __ldcg(tm.v + i); });
+            if constexpr (DF)
+                gather_unrolled(reinterpret_cast<float*>(S.vfull), n,
+                                [&](int i) { return __ldcg(reinterpret_cast<const float*>(tm.v) + i); });
+            else
+                gather_unrolled(S.vfull, n, [&](int i) { return __ldcg(tm.v + i); });
         } else {
             cl.sync();
-            gather_unrolled(S.vfull, n, [&](int i) {
-                const int src = i / R;
-                return cl.map_shared_rank(S.vloc, src)[i - src * R];
-            });
+            if constexpr (DF)
+                gather_unrolled(reinterpret_cast<float*>(S.vfull), n, [&](int i) {
+                    const int src = i / R;
+                    return reinterpret_cast<const float*>(cl.map_shared_rank(S.vloc, src))[i - src * R];
+                });
+            else
+                gather_unrolled(S.vfull, n, [&](int i) {
+                    const int src = i / R;
+                    return cl.map_shared_rank(S.vloc, src)[i - src * R];
+                });
         }
         if (j > 0) {
             deferred_collect(cl, tm, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, 0, j + 1, S.ttmp);
@@ -889,8 +912,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                     const float2 v = df_mul(reinterpret_cast<const float2*>(S.wloc)[rr], binv);
                     reinterpret_cast<float*>(B)[(int64_t)j * ldq + r0 + rr] = __fadd_rn(v.x, v.y);
                 }
-                for (int i = tid; i < n; i += kThreads)
-                    reinterpret_cast<float2*>(S.vfull)[i] = df_mul(reinterpret_cast<const float2*>(S.vfull)[i], binv);
+                const float bf = __fadd_rn(binv.x, binv.y);
+                for (int i = tid; i < n; i += kThreads) reinterpret_cast<float*>(S.vfull)[i] *= bf;
             } else {
                 const double binv = S.red[42];
                 for (int rr = tid; rr < nr; rr += kThreads) B[(int64_t)j * ldq + r0 + rr] = S.wloc[rr] * binv;
@@ -1067,8 +1090,16 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         __syncthreads();
         deferred_publish(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, 0, j + 2);
         for (int rr = tid; rr < nr; rr += kThreads) {
-            S.vloc[rr] = S.wloc[rr];
-            if (tm.G > 1) tm.v[r0 + rr] = S.wloc[rr];
+            if constexpr (DF) {
+                // the matvec input is published in FP32 (the basis is FP32 too)
+                const float2 w = reinterpret_cast<const float2*>(S.wloc)[rr];
+                const float f = __fadd_rn(w.x, w.y);
+                reinterpret_cast<float*>(S.vloc)[rr] = f;
+                if (tm.G > 1) reinterpret_cast<float*>(tm.v)[r0 + rr] = f;
+            } else {
+                S.vloc[rr] = S.wloc[rr];
+                if (tm.G > 1) tm.v[r0 + rr] = S.wloc[rr];
+            }
         }
     }
 
