@@ -564,7 +564,7 @@ def ours(args):
               "eig_steps_per_call": stats[-1]["eig_steps"],
               "roofline": roof, "roofline_other_kernel": roof_other, "cpu_baseline": cpu,
               "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h)},
+                      "d2h_bytes_per_step": int(d2h), "ms_steps": [round(t, 3) for t in e2e_ms]},
               "gpu_launches": int(sum(s["launches"] for s in stats)),
               "clocks": clk, "gpu": torch.cuda.get_device_name(dev), "note": peaks_note, "serve": serve})
     if world > 1:
