@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of measured capacity")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (for launch lists)")
+    ap.add_argument("--full-matvec", action="store_true",
+                    help="D&C eigen-solver: stream whole rows of Q instead of the symmetric ranges")
     ap.add_argument("--n", type=int, default=0,
                     help="points per GPU (default: the workload's full size; smaller sizes are for profiling)")
     return ap.parse_args()
@@ -381,7 +383,7 @@ def ours(args):
         own = torch.from_numpy(part.own).to(dev)
         # the whole divide-and-conquer call as one autotuned, graph-captured plan
         plan = M.DcPlan(w.n, w.d, Yd.dtype, part.ptr, w.c, w.r, w.prec, tune=args.cluster == 0,
-                        cluster=args.cluster, device=dev)
+                        cluster=args.cluster, device=dev, full_matvec=args.full_matvec)
         Xbuf = torch.zeros((w.n, w.r), dtype=torch.float64 if w.prec == "f64" else torch.float32, device=dev)
         vbuf = torch.empty(w.r, dtype=torch.float64, device=dev)
 
@@ -434,10 +436,11 @@ def ours(args):
     eig_ms = statistics.mean(s["stage_ms"]["eig"] for s in stats)
 
     def lanczos_roof():
-        # The Lanczos steps stream Q (4 bytes per entry for FP32 storage) once
-        # per step through a double-FP32 product on the FP32 pipe.
+        # Algorithmic bytes: all n^2 entries of Q (4 bytes each in FP32
+        # storage) once per Lanczos step, summed over the parts' steps.
         flops = statistics.mean(s["eig_flops"] for s in stats)
         qbytes = statistics.mean(s["eig_qbytes"] for s in stats)
+        qread = statistics.mean(s["eig_qread"] for s in stats)
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = qbytes / (eig_ms * 1e-3) / 1e9
         kind = "batched Lanczos, one cluster per part" if is_dc(args.workload) else \
@@ -446,6 +449,9 @@ def ours(args):
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "launch_ms": eig_ms, "bytes_per_launch": qbytes,
+                # what the kernel streams: the symmetric ranges read each
+                # off-diagonal block of Q once for both triangles
+                "streamed_bytes_per_launch": qread, "streamed_gbs": qread / (eig_ms * 1e-3) / 1e9,
                 "fp64_equiv_flops_per_launch": flops,
                 "fp64_equiv_tflops": flops / (eig_ms * 1e-3) / 1e12, "traffic": None}
         return roof
@@ -555,7 +561,11 @@ def ours(args):
                          "parts": (part.p if is_dc(args.workload) else None),
                          "c": (w.c if is_dc(args.workload) else None),
                          "l": (w.l if not is_dc(args.workload) else None),
-                         "eigensolve": "Lanczos (FP64 scalars, double-FP32 working vectors, FP32 basis)", "cluster": stats[-1]["cluster"],
+                         "eigensolve": "Lanczos (FP64 scalars, double-FP32 working vectors, FP32 basis)",
+                         "matvec": ("whole rows of Q" if args.full_matvec or w.prec == "f64" or not is_dc(args.workload)
+                                    else "symmetric ranges of Q where every CTA's range is at most 1,024 columns"
+                                         " (cluster of 3+ CTAs), else whole rows"),
+                         "cluster": stats[-1]["cluster"],
                          "plan": (dict(plan.info(), graph=True, autotuned=args.cluster == 0)
                                   if is_dc(args.workload) else None),
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},

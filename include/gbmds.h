@@ -77,8 +77,15 @@ typedef struct {
     void* workspace;         /* device scratch (see *_workspace_size) */
     size_t workspace_bytes;
     int32_t cluster;         /* CTAs per eigenproblem (1..16); 0 = automatic */
-    int32_t flags;           /* reserved, must be 0 */
+    int32_t flags;           /* 0 or MDS_FLAG_FULL_MATVEC */
 } mds_opts;
+
+/* Flag of mds_opts.flags.  MDS_FLAG_FULL_MATVEC: the eigen-solver streams
+ * every row of Q whole.  Without it, an FP32 Q solved by one cluster of 3 or
+ * more CTAs is read in symmetric ranges: each off-diagonal block once, used
+ * for both triangles (Q = -1/2 P Delta P is symmetric, Section 2).  The two
+ * forms differ only in rounding. */
+#define MDS_FLAG_FULL_MATVEC 1
 
 /* Opaque device-resident landmark configuration of interpolation MDS: the l
  * landmark rows, their classical-MDS eigenpairs and the Gower projection
@@ -315,6 +322,9 @@ typedef struct {
     double eig_qbytes;
     int32_t problems;      /* eigenproblems in the call */
     int32_t cluster;       /* CTAs per eigenproblem used */
+    double eig_qread;      /* bytes of Q the eigen-solver streamed: eig_qbytes, or
+                              less where it read symmetric ranges (each
+                              off-diagonal block of Q once) */
 } mds_stats;
 
 void mds_set_timing(int on);

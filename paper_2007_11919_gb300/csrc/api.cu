@@ -107,13 +107,14 @@ struct Opts {
     char* ws;
     size_t wsb;
     int cluster;
+    int flags;
 };
 
 int read_opts(const mds_opts* o, Opts* out) {
     if (!o) return MDS_ERR_ARG;
     if (o->prec < MDS_PREC_F64 || o->prec > MDS_PREC_FP8) return MDS_ERR_ARG;
     if (o->max_steps < 0 || o->eig_tol < 0 || o->rank_tol < 0 || o->cluster < 0 ||
-        o->cluster > 16 || o->flags != 0)
+        o->cluster > 16 || (o->flags & ~MDS_FLAG_FULL_MATVEC) != 0)
         return MDS_ERR_ARG;
     out->prec = o->prec;
     out->mmax = o->max_steps ? o->max_steps : kDefaultSteps;
@@ -126,6 +127,7 @@ int read_opts(const mds_opts* o, Opts* out) {
     out->ws = (char*)o->workspace;
     out->wsb = o->workspace_bytes;
     out->cluster = o->cluster;
+    out->flags = o->flags;
     if (out->mmax < 2) return MDS_ERR_ARG;
     return MDS_OK;
 }
@@ -142,6 +144,7 @@ struct Batch {
     std::vector<ProbDesc> desc;
     int p = 0, max_n = 0, max_tiles = 0, mmax = 0, r = 0;
     int q_bytes = 8;                   // bytes per entry of Q as the eigen-solver reads it
+    int sym = 1;                       // symmetric ranges allowed (mds_opts flags)
     size_t q_el = 0, rp_el = 0, rm_el = 0, b_el = 0, v_el = 0;
     ProbDesc* d_desc = nullptr;
     double *q = nullptr, *rp = nullptr, *rm = nullptr, *grand = nullptr, *b = nullptr,
@@ -297,6 +300,8 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.team = 1;
     a.tscr = B.tscr;
     a.tbar = B.tbar;
+    a.sym = (o.flags & MDS_FLAG_FULL_MATVEC) == 0;
+    B.sym = a.sym;
     if (B.tbar) CK(cudaMemsetAsync(B.tbar, 0, 4 * sizeof(unsigned), o.st));
     tmark(2, o.st);
     g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r);
@@ -493,6 +498,7 @@ int batch_status(const Batch& B, const int* hs, const int* steps, int flag, int 
         g_last.eig_steps += steps[j];
         g_last.eig_flops += 2.0 * n * n * k + 8.0 * n * k + 2.0 * n * k * (k + 1) + 2.0 * n * k * B.r;
         g_last.eig_qbytes += (double)B.q_bytes * n * n * k;
+        g_last.eig_qread += lanczos_step_bytes(B.desc[j].n, g_cluster, B.q_bytes == 4, B.sym, lanczos_last_team()) * k;
     }
     if (flag) return MDS_ERR_ARG;
     if (kerr) return kerr;

@@ -158,6 +158,7 @@ struct LanczosArgs {
     int team;           // clusters sharing one problem (1 = the cluster alone)
     double* tscr;       // team exchange buffers (lanczos_team_scratch_doubles)
     unsigned* tbar;     // team barrier words [arrivals, generation, abort], zero before the launch
+    int sym;            // FP32 Q in a cluster alone: read each off-diagonal block of Q once (symmetric ranges)
 };
 constexpr int kMaxTeam = 32;   // clusters per team
 size_t lanczos_team_scratch_doubles(int max_n, int mmax, int r);
@@ -165,6 +166,11 @@ __host__ __device__ inline size_t lanczos_scratch_per_problem(int mmax, int r) {
     return (size_t)(r * 7 + 2) * (mmax + 1) + 8;
 }
 cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st, bool allow_team);
+// Bytes of Q one Lanczos step streams for an n x n problem: whole rows, or
+// the symmetric ranges of a cluster of cs CTAs (q_f32, sym, not a team).
+double lanczos_step_bytes(int n, int cs, int q_f32, int sym, int team);
+// 1 when the last launch_lanczos on this thread ran a team of clusters.
+int lanczos_last_team();
 // Shared memory one CTA of the eigen-solver needs for a cluster of cs CTAs.
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r);
 constexpr size_t kMaxSmem = 220 * 1024;

@@ -35,6 +35,18 @@
 // reduced across the cluster through DSMEM in rank order, so every CTA holds
 // bitwise-identical scalars and takes identical decisions.
 //
+// Symmetric ranges (FP32 Q, a cluster of cs >= 3 CTAs alone on a problem):
+// Q = Q^T, so each entry of an off-diagonal block needs to be read once.  The
+// rows are cut into cs blocks of R rows (R a multiple of 4, so every block
+// starts on a 16-byte boundary) and CTA q reads, for each of its rows, the
+// columns of blocks q, q+1, ..., q+m_q-1 (cyclically): (cs-1)/2 blocks past
+// its own, and one more for the first cs/2 CTAs when cs is even.  Every
+// unordered pair of blocks then lies in the range of exactly one CTA, which
+// uses an entry q_ab of an off-diagonal block twice: in row a's dot and, by
+// symmetry, as q_ba x_a towards entry b of the product.  Each row costs
+// about (cs+1)/(2cs) of its bytes; the CTAs add the transposed sums of the
+// blocks they own through DSMEM after the matvec.
+//
 // Streaming: Q is read once per step and does not change, so each warp
 // streams its rows of Q in row segments of at most 4 KB through its own ring
 // of shared-memory stages with asynchronous bulk copies (cp.async.bulk,
@@ -85,9 +97,20 @@ struct Smem {
     double* red;     // 64 : scratch
     double* sgn;     // 4 * kMaxR : (|max|, row, signed) per eigenvector, then sign flips
     double* ttmp;    // teams only: kMaxTeam x (mmax + 2), the clusters' partial sums
+    float2* yoff;    // clusters alone: (cs / 2) x rows_max double-FP32 transposed sums of the range
 };
 
 __host__ __device__ inline int owned_max(int r, int cs) { return (r + cs - 1) / cs; }
+
+// Rows of a CTA's slice at most: ceil(max_n / cs), rounded up to a multiple
+// of 4 for the symmetric ranges' blocks.
+__host__ __device__ inline int rows_max(int max_n, int cs) { return (int)round_up((max_n + cs - 1) / cs, 4); }
+
+// Entries of the transposed sums of a symmetric range: at most cs / 2
+// off-diagonal blocks of rows_max columns.
+__host__ __device__ inline size_t yoff_entries(int max_n, int cs) {
+    return (size_t)round_up((int64_t)(cs / 2) * rows_max(max_n, cs) + 4, 2);
+}
 
 // Doubles of the ring region: the Q stages or the check workspace, whichever is larger.
 __host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
@@ -98,15 +121,15 @@ __host__ __device__ inline size_t ring_doubles(int cs, int mmax, int r) {
 }
 
 __host__ __device__ inline size_t smem_doubles(int max_n, int cs, int mmax, int r, bool team = false) {
-    const size_t rmax = (size_t)((max_n + cs - 1) / cs);
-    return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 4, 4) + 2 * round_up(rmax, 2) +
+    const size_t rmax = (size_t)rows_max(max_n, cs);
+    return ring_doubles(cs, mmax, r) + (size_t)kWarps * kRing + round_up(max_n + 4, 4) + 2 * rmax +
            6 * (size_t)(mmax + 2) + 3 * (size_t)(mmax + 1) + 2 * kMaxR + 64 + 4 * kMaxR + 8 +
-           (team ? (size_t)kMaxTeam * (mmax + 2) : 0);
+           (team ? (size_t)kMaxTeam * (mmax + 2) : yoff_entries(max_n, cs));
 }
 
 __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r, bool team = false) {
     Smem s;
-    const int rmax = (max_n + cs - 1) / cs;
+    const int rmax = rows_max(max_n, cs);
     double* p = base;
     s.ring = reinterpret_cast<uint8_t*>(p);
     s.xv = p;
@@ -118,8 +141,8 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r, bool tea
     p += ring_doubles(cs, mmax, r);
     s.full = reinterpret_cast<uint64_t*>(p); p += kWarps * kRing;
     s.vfull = p; p += round_up(max_n + 4, 4);
-    s.vloc = p; p += round_up(rmax, 2);
-    s.wloc = p; p += round_up(rmax, 2);
+    s.vloc = p; p += rmax;
+    s.wloc = p; p += rmax;
     s.part0 = p; p += mmax + 2;
     s.part1 = p; p += mmax + 2;
     s.cfull = p; p += mmax + 2;
@@ -134,6 +157,7 @@ __device__ Smem carve(double* base, int max_n, int cs, int mmax, int r, bool tea
     s.red = p; p += 64;
     s.sgn = p; p += 4 * kMaxR;
     s.ttmp = team ? p : nullptr;
+    s.yoff = team ? nullptr : reinterpret_cast<float2*>(p);
     return s;
 }
 
@@ -471,6 +495,56 @@ __device__ __forceinline__ double start_entry(int row) {
     return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
+// ------------------------------------------------------ symmetric ranges
+//
+// The range of CTA q (see the header): blocks q, ..., q+m_q-1 of R columns,
+// cyclically, read as the columns [a0, a0 + la) followed, once it wraps, by
+// [0, lb).  The own block comes first: columns [0, wd) of the range.
+
+constexpr int kSymCols = kChunkB / 4;   // longest symmetric range (one stage of FP32)
+
+struct SymPlan {
+    bool on;     // the symmetric matvec is in use for this problem
+    int R;       // rows per CTA slice
+    int a0, la;  // first piece of the range
+    int lb;      // second piece (after the wrap), from column 0
+    int wd;      // width of the own block
+    int len;     // la + lb
+};
+
+__host__ __device__ inline int sym_blocks(int q, int cs) { return (cs - 1) / 2 + 1 + ((cs % 2 == 0 && q < cs / 2) ? 1 : 0); }
+
+// Columns of block b (the last one includes the zero padding up to npad).
+__host__ __device__ inline int sym_width(int b, int R, int npad) { return R < npad - b * R ? R : npad - b * R; }
+
+// The plan of rank q; identical decisions on every CTA of the cluster.  The
+// ranges are used when every CTA has rows and every range fits one stage
+// (kSymCols columns, at most 8 float4 per lane).
+__host__ __device__ inline SymPlan sym_plan(int n, int cs, int q, bool allowed) {
+    SymPlan p;
+    p.on = false;
+    p.R = (n + cs - 1) / cs;
+    p.a0 = p.la = p.lb = p.wd = p.len = 0;
+    if (!allowed || cs < 3) return p;
+    const int npad = (int)round_up(n, 4);
+    const int R = (int)round_up(p.R, 4);
+    if ((cs - 1) * R >= n) return p;
+    for (int t = 0; t < cs; ++t) {
+        int len = 0;
+        for (int k = 0; k < sym_blocks(t, cs); ++k) len += sym_width((t + k) % cs, R, npad);
+        if (len > kSymCols) return p;
+    }
+    const int last = q + sym_blocks(q, cs) - 1;   // the range's last block, before the wrap
+    p.on = true;
+    p.R = R;
+    p.a0 = q * R;
+    p.la = (last < cs && (last + 1) * R < npad ? (last + 1) * R : npad) - p.a0;
+    p.lb = last < cs ? 0 : (last - cs + 1) * R;
+    p.wd = sym_width(q, R, npad);
+    p.len = p.la + p.lb;
+    return p;
+}
+
 // ---------------------------------------------------------------- Q stream
 //
 // Warp w of a CTA owns rows [wr0, wr0 + per_step / nseg) of the CTA's slice
@@ -483,6 +557,8 @@ struct QStream {
     size_t rstride;     // bytes per row of Q (ldq * 8)
     int rowbytes;       // bytes a row's copies cover: FP32 round_up(n, 4) * 4, FP64 round_up(n, 2) * 8
     int nseg, segb;     // segments per row and bytes per segment (the last may be shorter)
+    int aoff;           // symmetric range: byte offset in the row of its first column, else 0
+    int abytes;         // symmetric range: bytes of its first piece (the rest is read from column 0), else 0
     int wr0, per_step;  // first row of this warp and segments per step
     uint8_t* ring;      // this warp's stages
     uint64_t* full;     // their mbarriers
@@ -511,11 +587,21 @@ __device__ __forceinline__ void qs_fill(QStream& s) {
     while (s.inflight < s.nst && s.issue_left > 0) {
         if ((threadIdx.x & 31) == 0) {
             const int row = s.wr0 + s.ipos / s.nseg, seg = s.ipos % s.nseg;
-            const int off = seg * s.segb;
-            const int bytes = min(s.segb, s.rowbytes - off);
-            tc::mbar_expect_tx(&s.full[s.ist], (uint32_t)bytes);
-            tc::bulk_load(s.ring + (size_t)s.ist * s.stride, s.q + (size_t)row * s.rstride + off, (uint32_t)bytes,
-                          &s.full[s.ist]);
+            const uint8_t* src = s.q + (size_t)row * s.rstride;
+            uint8_t* dst = s.ring + (size_t)s.ist * s.stride;
+            if (s.abytes == 0) {
+                const int off = seg * s.segb;
+                const int bytes = min(s.segb, s.rowbytes - off);
+                tc::mbar_expect_tx(&s.full[s.ist], (uint32_t)bytes);
+                tc::bulk_load(dst, src + off, (uint32_t)bytes, &s.full[s.ist]);
+            } else {
+                // a symmetric range (one segment): its first piece, then the
+                // part past the wrap (from column 0) when there is one
+                tc::mbar_expect_tx(&s.full[s.ist], (uint32_t)s.rowbytes);
+                tc::bulk_load(dst, src + s.aoff, (uint32_t)s.abytes, &s.full[s.ist]);
+                if (s.rowbytes > s.abytes)
+                    tc::bulk_load(dst + s.abytes, src, (uint32_t)(s.rowbytes - s.abytes), &s.full[s.ist]);
+            }
         }
         s.ipos = s.ipos + 1 == s.per_step ? 0 : s.ipos + 1;
         s.ist = s.ist + 1 == s.nst ? 0 : s.ist + 1;
@@ -551,17 +637,29 @@ __device__ __forceinline__ bool qs_drain(QStream& s) {
     return ok;
 }
 
-// Sets up the warp's stream for a problem and issues its first chunks.
+// Sets up the warp's stream for a problem and issues its first chunks: whole
+// rows, or the symmetric range of sp (FP32 Q) in one segment per row.
 template <bool DF>
-__device__ __forceinline__ void qs_setup(QStream& s, const double* Q, int ldq, int n, int r0, int nr) {
+__device__ __forceinline__ void qs_setup(QStream& s, const double* Q, int ldq, int n, int r0, int nr,
+                                         const SymPlan& sp) {
     const int warp = threadIdx.x >> 5;
     const int per_warp = (nr + kWarps - 1) / kWarps;
     const int a = min(nr, warp * per_warp), b = min(nr, (warp + 1) * per_warp);
     s.q = reinterpret_cast<const uint8_t*>(Q);
     s.rstride = (size_t)ldq * 8;
-    s.rowbytes = DF ? (int)round_up(n, 4) * 4 : (int)round_up(n, 2) * 8;
-    s.nseg = (s.rowbytes + kChunkB - 1) / kChunkB;
-    s.segb = (int)round_up((s.rowbytes + s.nseg - 1) / s.nseg, 16);
+    if (sp.on) {
+        s.rowbytes = sp.len * 4;
+        s.aoff = sp.a0 * 4;
+        s.abytes = sp.la * 4;
+        s.nseg = 1;
+        s.segb = s.rowbytes;
+    } else {
+        s.rowbytes = DF ? (int)round_up(n, 4) * 4 : (int)round_up(n, 2) * 8;
+        s.aoff = 0;
+        s.abytes = 0;
+        s.nseg = (s.rowbytes + kChunkB - 1) / kChunkB;
+        s.segb = (int)round_up((s.rowbytes + s.nseg - 1) / s.nseg, 16);
+    }
     s.wr0 = r0 + a;
     s.per_step = (b - a) * s.nseg;
     s.cpos = s.ipos = 0;
@@ -645,6 +743,115 @@ __device__ __forceinline__ bool qs_matvec(QStream& s, int n, int r0, const doubl
         }
     }
     return ok;
+}
+
+// One step of the symmetric-range stream (FP32 Q, one segment per row).
+// vv holds u_j over the range (own block first, so u_j[a] = vv[a - r0]).
+// For each of the warp's rows a, the dot over the range goes to w[a - r0]
+// (double-FP32: four FP32 FMA chains per lane, met at the row's end), and
+// q_ab u_j[a] for the off-diagonal columns b gathers in FP32 chains per lane
+// over the warp's rows (slot u of a lane holds float4 lane + 32u of the
+// range on every row).  The warps then add their chains into yoff
+// (double-FP32, entry b - wd of the range) in a fixed order: in round t warp
+// w takes slot (w + t) mod 8, so no two warps touch one column in a round.
+// One stage per row keeps each copy as large as the range: splitting rows
+// into two stages of half the size (four in flight per warp instead of two)
+// made this phase 1.5x slower.
+constexpr int kSymF4 = 8;   // float4 slots per lane of a range: kSymCols / 128
+static_assert(kSymF4 == kWarps && kSymCols == kSymF4 * 128, "one slot per warp and round");
+
+__device__ __forceinline__ bool qs_matvec_sym(QStream& s, const SymPlan& sp, int r0, const float* vv, float2* w,
+                                              float2* yoff, bool prefetch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool ok = true;
+    s.issue_left = s.per_step - s.inflight + (prefetch ? min(s.nst, s.per_step) : 0);
+    qs_fill(s);
+    const int nf4 = sp.len >> 2, dg4 = sp.wd >> 2;
+    const float4* v4 = reinterpret_cast<const float4*>(vv);
+    float4 acc[kSymF4];
+#pragma unroll
+    for (int u = 0; u < kSymF4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = 0; it < s.per_step; ++it) {
+        ok = qs_wait_front(s) && ok;
+        const int row = s.wr0 + s.cpos;
+        const float4* st4 = reinterpret_cast<const float4*>(s.ring + (size_t)s.cst * s.stride);
+        const float xa = vv[row - r0];
+        float sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
+#pragma unroll
+        for (int u = 0; u < kSymF4; ++u) {
+            const int g = lane + 32 * u;
+            if (g < nf4) {
+                const float4 x = st4[g];
+                const float4 v = v4[g];
+                sh = fmaf(x.x, v.x, sh);
+                sl = fmaf(x.y, v.y, sl);
+                th = fmaf(x.z, v.z, th);
+                tl = fmaf(x.w, v.w, tl);
+                if (g >= dg4) {
+                    acc[u].x = fmaf(x.x, xa, acc[u].x);
+                    acc[u].y = fmaf(x.y, xa, acc[u].y);
+                    acc[u].z = fmaf(x.z, xa, acc[u].z);
+                    acc[u].w = fmaf(x.w, xa, acc[u].w);
+                }
+            }
+        }
+        __syncwarp();
+        qs_pop(s);
+        qs_fill(s);
+        float h = sh, l = 0.f;
+        df_add(h, l, th, 0.f);
+        df_add(h, l, sl, 0.f);
+        df_add(h, l, tl, 0.f);
+        df_warp_sum(h, l);
+        if (lane == 0) w[row - r0] = df_norm(h, l);
+    }
+    for (int t = 0; t < kSymF4; ++t) {
+        const int u = (warp + t) & (kSymF4 - 1);
+        float4 a = acc[0];
+#pragma unroll
+        for (int k = 1; k < kSymF4; ++k)
+            if (k == u) a = acc[k];
+        const int g = lane + 32 * u;
+        if (g < nf4 && g >= dg4) {
+            float2* y = yoff + 4 * (g - dg4);
+            if (t == 0) {
+                y[0] = make_float2(a.x, 0.f);
+                y[1] = make_float2(a.y, 0.f);
+                y[2] = make_float2(a.z, 0.f);
+                y[3] = make_float2(a.w, 0.f);
+            } else {
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float2 c = y[e];
+                    df_add(c.x, c.y, av[e], 0.f);
+                    y[e] = c;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return ok;
+}
+
+// After every CTA's qs_matvec_sym and a cluster barrier: w[rr] (the row dots
+// of this CTA's rows) += the transposed sums of the CTAs whose ranges hold
+// this CTA's block, in rank order.
+__device__ __forceinline__ void sym_collect(cg::cluster_group& cl, const SymPlan& sp, int n, int cs, int q, int nr,
+                                            float2* w, float2* yoff) {
+    const int npad = (int)round_up(n, 4);
+    for (int rr = threadIdx.x; rr < nr; rr += kThreads) {
+        float2 t = w[rr];
+        for (int p = 0; p < cs; ++p) {
+            const int k = (q - p + cs) % cs;
+            if (k < 1 || k >= sym_blocks(p, cs)) continue;
+            int off = 0;
+            for (int kk = 1; kk < k; ++kk) off += sym_width((p + kk) % cs, sp.R, npad);
+            const float2 y = cl.map_shared_rank(yoff, p)[off + rr];
+            df_add(t.x, t.y, y.x, y.y);
+        }
+        w[rr] = df_norm(t.x, t.y);
+    }
 }
 
 // ------------------------------------------------------------ Gram-Schmidt
@@ -772,7 +979,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     const ProbDesc P = A.desc[pj];
     const int n = P.n, ldq = P.ldq, r = A.r;
     const int T = tm.T, qt = tm.qt;   // CTAs of the team and this CTA's rank (cs, q when G = 1)
-    const int R = (n + T - 1) / T;
+    const SymPlan sp = sym_plan(n, cs, q, DF && tm.G == 1 && A.sym != 0);
+    const int R = tm.G > 1 ? (n + T - 1) / T : sp.R;
     const int r0 = min(n, qt * R), r1 = min(n, r0 + R), nr = r1 - r0;
     const double* Q = A.qarena + P.q_off;
     double* B = A.barena + P.b_off;
@@ -786,7 +994,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     bool qok = true;
 
     // start streaming this warp's rows of Q right away
-    qs_setup<DF>(Qs, Q, ldq, n, r0, nr);
+    qs_setup<DF>(Qs, Q, ldq, n, r0, nr, sp);
 
     // ---- start vector: pseudo-random, unit norm
     double loc = 0.0;
@@ -853,6 +1061,15 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                                 [&](int i) { return __ldcg(reinterpret_cast<const float*>(tm.v) + i); });
             else
                 gather_unrolled(S.vfull, n, [&](int i) { return __ldcg(tm.v + i); });
+        } else if (sp.on) {
+            // the range's columns, own block first (zero past n)
+            cl.sync();
+            gather_unrolled(reinterpret_cast<float*>(S.vfull), sp.len, [&](int g) {
+                const int c = g < sp.la ? sp.a0 + g : g - sp.la;
+                if (c >= n) return 0.f;
+                const int src = c / R;
+                return reinterpret_cast<const float*>(cl.map_shared_rank(S.vloc, src))[c - src * R];
+            });
         } else {
             cl.sync();
             if constexpr (DF)
@@ -913,7 +1130,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                     reinterpret_cast<float*>(B)[(int64_t)j * ldq + r0 + rr] = __fadd_rn(v.x, v.y);
                 }
                 const float bf = __fadd_rn(binv.x, binv.y);
-                for (int i = tid; i < n; i += kThreads) reinterpret_cast<float*>(S.vfull)[i] *= bf;
+                const int nv = sp.on ? sp.len : n;
+                for (int i = tid; i < nv; i += kThreads) reinterpret_cast<float*>(S.vfull)[i] *= bf;
             } else {
                 const double binv = S.red[42];
                 for (int rr = tid; rr < nr; rr += kThreads) B[(int64_t)j * ldq + r0 + rr] = S.wloc[rr] * binv;
@@ -1059,7 +1277,14 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
 
         // ---- w = Q u_j on this CTA's rows (streamed); no prefetch into a step
         // that starts with a predicted check
-        qok = qs_matvec<DF>(Qs, n, r0, S.vfull, S.wloc, j + 1 < next_check && j + 1 < kmax) && qok;
+        if (sp.on) {
+            qok = qs_matvec_sym(Qs, sp, r0, reinterpret_cast<const float*>(S.vfull), reinterpret_cast<float2*>(S.wloc),
+                                S.yoff, j + 1 < next_check && j + 1 < kmax) && qok;
+            cl.sync();   // every CTA's row dots and transposed sums are complete
+            sym_collect(cl, sp, n, cs, q, nr, reinterpret_cast<float2*>(S.wloc), S.yoff);
+        } else {
+            qok = qs_matvec<DF>(Qs, n, r0, S.vfull, S.wloc, j + 1 < next_check && j + 1 < kmax) && qok;
+        }
         __syncthreads();
 
         // ---- pass against v_{j-1}, v_j: w_1 = w - c_{j-1} v_{j-1} - c_j v_j
@@ -1391,7 +1616,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     }
 }
 
+thread_local int g_last_team = 0;
+
 }  // namespace
+
+double lanczos_step_bytes(int n, int cs, int q_f32, int sym, int team) {
+    if (!q_f32) return (double)n * round_up(n, 2) * 8;
+    const SymPlan p0 = sym_plan(n, cs, 0, sym && !team);
+    if (!p0.on) return (double)n * round_up(n, 4) * 4;
+    double b = 0.0;
+    for (int q = 0; q < cs; ++q) {
+        const SymPlan p = sym_plan(n, cs, q, true);
+        const int r0 = q * p.R < n ? q * p.R : n;
+        const int nr = (r0 + p.R < n ? r0 + p.R : n) - r0;
+        b += (double)nr * p.len * 4;
+    }
+    return b;
+}
+
+int lanczos_last_team() { return g_last_team; }
 
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
     return smem_doubles(max_n, cs, mmax, r) * sizeof(double) + kMaxR * sizeof(double);
@@ -1486,9 +1729,13 @@ static cudaError_t launch_lanczos_t(const LanczosArgs& a, int cs, cudaStream_t s
 
 cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st, bool allow_team) {
     if (a.p <= 0) return cudaSuccess;
+    g_last_team = 0;
     if (allow_team && a.p == 1 && a.tscr) {
         const cudaError_t e = a.q_f32 ? launch_lanczos_team<true>(a, st) : launch_lanczos_team<false>(a, st);
-        if (e == cudaSuccess) return e;
+        if (e == cudaSuccess) {
+            g_last_team = 1;
+            return e;
+        }
         cudaGetLastError();   // not available: one cluster below
     }
     LanczosArgs b = a;

@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbmds.so")
 
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
+FLAG_FULL_MATVEC = 1   # mds_opts.flags: stream every row of Q whole (no symmetric ranges)
 DTYPE = {torch.float64: 0, torch.float32: 1, torch.uint8: 2}
 STATUS = {0: "MDS_OK", 1: "MDS_ERR_ARG", 2: "MDS_ERR_NOMEM", 3: "MDS_ERR_CUDA", 4: "MDS_ERR_RANK",
           5: "MDS_ERR_NOCONV", 6: "MDS_ERR_TIMEOUT", 7: "MDS_ERR_UNSUPPORTED",
@@ -88,13 +89,14 @@ def _check(status: int, where: str):
 
 
 def _opts(device, prec, nbytes, stream=None, max_steps=0, eig_tol=0.0, rank_tol=0.0, cluster=0,
-          workspace=None):
+          workspace=None, full_matvec=False):
     if workspace is None or workspace.numel() < nbytes:
         workspace = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
     st = stream if stream is not None else torch.cuda.current_stream(device)
     o = MdsOpts(prec=PREC[prec], max_steps=max_steps, eig_tol=eig_tol, rank_tol=rank_tol,
                 stream=ctypes.c_void_p(st.cuda_stream), workspace=_ptr(workspace),
-                workspace_bytes=workspace.numel(), cluster=cluster, flags=0)
+                workspace_bytes=workspace.numel(), cluster=cluster,
+                flags=FLAG_FULL_MATVEC if full_matvec else 0)
     return o, workspace
 
 
@@ -262,7 +264,7 @@ class MdsStats(ctypes.Structure):
     _fields_ = [("stage_ms", ctypes.c_double * 5), ("launches", ctypes.c_int64),
                 ("eig_steps", ctypes.c_int64), ("eig_flops", ctypes.c_double),
                 ("eig_qbytes", ctypes.c_double), ("problems", ctypes.c_int32),
-                ("cluster", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("eig_qread", ctypes.c_double)]
 
 
 STAGES = ("prep", "dist", "center", "eig", "post")
@@ -285,7 +287,7 @@ def mds_last_stats() -> dict:
     _check(L.mds_last_stats(ctypes.byref(s)), "mds_last_stats")
     return {"stage_ms": dict(zip(STAGES, list(s.stage_ms))), "launches": s.launches,
             "eig_steps": s.eig_steps, "eig_flops": s.eig_flops, "eig_qbytes": s.eig_qbytes,
-            "problems": s.problems, "cluster": s.cluster}
+            "problems": s.problems, "cluster": s.cluster, "eig_qread": s.eig_qread}
 
 
 def mds_embed_new_static(model: Model, Ynew, stream=None):
@@ -411,7 +413,8 @@ class DcPlan:
     the whole launch sequence replayed as one CUDA graph; ``tune=True`` makes
     the first ``execute`` pick the eigen-solver cluster size by timing."""
 
-    def __init__(self, n, d, dtype, part_ptr, c, r, prec="f32", tune=True, cluster=0, device="cuda"):
+    def __init__(self, n, d, dtype, part_ptr, c, r, prec="f32", tune=True, cluster=0, device="cuda",
+                 full_matvec=False):
         L = _lib()
         for name, res, args in [
             ("mds_dc_plan_create", _I, [_I64, _I, _I, _I, _P, _I, _I, _P, _I, _P]),
@@ -426,7 +429,7 @@ class DcPlan:
         self.ptr = np.ascontiguousarray(np.asarray(part_ptr, dtype=np.int64))
         self.p = len(self.ptr) - 1
         self.n, self.d, self.r, self.prec = n, d, r, prec
-        o = MdsOpts(prec=PREC[prec], cluster=cluster, flags=0)
+        o = MdsOpts(prec=PREC[prec], cluster=cluster, flags=FLAG_FULL_MATVEC if full_matvec else 0)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(L.mds_dc_plan_create(n, d, DTYPE[dtype], self.p, self.ptr.ctypes.data_as(ctypes.c_void_p), c, r,

@@ -93,6 +93,23 @@ def test_cluster_sizes_agree(gb, cluster):
     assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
 
 
+@pytest.mark.parametrize("n,cluster", [(500, 3), (500, 4), (500, 5), (500, 8), (500, 16), (1021, 3),
+                                       (1021, 6), (1021, 7), (130, 5), (130, 16), (2050, 8)])
+def test_symmetric_ranges_classical_f32(gb, n, cluster):
+    """FP32 Q in one cluster: the symmetric ranges (each off-diagonal block of
+    Q read once, used for both triangles) against the oracle and against the
+    whole-row matvec, for odd and even cluster sizes, ranges that wrap, and
+    sizes where the ranges are not used (too few rows per CTA, rows too long)."""
+    Y = W.gaussian_dominant(n, 30, 5, seed=n + cluster, dtype=np.float32)
+    Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 5)
+    X, lam = gb.mds_classical(dev(Y), 5, "f32", cluster=cluster)
+    Xf, lamf = gb.mds_classical(dev(Y), 5, "f32", cluster=cluster, full_matvec=True)
+    for Xg, lg in ((X, lam), (Xf, lamf)):
+        assert rel(host(lg), lo) < LAM_TOL["f32"]
+        assert O.aligned_rel_error(host(Xg), Xo) < TOL["f32"]
+    assert rel(host(lam), host(lamf)) < 1e-6
+
+
 def test_tiny_problems(gb):
     Y = W.gaussian_dominant(5, 4, 3, seed=1)                   # n = r + 2
     Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 3)
@@ -247,6 +264,28 @@ def test_dc_f32(gb):
     X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), 10, "f32")
     assert rel(host(var), lo) < LAM_TOL["f32"]
     assert O.aligned_rel_error(host(X), Xo) < TOL["f32"]
+
+
+@pytest.mark.parametrize("cluster", [3, 4, 5, 8])
+def test_dc_f32_symmetric_ranges(gb, cluster):
+    """D&C parts of uneven sizes at a fixed cluster size: symmetric ranges and
+    whole rows both match the oracle."""
+    Y = W.gaussian_dominant(6_000, 100, 5, seed=cluster, dtype=np.float32)
+    part = W.partitions_uneven(6_000, 20, 800, 1200, seed=cluster)
+    Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 10)
+    for full in (False, True):
+        X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), 10, "f32",
+                                       cluster=cluster, full_matvec=full)
+        assert rel(host(var), lo) < LAM_TOL["f32"]
+        assert O.aligned_rel_error(host(X), Xo) < TOL["f32"]
+        st = gb.mds.mds_last_stats()
+        # streamed bytes: whole rows, or about (cs + 1) / (2 cs) of them for
+        # the parts whose ranges fit a stage (the last, largest part may not)
+        ratio = st["eig_qread"] / st["eig_qbytes"]
+        if full:
+            assert ratio == pytest.approx(1.0, rel=1e-2)
+        else:
+            assert (cluster + 1) / (2 * cluster) - 0.01 < ratio < 0.95
 
 
 def test_dc_exact_rank_r(gb):

@@ -63,7 +63,7 @@ def test_argument_checks_without_gpu(lib):
     assert lib.mds_interpolate(p, 1, 100, 3, p, 50, 40, ctypes.byref(o), p, p, None) == 1
     bad = _opts(prec=9)
     assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(bad), p, p) == 1
-    flags = _opts(prec=1, flags=1)
+    flags = _opts(prec=1, flags=2)   # an unknown flag bit
     assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(flags), p, p) == 1
     # divide-and-conquer: c must exceed r (Procrustes needs c >= r + 1)
     ptr = np.array([0, 100, 200], dtype=np.int64)
