@@ -49,11 +49,16 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic per launch of the dominant kernel from an ncu capture, valid
 # only while the kernel source is unchanged (sha256 of the .cu file).
 NCU_TRAFFIC = {
-    # ncu DRAM bytes of a smaller case scaled to a full launch by rows
-    # (profiles/k_gower_tck_image_fp8_n814255.md, profiles/k_gower_tc_interp_bf16_n1000000.md);
-    # k_lanczos has no full-size figure (its small case is L2-resident)
-    "k_gower_tck.cu": {"sha": "54d0c9db6af3e843", "bytes_per_launch": 1.375e9},
-    "k_gower_tc.cu": {"sha": "e9fb88006c17e731", "bytes_per_launch": 453e6},
+    # ncu DRAM bytes (read + write) of one launch on a smaller case, per unit
+    # of work, scaled to the full launch: per row of Y for the projection
+    # kernels (profiles/k_gower_tck_image_fp8_n814255.md,
+    # profiles/k_gower_tc_interp_bf16_n1000000.md), per byte of Q streamed for
+    # the batched D&C eigen-solver (profiles/k_lanczos_dc_f32_n100000.md; the
+    # landmark problems of the interpolation workloads are L2-resident and
+    # the image-like D&C parts stream whole rows, so neither uses it)
+    "k_gower_tck.cu": {"sha": "54d0c9db6af3e843", "per": "row", "bytes": 1688.6},
+    "k_gower_tc.cu": {"sha": "a89affadd1612472", "per": "row", "bytes": 452.0},
+    "k_lanczos.cu": {"sha": "2b3722bfea4ec539", "per": "streamed byte", "bytes": 0.8287, "workloads": ("dc",)},
 }
 
 
@@ -454,6 +459,10 @@ def ours(args):
                 "streamed_bytes_per_launch": qread, "streamed_gbs": qread / (eig_ms * 1e-3) / 1e9,
                 "fp64_equiv_flops_per_launch": flops,
                 "fp64_equiv_tflops": flops / (eig_ms * 1e-3) / 1e12, "traffic": None}
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_lanczos.cu")
+        tr = NCU_TRAFFIC["k_lanczos.cu"]
+        if tr["sha"] == file_sha(src) and args.workload in tr["workloads"]:
+            roof["traffic"] = tr["bytes"] * qread
         return roof
 
     def projection_roof():
@@ -483,7 +492,7 @@ def ours(args):
                 "peak_source": src_note, "launch_ms": kms, "flops_per_launch": flops}
         src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_gower_tck.cu" if byte_rows else "k_gower_tc.cu")
         tr = NCU_TRAFFIC.get(os.path.basename(src))
-        roof["traffic"] = tr["bytes_per_launch"] if tr and tr["sha"] == file_sha(src) else None
+        roof["traffic"] = tr["bytes"] * w.n if tr and tr["sha"] == file_sha(src) else None
         return roof
 
     roof_other = None
