@@ -19,6 +19,19 @@ Parity pins (each checked by a ``-m "not gpu"`` test in tests/test_oracle_pins.p
                        rank-r data; p = 1 reduces to classical MDS;
                        Table 1 correlation band.
   embed_new            equals interpolation_mds on the same points.
+  (tests/test_oracle_variants.py, the variants of oracle/variants.py)
+  affine_interpolation equals interpolation_mds (distance form) for
+                       Euclidean rows; landmarks reproduce X_1.
+  maxmin_landmarks     a hand-derived order on a line; picks distinct; the
+                       gap of each new pick never grows; covering radius
+                       within 2x of the brute-force optimal l-center.
+  pivot_mds            pivots = all points is classical MDS; exact classical
+                       MDS of a set made of two copies of a cloud, pivots one
+                       copy (V_P^T V_P = I/2 exactly).
+  fast_mds             n <= l is classical MDS; exact recovery of rank-r data
+                       through one and two levels of division; each leaf's
+                       aligned rows keep the covariance eigenvalues
+                       lambda^j / n_j (orthogonal alignment).
 No oracle function is "parity unpinned".
 """
 from .mds import (RankError, classical_mds, divide_conquer_mds, divide_conquer_part, double_center,
@@ -26,9 +39,11 @@ from .mds import (RankError, classical_mds, divide_conquer_mds, divide_conquer_p
                   sign_convention, sq_dist)
 from .compare import aligned_rel_error, column_correlations
 from .jacobi import jacobi_eigh
+from .variants import affine_interpolation, fast_mds, maxmin_landmarks, pivot_mds
 
 __all__ = [
     "RankError", "classical_mds", "divide_conquer_mds", "divide_conquer_part", "double_center",
     "embed_new", "gower_interpolate", "interpolation_mds", "lmds_triangulate", "procrustes",
     "sign_convention", "sq_dist", "aligned_rel_error", "column_correlations", "jacobi_eigh",
+    "affine_interpolation", "fast_mds", "maxmin_landmarks", "pivot_mds",
 ]

@@ -24,7 +24,7 @@ import math
 import numpy as np
 
 # Stream ids: one independent Philox stream per purpose.
-_S_DATA, _S_LANDMARK, _S_ANCHOR, _S_PART, _S_SIZE, _S_SERVE = range(6)
+_S_DATA, _S_LANDMARK, _S_ANCHOR, _S_PART, _S_SIZE, _S_SERVE, _S_FAST = range(7)
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:
@@ -177,6 +177,54 @@ def partitions_equal(n: int, l: int, c: int, seed: int) -> Partitioning:
     nparts = max(1, math.ceil(len(rest) / own))
     ptr = np.minimum(np.arange(nparts + 1, dtype=np.int64) * own, len(rest))
     return Partitioning(anchors=anchors, ptr=ptr, own=rest)
+
+
+@dataclasses.dataclass
+class FastNode:
+    """One node of fast MDS's random division (Section 3.3).
+
+    ``idx`` are the node's points; an inner node's ``children`` partition
+    ``idx`` in order (idx = concatenation of the children's idx), and the
+    first ``s`` points of each child are its sampling points."""
+    idx: np.ndarray
+    children: list
+
+    def leaves(self):
+        if not self.children:
+            return [self]
+        return [leaf for ch in self.children for leaf in ch.leaves()]
+
+
+def fast_mds_tree(n: int, l: int, s: int, seed: int, min_size: int = 0) -> FastNode:
+    """Fast MDS's recursive random division (Section 3.3) of range(n): a node
+    of m > l points is split, in a random order, into p = floor(l / s)
+    subsets of ceil(m / p) points (the last one smaller; a last subset of
+    fewer than max(s, min_size) points is folded into the one before it),
+    and each subset larger than l is divided again.  Each split draws its
+    own permutation from a Philox stream keyed by (seed, split number in
+    depth-first order)."""
+    p = l // s
+    if p < 2:
+        raise ValueError("need l >= 2 s so that a division makes progress")
+    counter = [0]
+
+    def build(idx):
+        m = len(idx)
+        if m <= l:
+            return FastNode(idx, [])
+        g = np.random.Generator(np.random.Philox(key=[int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                                     (_S_FAST << 32) | counter[0]]))
+        counter[0] += 1
+        perm = idx[g.permutation(m)]
+        size = -(-m // p)
+        cuts = [perm[i:i + size] for i in range(0, m, size)]
+        if len(cuts) > 1 and len(cuts[-1]) < max(s, min_size):
+            tail = cuts.pop()
+            cuts[-1] = np.concatenate([cuts[-1], tail])
+        children = [build(c) for c in cuts]
+        return FastNode(np.concatenate([ch.idx for ch in children]), children)
+
+    return build(np.arange(n, dtype=np.int64))
 
 
 # -------------------------------------------------------------------- serving
