@@ -145,6 +145,7 @@ struct Batch {
     int p = 0, max_n = 0, max_tiles = 0, mmax = 0, r = 0;
     int q_bytes = 8;                   // bytes per entry of Q as the eigen-solver reads it
     int sym = 1;                       // symmetric ranges allowed (mds_opts flags)
+    int team = 0;                      // the eigen-solver ran as a team of clusters
     size_t q_el = 0, rp_el = 0, rm_el = 0, b_el = 0, v_el = 0;
     ProbDesc* d_desc = nullptr;
     double *q = nullptr, *rp = nullptr, *rm = nullptr, *grand = nullptr, *b = nullptr,
@@ -306,6 +307,7 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     tmark(2, o.st);
     g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r);
     CK(launch_lanczos(a, g_cluster, o.st, o.cluster == 0));
+    B.team = lanczos_last_team();
     tmark(3, o.st);
     return MDS_OK;
 }
@@ -498,7 +500,7 @@ int batch_status(const Batch& B, const int* hs, const int* steps, int flag, int 
         g_last.eig_steps += steps[j];
         g_last.eig_flops += 2.0 * n * n * k + 8.0 * n * k + 2.0 * n * k * (k + 1) + 2.0 * n * k * B.r;
         g_last.eig_qbytes += (double)B.q_bytes * n * n * k;
-        g_last.eig_qread += lanczos_step_bytes(B.desc[j].n, g_cluster, B.q_bytes == 4, B.sym, lanczos_last_team()) * k;
+        g_last.eig_qread += lanczos_step_bytes(B.desc[j].n, g_cluster, B.q_bytes == 4, B.sym, B.team) * k;
     }
     if (flag) return MDS_ERR_ARG;
     if (kerr) return kerr;
