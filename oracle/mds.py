@@ -13,7 +13,7 @@ what that passage states.  Library primitives used as single steps:
 ``numpy.linalg.svd`` (the SVD inside orthogonal Procrustes) and matrix
 products.
 
-Readings of points the paper leaves open (listed in the design doc too):
+Readings of points the paper leaves open:
   * Delta holds squared Euclidean distances (Section 2); they are formed
     here in the direct difference form sum_k (y_ik - y_jk)^2, never through
     norms, so this side has no cancellation to guard against.

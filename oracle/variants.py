@@ -16,7 +16,7 @@ product path shares no code with it.
                          MDS on the leaves, Procrustes alignment of every
                          subset to an alignment configuration.
 
-Readings of points the paper leaves open (listed in the design doc too):
+Readings of points the paper leaves open:
   * MaxMin: the first landmark is an input (the paper's implementations draw
     it at random); each next one maximises the smallest squared Euclidean
     distance to those already chosen; ties go to the lowest row index among
