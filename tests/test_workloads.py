@@ -71,3 +71,33 @@ def test_graded_variances_and_serve_sizes():
     # log-uniform sizes: mean (hi - lo) / ln(hi / lo) within sampling error
     assert abs(sizes.mean() / (50_000 / np.log(50_001)) - 1) < 0.05
     assert abs(len(t) / t[-1] / 1000.0 - 1) < 0.05
+
+
+def test_fast_mds_tree():
+    """Section 3.3's division: every row once, children partition their
+    parent in order, leaves of at most l rows, p = floor(l / s) subsets of
+    ceil(m / p) rows per split (one fewer after folding a small last one),
+    and the same tree for the same seed."""
+    n, l, s = 5000, 200, 20
+    tree = W.fast_mds_tree(n, l, s, seed=3, min_size=8)
+    assert np.array_equal(np.sort(tree.idx), np.arange(n))
+
+    def walk(node):
+        if not node.children:
+            assert 0 < len(node.idx) <= l
+            return
+        m, p = len(node.idx), l // s
+        assert len(node.idx) > l
+        assert np.array_equal(node.idx, np.concatenate([c.idx for c in node.children]))
+        assert len(node.children) in (p, p - 1)
+        size = -(-m // p)
+        assert all(len(c.idx) == size for c in node.children[:-1])
+        assert max(s, 8) <= len(node.children[-1].idx) < size + max(s, 8)
+        for c in node.children:
+            walk(c)
+    walk(tree)
+    again = W.fast_mds_tree(n, l, s, seed=3, min_size=8)
+    assert all(np.array_equal(a.idx, b.idx) for a, b in zip(tree.leaves(), again.leaves()))
+    other = W.fast_mds_tree(n, l, s, seed=4, min_size=8)
+    assert not np.array_equal(tree.leaves()[0].idx, other.leaves()[0].idx)
+    assert not W.fast_mds_tree(150, l, s, seed=3).children
