@@ -74,6 +74,9 @@ def test_argument_checks_without_gpu(lib):
                                   ctypes.byref(o), p, p) == 1
     # missing workspace is reported as such (still no GPU work)
     assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(o), p, p) == 8
+    # MDS_FLAG_FULL_MATVEC is a known flag: the same call gets as far as the workspace check
+    full = _opts(prec=1, flags=1)
+    assert lib.mds_classical(p, 1, 100, 3, 2, ctypes.byref(full), p, p) == 8
     # FP8 needs uint8 data paths not built for classical MDS
     o8 = _opts(prec=3)
     assert lib.mds_classical(p, 2, 100, 3, 2, ctypes.byref(o8), p, p) == 7
