@@ -149,6 +149,21 @@ int mds_interpolate_host(const void* Y, int dt, int64_t n, int d, const int64_t*
                          int r, int64_t chunk_rows, const mds_opts* opts, void* X, double* var,
                          mds_model* out_model);
 
+/* Interpolation MDS (Section 3.1) in its affine form, for rows given by
+ * Euclidean coordinates: with squared Euclidean distances Q_1 = L_c L_c^T
+ * (Section 2, L_c the landmark rows minus their mean y_L), so Eq. (2) is
+ *   Xdot = (Y - 1 y_L^T) U_r,  U_r = L_c^T V_r Lambda_r^{-1/2}  (d x r),
+ * one pass over Y instead of n x l distances.  The landmark eigenproblem is
+ * that of mds_interpolate; every row, landmarks included, gets (y - y_L) U_r
+ * (for the landmarks this is X_1 up to rounding).  Arguments as for
+ * mds_interpolate (device pointers; X float, or double for MDS_PREC_F64);
+ * opts->prec must be MDS_PREC_F64 or MDS_PREC_F32 (else
+ * MDS_ERR_UNSUPPORTED); no model is made.  The result equals
+ * mds_interpolate's for Euclidean input, up to rounding. */
+size_t mds_interpolate_affine_workspace_size(int64_t n, int d, int l, int r, int prec);
+int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
+                           int r, const mds_opts* opts, void* X, double* var);
+
 /* Gower's formula, Eq. (2), for m new rows Ynew (m x d, dtype dt) against a
  * stored model; X is m x r.  opts->prec must equal the model's precision.
  * Equal inputs give bitwise-equal outputs regardless of what else is batched

@@ -712,6 +712,69 @@ static int make_model(InterpWs& W, int kind, const Opts& o, int l, int d, int r,
     return MDS_OK;
 }
 
+// ------------------------------------------------ affine interpolation
+
+struct AffineWs {
+    int* flag;
+    double* nrm;      // n: norms of the landmark rows (at their row indices)
+    Batch B;
+    double* ybar;     // d
+    float* ybar_f;
+    double* U;        // d x r
+    float* U_f;
+    double* bias;     // r: the Gower bias (not used by the affine form)
+};
+
+static size_t affine_layout(AffineWs& W, char* base, int64_t n, int d, int l, int r, int mmax) {
+    Arena A{base, 0};
+    W.flag = A.take<int>(1);
+    W.nrm = A.take<double>(n);
+    plan_batch(W.B, {l}, {0}, 0, r, mmax, n);
+    carve_batch(W.B, A);
+    W.ybar = A.take<double>(d);
+    W.ybar_f = A.take<float>(d);
+    W.U = A.take<double>((size_t)d * r);
+    W.U_f = A.take<float>((size_t)d * r);
+    W.bias = A.take<double>(r);
+    return A.off;
+}
+
+size_t mds_interpolate_affine_workspace_size(int64_t n, int d, int l, int r, int prec) {
+    if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0 || r > kMaxR) return 0;
+    if (prec != MDS_PREC_F64 && prec != MDS_PREC_F32) return 0;
+    AffineWs W;
+    return affine_layout(W, nullptr, n, d, l, r, kDefaultSteps) + 256;
+}
+
+int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l, int r,
+                           const mds_opts* opts, void* X, double* var) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!Y || !X || !var || !landmark_idx || !valid_dt(dt) || n < 2 || d <= 0 || l < 2 || l > n ||
+        l > kMaxEigN || r <= 0 || r > kMaxR || r >= l)
+        return MDS_ERR_ARG;
+    if (o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) return MDS_ERR_UNSUPPORTED;
+    AffineWs W;
+    const size_t need = affine_layout(W, nullptr, n, d, l, r, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    if (affine_layout(W, o.ws, n, d, l, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
+    begin_call(o.st);
+    const int f64 = o.prec == MDS_PREC_F64;
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(launch_check_idx(landmark_idx, l, n, W.flag, o.st));
+    // the landmark problem of mds_interpolate: norms of the landmark rows,
+    // their distances and classical MDS
+    CK(launch_rownorm_idx(Y, dt, n, d, landmark_idx, l, f64, W.nrm, o.st));
+    tmark(0, o.st);
+    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, landmark_idx, f64, o))) return s;
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, !f64, l, r, nullptr, nullptr, nullptr,
+                           nullptr, W.bias, var, o.st));
+    CK(launch_affine(Y, dt, n, d, landmark_idx, l, W.B.v, W.B.lam, r, f64, W.ybar, W.ybar_f, W.U, W.U_f, X,
+                     o.st));
+    return finish(&W.B, W.flag, o);
+}
+
 int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
                     int r, const mds_opts* opts, void* X, double* var, mds_model* out_model) {
     Opts o;
@@ -800,7 +863,7 @@ struct InterpHostWs {
 
 static size_t in_size(int dt) { return dt == MDS_IN_F64 ? 8 : (dt == MDS_IN_F32 ? 4 : 1); }
 
-size_t interp_host_layout(InterpHostWs& H, char* base, int64_t n, int d, int l, int r, int prec, int kind,
+static size_t interp_host_layout(InterpHostWs& H, char* base, int64_t n, int d, int l, int r, int prec, int kind,
                           int dt, int mmax) {
     Arena A{base, interp_layout(H.W, base, n, d, l, r, prec, kind, mmax)};
     const size_t es = in_size(dt), ex = prec == MDS_PREC_F64 ? 8 : 4;
@@ -819,7 +882,7 @@ size_t interp_host_layout(InterpHostWs& H, char* base, int64_t n, int d, int l, 
 // Default chunk: ~96 MiB of input rows (fewer, larger copies and launches
 // measured faster than 64k-row chunks: 1M x 100 FP32 rows in 3.9 vs 4.2 ms),
 // at least 16k rows.
-int64_t host_chunk_rows(int64_t n, int d, size_t es) {
+static int64_t host_chunk_rows(int64_t n, int d, size_t es) {
     const int64_t rows = (int64_t)((96ull << 20) / ((size_t)d * es));
     return std::max<int64_t>(16384, std::min<int64_t>(rows, n));
 }

@@ -184,6 +184,13 @@ cudaError_t launch_interp_model(const double* V, const double* lam, const double
                                 double* x1_64, float* x1_32, double* bias, double* var_out,
                                 cudaStream_t st);
 
+// Affine form of Eq. (2) for coordinate rows: y_L (FP64 and FP32 copies),
+// U_r = L_c^T V Lambda^{-1/2} (d x r, both copies) and X = (Y - y_L) U_r for
+// all n rows (double X when f64, else float).
+cudaError_t launch_affine(const void* Y, int dt, int64_t n, int d, const int64_t* idx, int l, const double* V,
+                          const double* lam, int r, int f64, double* ybar, float* ybar_f, double* U, float* U_f,
+                          void* X, cudaStream_t st);
+
 // Gather rows Y[idx[i]] into a dense l x d matrix of the accumulation type.
 // For dt == kDtBF16, Y is the split planes of an ny-row matrix.
 cudaError_t launch_gather_rows(const void* Y, int dt, int64_t ny, int d, const int64_t* idx,

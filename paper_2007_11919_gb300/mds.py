@@ -60,6 +60,8 @@ def _lib():
             "mds_classical_dist": (_I, [_P, _I64, _I, _P, _P, _P]),
             "mds_interpolate_workspace_size": (_SZ, [_I64, _I, _I, _I, _I]),
             "mds_interpolate": (_I, [_P, _I, _I64, _I, _P, _I, _I, _P, _P, _P, _P]),
+            "mds_interpolate_affine_workspace_size": (_SZ, [_I64, _I, _I, _I, _I]),
+            "mds_interpolate_affine": (_I, [_P, _I, _I64, _I, _P, _I, _I, _P, _P, _P]),
             "mds_interpolate_host_workspace_size": (_SZ, [_I64, _I, _I, _I, _I, _I]),
             "mds_interpolate_host": (_I, [_P, _I, _I64, _I, _P, _I, _I, _I64, _P, _P, _P, _P]),
             "mds_embed_new_workspace_size": (_SZ, [_P, _I64]),
@@ -198,6 +200,24 @@ def mds_interpolate(Y, landmark_idx, r, prec="f32", want_model=False, **kw):
     _check(L.mds_interpolate(_ptr(Y), dt, n, d, _ptr(idx), l, r, ctypes.byref(o), _ptr(X), _ptr(var),
                              ctypes.byref(h) if want_model else None), "mds_interpolate")
     return X, var, (Model(h.value, Y.device) if want_model else None)
+
+
+def mds_interpolate_affine(Y, landmark_idx, r, prec="f32", **kw):
+    """Interpolation MDS (Section 3.1) in its affine form for coordinate rows:
+    X = (Y - y_L) U_r with U_r the landmarks' principal axes scaled by
+    Lambda^{-1/2} (Eq. (2) for Euclidean distances).  prec "f64" or "f32".
+    Returns (X n x r, var r)."""
+    dt = _data(Y)
+    n, d = Y.shape
+    idx = _idx(landmark_idx, Y.device)
+    l = idx.numel()
+    L = _lib()
+    o, ws = _opts(Y.device, prec, L.mds_interpolate_affine_workspace_size(n, d, l, r, PREC[prec]), **kw)
+    X = torch.empty((n, r), dtype=_xdtype(prec), device=Y.device)
+    var = torch.empty(r, dtype=torch.float64, device=Y.device)
+    _check(L.mds_interpolate_affine(_ptr(Y), dt, n, d, _ptr(idx), l, r, ctypes.byref(o), _ptr(X), _ptr(var)),
+           "mds_interpolate_affine")
+    return X, var
 
 
 def mds_interpolate_host(Y, landmark_idx, r, prec="f32", want_model=False, chunk_rows=0, out=None,

@@ -193,6 +193,37 @@ def test_interp_full_size_sampled(gb):
     assert np.all(np.isfinite(Xh))
 
 
+@pytest.mark.parametrize("prec,kind,n,d,l,r", [("f64", "f64", 3000, 20, 300, 5), ("f32", "f32", 5000, 100, 1000, 10),
+                                              ("f32", "u8", 2000, 64, 250, 6), ("f64", "f32", 777, 9, 129, 3)])
+def test_interp_affine(gb, prec, kind, n, d, l, r):
+    """Affine form of Eq. (2) for coordinate rows: the oracle's affine form
+    and its distance form (Gower) agree with the GPU result."""
+    if kind == "u8":
+        Y = W.image_like(n, d, seed=n)
+    else:
+        Y = W.gaussian_dominant(n, d, r, seed=n, dtype=np.float64 if kind == "f64" else np.float32)
+    idx = W.landmarks(n, l, seed=n)
+    Xo, vo, _ = O.affine_interpolation(Y, idx, r)
+    Xg, _, _ = O.interpolation_mds(Y, idx, r)
+    X, var = gb.mds_interpolate_affine(dev(Y), dev(idx), r, prec)
+    assert X.dtype == (torch.float64 if prec == "f64" else torch.float32)
+    assert rel(host(var), vo) < LAM_TOL[prec]
+    assert O.aligned_rel_error(host(X), Xo) < TOL[prec]
+    assert O.aligned_rel_error(host(X), Xg) < TOL[prec]
+
+
+def test_interp_affine_all_landmarks_and_errors(gb):
+    """l = n: every row is a landmark, the result is classical MDS; BF16
+    is not offered for the affine form."""
+    Y = W.gaussian_dominant(400, 8, 3, seed=2)
+    Xc, lc, _, _ = O.classical_mds(O.sq_dist(Y, Y), 3)
+    X, var = gb.mds_interpolate_affine(dev(Y), dev(np.arange(400)), 3, "f64")
+    assert O.aligned_rel_error(host(X), Xc) < TOL["f64"]
+    assert rel(host(var), lc / 400) < LAM_TOL["f64"]
+    with pytest.raises(gb.MdsError):
+        gb.mds_interpolate_affine(dev(Y.astype(np.float32)), dev(np.arange(50)), 3, "bf16")
+
+
 def test_bad_landmark_index(gb):
     Y = W.gaussian_dominant(500, 10, 3, seed=2)
     idx = W.landmarks(500, 100, seed=2)

@@ -120,6 +120,20 @@ def test_host_interpolation_checks_without_gpu(lib):
     assert lib.mds_interpolate_host_workspace_size(10_000, 100, 500, 10, 2, 9) == 0
 
 
+def test_affine_interpolation_checks_without_gpu(lib):
+    o = _opts(prec=1)
+    p = ctypes.c_void_p(8)
+    assert lib.mds_interpolate_affine(None, 1, 1000, 8, p, 100, 3, ctypes.byref(o), p, p) == 1
+    assert lib.mds_interpolate_affine(p, 1, 1000, 8, p, 2000, 3, ctypes.byref(o), p, p) == 1   # l > n
+    assert lib.mds_interpolate_affine(p, 1, 1000, 8, p, 100, 100, ctypes.byref(o), p, p) == 1  # r >= l
+    ob = _opts(prec=2)
+    assert lib.mds_interpolate_affine(p, 1, 1000, 8, p, 100, 3, ctypes.byref(ob), p, p) == 7   # BF16
+    assert lib.mds_interpolate_affine(p, 1, 1000, 8, p, 100, 3, ctypes.byref(o), p, p) == 8    # no workspace
+    assert lib.mds_interpolate_affine_workspace_size(1000, 8, 100, 3, 2) == 0
+    small = lib.mds_interpolate_affine_workspace_size(1000, 8, 100, 3, 1)
+    assert small > 100 * 100 * 4 and small < lib.mds_interpolate_affine_workspace_size(1000, 8, 400, 3, 1)
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     import paper_2007_11919_gb300.mds as M
     monkeypatch.setattr(M, "_L", None)
