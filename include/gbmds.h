@@ -56,11 +56,21 @@ typedef enum {
 
 typedef enum { MDS_IN_F64 = 0, MDS_IN_F32 = 1, MDS_IN_U8 = 2 } mds_dtype;
 
-/* Arithmetic of the distance contractions.  FP64 eigen-solves, centering
- * means and Procrustes SVDs are used for every precision. */
+/* Arithmetic of the distance contractions.  For every precision the
+ * centering means, the Procrustes SVDs and the scalars of the eigen-solver
+ * (Lanczos coefficients, Ritz values, convergence tests) are FP64, and the
+ * landmark eigenproblem of interpolation MDS (Section 3.1, one l x l problem)
+ * is solved entirely in FP64 (Q, Lanczos vectors and products), from FP32
+ * distances of the unrounded rows unless the precision is MDS_PREC_F64.
+ * Eigenproblems of the other calls (classical MDS, the parts of
+ * divide-and-conquer MDS) follow the precision: FP64 for MDS_PREC_F64;
+ * otherwise Q is double-centred in FP64 from the FP32 (or tensor-core)
+ * distances and stored in FP32, the Lanczos basis is FP32, and the
+ * products and working vectors run in double-FP32 (about 48 significand
+ * bits) with FP64 scalars. */
 typedef enum {
     MDS_PREC_F64 = 0,   /* FP64 throughout */
-    MDS_PREC_F32 = 1,   /* FP32 distances, FP64 eigen-solve */
+    MDS_PREC_F32 = 1,   /* FP32 distances (CUDA cores) */
     MDS_PREC_BF16 = 2,  /* BF16 tensor-core distances, FP32 accumulate */
     MDS_PREC_FP8 = 3    /* E4M3 tensor-core distances (uint8 data), FP32 accumulate */
 } mds_precision;
@@ -251,6 +261,17 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
                        const mds_opts* opts, int tune, mds_dc_plan* out);
 int mds_dc_plan_execute(mds_dc_plan plan, const void* Y, const int64_t* part_own, const int64_t* anchors,
                         void* X, double* var, void* stream);
+/* Execute on data in HOST memory (Section 3.2, the same computation as
+ * mds_dc_plan_execute, bitwise the same result): Y (n x d), part_own,
+ * anchors, X (n x r: double for MDS_PREC_F64, else float) and var (r) are
+ * host pointers.  The plan copies the inputs into device buffers it owns
+ * (allocated at the first call: n x d input elements, the indices, n x r
+ * outputs; MDS_ERR_NOMEM if that fails), replays its graph on them, copies
+ * X and var back, and returns when they are in host memory.  Rows of X
+ * outside every part are zero.  Page-locked host buffers make the copies
+ * asynchronous DMA; pageable ones work too. */
+int mds_dc_plan_execute_host(mds_dc_plan plan, const void* Y, const int64_t* part_own, const int64_t* anchors,
+                             void* X, double* var, void* stream);
 int mds_dc_plan_info(mds_dc_plan plan, int* cluster, int64_t* graph_nodes, double* trial_ms);
 void mds_dc_plan_destroy(mds_dc_plan plan);
 

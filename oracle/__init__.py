@@ -18,6 +18,9 @@ Parity pins (each checked by a ``-m "not gpu"`` test in tests/test_oracle_pins.p
   divide_conquer_mds   exact recovery (up to one global orthogonal map) of
                        rank-r data; p = 1 reduces to classical MDS;
                        Table 1 correlation band.
+  divide_conquer_parts exact recovery of rank-r data on a subset of parts.
+  sign_convention      hand-built columns with a known largest entry (and
+                       a tie) come out flipped or kept as expected.
   embed_new            equals interpolation_mds on the same points.
   (tests/test_oracle_variants.py, the variants of oracle/variants.py)
   affine_interpolation equals interpolation_mds (distance form) for
@@ -34,7 +37,8 @@ Parity pins (each checked by a ``-m "not gpu"`` test in tests/test_oracle_pins.p
                        lambda^j / n_j (orthogonal alignment).
 No oracle function is "parity unpinned".
 """
-from .mds import (RankError, classical_mds, divide_conquer_mds, divide_conquer_part, double_center,
+from .mds import (RankError, classical_mds, divide_conquer_mds, divide_conquer_part, divide_conquer_parts,
+                  double_center,
                   embed_new, gower_interpolate, interpolation_mds, lmds_triangulate, procrustes,
                   sign_convention, sq_dist)
 from .compare import aligned_rel_error, column_correlations
@@ -42,7 +46,8 @@ from .jacobi import jacobi_eigh
 from .variants import affine_interpolation, fast_mds, maxmin_landmarks, pivot_mds
 
 __all__ = [
-    "RankError", "classical_mds", "divide_conquer_mds", "divide_conquer_part", "double_center",
+    "RankError", "classical_mds", "divide_conquer_mds", "divide_conquer_part", "divide_conquer_parts",
+    "double_center",
     "embed_new", "gower_interpolate", "interpolation_mds", "lmds_triangulate", "procrustes",
     "sign_convention", "sq_dist", "aligned_rel_error", "column_correlations", "jacobi_eigh",
     "affine_interpolation", "fast_mds", "maxmin_landmarks", "pivot_mds",

@@ -186,7 +186,22 @@ def procrustes(A, B):
     return T, t
 
 
-def divide_conquer_mds(Y, anchors, ptr, own, r: int, rank_tol: float = 1e-12):
+def _part_classical(job):
+    """Classical MDS of one part from its rows (Section 3.2: each part is an
+    ordinary classical-MDS problem).  ``job`` = (rows of the part, r,
+    rank_tol); returns (X_j, lambda^j)."""
+    Yj, r, rank_tol = job
+    Yj = np.asarray(Yj, dtype=np.float64)
+    Xj, lam_j, _, _ = classical_mds(sq_dist(Yj, Yj), r, rank_tol)
+    return Xj, lam_j
+
+
+def _members(anchors, ptr, own, j):
+    """Points of part j: the c connecting points, then its own points."""
+    return np.concatenate([anchors, np.asarray(own[ptr[j]:ptr[j + 1]], dtype=np.int64)])
+
+
+def divide_conquer_mds(Y, anchors, ptr, own, r: int, rank_tol: float = 1e-12, map_fn=map):
     """Divide-and-conquer MDS (Section 3.2).
 
     Part j's points are the c connecting points ``anchors`` followed by its
@@ -195,6 +210,9 @@ def divide_conquer_mds(Y, anchors, ptr, own, r: int, rank_tol: float = 1e-12):
     the connecting points, X_1^c ~ X_j^c T_j + 1 t_j^T; the aligned rows
     without the connecting points, X_j^a T_j + 1 t_j^T, and X_1 whole are put
     in original row order.  lambda_bar_i = (1/p) sum_j lambda_i^j / n_j.
+    The parts' classical MDS problems are independent of one another
+    (Section 3.2 solves them separately); ``map_fn`` (default: the builtin
+    map, in part order) may run them in parallel processes.
     Returns (X n x r, lambda_bar r, extras)."""
     Y = np.asarray(Y)
     anchors = np.asarray(anchors, dtype=np.int64)
@@ -205,40 +223,51 @@ def divide_conquer_mds(Y, anchors, ptr, own, r: int, rank_tol: float = 1e-12):
     n = Y.shape[0]
     X = np.full((n, r), np.nan)
     lam_sum = np.zeros(r)
+    members = [_members(anchors, ptr, own, j) for j in range(p)]
+    solved = list(map_fn(_part_classical, [(Y[m], r, rank_tol) for m in members]))
     X1c = None
     per_part = []
     for j in range(p):
-        members = np.concatenate([anchors, own[ptr[j]:ptr[j + 1]]])
-        Yj = Y[members].astype(np.float64)
-        Xj, lam_j, _, _ = classical_mds(sq_dist(Yj, Yj), r, rank_tol)
-        lam_sum += lam_j / len(members)
+        Xj, lam_j = solved[j]
+        lam_sum += lam_j / len(members[j])
         if j == 0:
             X1c = Xj[:c]
-            X[members] = Xj
+            X[members[j]] = Xj
             per_part.append((np.eye(r), np.zeros(r), lam_j))
         else:
             T, t = procrustes(X1c, Xj[:c])
-            X[members[c:]] = Xj[c:] @ T + t[None, :]
+            X[members[j][c:]] = Xj[c:] @ T + t[None, :]
             per_part.append((T, t, lam_j))
     return X, lam_sum / p, {"parts": per_part}
 
 
-def divide_conquer_part(Y, anchors, ptr, own, j: int, r: int, rank_tol: float = 1e-12):
-    """Rows of part j (j >= 1) of ``divide_conquer_mds``, computed alone:
-    the classical MDS of parts 1 and j and their Procrustes alignment.
-    Returns (row indices, aligned coordinates, lambda^j)."""
+def divide_conquer_parts(Y, anchors, ptr, own, parts, r: int, rank_tol: float = 1e-12, map_fn=map):
+    """The rows of the listed parts of ``divide_conquer_mds``, computed alone:
+    classical MDS of part 1 (index 0, solved once whether listed or not) and
+    of every listed part, each listed part j >= 2 aligned to part 1 by
+    Procrustes on the connecting points (Section 3.2).  Returns a list of
+    (row indices, aligned coordinates, lambda^j), one per listed part, in
+    the order listed."""
     anchors = np.asarray(anchors, dtype=np.int64)
     c = len(anchors)
+    parts = [int(j) for j in parts]
+    need = [0] + [j for j in parts if j != 0]
+    members = {j: _members(anchors, ptr, own, j) for j in need}
+    solved = dict(zip(need, map_fn(_part_classical, [(np.asarray(Y)[members[j]], r, rank_tol) for j in need])))
+    X1, _ = solved[0]
+    out = []
+    for j in parts:
+        Xj, lam_j = solved[j]
+        if j == 0:
+            out.append((members[0], Xj, lam_j))
+        else:
+            T, t = procrustes(X1[:c], Xj[:c])
+            out.append((members[j][c:], Xj[c:] @ T + t[None, :], lam_j))
+    return out
 
-    def part(k):
-        members = np.concatenate([anchors, np.asarray(own[ptr[k]:ptr[k + 1]], dtype=np.int64)])
-        Yk = np.asarray(Y[members], dtype=np.float64)
-        Xk, lam_k, _, _ = classical_mds(sq_dist(Yk, Yk), r, rank_tol)
-        return members, Xk, lam_k
 
-    m1, X1, lam1 = part(0)
-    if j == 0:
-        return m1, X1, lam1
-    mj, Xj, lamj = part(j)
-    T, t = procrustes(X1[:c], Xj[:c])
-    return mj[c:], Xj[c:] @ T + t[None, :], lamj
+def divide_conquer_part(Y, anchors, ptr, own, j: int, r: int, rank_tol: float = 1e-12):
+    """Rows of part j of ``divide_conquer_mds``, computed alone (parts 1 and
+    j, then their Procrustes alignment).  Returns (row indices, aligned
+    coordinates, lambda^j)."""
+    return divide_conquer_parts(Y, anchors, ptr, own, [j], r, rank_tol)[0]

@@ -249,9 +249,12 @@ struct GramOp {
 };
 
 // Uploads descriptors, forms Q_j for every problem (squared distances +
-// double centering) and runs the batched eigen-solver.
+// double centering) and runs the batched eigen-solver.  acc_f64: FP64 dot
+// products for the distances.  eig_f64: Q, the Lanczos vectors and the
+// products in IEEE FP64; otherwise Q is stored in FP32 and the products and
+// vector work run in double-FP32 (with FP64 scalars).
 int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
-                  const int64_t* anchors, const int64_t* own, int acc_f64, const Opts& o,
+                  const int64_t* anchors, const int64_t* own, int acc_f64, int eig_f64, const Opts& o,
                   bool upload = true, const GramOp* gram = nullptr) {
     if (upload) {
         CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
@@ -270,14 +273,15 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
         CK(launch_gram_tck(gram->mode, gram->ops, gram->slots, d, gram->nrm, gram->units,
                            (int)gram->h_units.size(), B.d_desc, B.q, B.rp, gram->kerr, o.st));
     } else if (Y) {
-        CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64,
+        CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64, eig_f64,
                                  B.q, B.rp, o.st));
     }
     tmark(1, o.st);
-    // FP64 precision keeps Q and the products in IEEE FP64.  The other
-    // precisions, whose Q carries FP32-level distance rounding anyway, store Q
-    // in FP32 and run the products and vector work in double-FP32.
-    const int q_f32 = o.prec != MDS_PREC_F64;
+    // An FP64 eigenproblem keeps Q and the products in IEEE FP64.  The
+    // divide-and-conquer parts of the other precisions, whose Q carries
+    // FP32-level distance rounding anyway, store Q in FP32 and run the
+    // products and vector work in double-FP32.
+    const int q_f32 = !eig_f64;
     B.q_bytes = q_f32 ? 4 : 8;
     CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, q_f32, o.st));
     LanczosArgs a;
@@ -482,7 +486,7 @@ int dc_enqueue(DcWs& W, const void* Y, int dt, int64_t n, int d, int p, const in
     int s = MDS_OK;
     if (W.G.mode < 0 && (s = prep_data(Y, dt, n, d, o.prec, W.nrm, W.Yq, o, &Ye, &dte))) return s;
     tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, o, upload, &W.G))) return s;
+    if ((s = run_eig_batch(W.B, Ye, dte, d, W.nrm, anchors, part_own, f64, f64, o, upload, &W.G))) return s;
     CK(launch_dc_procrustes(W.B.d_desc, p, W.B.v, W.B.lam, r, c, W.Tt, o.st));
     CK(launch_dc_align(W.B.d_desc, p, W.B.max_n, W.B.v, W.B.lam, W.Tt, r, anchors, part_own, f64, X, o.st));
     CK(launch_dc_lambda_bar(W.B.d_desc, p, W.B.lam, r, var, o.st));
@@ -617,7 +621,7 @@ int mds_classical(const void* Y, int dt, int64_t n, int d, int r, const mds_opts
     const int f64 = o.prec == MDS_PREC_F64;
     CK(launch_rownorm(Y, dt, n, d, f64, W.nrm, o.st));
     tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, W.iota, f64, o))) return s;
+    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, W.iota, f64, f64, o))) return s;
     CK(launch_classical_out(W.B.v, W.B.lam, (int)n, r, f64, X, lambda, o.st));
     return finish(&W.B, W.flag, o);
 }
@@ -643,7 +647,7 @@ int mds_classical_dist(const double* D2, int64_t n, int r, const mds_opts* opts,
     CK(cudaMemcpyAsync(W.B.d_desc, W.B.desc.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, o.st));
     tmark(0, o.st);
     CK(launch_load_dist(D2, W.B.d_desc, W.B.q, W.B.rp, (int)n, W.B.max_tiles, o.st));
-    if ((s = run_eig_batch(W.B, nullptr, 0, 0, nullptr, nullptr, nullptr, 1, o))) return s;
+    if ((s = run_eig_batch(W.B, nullptr, 0, 0, nullptr, nullptr, nullptr, 1, 1, o))) return s;
     CK(launch_classical_out(W.B.v, W.B.lam, (int)n, r, 1, X, lambda, o.st));
     return finish(&W.B, nullptr, o);
 }
@@ -767,8 +771,8 @@ int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_
     // their distances and classical MDS
     CK(launch_rownorm_idx(Y, dt, n, d, landmark_idx, l, f64, W.nrm, o.st));
     tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, landmark_idx, f64, o))) return s;
-    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, !f64, l, r, nullptr, nullptr, nullptr,
+    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, landmark_idx, f64, 1, o))) return s;
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, 0, l, r, nullptr, nullptr, nullptr,
                            nullptr, W.bias, var, o.st));
     CK(launch_affine(Y, dt, n, d, landmark_idx, l, W.B.v, W.B.lam, r, f64, W.ybar, W.ybar_f, W.U, W.U_f, X,
                      o.st));
@@ -816,10 +820,11 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
         nrml = W.nrm_raw;
     }
     tmark(0, o.st);
-    // classical MDS of the landmarks (first subset of Section 3.1)
-    if ((s = run_eig_batch(W.B, Yl, dtl, d, nrml, nullptr, landmark_idx, f64, o))) return s;
+    // classical MDS of the landmarks (first subset of Section 3.1): one small
+    // l x l problem, solved in FP64 whatever the precision of the projection
+    if ((s = run_eig_batch(W.B, Yl, dtl, d, nrml, nullptr, landmark_idx, f64, 1, o))) return s;
     // Gower operator, landmark rows, projection of every row, landmark rows <- X_1
-    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, o.prec != MDS_PREC_F64, l, r,
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, 0, l, r,
                            f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
                            f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
                            var, o.st));
@@ -980,8 +985,8 @@ int mds_interpolate_host(const void* Y, int dt, int64_t n, int d, const int64_t*
     // unrounded landmark rows, then the Gower operator and its operands
     CK(launch_rownorm(H.Ylm, dt, l, d, f64, H.nrm_lm, o.st));
     tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, H.Ylm, dt, d, H.nrm_lm, nullptr, H.iota, f64, o))) return s;
-    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, o.prec != MDS_PREC_F64, l, r,
+    if ((s = run_eig_batch(W.B, H.Ylm, dt, d, H.nrm_lm, nullptr, H.iota, f64, 1, o))) return s;
+    CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, 0, l, r,
                            f64 ? (double*)W.W : nullptr, f64 ? nullptr : (float*)W.W,
                            f64 ? (double*)W.X1 : nullptr, f64 ? nullptr : (float*)W.X1, W.bias,
                            H.var, o.st));
@@ -1234,6 +1239,12 @@ struct mds_dc_plan_s {
     cudaEvent_t join = nullptr; // orders it after the caller's stream
     int* hbuf = nullptr;        // page-locked: status[p], steps[p], flag
     cudaEvent_t ev[6] = {};
+    // device buffers of mds_dc_plan_execute_host (allocated at its first call)
+    void* dY = nullptr;
+    int64_t* down = nullptr;
+    int64_t* danc = nullptr;
+    void* dX = nullptr;
+    double* dvar = nullptr;
 };
 
 namespace {
@@ -1420,6 +1431,48 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
     return batch_status(B, P->hbuf, P->hbuf + P->p, P->hbuf[2 * P->p], P->W.G.mode >= 0 ? P->hbuf[2 * P->p + 1] : 0);
 }
 
+int mds_dc_plan_execute_host(mds_dc_plan P, const void* Y, const int64_t* part_own, const int64_t* anchors, void* X,
+                             double* var, void* stream) {
+    if (!P || !Y || !X || !var || !anchors || (P->ptr[P->p] > 0 && !part_own)) return MDS_ERR_ARG;
+    const size_t es = P->dt == MDS_IN_F64 ? 8 : (P->dt == MDS_IN_F32 ? 4 : 1);
+    const size_t ex = P->o.prec == MDS_PREC_F64 ? 8 : 4;
+    const size_t yb = (size_t)P->n * P->d * es, xb = (size_t)P->n * P->r * ex;
+    const size_t ob = sizeof(int64_t) * (size_t)P->ptr[P->p], ab = sizeof(int64_t) * P->c;
+    if (!P->dY) {
+        // the plan's own device copies of the inputs and outputs; X starts at
+        // zero (rows outside every part are never written)
+        bool ok = cudaMalloc(&P->dY, yb) == cudaSuccess && cudaMalloc((void**)&P->down, ob + 8) == cudaSuccess &&
+                  cudaMalloc((void**)&P->danc, ab) == cudaSuccess && cudaMalloc(&P->dX, xb) == cudaSuccess &&
+                  cudaMalloc((void**)&P->dvar, sizeof(double) * P->r) == cudaSuccess &&
+                  cudaMemset(P->dX, 0, xb) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            cudaFree(P->dY);
+            cudaFree(P->down);
+            cudaFree(P->danc);
+            cudaFree(P->dX);
+            cudaFree(P->dvar);
+            P->dY = P->dX = nullptr;
+            P->down = P->danc = nullptr;
+            P->dvar = nullptr;
+            return MDS_ERR_NOMEM;
+        }
+    }
+    const cudaStream_t ust = stream ? (cudaStream_t)stream : P->o.st;
+    const cudaStream_t st = P->pst;
+    CK(cudaEventRecord(P->join, ust));
+    CK(cudaStreamWaitEvent(st, P->join, 0));
+    CK(cudaMemcpyAsync(P->dY, Y, yb, cudaMemcpyHostToDevice, st));
+    if (ob) CK(cudaMemcpyAsync(P->down, part_own, ob, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P->danc, anchors, ab, cudaMemcpyHostToDevice, st));
+    int s = mds_dc_plan_execute(P, P->dY, P->down, P->danc, P->dX, P->dvar, st);
+    if (s != MDS_OK) return s;
+    CK(cudaMemcpyAsync(X, P->dX, xb, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(var, P->dvar, sizeof(double) * P->r, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return MDS_OK;
+}
+
 int mds_dc_plan_info(mds_dc_plan P, int* cluster, int64_t* graph_nodes, double* trial_ms) {
     if (!P) return MDS_ERR_ARG;
     if (cluster) *cluster = P->cs;
@@ -1440,6 +1493,11 @@ void mds_dc_plan_destroy(mds_dc_plan P) {
     if (P->join) cudaEventDestroy(P->join);
     if (P->ws) cudaFree(P->ws);
     if (P->hbuf) cudaFreeHost(P->hbuf);
+    if (P->dY) cudaFree(P->dY);
+    if (P->down) cudaFree(P->down);
+    if (P->danc) cudaFree(P->danc);
+    if (P->dX) cudaFree(P->dX);
+    if (P->dvar) cudaFree(P->dvar);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     cudaGetLastError();

@@ -118,11 +118,13 @@ cudaError_t launch_rownorm(const void* Y, int dt, int64_t n, int d, int acc_f64,
 cudaError_t launch_rownorm_idx(const void* Y, int dt, int64_t ny, int d, const int64_t* idx, int64_t count,
                                int acc_f64, double* nrm, cudaStream_t st);
 
-// Delta_j tiles for every problem of a batch, written as FP64 into the Q arena,
-// plus per-tile row sums.  acc_f64 selects FP64 (else FP32) dot products.
+// Delta_j tiles for every problem of a batch into the Q arena, plus per-tile
+// row sums.  acc_f64 selects FP64 (else FP32) dot products; Delta is stored
+// as FP64 when acc_f64 or out_f64 is set, else as FP32 rows (row stride
+// 2 * ldq floats) for an FP32 Q.
 cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nrm,
                                   const int64_t* anchors, const int64_t* own,
-                                  const ProbDesc* desc, int p, int max_tiles, int acc_f64,
+                                  const ProbDesc* desc, int p, int max_tiles, int acc_f64, int out_f64,
                                   double* qarena, double* rparena, cudaStream_t st);
 
 // Copy an external n x n FP64 squared-distance matrix into problem 0's Q slot

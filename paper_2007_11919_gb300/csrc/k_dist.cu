@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(256) k_rownorm(const T* __restrict__ Y, int64_
 // accumulating in FP32, as FP32 at the start of each row's storage (row stride
 // 2 * ldq floats), and each tile's row sums into rp[tb * n + a] (the mirrored
 // tile's into rp[ta * n + b], from the tile's column sums; all summed later in
-// a fixed order).
+// a fixed order).  O64 writes Delta as FP64 whatever the accumulation type
+// (FP32 dot products feeding an FP64 eigenproblem).
 
-template <typename T, typename A>
+template <typename T, typename A, bool O64>
 __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
                                                 const double* __restrict__ nrm,
                                                 const int64_t* __restrict__ anchors,
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int a = a0 + ty * 4 + i;
-        if constexpr (sizeof(A) == 8) {
+        if constexpr (O64) {
             double rs = 0.0;
             if (a < n) {
                 const A na = (A)nrm[rowA[ty * 4 + i]];
@@ -139,8 +140,8 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
                         A dist = na + nb[jj] - A(2) * acc[i][jj];
                         dist = dist > A(0) ? dist : A(0);
                         if (a == b) dist = A(0);
-                        Q[(int64_t)a * P.ldq + b] = dist;
-                        rs += dist;
+                        Q[(int64_t)a * P.ldq + b] = (double)dist;
+                        rs += (double)dist;
                     }
                 }
             }
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
         const int b = b0 + tx * 4 + jj;
-        if constexpr (sizeof(A) == 8) {
+        if constexpr (O64) {
             double cs = 0.0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -192,8 +193,8 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
                 if (a < n && b < n) {
                     A dist = (A)nrm[rowA[ty * 4 + i]] + nb[jj] - A(2) * acc[i][jj];
                     dist = dist > A(0) ? dist : A(0);
-                    Q[(int64_t)b * P.ldq + a] = dist;
-                    cs += dist;
+                    Q[(int64_t)b * P.ldq + a] = (double)dist;
+                    cs += (double)dist;
                 }
             }
             csum[ty][tx * 4 + jj] = cs;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
     if (tid < kTile) {
         const int b = b0 + tid;
         if (b < n) {
-            if constexpr (sizeof(A) == 8) {
+            if constexpr (O64) {
                 double s = 0.0;
                 for (int g = 0; g < 16; ++g) s += csum[g][tid];
                 rp[(int64_t)ta * n + b] = s;
@@ -484,27 +485,27 @@ cudaError_t launch_rownorm_idx(const void* Y, int dt, int64_t ny, int d, const i
     return rownorm_any(Y, dt, count, d, acc_f64, nrm, idx, ny, st);
 }
 
+template <typename T>
+static void sqdist_any(const T* Y, int d, const double* nrm, const int64_t* anchors, const int64_t* own,
+                       const ProbDesc* desc, int acc_f64, int out_f64, double* qarena, double* rparena, dim3 grid,
+                       cudaStream_t st) {
+    if (acc_f64) k_sqdist<T, double, true><<<grid, 256, 0, st>>>(Y, d, nrm, anchors, own, desc, qarena, rparena);
+    else if (out_f64) k_sqdist<T, float, true><<<grid, 256, 0, st>>>(Y, d, nrm, anchors, own, desc, qarena, rparena);
+    else k_sqdist<T, float, false><<<grid, 256, 0, st>>>(Y, d, nrm, anchors, own, desc, qarena, rparena);
+}
+
 cudaError_t launch_sqdist_batched(const void* Y, int dt, int d, const double* nrm,
                                   const int64_t* anchors, const int64_t* own,
-                                  const ProbDesc* desc, int p, int max_tiles, int acc_f64,
+                                  const ProbDesc* desc, int p, int max_tiles, int acc_f64, int out_f64,
                                   double* qarena, double* rparena, cudaStream_t st) {
     if (p <= 0) return cudaSuccess;
-    dim3 grid((unsigned)(max_tiles * (max_tiles + 1) / 2), (unsigned)p), block(256);
-    if (acc_f64) {
-        if (dt == MDS_IN_F64)
-            k_sqdist<double, double><<<grid, block, 0, st>>>((const double*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-        else if (dt == MDS_IN_F32)
-            k_sqdist<float, double><<<grid, block, 0, st>>>((const float*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-        else
-            k_sqdist<uint8_t, double><<<grid, block, 0, st>>>((const uint8_t*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-    } else {
-        if (dt == MDS_IN_F64)
-            k_sqdist<double, float><<<grid, block, 0, st>>>((const double*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-        else if (dt == MDS_IN_F32)
-            k_sqdist<float, float><<<grid, block, 0, st>>>((const float*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-        else
-            k_sqdist<uint8_t, float><<<grid, block, 0, st>>>((const uint8_t*)Y, d, nrm, anchors, own, desc, qarena, rparena);
-    }
+    const dim3 grid((unsigned)(max_tiles * (max_tiles + 1) / 2), (unsigned)p);
+    if (dt == MDS_IN_F64)
+        sqdist_any((const double*)Y, d, nrm, anchors, own, desc, acc_f64, out_f64, qarena, rparena, grid, st);
+    else if (dt == MDS_IN_F32)
+        sqdist_any((const float*)Y, d, nrm, anchors, own, desc, acc_f64, out_f64, qarena, rparena, grid, st);
+    else
+        sqdist_any((const uint8_t*)Y, d, nrm, anchors, own, desc, acc_f64, out_f64, qarena, rparena, grid, st);
     note_launch(1);
     return cudaGetLastError();
 }

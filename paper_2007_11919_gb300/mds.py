@@ -439,6 +439,7 @@ class DcPlan:
         for name, res, args in [
             ("mds_dc_plan_create", _I, [_I64, _I, _I, _I, _P, _I, _I, _P, _I, _P]),
             ("mds_dc_plan_execute", _I, [_P, _P, _P, _P, _P, _P, _P]),
+            ("mds_dc_plan_execute_host", _I, [_P, _P, _P, _P, _P, _P, _P]),
             ("mds_dc_plan_info", _I, [_P, _P, _P, _P]),
             ("mds_dc_plan_destroy", None, [_P]),
         ]:
@@ -465,6 +466,26 @@ class DcPlan:
         st = stream if stream is not None else torch.cuda.current_stream(Y.device)
         _check(_lib().mds_dc_plan_execute(self.handle, _ptr(Y), _ptr(part_own), _ptr(anchors), _ptr(X), _ptr(var),
                                           ctypes.c_void_p(st.cuda_stream)), "mds_dc_plan_execute")
+        return X, var
+
+    def execute_host(self, Y, anchors, part_own, X=None, var=None, stream=None):
+        """The same run on host data: ``Y``, ``anchors`` and ``part_own`` are
+        CPU tensors (pin them for asynchronous copies); returns CPU tensors
+        (X pinned unless given).  The plan copies into device buffers it
+        owns, replays its graph, and copies the results back."""
+        if not (isinstance(Y, torch.Tensor) and not Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()):
+            raise ValueError("data must be a contiguous 2-D CPU tensor")
+        anc = torch.as_tensor(anchors, dtype=torch.int64).contiguous()
+        own = torch.as_tensor(part_own, dtype=torch.int64).contiguous()
+        if anc.is_cuda or own.is_cuda:
+            raise ValueError("anchors and part_own must be CPU tensors")
+        if X is None:
+            X = torch.empty((self.n, self.r), dtype=_xdtype(self.prec), pin_memory=True)
+        if var is None:
+            var = torch.empty(self.r, dtype=torch.float64)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(_lib().mds_dc_plan_execute_host(self.handle, _ptr(Y), _ptr(own), _ptr(anc), _ptr(X), _ptr(var),
+                                               ctypes.c_void_p(st.cuda_stream)), "mds_dc_plan_execute_host")
         return X, var
 
     def info(self):

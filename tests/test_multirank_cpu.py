@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
         ms = bench.max_over_ranks(local_ms)
         value = bench.job_throughput(wsz, 100_000, ms)
         seed = bench.rank_seed(0, r)
-        w, Y, part = bench.make_workload("dc", seed, 3000)
+        w, _, Y, part = bench.make_workload("dc", seed, 3000)
         out.put((r, wsz, local, ms, value, seed, float(Y[:4].sum()), part.p, int(part.ptr[-1]) + len(part.anchors)))
     finally:
         tdist.destroy_process_group()

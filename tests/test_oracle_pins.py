@@ -253,6 +253,63 @@ def test_dc_exact_recovery():
     assert err_dc_exact() < 1e-10
 
 
+def err_sign_convention(sign=O.sign_convention):
+    """Columns whose entry of largest magnitude is known by construction:
+    col 0 has its largest |.| at row 1 (negative: flipped), col 1 at row 0
+    (positive: kept), col 2 a tie of |.| = 0.5 between rows 1 (negative) and
+    3 (positive) that the lowest row index decides (flipped), col 3 a tie
+    between rows 0 (positive) and 2 (negative) (kept)."""
+    V = np.array([[0.1, 0.9, 0.2, 0.5],
+                  [-0.7, -0.3, -0.5, 0.1],
+                  [0.2, 0.1, 0.1, -0.5],
+                  [0.3, 0.2, 0.5, 0.0]])
+    want = V * np.array([-1.0, 1.0, -1.0, 1.0])[None, :]
+    return float(np.max(np.abs(sign(V) - want)))
+
+
+def test_sign_convention_hand_built():
+    assert err_sign_convention() == 0.0
+    # the input is not modified, and a column of one sign is a fixed point
+    V = -np.eye(3)
+    assert np.array_equal(O.sign_convention(V), np.eye(3)) and np.array_equal(V, -np.eye(3))
+
+
+def test_planted_sign_convention_signed_max():
+    def bad(V):                                   # largest signed entry instead of largest |.|
+        V = V.copy()
+        for i in range(V.shape[1]):
+            if V[int(np.argmax(V[:, i])), i] < 0:
+                V[:, i] = -V[:, i]
+        return V
+    assert err_sign_convention(sign=bad) > 0.1
+
+    def bad_tie(V):                               # highest index wins a tie
+        V = V.copy()
+        for i in range(V.shape[1]):
+            a = np.abs(V[:, i])
+            k = len(a) - 1 - int(np.argmax(a[::-1]))
+            if V[k, i] < 0:
+                V[:, i] = -V[:, i]
+        return V
+    assert err_sign_convention(sign=bad_tie) > 0.1
+
+
+def test_dc_parts_exact_recovery():
+    """A subset of the parts (the first one not included), each solved once:
+    on rank-r data its aligned rows are the planted points up to one
+    orthogonal map, and they equal the same rows of the whole computation."""
+    rng = np.random.default_rng(6)
+    n, r = 1500, 4
+    Zc, Y = planted_rank_r(n, r, 8, rng)
+    part = W.partitions_uneven(n, 12, 200, 330, 6)
+    got = O.divide_conquer_parts(Y, part.anchors, part.ptr, part.own, [2, part.p - 1], r)
+    rows = np.concatenate([g[0] for g in got])
+    Xs = np.vstack([g[1] for g in got])
+    assert O.aligned_rel_error(Xs, Zc[rows]) < 1e-10
+    X, _, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, r)
+    assert np.array_equal(X[rows], Xs)
+
+
 def test_dc_part_matches_whole():
     rng = np.random.default_rng(17)
     Y = rng.standard_normal((900, 6)) * np.array([4, 3, 2, 1, 1, 1.0])

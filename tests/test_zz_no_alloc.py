@@ -16,7 +16,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "f32": 1e-5}
+TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -28,8 +28,10 @@ def gb():
     return G
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "bf16"])
 def test_static_matches_allocating_entry_point(gb, prec):
+    """BF16 models also stage the rounded rows in the array; FP32/FP64 models
+    only the row norms."""
     from paper_2007_11919_gb300 import mds as M
     dt = np.float64 if prec == "f64" else np.float32
     Y = W.gaussian_dominant(4000, 40, 5, seed=31, dtype=dt)

@@ -246,7 +246,7 @@ def serve_requests(count: int, lo: int, hi: int, rate_per_s: float, seed: int):
 @dataclasses.dataclass(frozen=True)
 class Workload:
     name: str
-    kind: str          # "interp", "dc", "serve"
+    kind: str          # "interp", "dc", "affine", "serve"
     n: int
     d: int
     r: int
@@ -268,6 +268,10 @@ INTERP_BF16 = Workload("interp_bf16_n1000000_d100_l1000_r10", "interp", 1_000_00
 # compared against.
 INTERP_F32 = Workload("interp_f32_n1000000_d100_l1000_r10", "interp", 1_000_000, 100, 10, "f32",
                       l=1000)
+# The same data by the affine form of Eq. (2) (rows given by coordinates): one
+# pass over Y after the landmark eigenproblem.
+INTERP_AFFINE_F32 = Workload("affine_f32_n1000000_d100_l1000_r10", "affine", 1_000_000, 100, 10, "f32",
+                             l=1000)
 SERVE_BF16 = Workload("serve_bf16_d100_l500r2_l1000r5_l2000r10_req1-50000", "serve", 200_000, 100, 10,
                       "bf16", l=2000)
 # Resident models of the serving workload: (landmarks, r).
@@ -288,7 +292,7 @@ def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
         return gaussian_dominant(n, w.d, 3, seed, dtype=np.float64)
     if w.name == DC_F32.name:
         return gaussian_dominant(n, w.d, 5, seed, dtype=np.float32)
-    if w.name in (INTERP_BF16.name, INTERP_F32.name):
+    if w.name in (INTERP_BF16.name, INTERP_F32.name, INTERP_AFFINE_F32.name):
         return gaussian_mixture(n, w.d, 4, 5.0, seed, dtype=np.float32)
     if w.name == SERVE_BF16.name:
         return gaussian_graded(n, w.d, seed)
