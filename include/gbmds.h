@@ -174,6 +174,45 @@ size_t mds_interpolate_affine_workspace_size(int64_t n, int d, int l, int r, int
 int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
                            int r, const mds_opts* opts, void* X, double* var);
 
+/* MaxMin choice of l landmarks (Section 3.1, the LMDS variant of the first
+ * subset): starting from row `first`, each next landmark is the row of Y
+ * whose smallest squared Euclidean distance to the landmarks already chosen
+ * is largest; ties go to the lowest row index; a chosen row is never chosen
+ * again (a duplicate of a chosen row can be).  idx_out (device, l int64)
+ * receives the rows in the order chosen; pass them to mds_interpolate as
+ * landmark_idx.  The argmax is taken on FP64 distances: exact integer sums
+ * for MDS_IN_U8 rows, the FP64 difference form sum_k (y_k - l_k)^2 for FP64
+ * rows, and for FP32 rows an FP32 difference form whose rounding bound
+ * proves the running minimum unchanged, else the FP64 difference form.
+ * opts->prec is ignored; opts->workspace holds
+ * mds_landmarks_maxmin_workspace_size(n, d) bytes (n FP64 running minima).
+ * Errors: MDS_ERR_ARG for l outside [1, n] or first outside [0, n);
+ * MDS_ERR_UNSUPPORTED for d > 12288. */
+size_t mds_landmarks_maxmin_workspace_size(int64_t n, int d);
+int mds_landmarks_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t first, const mds_opts* opts,
+                         int64_t* idx_out);
+
+/* Pivot MDS (Section 3.1): with C the n x l block of Q = -1/2 P Delta P
+ * (all n points) between every point and the l pivots pivot_idx (device, l
+ * int64 rows), the SVD C = U Sigma W^T approximates the eigendecomposition of
+ * Q: X = U_r diag(lambda_r)^{1/2} (n x r: double for MDS_PREC_F64, else
+ * float), lambda_i = sigma_i sqrt(n / l) (random pivots give
+ * V_P^T V_P ~ (l/n) I, so C C^T ~ (l/n) Q^2), var (r) = lambda / n.  Rows
+ * are Euclidean coordinates, so C = Y_c P_c^T (Y_c the rows centred at their
+ * mean, P_c the centred pivot rows) and C^T C = P_c S P_c^T with
+ * S = Y_c^T Y_c: the call computes the column means and S of Y, the l x l
+ * matrix C^T C and its top-r eigenpairs in FP64, and one pass
+ * X = Y_c M, M = P_c^T W_r Sigma_r^{-1} Lambda_r^{1/2} (d x r).  Each column
+ * of X has its entry of largest magnitude positive (lowest row on a tie).
+ * opts->prec: MDS_PREC_F64 (FP64 throughout) or MDS_PREC_F32 (the scatter
+ * matrix from FP32 products summed in double-FP32, the projection in FP32;
+ * the means, C^T C and the eigen-solve in FP64); else MDS_ERR_UNSUPPORTED.
+ * Requires 1 <= r <= min(l, d, 32); MDS_ERR_RANK if sigma_r^2 <=
+ * rank_tol * sigma_1^2. */
+size_t mds_pivot_workspace_size(int64_t n, int d, int l, int r, int prec);
+int mds_pivot(const void* Y, int dt, int64_t n, int d, const int64_t* pivot_idx, int l, int r, const mds_opts* opts,
+              void* X, double* var);
+
 /* Gower's formula, Eq. (2), for m new rows Ynew (m x d, dtype dt) against a
  * stored model; X is m x r.  opts->prec must equal the model's precision.
  * Equal inputs give bitwise-equal outputs regardless of what else is batched

@@ -255,7 +255,7 @@ struct GramOp {
 // vector work run in double-FP32 (with FP64 scalars).
 int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
                   const int64_t* anchors, const int64_t* own, int acc_f64, int eig_f64, const Opts& o,
-                  bool upload = true, const GramOp* gram = nullptr) {
+                  bool upload = true, const GramOp* gram = nullptr, bool center = true) {
     if (upload) {
         CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
         CK(cudaMemcpyAsync(B.d_order, B.order.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
@@ -283,7 +283,8 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     // products and vector work in double-FP32.
     const int q_f32 = !eig_f64;
     B.q_bytes = q_f32 ? 4 : 8;
-    CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, q_f32, o.st));
+    // (center = false: Q is already in the arena, FP64, e.g. pivot MDS's C^T C)
+    if (center) CK(launch_center_batched(B.d_desc, B.p, B.max_n, B.q, B.rp, B.rm, B.grand, q_f32, o.st));
     LanczosArgs a;
     a.desc = B.d_desc;
     a.p = B.p;
@@ -592,6 +593,45 @@ int mds_last_stats(mds_stats* out) {
     return MDS_OK;
 }
 
+// ------------------------------------------------------ MaxMin landmarks
+
+static size_t maxmin_layout(MaxminWs& M, char* base, int64_t n) {
+    Arena A{base, 0};
+    M.mind = A.take<double>(n);
+    M.cur = A.take<int64_t>(1);
+    M.part_v = A.take<double>(kMaxminGridCap);
+    M.part_i = A.take<int64_t>(kMaxminGridCap);
+    M.counter = A.take<unsigned>(1);
+    return A.off;
+}
+
+size_t mds_landmarks_maxmin_workspace_size(int64_t n, int d) {
+    if (n <= 0 || d <= 0) return 0;
+    MaxminWs M;
+    return maxmin_layout(M, nullptr, n) + 256;
+}
+
+int mds_landmarks_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t first, const mds_opts* opts,
+                         int64_t* idx_out) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!Y || !idx_out || !valid_dt(dt) || n < 1 || d <= 0 || l < 1 || l > n || first < 0 || first >= n)
+        return MDS_ERR_ARG;
+    if (d > kMaxminD) return MDS_ERR_UNSUPPORTED;
+    MaxminWs M;
+    const size_t need = maxmin_layout(M, nullptr, n);
+    if ((s = check_ws(o, need))) return s;
+    maxmin_layout(M, o.ws, n);
+    begin_call(o.st);
+    tmark(0, o.st);
+    CK(launch_maxmin(Y, dt, n, d, l, first, M, idx_out, o.st));
+    tmark(1, o.st);   // stage "dist": the l - 1 distance passes and picks
+    tmark(2, o.st);
+    tmark(3, o.st);
+    return finish(nullptr, nullptr, o);
+}
+
 // ------------------------------------------------------------- classical
 
 size_t mds_classical_workspace_size(int64_t n, int d, int r, int prec) {
@@ -720,23 +760,29 @@ static int make_model(InterpWs& W, int kind, const Opts& o, int l, int d, int r,
 
 struct AffineWs {
     int* flag;
-    double* nrm;      // n: norms of the landmark rows (at their row indices)
+    double* Lg;       // l x d: the landmark rows, gathered as FP64
+    int64_t* iota;    // l
+    double* nrm;      // l: their squared norms (the landmark problem indexes Lg through iota)
     Batch B;
     double* ybar;     // d
     float* ybar_f;
+    double* scale;    // r: Lambda^{-1/2}
     double* U;        // d x r
     float* U_f;
-    double* bias;     // r: the Gower bias (not used by the affine form)
+    double* bias;     // r: the Gower bias (written with the variances; not used by the affine form)
 };
 
-static size_t affine_layout(AffineWs& W, char* base, int64_t n, int d, int l, int r, int mmax) {
+static size_t affine_layout(AffineWs& W, char* base, int d, int l, int r, int mmax) {
     Arena A{base, 0};
     W.flag = A.take<int>(1);
-    W.nrm = A.take<double>(n);
-    plan_batch(W.B, {l}, {0}, 0, r, mmax, n);
+    W.Lg = A.take<double>((size_t)l * d);
+    W.iota = A.take<int64_t>(l);
+    W.nrm = A.take<double>(l);
+    plan_batch(W.B, {l}, {0}, 0, r, mmax, l);
     carve_batch(W.B, A);
     W.ybar = A.take<double>(d);
     W.ybar_f = A.take<float>(d);
+    W.scale = A.take<double>(r);
     W.U = A.take<double>((size_t)d * r);
     W.U_f = A.take<float>((size_t)d * r);
     W.bias = A.take<double>(r);
@@ -747,7 +793,7 @@ size_t mds_interpolate_affine_workspace_size(int64_t n, int d, int l, int r, int
     if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0 || r > kMaxR) return 0;
     if (prec != MDS_PREC_F64 && prec != MDS_PREC_F32) return 0;
     AffineWs W;
-    return affine_layout(W, nullptr, n, d, l, r, kDefaultSteps) + 256;
+    return affine_layout(W, nullptr, d, l, r, kDefaultSteps) + 256;
 }
 
 int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l, int r,
@@ -760,22 +806,112 @@ int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_
         return MDS_ERR_ARG;
     if (o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) return MDS_ERR_UNSUPPORTED;
     AffineWs W;
-    const size_t need = affine_layout(W, nullptr, n, d, l, r, o.mmax);
+    const size_t need = affine_layout(W, nullptr, d, l, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
-    if (affine_layout(W, o.ws, n, d, l, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
+    if (affine_layout(W, o.ws, d, l, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
     begin_call(o.st);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(launch_check_idx(landmark_idx, l, n, W.flag, o.st));
-    // the landmark problem of mds_interpolate: norms of the landmark rows,
-    // their distances and classical MDS
-    CK(launch_rownorm_idx(Y, dt, n, d, landmark_idx, l, f64, W.nrm, o.st));
+    // the landmark problem of mds_interpolate on the gathered landmark rows
+    // (FP64 copies of the inputs: the same distances in the same arithmetic)
+    CK(launch_gather_rows(Y, dt, n, d, landmark_idx, l, 1, W.Lg, nullptr, nullptr, o.st));
+    CK(launch_iota(W.iota, l, o.st));
+    CK(launch_rownorm(W.Lg, MDS_IN_F64, l, d, f64, W.nrm, o.st));
     tmark(0, o.st);
-    if ((s = run_eig_batch(W.B, Y, dt, d, W.nrm, nullptr, landmark_idx, f64, 1, o))) return s;
+    if ((s = run_eig_batch(W.B, W.Lg, MDS_IN_F64, d, W.nrm, nullptr, W.iota, f64, 1, o))) return s;
     CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, 0, l, r, nullptr, nullptr, nullptr,
                            nullptr, W.bias, var, o.st));
-    CK(launch_affine(Y, dt, n, d, landmark_idx, l, W.B.v, W.B.lam, r, f64, W.ybar, W.ybar_f, W.U, W.U_f, X,
+    CK(launch_affine(Y, dt, n, d, W.Lg, l, W.B.v, W.B.lam, r, f64, W.scale, W.ybar, W.ybar_f, W.U, W.U_f, X,
                      o.st));
+    return finish(&W.B, W.flag, o);
+}
+
+// ---------------------------------------------------------------- pivot MDS
+
+struct PivotWs {
+    int* flag;
+    double* cpart;    // column-sum partials
+    double* mean;     // d: mean of all n rows
+    float* mean_f;
+    double* spart;    // scatter partials
+    double* S;        // d x d
+    double* Lg;       // l x d: the pivot rows (FP64)
+    double* T;        // l x d: (Lg - mean) S
+    Batch B;          // the l x l problem C^T C
+    double* scale;    // r
+    double* U;        // d x r
+    float* U_f;
+    double* sg_v;     // sign-convention partials
+    int64_t* sg_i;
+    unsigned* sg_cnt;
+    double* sign;     // r
+};
+
+static size_t pivot_layout(PivotWs& W, char* base, int64_t n, int d, int l, int r, int mmax) {
+    Arena A{base, 0};
+    W.flag = A.take<int>(1);
+    W.cpart = A.take<double>(colmean_part_doubles(n, d));
+    W.mean = A.take<double>(d);
+    W.mean_f = A.take<float>(d);
+    W.spart = A.take<double>(scatter_part_doubles(n, d));
+    W.S = A.take<double>((size_t)d * d);
+    W.Lg = A.take<double>((size_t)l * d);
+    W.T = A.take<double>((size_t)l * d);
+    plan_batch(W.B, {l}, {0}, 0, r, mmax, l);
+    carve_batch(W.B, A);
+    W.scale = A.take<double>(r);
+    W.U = A.take<double>((size_t)d * r);
+    W.U_f = A.take<float>((size_t)d * r);
+    const int g = colsign_grid(n);
+    W.sg_v = A.take<double>((size_t)g * r);
+    W.sg_i = A.take<int64_t>((size_t)g * r);
+    W.sg_cnt = A.take<unsigned>(1);
+    W.sign = A.take<double>(r);
+    return A.off;
+}
+
+size_t mds_pivot_workspace_size(int64_t n, int d, int l, int r, int prec) {
+    if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0 || r > kMaxR) return 0;
+    if (prec != MDS_PREC_F64 && prec != MDS_PREC_F32) return 0;
+    PivotWs W;
+    return pivot_layout(W, nullptr, n, d, l, r, kDefaultSteps) + 256;
+}
+
+int mds_pivot(const void* Y, int dt, int64_t n, int d, const int64_t* pivot_idx, int l, int r, const mds_opts* opts,
+              void* X, double* var) {
+    Opts o;
+    int s = read_opts(opts, &o);
+    if (s) return s;
+    if (!Y || !X || !var || !pivot_idx || !valid_dt(dt) || n < 2 || d <= 0 || l < 1 || l > n || l > kMaxEigN ||
+        r <= 0 || r > kMaxR || r > l || r > d)
+        return MDS_ERR_ARG;
+    if (o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) return MDS_ERR_UNSUPPORTED;
+    PivotWs W;
+    const size_t need = pivot_layout(W, nullptr, n, d, l, r, o.mmax);
+    if ((s = check_ws(o, need))) return s;
+    if (pivot_layout(W, o.ws, n, d, l, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
+    begin_call(o.st);
+    const int f64 = o.prec == MDS_PREC_F64;
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(cudaMemsetAsync(W.sg_cnt, 0, sizeof(unsigned), o.st));
+    CK(launch_check_idx(pivot_idx, l, n, W.flag, o.st));
+    // the centre and the scatter matrix of all n rows, the pivot rows
+    CK(launch_colmean(Y, dt, n, d, W.cpart, W.mean, W.mean_f, o.st));
+    CK(launch_gather_rows(Y, dt, n, d, pivot_idx, l, 1, W.Lg, nullptr, nullptr, o.st));
+    tmark(0, o.st);
+    CK(launch_scatter(Y, dt, n, d, W.mean, f64, W.spart, W.S, o.st));
+    // C^T C = P_c S P_c^T into the eigen-solver's Q slot (FP64)
+    CK(launch_gemm_nt(W.Lg, d, W.mean, W.S, d, nullptr, l, d, d, W.T, d, o.st));
+    const ProbDesc& P0 = W.B.desc[0];
+    CK(launch_gemm_nt(W.T, d, nullptr, W.Lg, d, W.mean, l, l, d, W.B.q + P0.q_off, P0.ldq, o.st));
+    tmark(1, o.st);
+    if ((s = run_eig_batch(W.B, nullptr, 0, 0, nullptr, nullptr, nullptr, 1, 1, o, true, nullptr, false))) return s;
+    // M = P_c^T W_r Sigma_r^{-1} Lambda_r^{1/2}; X = Y_c M; the sign convention
+    CK(launch_pivot_scale(W.B.lam, r, n, l, W.scale, var, o.st));
+    CK(launch_axes(W.Lg, l, d, W.mean, W.B.v, W.scale, r, W.U, W.U_f, o.st));
+    CK(launch_affine_project(Y, dt, n, d, W.mean, W.mean_f, W.U, W.U_f, r, f64, X, o.st));
+    CK(launch_colsign(X, f64, n, r, W.sg_v, W.sg_i, W.sg_cnt, W.sign, o.st));
     return finish(&W.B, W.flag, o);
 }
 

@@ -186,12 +186,41 @@ cudaError_t launch_interp_model(const double* V, const double* lam, const double
                                 double* x1_64, float* x1_32, double* bias, double* var_out,
                                 cudaStream_t st);
 
-// Affine form of Eq. (2) for coordinate rows: y_L (FP64 and FP32 copies),
+// Affine form of Eq. (2) for coordinate rows, from the gathered landmark rows
+// Lg (dense l x d FP64): y_L (FP64 and FP32 copies), scale = Lambda^{-1/2},
 // U_r = L_c^T V Lambda^{-1/2} (d x r, both copies) and X = (Y - y_L) U_r for
 // all n rows (double X when f64, else float).
-cudaError_t launch_affine(const void* Y, int dt, int64_t n, int d, const int64_t* idx, int l, const double* V,
-                          const double* lam, int r, int f64, double* ybar, float* ybar_f, double* U, float* U_f,
-                          void* X, cudaStream_t st);
+cudaError_t launch_affine(const void* Y, int dt, int64_t n, int d, const double* Lg, int l, const double* V,
+                          const double* lam, int r, int f64, double* scale, double* ybar, float* ybar_f, double* U,
+                          float* U_f, void* X, cudaStream_t st);
+// The pieces (k_affine.cu): row mean of a dense l x d FP64 matrix; axes
+// U[k][i] = scale_i sum_j (L[j][k] - c_k) V[j][i]; projection X = (Y - 1 c^T) U
+// (FP64 when f64, else FP32 with the FP32 copies cen_f, U_f).
+cudaError_t launch_rows_mean(const double* L, int l, int d, double* mean, float* mean_f, cudaStream_t st);
+cudaError_t launch_axes(const double* L, int l, int d, const double* c, const double* V, const double* scale, int r,
+                        double* U, float* U_f, cudaStream_t st);
+cudaError_t launch_affine_project(const void* Y, int dt, int64_t n, int d, const double* cen, const float* cen_f,
+                                  const double* U, const float* U_f, int r, int f64, void* X, cudaStream_t st);
+
+// Pivot MDS pieces (k_pivot.cu): column means of all n rows (partials of
+// colmean_part_doubles(n, d)), the scatter matrix S = Y_c^T Y_c (d x d FP64,
+// partials of scatter_part_doubles(n, d); f64 = FP64 products, else FP32
+// products in double-FP32 sums), FP64 products C = (A - 1 ca^T)(B - 1 cb^T)^T,
+// the scale factors from the eigenvalues of C^T C, and the sign convention on
+// the columns of X (partials of colsign_grid(n) x r pairs).
+size_t colmean_part_doubles(int64_t n, int d);
+size_t scatter_part_doubles(int64_t n, int d);
+int colsign_grid(int64_t n);
+cudaError_t launch_colmean(const void* Y, int dt, int64_t n, int d, double* part, double* mean, float* mean_f,
+                           cudaStream_t st);
+cudaError_t launch_scatter(const void* Y, int dt, int64_t n, int d, const double* mean, int f64, double* part,
+                           double* S, cudaStream_t st);
+cudaError_t launch_gemm_nt(const double* A, int lda, const double* ca, const double* B, int ldb, const double* cb,
+                           int m, int nb, int K, double* C, int ldc, cudaStream_t st);
+cudaError_t launch_pivot_scale(const double* mu, int r, int64_t n, int l, double* scale, double* var,
+                               cudaStream_t st);
+cudaError_t launch_colsign(void* X, int out_f64, int64_t n, int r, double* part_v, int64_t* part_i, unsigned* counter,
+                           double* sign, cudaStream_t st);
 
 // Gather rows Y[idx[i]] into a dense l x d matrix of the accumulation type.
 // For dt == kDtBF16, Y is the split planes of an ny-row matrix.
@@ -297,6 +326,22 @@ cudaError_t launch_encode_parts_u8(int mode, const uint8_t* Y, int d, const int6
 cudaError_t launch_gram_tck(int mode, const void* ops, int64_t slots, int d, const float* nrm, const int4* units,
                             int nunits, const ProbDesc* desc, double* qarena, double* rparena, int* err,
                             cudaStream_t st);
+
+// MaxMin landmark choice (k_maxmin.cu): running minima (n FP64), the newest
+// landmark row, per-CTA best pairs (maxmin_grid() entries each) and the
+// arrival counter of the last-CTA reduction.  idx_out receives the l picks.
+constexpr int kMaxminD = 12288;      // widest rows (the landmark row is staged in shared memory as FP64 and as T)
+constexpr int kMaxminGridCap = 4096; // most CTAs of a round (partials sized for this many)
+struct MaxminWs {
+    double* mind;
+    int64_t* cur;
+    double* part_v;
+    int64_t* part_i;
+    unsigned* counter;
+};
+int maxmin_grid();
+cudaError_t launch_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t first, MaxminWs ws,
+                          int64_t* idx_out, cudaStream_t st);
 
 // Host side (api.cu): queue an embedding against a model without waiting.
 int embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, char* ws, cudaStream_t st, void* X,

@@ -7,6 +7,11 @@
 // with y_L the landmark mean and V_r, Lambda_r the landmarks' classical-MDS
 // eigenpairs.  The landmark rows get X_1 = V_r Lambda_r^{1/2} back.  One pass
 // over Y (HBM-bound) instead of n x l distances.
+//
+// The same two pieces serve pivot MDS (k_pivot.cu): the axes of a set of
+// centred rows weighted by eigenvectors, and the projection (Y - 1 c^T) U.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace gbmds {
@@ -15,52 +20,138 @@ namespace {
 __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
 
-// Row idx[j] of Y, clamped into [0, ny): a bad index (flagged by the index
-// check, which fails the call) never reads outside Y.
-__device__ __forceinline__ int64_t clamp_row(int64_t row, int64_t ny) { return row < 0 ? 0 : (row >= ny ? ny - 1 : row); }
+constexpr int kAxThreads = 256;
 
-// y_L[k] = mean over the landmark rows of y_jk, in FP64 (one thread per column).
-template <typename T>
-__global__ void __launch_bounds__(256) k_affine_mean(const T* __restrict__ Y, int64_t ny, int d,
-                                                     const int64_t* __restrict__ idx, int l,
-                                                     double* __restrict__ ybar, float* __restrict__ ybar_f) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d) return;
+// mean[k] = (1/l) sum_j L[j][k] over the rows of a dense l x d FP64 matrix:
+// one CTA per column, the rows split over the threads, a fixed-order tree sum.
+__global__ void __launch_bounds__(kAxThreads) k_rows_mean(const double* __restrict__ L, int l, int d,
+                                                          double* __restrict__ mean, float* __restrict__ mean_f) {
+    __shared__ double red[kAxThreads];
+    const int k = blockIdx.x;
     double s = 0.0;
-    for (int j = 0; j < l; ++j) s += load_as<double, T>(Y + clamp_row(idx[j], ny) * d + k);
-    const double m = s / l;
-    ybar[k] = m;
-    ybar_f[k] = (float)m;
+    for (int j = threadIdx.x; j < l; j += kAxThreads) s += L[(int64_t)j * d + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kAxThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double m = red[0] / l;
+        mean[k] = m;
+        if (mean_f) mean_f[k] = (float)m;
+    }
 }
 
-// U[k][i] = sum_j (y_jk - y_L[k]) V[j][i] / sqrt(lambda_i), in FP64 (one
-// thread per entry of the d x r matrix U, row-major).
-template <typename T>
-__global__ void __launch_bounds__(256) k_affine_axes(const T* __restrict__ Y, int64_t ny, int d,
-                                                     const int64_t* __restrict__ idx, int l,
-                                                     const double* __restrict__ ybar,
-                                                     const double* __restrict__ V,
-                                                     const double* __restrict__ lam, int r,
+// U[k][i] = scale_i sum_j (L[j][k] - c_k) V[j][i] (d x r, row-major), FP64:
+// one CTA per column k, the rows split over the threads, r partial sums per
+// thread, a fixed-order tree sum per output.
+__global__ void __launch_bounds__(kAxThreads) k_axes(const double* __restrict__ L, int l, int d,
+                                                     const double* __restrict__ c, const double* __restrict__ V,
+                                                     const double* __restrict__ scale, int r,
                                                      double* __restrict__ U, float* __restrict__ U_f) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)d * r) return;
-    const int k = (int)(e / r), i = (int)(e % r);
-    const double m = ybar[k];
-    double s = 0.0;
-    for (int j = 0; j < l; ++j)
-        s = fma(load_as<double, T>(Y + clamp_row(idx[j], ny) * d + k) - m, V[(int64_t)j * r + i], s);
-    const double u = s / sqrt(lam[i]);
-    U[e] = u;
-    U_f[e] = (float)u;
+    __shared__ double red[kAxThreads];
+    const int k = blockIdx.x;
+    const double ck = c[k];
+    double acc[kMaxR];
+#pragma unroll
+    for (int i = 0; i < kMaxR; ++i) acc[i] = 0.0;
+    for (int j = threadIdx.x; j < l; j += kAxThreads) {
+        const double x = L[(int64_t)j * d + k] - ck;
+        const double* v = V + (int64_t)j * r;
+#pragma unroll
+        for (int i = 0; i < kMaxR; ++i)
+            if (i < r) acc[i] = fma(x, v[i], acc[i]);
+    }
+    for (int i = 0; i < r; ++i) {
+        red[threadIdx.x] = acc[i];
+        __syncthreads();
+        for (int h = kAxThreads / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double u = red[0] * scale[i];
+            U[(int64_t)k * r + i] = u;
+            if (U_f) U_f[(int64_t)k * r + i] = (float)u;
+        }
+        __syncthreads();
+    }
 }
 
-// X[row] = (y_row - y_L) U: one warp per row, lanes over the columns (the
-// row's loads coalesce), r accumulators per lane in the arithmetic type A,
-// then one warp sum per output column.  U and y_L are small and stay in L1.
+// scale_i = 1 / sqrt(lambda_i): the affine form's U_r = L_c^T V_r Lambda_r^{-1/2}.
+__global__ void k_inv_sqrt(const double* __restrict__ lam, int r, double* __restrict__ scale) {
+    const int i = threadIdx.x;
+    if (i < r) scale[i] = 1.0 / sqrt(lam[i]);
+}
+
+// X[row] = (y_row - c) U for FP32 rows with d <= 128, d a multiple of 4 and
+// a 16-byte aligned base: one warp per group of ROWS consecutive rows, lane q
+// owns the columns 4q .. 4q + 3 and keeps their rows of U (r <= RB columns)
+// and of the centre in registers; one 16-byte streaming load per row and
+// lane (ROWS of them in flight), 4 RB FMAs, then one warp sum per output.
+template <int RB, int ROWS>
+__global__ void __launch_bounds__(256) k_affine_project_f4(const float* __restrict__ Y, int64_t n, int d,
+                                                           const float* __restrict__ cen,
+                                                           const float* __restrict__ U, int r,
+                                                           float* __restrict__ X) {
+    const int lane = threadIdx.x & 31;
+    const bool own = lane < (d >> 2);
+    float u[4][RB], c[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int k = 4 * lane + e;
+        c[e] = own ? cen[k] : 0.f;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) u[e][i] = (own && i < r) ? U[(int64_t)k * r + i] : 0.f;
+    }
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * ROWS < n; g += warps) {
+        float4 v[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int64_t row = g * ROWS + q;
+            v[q] = (own && row < n) ? __ldcs(reinterpret_cast<const float4*>(Y + row * d) + lane)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int64_t row = g * ROWS + q;
+            const float yc[4] = {v[q].x - c[0], v[q].y - c[1], v[q].z - c[2], v[q].w - c[3]};
+            float acc[RB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) acc[i] = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int i = 0; i < RB; ++i) acc[i] = fmaf(yc[e], u[e][i], acc[i]);
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                if (i < r) {   // r and row are the same for the whole warp: the shuffles stay convergent
+                    const float sum = warp_sum(acc[i]);
+                    if (lane == 0 && row < n) X[row * r + i] = sum;
+                }
+            }
+        }
+    }
+}
+
+// General form: any element type and width, arithmetic type A.  U is staged
+// transposed in shared memory (Us[i * d + k]) with the centre, so the lanes of
+// a warp (one row, lanes over the columns) read consecutive words.
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_affine_project(const T* __restrict__ Y, int64_t n, int d,
-                                                        const A* __restrict__ ybar, const A* __restrict__ U,
+                                                        const A* __restrict__ cen, const A* __restrict__ U,
                                                         int r, A* __restrict__ X) {
+    extern __shared__ __align__(16) unsigned char asm_raw[];
+    A* Us = reinterpret_cast<A*>(asm_raw);
+    A* cs = Us + (size_t)r * d;
+    for (int e = threadIdx.x; e < r * d; e += blockDim.x) {
+        const int i = e / d, k = e % d;
+        Us[e] = U[(int64_t)k * r + i];
+    }
+    for (int k = threadIdx.x; k < d; k += blockDim.x) cs[k] = cen[k];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
@@ -69,55 +160,102 @@ __global__ void __launch_bounds__(256) k_affine_project(const T* __restrict__ Y,
         for (int i = 0; i < kMaxR; ++i) acc[i] = A(0);
         const T* y = Y + row * d;
         for (int k = lane; k < d; k += 32) {
-            const A yc = load_as<A, T>(y + k) - ybar[k];
-            const A* u = U + (int64_t)k * r;
+            const A yc = load_as<A, T>(y + k) - cs[k];
 #pragma unroll
             for (int i = 0; i < kMaxR; ++i)
-                if (i < r) acc[i] = mad(yc, u[i], acc[i]);
+                if (i < r) acc[i] = mad(yc, Us[i * d + k], acc[i]);
         }
 #pragma unroll
         for (int i = 0; i < kMaxR; ++i) {
-            if (i < r) {   // r is the same for the whole warp: the shuffles stay convergent
-                A v = acc[i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (i < r) {
+                const A v = warp_sum(acc[i]);
                 if (lane == 0) X[row * r + i] = v;
             }
         }
     }
 }
 
-template <typename T>
-cudaError_t affine_launch(const T* Y, int64_t n, int d, const int64_t* idx, int l, const double* V,
-                          const double* lam, int r, int f64, double* ybar, float* ybar_f, double* U,
-                          float* U_f, void* X, cudaStream_t st) {
-    k_affine_mean<T><<<(unsigned)((d + 255) / 256), 256, 0, st>>>(Y, n, d, idx, l, ybar, ybar_f);
-    const int64_t dr = (int64_t)d * r;
-    k_affine_axes<T><<<(unsigned)((dr + 255) / 256), 256, 0, st>>>(Y, n, d, idx, l, ybar, V, lam, r, U, U_f);
+unsigned project_grid(int64_t n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = (n + 7) / 8;
-    const unsigned grid = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
-    if (f64)
-        k_affine_project<T, double><<<grid, 256, 0, st>>>(Y, n, d, ybar, U, r, (double*)X);
-    else
-        k_affine_project<T, float><<<grid, 256, 0, st>>>(Y, n, d, ybar_f, U_f, r, (float*)X);
-    note_launch(3);
+    return (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
+}
+
+template <typename T, typename A>
+cudaError_t project_general(const T* Y, int64_t n, int d, const A* cen, const A* U, int r, A* X, cudaStream_t st) {
+    const size_t smem = sizeof(A) * ((size_t)r * d + d);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_affine_project<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_affine_project<T, A><<<project_grid(n), 256, smem, st>>>(Y, n, d, cen, U, r, X);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t project_any(const T* Y, int64_t n, int d, const double* cen, const float* cen_f, const double* U,
+                        const float* U_f, int r, int f64, void* X, cudaStream_t st) {
+    cudaError_t e;
+    if (f64) {
+        e = project_general<T, double>(Y, n, d, cen, U, r, (double*)X, st);
+    } else if (std::is_same<T, float>::value && d % 4 == 0 && d <= 128 && r <= 16 &&
+               (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+        const float* Yf = reinterpret_cast<const float*>(Y);
+        const unsigned grid = project_grid((n + 3) / 4);
+        float* Xf = (float*)X;
+        if (r <= 4) k_affine_project_f4<4, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
+        else if (r <= 8) k_affine_project_f4<8, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
+        else if (r <= 12) k_affine_project_f4<12, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
+        else k_affine_project_f4<16, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
+        e = cudaSuccess;
+    } else {
+        e = project_general<T, float>(Y, n, d, cen_f, U_f, r, (float*)X, st);
+    }
+    if (e != cudaSuccess) return e;
+    note_launch(1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_affine(const void* Y, int dt, int64_t n, int d, const int64_t* idx, int l, const double* V,
-                          const double* lam, int r, int f64, double* ybar, float* ybar_f, double* U, float* U_f,
-                          void* X, cudaStream_t st) {
+cudaError_t launch_rows_mean(const double* L, int l, int d, double* mean, float* mean_f, cudaStream_t st) {
+    if (l <= 0 || d <= 0) return cudaErrorInvalidValue;
+    k_rows_mean<<<d, kAxThreads, 0, st>>>(L, l, d, mean, mean_f);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axes(const double* L, int l, int d, const double* c, const double* V, const double* scale, int r,
+                        double* U, float* U_f, cudaStream_t st) {
+    if (l <= 0 || d <= 0 || r <= 0 || r > kMaxR) return cudaErrorInvalidValue;
+    k_axes<<<d, kAxThreads, 0, st>>>(L, l, d, c, V, scale, r, U, U_f);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_affine_project(const void* Y, int dt, int64_t n, int d, const double* cen, const float* cen_f,
+                                  const double* U, const float* U_f, int r, int f64, void* X, cudaStream_t st) {
+    if (n <= 0 || d <= 0 || r <= 0 || r > kMaxR) return cudaErrorInvalidValue;
+    if (dt == MDS_IN_F64) return project_any((const double*)Y, n, d, cen, cen_f, U, U_f, r, f64, X, st);
+    if (dt == MDS_IN_F32) return project_any((const float*)Y, n, d, cen, cen_f, U, U_f, r, f64, X, st);
+    return project_any((const uint8_t*)Y, n, d, cen, cen_f, U, U_f, r, f64, X, st);
+}
+
+cudaError_t launch_affine(const void* Y, int dt, int64_t n, int d, const double* Lg, int l, const double* V,
+                          const double* lam, int r, int f64, double* scale, double* ybar, float* ybar_f, double* U,
+                          float* U_f, void* X, cudaStream_t st) {
     if (n <= 0 || d <= 0 || l <= 0 || r <= 0 || r > kMaxR) return cudaErrorInvalidValue;
-    if (dt == MDS_IN_F64)
-        return affine_launch((const double*)Y, n, d, idx, l, V, lam, r, f64, ybar, ybar_f, U, U_f, X, st);
-    if (dt == MDS_IN_F32)
-        return affine_launch((const float*)Y, n, d, idx, l, V, lam, r, f64, ybar, ybar_f, U, U_f, X, st);
-    return affine_launch((const uint8_t*)Y, n, d, idx, l, V, lam, r, f64, ybar, ybar_f, U, U_f, X, st);
+    cudaError_t e = launch_rows_mean(Lg, l, d, ybar, ybar_f, st);
+    if (e != cudaSuccess) return e;
+    k_inv_sqrt<<<1, 32, 0, st>>>(lam, r, scale);
+    note_launch(1);
+    e = launch_axes(Lg, l, d, ybar, V, scale, r, U, U_f, st);
+    if (e != cudaSuccess) return e;
+    return launch_affine_project(Y, dt, n, d, ybar, ybar_f, U, U_f, r, f64, X, st);
 }
 
 }  // namespace gbmds

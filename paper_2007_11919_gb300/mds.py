@@ -70,6 +70,10 @@ def _lib():
             "mds_model_save": (_I, [_P, ctypes.c_char_p]),
             "mds_model_load": (_I, [ctypes.c_char_p, _P]),
             "mds_model_free": (None, [_P]),
+            "mds_pivot_workspace_size": (_SZ, [_I64, _I, _I, _I, _I]),
+            "mds_pivot": (_I, [_P, _I, _I64, _I, _P, _I, _I, _P, _P, _P]),
+            "mds_landmarks_maxmin_workspace_size": (_SZ, [_I64, _I]),
+            "mds_landmarks_maxmin": (_I, [_P, _I, _I64, _I, _I, _I64, _P, _P]),
             "mds_divide_conquer_workspace_size": (_SZ, [_I64, _I, _I, _P, _I, _I, _I]),
             "mds_divide_conquer": (_I, [_P, _I, _I64, _I, _I, _P, _P, _P, _I, _I, _P, _P, _P]),
         }
@@ -258,6 +262,35 @@ def mds_embed_new(model: Model, Ynew, prec=None, **kw):
     X = torch.empty((m, r), dtype=_xdtype(info_prec), device=Ynew.device)
     _check(L.mds_embed_new(model.handle, _ptr(Ynew), dt, m, ctypes.byref(o), _ptr(X)), "mds_embed_new")
     return X
+
+
+def mds_pivot(Y, pivot_idx, r, prec="f32", **kw):
+    """Pivot MDS (Section 3.1) of the rows of Y with the given pivot rows.
+    Returns (X n x r, var r)."""
+    dt = _data(Y)
+    n, d = Y.shape
+    idx = _idx(pivot_idx, Y.device)
+    l = idx.numel()
+    L = _lib()
+    o, ws = _opts(Y.device, prec, L.mds_pivot_workspace_size(n, d, l, r, PREC[prec]), **kw)
+    X = torch.empty((n, r), dtype=_xdtype(prec), device=Y.device)
+    var = torch.empty(r, dtype=torch.float64, device=Y.device)
+    _check(L.mds_pivot(_ptr(Y), dt, n, d, _ptr(idx), l, r, ctypes.byref(o), _ptr(X), _ptr(var)), "mds_pivot")
+    return X, var
+
+
+def mds_landmarks_maxmin(Y, l, first=0, **kw):
+    """LMDS's MaxMin choice of l landmarks (Section 3.1) starting from row
+    ``first``; returns the l row indices (int64, on Y's device) in the order
+    chosen, ready for ``mds_interpolate``."""
+    dt = _data(Y)
+    n, d = Y.shape
+    L = _lib()
+    o, ws = _opts(Y.device, "f64", L.mds_landmarks_maxmin_workspace_size(n, d), **kw)
+    idx = torch.empty(l, dtype=torch.int64, device=Y.device)
+    _check(L.mds_landmarks_maxmin(_ptr(Y), dt, n, d, l, int(first), ctypes.byref(o), _ptr(idx)),
+           "mds_landmarks_maxmin")
+    return idx
 
 
 def mds_divide_conquer(Y, anchors, part_ptr, part_own, r, prec="f32", **kw):

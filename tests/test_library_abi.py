@@ -176,3 +176,17 @@ def test_dc_plan_argument_checks_without_gpu(lib):
     ob = MdsOpts(prec=2)
     assert lib.mds_dc_plan_create(220, 3, 1, 2, pp, 10, 3, ctypes.byref(ob), 1, ctypes.byref(h)) == 7
     assert lib.mds_dc_plan_create(220, 3, 1, 2, pp, 10, 3, ctypes.byref(o), 1, None) == 1
+
+
+def test_maxmin_argument_checks_without_gpu(lib):
+    o = _opts(prec=0)
+    p = ctypes.c_void_p(8)
+    lib.mds_landmarks_maxmin.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mds_landmarks_maxmin.restype = ctypes.c_int
+    assert lib.mds_landmarks_maxmin(p, 1, 100, 4, 0, 0, ctypes.byref(o), p) == 1      # l < 1
+    assert lib.mds_landmarks_maxmin(p, 1, 100, 4, 101, 0, ctypes.byref(o), p) == 1    # l > n
+    assert lib.mds_landmarks_maxmin(p, 1, 100, 4, 10, 100, ctypes.byref(o), p) == 1   # first out of range
+    assert lib.mds_landmarks_maxmin(None, 1, 100, 4, 10, 0, ctypes.byref(o), p) == 1
+    assert lib.mds_landmarks_maxmin(p, 1, 100, 20000, 10, 0, ctypes.byref(o), p) == 7  # rows too wide
+    assert lib.mds_landmarks_maxmin(p, 1, 100, 4, 10, 0, ctypes.byref(o), p) == 8     # no workspace
