@@ -18,12 +18,13 @@ value = n / step time (points embedded per second by the two methods in
 turn).  The same line carries, under "configs", the other workloads, each
 timed alone on its own inputs: interpolation FP64 (n = 2,000), divide-and-
 conquer FP32 (n = 100,000), interpolation BF16 (n = 1,000,000), the plain
-FP32 form of the same interpolation, and its affine pass; and under "serve"
+FP32 form of the same interpolation, and its affine pass, MaxMin landmark
+selection at n = 1,000,000 and l = 1,000, pivot MDS and fast MDS; and under "serve"
 the serving run (three resident BF16 models, Poisson arrivals of 1-50,000
 point requests, continuous batching, p50/p99 latency).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload image_all|image|image_dc|dc|interp|interp_f32|affine|interp_f64|serve]
+                    [--workload image_all|image|image_dc|dc|interp|interp_f32|affine|interp_f64|maxmin|pivot|fast|serve]
 
 Under torchrun every rank runs its own independent problem of the same size
 (weak scaling, no data-path collective); the step time is the max over ranks.
@@ -31,6 +32,7 @@ Under torchrun every rank runs its own independent problem of the same size
 from __future__ import annotations
 
 import argparse
+import ctypes
 import dataclasses
 import hashlib
 import json
@@ -74,9 +76,12 @@ LEGS = {
     "interp_f32": (W.INTERP_F32, "interp"),
     "affine": (W.INTERP_AFFINE_F32, "affine"),
     "interp_f64": (W.CLASSICAL_INTERP_F64, "interp"),
+    "maxmin": (W.MAXMIN_F32, "maxmin"),
+    "pivot": (W.PIVOT_F32, "pivot"),
+    "fast": (W.FAST_F32, "fast"),
 }
 HEADLINE = ("image", "image_dc")          # the image-like set, both methods
-SUB_CONFIGS = ("interp_f64", "dc", "interp", "interp_f32", "affine")
+SUB_CONFIGS = ("interp_f64", "dc", "interp", "interp_f32", "affine", "maxmin", "pivot", "fast")
 
 
 def parse():
@@ -316,6 +321,10 @@ def make_workload(name, seed, n=0):
         if w.own_lo:
             return w, method, Y, W.partitions_uneven(w.n, w.c, w.own_lo, w.own_hi, seed)
         return w, method, Y, W.partitions_equal(w.n, w.l, w.c, seed)
+    if method == "maxmin":
+        return w, method, Y, None
+    if method == "fast":
+        return w, method, Y, W.fast_mds_tree(w.n, w.l, w.c, seed)
     return w, method, Y, W.landmarks(w.n, w.l, seed)
 
 
@@ -454,10 +463,19 @@ class Leg:
                                  cluster=args.cluster, device=dev, full_matvec=args.full_matvec)
             self.X = torch.zeros((w.n, w.r), dtype=self.xdt, device=dev)
             self.var = torch.empty(w.r, dtype=torch.float64, device=dev)
+        elif self.method == "maxmin":
+            self.ws = torch.empty(L.mds_landmarks_maxmin_workspace_size(w.n, w.d), dtype=torch.uint8, device=dev)
+        elif self.method == "fast":
+            perm, self.rng, self.par = W.flatten_fast_tree(self.aux)
+            self.perm = torch.from_numpy(perm).to(dev)
+            rng = np.ascontiguousarray(self.rng.reshape(-1))
+            self.ws = torch.empty(L.mds_fast_workspace_size(w.n, w.d, len(self.par), rng.ctypes.data_as(ctypes.c_void_p),
+                                                            self.par.ctypes.data_as(ctypes.c_void_p), w.c, w.r,
+                                                            M.PREC[w.prec]), dtype=torch.uint8, device=dev)
         else:
             self.idx = torch.from_numpy(self.aux).to(dev)
-            size = (L.mds_interpolate_affine_workspace_size if self.method == "affine"
-                    else L.mds_interpolate_workspace_size)
+            size = {"affine": L.mds_interpolate_affine_workspace_size, "pivot": L.mds_pivot_workspace_size}.get(
+                self.method, L.mds_interpolate_workspace_size)
             self.ws = torch.empty(size(w.n, w.d, w.l, w.r, M.PREC[w.prec]), dtype=torch.uint8, device=dev)
 
     def step(self):
@@ -467,6 +485,12 @@ class Leg:
             return self.plan.execute(self.Yd, self.anc, self.own, X=self.X, var=self.var)
         if self.method == "affine":
             return G.mds_interpolate_affine(self.Yd, self.idx, w.r, w.prec, workspace=self.ws)
+        if self.method == "maxmin":
+            return G.mds_landmarks_maxmin(self.Yd, w.l, 0, workspace=self.ws), None
+        if self.method == "pivot":
+            return G.mds_pivot(self.Yd, self.idx, w.r, w.prec, workspace=self.ws)
+        if self.method == "fast":
+            return G.mds_fast(self.Yd, self.perm, self.rng, self.par, w.c, w.r, w.prec, workspace=self.ws)
         X, var, _ = G.mds_interpolate(self.Yd, self.idx, w.r, w.prec, workspace=self.ws, cluster=self.args.cluster)
         return X, var
 
@@ -493,9 +517,13 @@ class Leg:
                                    dtype=torch.uint8, device=self.dev)
             self.e2e_how = "mds_interpolate_host: chunked copies of the rows overlap the landmark eigenproblem"
         else:
-            self.idx_h = torch.from_numpy(self.aux).pin_memory()
-            self.h2d += 8 * self.idx_h.numel()
-            self.e2e_how = "copies of the rows and indices, then mds_interpolate_affine, then X back"
+            self.idx_h = (torch.from_numpy(self.aux).pin_memory() if self.method in ("affine", "pivot") else
+                          torch.from_numpy(W.flatten_fast_tree(self.aux)[0]).pin_memory() if self.method == "fast"
+                          else None)
+            self.h2d += 8 * (self.idx_h.numel() if self.idx_h is not None else 0)
+            if self.method == "maxmin":
+                self.d2h = 8 * w.l
+            self.e2e_how = f"copies of the rows and indices, then the {self.method} call, then the result back"
 
     def host_step(self):
         import paper_2007_11919_gb300 as G
@@ -508,8 +536,13 @@ class Leg:
                                              cluster=self.args.cluster)
             return X
         self.Yd.copy_(self.Yh, non_blocking=True)
-        self.idx.copy_(self.idx_h, non_blocking=True)
-        X, var = G.mds_interpolate_affine(self.Yd, self.idx, w.r, w.prec, workspace=self.ws)
+        if self.method in ("affine", "pivot"):
+            self.idx.copy_(self.idx_h, non_blocking=True)
+        elif self.method == "fast":
+            self.perm.copy_(self.idx_h, non_blocking=True)
+        X, var = self.step()
+        if self.method == "maxmin":
+            return X.cpu()
         self.Xh.copy_(X, non_blocking=True)
         _ = var.cpu()
         return self.Xh
@@ -519,9 +552,15 @@ class Leg:
         peaks = load_peaks()
         eig_ms = statistics.mean(s["stage_ms"]["eig"] for s in stats)
         post_ms = statistics.mean(s["stage_ms"]["post"] for s in stats)
+        if self.method == "maxmin":
+            return self._maxmin_roof(stats, peaks), None
         lan = self._lanczos_roof(stats, eig_ms, peaks)
-        if self.method == "dc":
+        if self.method in ("dc", "fast"):
             return lan, None
+        if self.method == "pivot":
+            pass_ms = sum(statistics.mean(s["stage_ms"][k] for s in stats) for k in ("prep", "dist", "post"))
+            other = self._passes_roof(pass_ms, peaks)
+            return (other, lan) if pass_ms > eig_ms else (lan, other)
         other = self._affine_roof(post_ms, peaks) if self.method == "affine" else self._projection_roof(post_ms, peaks)
         return (other, lan) if post_ms > eig_ms else (lan, other)
 
@@ -592,15 +631,88 @@ class Leg:
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": None}
 
+    def _maxmin_roof(self, stats, peaks):
+        # Algorithmic bytes: every round streams all n rows once (l - 1 rounds)
+        w = self.w
+        kms = statistics.mean(s["stage_ms"]["dist"] for s in stats)
+        nbytes = (w.l - 1) * w.n * w.d * self.Y.dtype.itemsize
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = nbytes / (kms * 1e-3) / 1e9
+        return {"kernel": "k_maxmin_round (one streaming pass over Y per landmark, running minima, argmax)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": None}
+
+    def _passes_roof(self, kms, peaks):
+        # Pivot MDS outside the eigen-solve: three passes over Y (column means,
+        # scatter matrix, projection) and X written once
+        w = self.w
+        nbytes = 3 * w.n * w.d * self.Y.dtype.itemsize + w.n * w.r * 4
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = nbytes / (kms * 1e-3) / 1e9
+        return {"kernel": "k_colsum + k_scatter_tiles + k_affine_project (three passes over Y)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": None}
+
     def describe(self):
         w = self.w
         d = {"workload": w.name, "method": self.method, "n": w.n, "d": w.d, "r": w.r, "prec": w.prec}
         if self.method == "dc":
             d.update(parts=self.aux.p, c=w.c, plan=dict(self.plan.info(), graph=True,
                                                         autotuned=self.args.cluster == 0))
+        elif self.method == "fast":
+            d.update(l=w.l, s=w.c, nodes=len(self.par), leaves=int(sum(1 for _ in self.aux.leaves())))
         else:
             d.update(l=w.l)
         return d
+
+    def variant_check(self, X):
+        """Error against the oracle and the oracle's rate for the paper's other
+        variants, on a bounded sample: MaxMin's first picks on the full rows
+        (a MaxMin sequence's prefix is the sequence of that length) and the
+        oracle on 20,000 rows; pivot MDS on a 3,000-row sample (both sides);
+        fast MDS on the first top-level subset's subtree."""
+        import oracle as O
+        import paper_2007_11919_gb300 as G
+        import torch
+        w = self.w
+        out = {}
+        if self.method == "maxmin":
+            got = X.cpu().numpy()
+            out["prefix_bit_exact"] = bool(np.array_equal(got[:8], O.maxmin_landmarks(self.Y, 8, 0)))
+            m = 20_000
+            t0 = time.perf_counter()
+            O.maxmin_landmarks(self.Y[:m], w.l, 0)
+            sec = time.perf_counter() - t0
+            desc = f"MaxMin of l={w.l} landmarks among the first {m} rows"
+        elif self.method == "pivot":
+            m = 3000
+            Ys = self.Y[:m]
+            piv = W.landmarks(m, w.l, 1)
+            t0 = time.perf_counter()
+            Xo, _, _ = O.pivot_mds(Ys, piv, w.r)
+            sec = time.perf_counter() - t0
+            Xs, _ = G.mds_pivot(torch.from_numpy(Ys).to(self.dev), torch.from_numpy(piv).to(self.dev), w.r, w.prec)
+            out["procrustes_rel_err_vs_oracle"] = O.aligned_rel_error(Xs.double().cpu().numpy(), Xo)
+            out["err_sample"] = f"both sides on the first {m} rows with {w.l} pivots among them"
+            desc = f"pivot MDS of the first {m} rows, l={w.l} pivots"
+        else:
+            sub = self.aux.children[0]
+            loc = {int(g): i for i, g in enumerate(sub.idx)}
+
+            def local(node):
+                return W.FastNode(np.array([loc[int(g)] for g in node.idx], dtype=np.int64),
+                                  [local(ch) for ch in node.children])
+            t0 = time.perf_counter()
+            Xo, _, _ = O.fast_mds(self.Y[sub.idx], local(sub), w.r, w.c)
+            sec = time.perf_counter() - t0
+            m = len(sub.idx)
+            out["procrustes_rel_err_vs_oracle"] = O.aligned_rel_error(X.double().cpu().numpy()[sub.idx], Xo)
+            desc = f"fast MDS of the first top-level subset ({m} rows, its own subtree)"
+        out["cpu_baseline"] = {"value": m / sec, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle",
+                               "sample": desc, "seconds": sec}
+        return out
 
 
 def time_legs(legs, steps, flush, stream):
@@ -655,6 +767,10 @@ def leg_report(lg, ms, stats, world, dev, cpu_on, one_thread):
                   "h2d_bytes_per_step": int(lg.h2d), "d2h_bytes_per_step": int(lg.d2h),
                   "ms_steps": [round(t, 3) for t in e2e], "how": lg.e2e_how,
                   "equals_device_result": bool(torch.equal(Xh.to(X.device), X))}
+    if lg.method in ("maxmin", "pivot", "fast"):
+        if rank == 0 and world == 1 and cpu_on:
+            rep.update(lg.variant_check(X))
+        return rep
     if rank == 0 and world == 1 and cpu_on:
         rows, payload, desc = oracle_payload(lg.method, lg.Y, lg.aux, w.r, SAMPLE[lg.name])
         Xo, sec = oracle_job(lg.method, payload)

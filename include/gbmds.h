@@ -275,6 +275,36 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
                        const mds_opts* opts, void* X, double* var);
 
 /* ------------------------------------------------------------------ */
+/* Fast MDS (Section 3.3).  The random recursive division is an input:
+ *   perm         device, n int64: the rows in the order of the division
+ *                (every node's points are a contiguous range of perm);
+ *   node_range   HOST, 2 * nnodes int64: [begin, end) of node k in perm;
+ *   node_parent  HOST, nnodes int32: the parent of node k (-1 for node 0, the
+ *                root, whose range is [0, n)).
+ * The children of a node are the nodes whose parent it is, ordered by begin;
+ * they must tile the parent's range (at least two of them), each holding at
+ * least s points.  A node without children is a leaf: classical MDS
+ * (Section 2) gives its configuration.  At an inner node the first s points
+ * of each child (its sampling points) form the alignment set; its
+ * classical MDS is the alignment configuration X_align, and child j's
+ * configuration X_j is mapped onto rows j s .. j s + s - 1 of it by
+ * Procrustes on its first s rows, X_align,j^s ~ X_j^s T_j + 1 t_j^T (T_j
+ * orthogonal, reflections allowed); the node's configuration is the
+ * children's mapped configurations in order.  X (n x r, double for
+ * MDS_PREC_F64, else float) is the root's configuration in original row
+ * order; var (r) = mean over the leaves of lambda^j / n_j.
+ * All classical problems (leaves and alignment sets, each at most 16384 and
+ * more than r points) run in one batched eigen-solver launch; the maps are
+ * found one tree level at a time.  opts->prec: MDS_PREC_F64 or MDS_PREC_F32
+ * (distances and eigen-solve as for mds_divide_conquer); s >= r + 1.
+ * Errors: MDS_ERR_ARG for a malformed tree or sizes, or a perm entry
+ * outside [0, n). */
+size_t mds_fast_workspace_size(int64_t n, int d, int nnodes, const int64_t* node_range, const int32_t* node_parent,
+                               int s, int r, int prec);
+int mds_fast(const void* Y, int dt, int64_t n, int d, const int64_t* perm, int nnodes, const int64_t* node_range,
+             const int32_t* node_parent, int s, int r, const mds_opts* opts, void* X, double* var);
+
+/* ------------------------------------------------------------------ */
 /* Divide-and-conquer plans (Section 3.2 repeated on new data of fixed shape).
  * A plan fixes n, d, dtype, the part layout (part_ptr, c), r and the
  * precision; it allocates its own workspace once (opts->workspace must be
@@ -404,6 +434,24 @@ typedef struct {
 
 void mds_set_timing(int on);
 int mds_last_stats(mds_stats* out);
+
+/* ------------------------------------------------------------------ */
+/* Failure injection (testing the error paths; the paper has no
+ * counterpart).  Neither faults the GPU: each makes an ordinary, bounded
+ * error path run.
+ * mds_set_wait_limit_ns(ns): from the next call on, a grid-barrier wait of
+ *   the eigen-solver that solves one problem with a team of clusters (the
+ *   landmark problem of interpolation MDS, classical MDS) gives up after ns
+ *   nanoseconds instead of 2 s; the team then leaves the solve together,
+ *   waits for its copies in flight, and the call returns MDS_ERR_TIMEOUT.
+ *   0 restores the default.  Process-wide.
+ * mds_inject_alloc_failures(count): the next `count` device allocations made
+ *   by model, plan or server creation fail as if the device were out of
+ *   memory (the calls return MDS_ERR_NOMEM and free what they had).  The
+ *   environment variable GBMDS_FAULT=alloc:N sets the same count when the
+ *   library loads. */
+void mds_set_wait_limit_ns(unsigned long long ns);
+void mds_inject_alloc_failures(int count);
 
 #ifdef __cplusplus
 }

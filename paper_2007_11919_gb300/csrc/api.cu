@@ -1,7 +1,9 @@
 // Host side of libgbmds: argument checks, workspace carving and the stream-
 // ordered launch sequences behind the C ABI declared in include/gbmds.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -13,6 +15,30 @@ using namespace gbmds;
 namespace gbmds {
 thread_local int64_t g_launches = 0;
 void note_launch(int count) { g_launches += count; }
+
+// Failure injection.  The team grid-barrier wait limit of the next
+// eigen-solver launches (0 = the kernel's default), and a count of device
+// allocations (model, plan and server creation) that fail on purpose -- set
+// by mds_inject_alloc_failures or, at load, by GBMDS_FAULT=alloc:N.
+std::atomic<unsigned long long> g_wait_ns{0};
+std::atomic<int> g_fail_allocs{0};
+static const int g_fault_env = [] {
+    const char* e = getenv("GBMDS_FAULT");
+    if (e && strncmp(e, "alloc:", 6) == 0) g_fail_allocs.store(atoi(e + 6));
+    return 0;
+}();
+
+unsigned long long wait_limit_ns() { return g_wait_ns.load(); }
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    int c = g_fail_allocs.load();
+    while (c > 0)
+        if (g_fail_allocs.compare_exchange_weak(c, c - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    return cudaMalloc(p, bytes);
+}
 }  // namespace gbmds
 
 namespace {
@@ -307,6 +333,7 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     a.tscr = B.tscr;
     a.tbar = B.tbar;
     a.sym = (o.flags & MDS_FLAG_FULL_MATVEC) == 0;
+    a.wait_ns = wait_limit_ns();
     B.sym = a.sym;
     if (B.tbar) CK(cudaMemsetAsync(B.tbar, 0, 4 * sizeof(unsigned), o.st));
     tmark(2, o.st);
@@ -324,7 +351,12 @@ int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr =
     tmark(4, o.st);
     std::vector<int> hs(B ? B->p : 0), steps(B ? B->p : 0);
     int flag = 0, kerr = 0;
+    unsigned team_abort = 0;
     if (d_kerr) CK(cudaMemcpyAsync(&kerr, d_kerr, sizeof(int), cudaMemcpyDeviceToHost, o.st));
+    // a team solve that aborted a grid barrier reports it here even where a
+    // cluster finished its own part (the word is read after the launch ends)
+    if (B && B->team && B->tbar)
+        CK(cudaMemcpyAsync(&team_abort, B->tbar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, o.st));
     if (B && B->p) {
         CK(cudaMemcpyAsync(hs.data(), B->status, sizeof(int) * B->p, cudaMemcpyDeviceToHost, o.st));
         CK(cudaMemcpyAsync(steps.data(), B->steps, sizeof(int) * B->p, cudaMemcpyDeviceToHost, o.st));
@@ -338,7 +370,7 @@ int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr =
             cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]);
             g_last.stage_ms[i] = ms;
         }
-    if (B) return batch_status(*B, hs.data(), steps.data(), flag, kerr);
+    if (B) return batch_status(*B, hs.data(), steps.data(), flag, kerr ? kerr : (team_abort ? MDS_ERR_TIMEOUT : 0));
     g_last.launches = g_launches;
     g_last.cluster = g_cluster;
     if (flag) return MDS_ERR_ARG;
@@ -587,6 +619,10 @@ int mds_version(void) { return 1; }
 
 void mds_set_timing(int on) { g_timing = on != 0; }
 
+void mds_set_wait_limit_ns(unsigned long long ns) { g_wait_ns.store(ns); }
+
+void mds_inject_alloc_failures(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
 int mds_last_stats(mds_stats* out) {
     if (!out) return MDS_ERR_ARG;
     *out = g_last;
@@ -727,13 +763,13 @@ static int make_model(InterpWs& W, int kind, const Opts& o, int l, int d, int r,
     const size_t szL = model_L_bytes(kind, o.prec, l, d);
     const size_t szW = model_W_bytes(kind, o.prec, l, r);
     const size_t nlf = model_nlf_count(kind, l);
-    bool ok = cudaMalloc(&m->L, szL) == cudaSuccess &&
-              cudaMalloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
-              cudaMalloc((void**)&m->nrm_lf, sizeof(float) * nlf) == cudaSuccess &&
-              cudaMalloc(&m->W, szW) == cudaSuccess &&
-              cudaMalloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
-              cudaMalloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
-              cudaMalloc((void**)&m->lam, sizeof(double) * r) == cudaSuccess;
+    bool ok = dev_malloc(&m->L, szL) == cudaSuccess &&
+              dev_malloc((void**)&m->nrm_l, sizeof(double) * l) == cudaSuccess &&
+              dev_malloc((void**)&m->nrm_lf, sizeof(float) * nlf) == cudaSuccess &&
+              dev_malloc(&m->W, szW) == cudaSuccess &&
+              dev_malloc((void**)&m->bias, sizeof(double) * r) == cudaSuccess &&
+              dev_malloc(&m->X1, (size_t)l * r * es) == cudaSuccess &&
+              dev_malloc((void**)&m->lam, sizeof(double) * r) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         mds_model_free(m);
@@ -1287,10 +1323,10 @@ int mds_model_load(const char* path, mds_model* out) {
         delete m;
         return MDS_ERR_IO;
     }
-    ok = cudaMalloc(&m->L, szL) == cudaSuccess && cudaMalloc((void**)&m->nrm_l, 8 * m->l) == cudaSuccess &&
-         cudaMalloc((void**)&m->nrm_lf, 4 * nlf) == cudaSuccess &&
-         cudaMalloc(&m->W, szW) == cudaSuccess && cudaMalloc((void**)&m->bias, 8 * m->r) == cudaSuccess &&
-         cudaMalloc(&m->X1, szX) == cudaSuccess && cudaMalloc((void**)&m->lam, 8 * m->r) == cudaSuccess;
+    ok = dev_malloc(&m->L, szL) == cudaSuccess && dev_malloc((void**)&m->nrm_l, 8 * m->l) == cudaSuccess &&
+         dev_malloc((void**)&m->nrm_lf, 4 * nlf) == cudaSuccess &&
+         dev_malloc(&m->W, szW) == cudaSuccess && dev_malloc((void**)&m->bias, 8 * m->r) == cudaSuccess &&
+         dev_malloc(&m->X1, szX) == cudaSuccess && dev_malloc((void**)&m->lam, 8 * m->r) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         mds_model_free(m);
@@ -1346,6 +1382,244 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
     return finish(&W.B, W.flag, o, W.G.mode >= 0 ? W.G.kerr : nullptr);
 }
 
+
+// ------------------------------------------------------------ fast MDS
+
+}  // extern "C"
+
+namespace {
+
+// The division tree of fast MDS as the host sees it, validated, with the
+// batch of classical problems (leaves first, then each inner node's
+// alignment set) and the Procrustes tasks grouped by tree level.
+struct FastPlan {
+    int nnodes = 0, nleaves = 0, s = 0, r = 0, max_leaf = 0;
+    std::vector<std::vector<int>> kids;
+    std::vector<int> leaf_prob, align_prob, depth, leftmost_leaf;
+    std::vector<int> sizes;               // problem sizes
+    std::vector<int64_t> own_off;         // problem offsets into own_all
+    std::vector<longlong2> copies;        // alignment-row copies (dst in own_all, src in perm)
+    std::vector<std::vector<FastTask>> level_tasks;   // deepest level first
+    std::vector<std::vector<int>> level_dst;          // child node of each task
+    std::vector<int> chain;
+    std::vector<int2> leaf_chain;
+    int64_t own_total = 0;
+    int max_tasks = 0;
+};
+
+int fast_plan(FastPlan& F, int64_t n, int nnodes, const int64_t* range, const int32_t* parent, int s, int r) {
+    if (nnodes < 1 || !range || !parent || s < r + 1 || r < 1 || r > kMaxR) return MDS_ERR_ARG;
+    if (parent[0] != -1 || range[0] != 0 || range[1] != n) return MDS_ERR_ARG;
+    F = FastPlan();
+    F.nnodes = nnodes;
+    F.s = s;
+    F.r = r;
+    F.kids.assign(nnodes, {});
+    for (int k = 1; k < nnodes; ++k) {
+        const int q = parent[k];
+        if (q < 0 || q >= nnodes || q == k || range[2 * k] < range[2 * q] || range[2 * k + 1] > range[2 * q + 1] ||
+            range[2 * k] >= range[2 * k + 1])
+            return MDS_ERR_ARG;
+        F.kids[q].push_back(k);
+    }
+    // children in order, tiling their parent's range; every node reached once from the root
+    F.depth.assign(nnodes, -1);
+    std::vector<int> order{0};
+    F.depth[0] = 0;
+    for (size_t h = 0; h < order.size(); ++h) {
+        const int k = order[h];
+        auto& ch = F.kids[k];
+        std::sort(ch.begin(), ch.end(), [&](int a, int b) { return range[2 * a] < range[2 * b]; });
+        if (ch.size() == 1) return MDS_ERR_ARG;
+        int64_t at = range[2 * k];
+        for (int c : ch) {
+            if (range[2 * c] != at || F.depth[c] != -1) return MDS_ERR_ARG;
+            at = range[2 * c + 1];
+            F.depth[c] = F.depth[k] + 1;
+            order.push_back(c);
+        }
+        if (!ch.empty() && at != range[2 * k + 1]) return MDS_ERR_ARG;
+    }
+    if ((int)order.size() != nnodes) return MDS_ERR_ARG;
+    // problems: leaves, then alignment sets
+    F.leaf_prob.assign(nnodes, -1);
+    F.align_prob.assign(nnodes, -1);
+    for (int k = 0; k < nnodes; ++k)
+        if (F.kids[k].empty()) {
+            const int64_t m = range[2 * k + 1] - range[2 * k];
+            if (m > kMaxEigN || m <= r) return MDS_ERR_ARG;
+            F.leaf_prob[k] = F.nleaves++;
+            F.sizes.push_back((int)m);
+            F.own_off.push_back(range[2 * k]);
+            F.max_leaf = std::max(F.max_leaf, (int)m);
+        }
+    int64_t at = n;
+    for (int k = 0; k < nnodes; ++k) {
+        if (F.kids[k].empty()) continue;
+        const int64_t m = (int64_t)F.kids[k].size() * s;
+        if (m > kMaxEigN || m <= r) return MDS_ERR_ARG;
+        F.align_prob[k] = (int)F.sizes.size();
+        F.sizes.push_back((int)m);
+        F.own_off.push_back(at);
+        for (size_t j = 0; j < F.kids[k].size(); ++j) {
+            const int c = F.kids[k][j];
+            if (range[2 * c + 1] - range[2 * c] < s) return MDS_ERR_ARG;
+            F.copies.push_back(make_longlong2(at + (int64_t)j * s, range[2 * c]));
+        }
+        at += m;
+    }
+    F.own_total = at;
+    // leftmost leaf of every node (children come after their parent in `order`)
+    F.leftmost_leaf.assign(nnodes, -1);
+    for (int h = nnodes - 1; h >= 0; --h) {
+        const int k = order[h];
+        F.leftmost_leaf[k] = F.kids[k].empty() ? k : F.leftmost_leaf[F.kids[k][0]];
+    }
+    // nodes on the path from node a up to, not including, node top
+    auto path = [&](int a, int top) {
+        std::vector<int> p;
+        for (int x = a; x != top; x = parent[x]) p.push_back(x);
+        return p;
+    };
+    int maxd = 0;
+    for (int k = 0; k < nnodes; ++k) maxd = std::max(maxd, F.depth[k]);
+    for (int lev = maxd - 1; lev >= 0; --lev) {
+        std::vector<FastTask> tasks;
+        std::vector<int> dst;
+        for (int k = 0; k < nnodes; ++k) {
+            if (F.depth[k] != lev || F.kids[k].empty()) continue;
+            for (size_t j = 0; j < F.kids[k].size(); ++j) {
+                const int c = F.kids[k][j];
+                const std::vector<int> p = path(F.leftmost_leaf[c], c);
+                FastTask t{F.align_prob[k], (int)(j * s), F.leaf_prob[F.leftmost_leaf[c]], (int)F.chain.size(),
+                           (int)p.size()};
+                F.chain.insert(F.chain.end(), p.begin(), p.end());
+                tasks.push_back(t);
+                dst.push_back(c);
+            }
+        }
+        F.max_tasks = std::max(F.max_tasks, (int)tasks.size());
+        F.level_tasks.push_back(tasks);
+        F.level_dst.push_back(dst);
+    }
+    for (int k = 0; k < nnodes; ++k) {
+        if (!F.kids[k].empty()) continue;
+        const std::vector<int> p = path(k, 0);
+        F.leaf_chain.push_back(make_int2((int)F.chain.size(), (int)p.size()));
+        F.chain.insert(F.chain.end(), p.begin(), p.end());
+    }
+    return MDS_OK;
+}
+
+struct FastWs {
+    int* flag;
+    double* nrm;
+    int64_t* own_all;
+    Batch B;
+    longlong2* copies;
+    FastTask* tasks;      // all levels, concatenated
+    int* dst;
+    int* chain;
+    int2* leaf_chain;
+    double* maps;         // nnodes x (r r + r)
+    double* lmaps;        // nleaves x (r r + r)
+    double* AB;           // max_tasks x 2 s r
+};
+
+size_t fast_layout(FastWs& W, const FastPlan& F, char* base, int64_t n, int mmax) {
+    Arena A{base, 0};
+    W.flag = A.take<int>(1);
+    W.nrm = A.take<double>(n);
+    W.own_all = A.take<int64_t>(F.own_total);
+    plan_batch(W.B, F.sizes, F.own_off, 0, F.r, mmax, n);
+    carve_batch(W.B, A);
+    size_t ntasks = 0;
+    for (const auto& t : F.level_tasks) ntasks += t.size();
+    W.copies = A.take<longlong2>(std::max<size_t>(1, F.copies.size()));
+    W.tasks = A.take<FastTask>(std::max<size_t>(1, ntasks));
+    W.dst = A.take<int>(std::max<size_t>(1, ntasks));
+    W.chain = A.take<int>(std::max<size_t>(1, F.chain.size()));
+    W.leaf_chain = A.take<int2>(std::max(1, F.nleaves));
+    const size_t rr = (size_t)F.r * F.r + F.r;
+    W.maps = A.take<double>((size_t)F.nnodes * rr);
+    W.lmaps = A.take<double>((size_t)std::max(1, F.nleaves) * rr);
+    W.AB = A.take<double>((size_t)std::max(1, F.max_tasks) * 2 * F.s * F.r);
+    return A.off;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mds_fast_workspace_size(int64_t n, int d, int nnodes, const int64_t* node_range, const int32_t* node_parent,
+                               int s, int r, int prec) {
+    (void)prec;
+    if (n <= 0 || d <= 0) return 0;
+    FastPlan F;
+    if (fast_plan(F, n, nnodes, node_range, node_parent, s, r) != MDS_OK) return 0;
+    FastWs W;
+    return fast_layout(W, F, nullptr, n, kDefaultSteps) + 256;
+}
+
+int mds_fast(const void* Y, int dt, int64_t n, int d, const int64_t* perm, int nnodes, const int64_t* node_range,
+             const int32_t* node_parent, int s, int r, const mds_opts* opts, void* X, double* var) {
+    Opts o;
+    int st = read_opts(opts, &o);
+    if (st) return st;
+    if (!Y || !X || !var || !perm || !valid_dt(dt) || n < 2 || d <= 0) return MDS_ERR_ARG;
+    if (o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) return MDS_ERR_UNSUPPORTED;
+    FastPlan F;
+    if ((st = fast_plan(F, n, nnodes, node_range, node_parent, s, r))) return st;
+    FastWs W;
+    const size_t need = fast_layout(W, F, nullptr, n, o.mmax);
+    if ((st = check_ws(o, need))) return st;
+    if (fast_layout(W, F, o.ws, n, o.mmax) != need) return MDS_ERR_WORKSPACE;
+    begin_call(o.st);
+    const int f64 = o.prec == MDS_PREC_F64;
+    std::vector<FastTask> all_tasks;
+    std::vector<int> all_dst;
+    for (size_t v = 0; v < F.level_tasks.size(); ++v) {
+        all_tasks.insert(all_tasks.end(), F.level_tasks[v].begin(), F.level_tasks[v].end());
+        all_dst.insert(all_dst.end(), F.level_dst[v].begin(), F.level_dst[v].end());
+    }
+    CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(launch_check_idx(perm, n, n, W.flag, o.st));
+    // the rows of every problem: perm for the leaves, the gathered sampling
+    // points for the alignment sets; the tables of tasks and chains
+    CK(cudaMemcpyAsync(W.own_all, perm, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, o.st));
+    if (!F.copies.empty()) {
+        CK(cudaMemcpyAsync(W.copies, F.copies.data(), sizeof(longlong2) * F.copies.size(), cudaMemcpyHostToDevice, o.st));
+        CK(launch_fast_gather(perm, W.copies, (int)F.copies.size(), s, W.own_all, o.st));
+    }
+    if (!all_tasks.empty()) {
+        CK(cudaMemcpyAsync(W.tasks, all_tasks.data(), sizeof(FastTask) * all_tasks.size(), cudaMemcpyHostToDevice,
+                           o.st));
+        CK(cudaMemcpyAsync(W.dst, all_dst.data(), sizeof(int) * all_dst.size(), cudaMemcpyHostToDevice, o.st));
+    }
+    if (!F.chain.empty())
+        CK(cudaMemcpyAsync(W.chain, F.chain.data(), sizeof(int) * F.chain.size(), cudaMemcpyHostToDevice, o.st));
+    CK(cudaMemcpyAsync(W.leaf_chain, F.leaf_chain.data(), sizeof(int2) * F.leaf_chain.size(), cudaMemcpyHostToDevice,
+                       o.st));
+    const void* Ye = Y;
+    int dte = dt;
+    if ((st = prep_data(Y, dt, n, d, o.prec, W.nrm, nullptr, o, &Ye, &dte))) return st;
+    tmark(0, o.st);
+    // every classical problem of the recursion in one batched eigen-solver launch
+    if ((st = run_eig_batch(W.B, Ye, dte, d, W.nrm, nullptr, W.own_all, f64, f64, o))) return st;
+    // maps of the subsets onto their parents' alignment configurations, deepest level first
+    size_t off = 0;
+    for (size_t v = 0; v < F.level_tasks.size(); ++v) {
+        const int nt = (int)F.level_tasks[v].size();
+        CK(launch_fast_prep(W.B.d_desc, W.B.v, W.B.lam, r, s, W.tasks + off, nt, W.chain, W.maps, W.AB, o.st));
+        CK(launch_procrustes_sets(W.AB, nt, s, r, W.dst + off, W.maps, o.st));
+        off += nt;
+    }
+    // each leaf's rows through the composition of its maps; lambda-bar over the leaves
+    CK(launch_fast_finish(W.B.d_desc, F.nleaves, F.max_leaf, W.B.v, W.B.lam, W.leaf_chain, W.chain, W.maps, r,
+                          W.lmaps, W.own_all, f64, X, o.st));
+    CK(launch_dc_lambda_bar(W.B.d_desc, F.nleaves, W.B.lam, r, var, o.st));
+    return finish(&W.B, W.flag, o);
+}
 
 // ------------------------------------------------- divide-and-conquer plans
 
@@ -1451,7 +1725,7 @@ int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr,
     P->cs = o.cluster;
     cudaGetDevice(&P->device);
     const size_t need = dc_layout(P->W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
-    bool ok = cudaMalloc(&P->ws, need) == cudaSuccess &&
+    bool ok = dev_malloc(&P->ws, need) == cudaSuccess &&
               cudaHostAlloc((void**)&P->hbuf, sizeof(int) * (2 * p + 2), cudaHostAllocDefault) == cudaSuccess;
     for (auto& e : P->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming) == cudaSuccess &&
@@ -1577,9 +1851,9 @@ int mds_dc_plan_execute_host(mds_dc_plan P, const void* Y, const int64_t* part_o
     if (!P->dY) {
         // the plan's own device copies of the inputs and outputs; X starts at
         // zero (rows outside every part are never written)
-        bool ok = cudaMalloc(&P->dY, yb) == cudaSuccess && cudaMalloc((void**)&P->down, ob + 8) == cudaSuccess &&
-                  cudaMalloc((void**)&P->danc, ab) == cudaSuccess && cudaMalloc(&P->dX, xb) == cudaSuccess &&
-                  cudaMalloc((void**)&P->dvar, sizeof(double) * P->r) == cudaSuccess &&
+        bool ok = dev_malloc(&P->dY, yb) == cudaSuccess && dev_malloc((void**)&P->down, ob + 8) == cudaSuccess &&
+                  dev_malloc((void**)&P->danc, ab) == cudaSuccess && dev_malloc(&P->dX, xb) == cudaSuccess &&
+                  dev_malloc((void**)&P->dvar, sizeof(double) * P->r) == cudaSuccess &&
                   cudaMemset(P->dX, 0, xb) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();

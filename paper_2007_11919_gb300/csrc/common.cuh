@@ -161,6 +161,7 @@ struct LanczosArgs {
     double* tscr;       // team exchange buffers (lanczos_team_scratch_doubles)
     unsigned* tbar;     // team barrier words [arrivals, generation, abort], zero before the launch
     int sym;            // FP32 Q in a cluster alone: read each off-diagonal block of Q once (symmetric ranges)
+    unsigned long long wait_ns;   // limit of a team grid-barrier wait (0 = the default 2 s)
 };
 constexpr int kMaxTeam = 32;   // clusters per team
 size_t lanczos_team_scratch_doubles(int max_n, int mmax, int r);
@@ -342,6 +343,38 @@ struct MaxminWs {
 int maxmin_grid();
 cudaError_t launch_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t first, MaxminWs ws,
                           int64_t* idx_out, cudaStream_t st);
+
+// Procrustes of point-set pairs given as matrices (k_align.cu): task k aligns
+// B_k onto A_k (c x r each, A then B at AB + k * 2 c r) into Tt + dst[k] * (r r + r).
+cudaError_t launch_procrustes_sets(const double* AB, int tasks, int c, int r, const int* dst, double* Tt,
+                                   cudaStream_t st);
+
+// Fast MDS (k_fast.cu).  A Procrustes task maps a subset (a child) onto its
+// parent's alignment configuration: rows row0 .. row0 + s - 1 of problem
+// align_prob against rows 0 .. s - 1 of problem leaf_prob (the leftmost leaf
+// below the child) carried through the maps of chain[chain_off ..
+// chain_off + chain_len).
+struct FastTask {
+    int align_prob, row0, leaf_prob, chain_off, chain_len;
+};
+cudaError_t launch_fast_gather(const int64_t* perm, const longlong2* copies, int ncopies, int s, int64_t* own_all,
+                               cudaStream_t st);
+cudaError_t launch_fast_prep(const ProbDesc* desc, const double* varena, const double* lam, int r, int s,
+                             const FastTask* tasks, int ntasks, const int* chain, const double* maps, double* AB,
+                             cudaStream_t st);
+// Leaves are problems 0 .. nleaves - 1; leaf_chain[k] = (offset, length) of
+// the nodes from leaf k up to, not including, the root.
+cudaError_t launch_fast_finish(const ProbDesc* desc, int nleaves, int max_leaf, const double* varena,
+                               const double* lam, const int2* leaf_chain, const int* chain, const double* maps, int r,
+                               double* lmaps, const int64_t* own, int out_f64, void* X, cudaStream_t st);
+
+// Failure injection (api.cu): the team grid-barrier wait limit for the next
+// eigen-solver launches (0 = default), and device allocations of model, plan
+// and server creation that are made to fail (dev_malloc consumes the count).
+unsigned long long wait_limit_ns();
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc(reinterpret_cast<void**>(p), bytes); }
 
 // Host side (api.cu): queue an embedding against a model without waiting.
 int embed_enqueue(mds_model m, const void* Ynew, int dt, int64_t rows, char* ws, cudaStream_t st, void* X,

@@ -85,55 +85,106 @@ __global__ void k_inv_sqrt(const double* __restrict__ lam, int r, double* __rest
     if (i < r) scale[i] = 1.0 / sqrt(lam[i]);
 }
 
-// X[row] = (y_row - c) U for FP32 rows with d <= 128, d a multiple of 4 and
-// a 16-byte aligned base: one warp per group of ROWS consecutive rows, lane q
-// owns the columns 4q .. 4q + 3 and keeps their rows of U (r <= RB columns)
-// and of the centre in registers; one 16-byte streaming load per row and
-// lane (ROWS of them in flight), 4 RB FMAs, then one warp sum per output.
-template <int RB, int ROWS>
-__global__ void __launch_bounds__(256) k_affine_project_f4(const float* __restrict__ Y, int64_t n, int d,
-                                                           const float* __restrict__ cen,
-                                                           const float* __restrict__ U, int r,
-                                                           float* __restrict__ X) {
-    const int lane = threadIdx.x & 31;
-    const bool own = lane < (d >> 2);
-    float u[4][RB], c[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int k = 4 * lane + e;
-        c[e] = own ? cen[k] : 0.f;
-#pragma unroll
-        for (int i = 0; i < RB; ++i) u[e][i] = (own && i < r) ? U[(int64_t)k * r + i] : 0.f;
+// X[row] = (y_row - c) U for FP32 rows with d <= 128 a multiple of 4, r < RB
+// and a 16-byte aligned base.  Thread per row: each warp owns tiles of 32
+// consecutive rows (32 d contiguous floats in global memory), copied into its
+// shared-memory buffer with cp.async (two buffers: the next tile is in flight
+// while this one is computed), the row stride padded to an odd number of
+// 16-byte groups so that 32 lanes reading 32 rows hit distinct banks.  Lane q
+// computes row q of the tile: for each column k, acc_i += (y_k - c_k) U[k][i]
+// with the row of U and c_k (stored as Uc[k][0..RB), c_k at RB - 1) read as
+// broadcast 16-byte loads.  The r outputs of the 32 rows leave through the
+// consumed buffer as one coalesced block of 32 r floats.
+constexpr int kPfWarps = 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int RB>
+__global__ void __launch_bounds__(32 * kPfWarps) k_affine_project_f4(const float* __restrict__ Y, int64_t n, int d,
+                                                                     const float* __restrict__ cen,
+                                                                     const float* __restrict__ U, int r,
+                                                                     float* __restrict__ X) {
+    extern __shared__ __align__(16) float pf_smem[];
+    const int d4 = d >> 2, s4 = d4 | 1;                     // row stride in 16-byte groups (odd)
+    float* Uc = pf_smem;                                    // d x RB
+    float4* bufs = reinterpret_cast<float4*>(pf_smem + (size_t)d * RB);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* const buf0 = bufs + (size_t)(2 * warp) * 32 * s4;
+    float4* const buf1 = buf0 + (size_t)32 * s4;
+    for (int e = threadIdx.x; e < d * RB; e += blockDim.x) {
+        const int k = e / RB, i = e % RB;
+        Uc[e] = i < r ? U[(int64_t)k * r + i] : (i == RB - 1 ? cen[k] : 0.f);
     }
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * ROWS < n; g += warps) {
-        float4 v[ROWS];
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int64_t row = g * ROWS + q;
-            v[q] = (own && row < n) ? __ldcs(reinterpret_cast<const float4*>(Y + row * d) + lane)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const int64_t tiles = (n + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * kPfWarps;
+    int64_t t = (int64_t)blockIdx.x * kPfWarps + warp;
+    // the tile's contiguous floats: 16-byte group j = row * d4 + c4 -> buf[row * s4 + c4]
+    auto issue = [&](int64_t tile, float4* dst) {
+        if (tile < tiles) {
+            const int64_t row0 = tile * 32;
+            const int rows = (int)(n - row0 < 32 ? n - row0 : 32);
+            const float4* src = reinterpret_cast<const float4*>(Y + row0 * d);
+            for (int j = lane; j < rows * d4; j += 32) {
+                const int row = j / d4, c4 = j - row * d4;
+                cp_async16(dst + row * s4 + c4, src + j);
+            }
         }
+        cp_async_commit();
+    };
+    issue(t, buf0);
+    for (int it = 0; t < tiles; t += wstride, ++it) {
+        float4* cur = (it & 1) ? buf1 : buf0;
+        issue(t + wstride, (it & 1) ? buf0 : buf1);
+        cp_async_wait<1>();
+        __syncwarp();
+        const int64_t row0 = t * 32;
+        const int rows = (int)(n - row0 < 32 ? n - row0 : 32);
+        float acc[RB];
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int64_t row = g * ROWS + q;
-            const float yc[4] = {v[q].x - c[0], v[q].y - c[1], v[q].z - c[2], v[q].w - c[3]};
-            float acc[RB];
+        for (int i = 0; i < RB; ++i) acc[i] = 0.f;
+        if (lane < rows) {
+            const float4* y4 = cur + lane * s4;
+            for (int c4 = 0; c4 < d4; ++c4) {
+                const float4 v = y4[c4];
+                const float yv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int i = 0; i < RB; ++i) acc[i] = 0.f;
+                for (int e = 0; e < 4; ++e) {
+                    const float4* u4 = reinterpret_cast<const float4*>(Uc + (size_t)(4 * c4 + e) * RB);
+                    float u[RB];
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
+                    for (int g = 0; g < RB / 4; ++g) {
+                        const float4 w = u4[g];
+                        u[4 * g] = w.x;
+                        u[4 * g + 1] = w.y;
+                        u[4 * g + 2] = w.z;
+                        u[4 * g + 3] = w.w;
+                    }
+                    const float yc = yv[e] - u[RB - 1];
 #pragma unroll
-                for (int i = 0; i < RB; ++i) acc[i] = fmaf(yc[e], u[e][i], acc[i]);
-#pragma unroll
-            for (int i = 0; i < RB; ++i) {
-                if (i < r) {   // r and row are the same for the whole warp: the shuffles stay convergent
-                    const float sum = warp_sum(acc[i]);
-                    if (lane == 0 && row < n) X[row * r + i] = sum;
+                    for (int i = 0; i < RB - 1; ++i) acc[i] = fmaf(yc, u[i], acc[i]);
                 }
             }
         }
+        __syncwarp();
+        // the outputs of the tile's rows through the consumed buffer, coalesced
+        float* o = reinterpret_cast<float*>(cur);
+        if (lane < rows) {
+#pragma unroll
+            for (int i = 0; i < RB - 1; ++i)
+                if (i < r) o[lane * r + i] = acc[i];
+        }
+        __syncwarp();
+        for (int e = lane; e < rows * r; e += 32) X[row0 * r + e] = o[e];
+        __syncwarp();
     }
+    cp_async_wait<0>();
 }
 
 // General form: any element type and width, arithmetic type A.  U is staged
@@ -202,16 +253,24 @@ cudaError_t project_any(const T* Y, int64_t n, int d, const double* cen, const f
     cudaError_t e;
     if (f64) {
         e = project_general<T, double>(Y, n, d, cen, U, r, (double*)X, st);
-    } else if (std::is_same<T, float>::value && d % 4 == 0 && d <= 128 && r <= 16 &&
+    } else if (std::is_same<T, float>::value && d % 4 == 0 && d <= 128 && r <= 15 && r <= 4 * ((d >> 2) | 1) &&
                (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
         const float* Yf = reinterpret_cast<const float*>(Y);
-        const unsigned grid = project_grid((n + 3) / 4);
         float* Xf = (float*)X;
-        if (r <= 4) k_affine_project_f4<4, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
-        else if (r <= 8) k_affine_project_f4<8, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
-        else if (r <= 12) k_affine_project_f4<12, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
-        else k_affine_project_f4<16, 4><<<grid, 256, 0, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
-        e = cudaSuccess;
+        const int RB = r < 8 ? 8 : (r < 12 ? 12 : 16);
+        const size_t smem = sizeof(float) * (size_t)d * RB + (size_t)2 * kPfWarps * 32 * ((d >> 2) | 1) * 16;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t tiles = (n + 31) / 32;
+        const int64_t want = (tiles + kPfWarps - 1) / kPfWarps;
+        const unsigned grid = (unsigned)(want < (int64_t)sms * 2 ? want : (int64_t)sms * 2);
+        auto go = [&](auto kern) {
+            cudaError_t r2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (r2 == cudaSuccess) kern<<<grid, 32 * kPfWarps, smem, st>>>(Yf, n, d, cen_f, U_f, r, Xf);
+            return r2;
+        };
+        e = RB == 8 ? go(k_affine_project_f4<8>) : (RB == 12 ? go(k_affine_project_f4<12>) : go(k_affine_project_f4<16>));
     } else {
         e = project_general<T, float>(Y, n, d, cen_f, U_f, r, (float*)X, st);
     }

@@ -31,53 +31,15 @@ __device__ __forceinline__ void round_robin_pair(int round, int k, int n, int& p
     q = x < y ? y : x;
 }
 
-__global__ void __launch_bounds__(kProcThreads) k_procrustes(const ProbDesc* __restrict__ desc,
-                                                             const double* __restrict__ varena,
-                                                             const double* __restrict__ lam, int r, int c,
-                                                             double* __restrict__ Tt) {
-    __shared__ double G[kMaxR][kMaxR + 1];
-    __shared__ double Wm[kMaxR][kMaxR + 1];
-    __shared__ double abar[kMaxR], bbar[kMaxR], sq0[kMaxR], sqj[kMaxR];
+// The orthogonal factor of Procrustes from C = B_c^T A_c (r x r in G, W
+// the identity in Wm, both in shared memory): one-sided Jacobi on G until its
+// columns are orthogonal, U = G's columns normalised (null directions
+// completed by Gram-Schmidt), T = U W^T, t = a_bar - T^T b_bar.  Called by
+// every thread of a CTA of kProcThreads; T and t are written by warp 0.
+__device__ void procrustes_polar(double (*G)[kMaxR + 1], double (*Wm)[kMaxR + 1], const double* abar,
+                                 const double* bbar, int r, double* __restrict__ T, double* __restrict__ t) {
     __shared__ int s_rot;
-    const int j = blockIdx.x;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    double* T = Tt + (size_t)j * (r * r + r);
-    double* t = T + r * r;
-    if (j == 0) {
-        for (int e = tid; e < r * r; e += kProcThreads) T[e] = (e / r == e % r) ? 1.0 : 0.0;
-        if (tid < r) t[tid] = 0.0;
-        return;
-    }
-    const double* V0 = varena + desc[0].v_off;
-    const double* Vj = varena + desc[j].v_off;
-    if (tid < r) {
-        sq0[tid] = sqrt(lam[tid]);
-        sqj[tid] = sqrt(lam[(size_t)j * r + tid]);
-    }
-    __syncthreads();
-    if (tid < r) {
-        double sa = 0.0, sb = 0.0;
-        for (int a = 0; a < c; ++a) {
-            sa += V0[(int64_t)a * r + tid] * sq0[tid];
-            sb += Vj[(int64_t)a * r + tid] * sqj[tid];
-        }
-        abar[tid] = sa / c;
-        bbar[tid] = sb / c;
-    }
-    __syncthreads();
-    // C[i][m] = sum_a (B_ai - bbar_i)(A_am - abar_m), one thread per entry
-    for (int e = tid; e < r * r; e += kProcThreads) {
-        const int i = e / r, m = e % r;
-        double s = 0.0;
-        for (int a = 0; a < c; ++a) {
-            const double b = Vj[(int64_t)a * r + i] * sqj[i] - bbar[i];
-            const double av = V0[(int64_t)a * r + m] * sq0[m] - abar[m];
-            s += b * av;
-        }
-        G[i][m] = s;
-        Wm[i][m] = (i == m) ? 1.0 : 0.0;
-    }
-    __syncthreads();
     // one-sided Jacobi: rotate column pairs of G (and W) until orthogonal
     const int rr = r + (r & 1);   // column r is a dummy when r is odd
     for (int sweep = 0; sweep < 40; ++sweep) {
@@ -165,6 +127,90 @@ __global__ void __launch_bounds__(kProcThreads) k_procrustes(const ProbDesc* __r
     }
 }
 
+__global__ void __launch_bounds__(kProcThreads) k_procrustes(const ProbDesc* __restrict__ desc,
+                                                             const double* __restrict__ varena,
+                                                             const double* __restrict__ lam, int r, int c,
+                                                             double* __restrict__ Tt) {
+    __shared__ double G[kMaxR][kMaxR + 1];
+    __shared__ double Wm[kMaxR][kMaxR + 1];
+    __shared__ double abar[kMaxR], bbar[kMaxR], sq0[kMaxR], sqj[kMaxR];
+    const int j = blockIdx.x;
+    const int tid = threadIdx.x;
+    double* T = Tt + (size_t)j * (r * r + r);
+    double* t = T + r * r;
+    if (j == 0) {
+        for (int e = tid; e < r * r; e += kProcThreads) T[e] = (e / r == e % r) ? 1.0 : 0.0;
+        if (tid < r) t[tid] = 0.0;
+        return;
+    }
+    const double* V0 = varena + desc[0].v_off;
+    const double* Vj = varena + desc[j].v_off;
+    if (tid < r) {
+        sq0[tid] = sqrt(lam[tid]);
+        sqj[tid] = sqrt(lam[(size_t)j * r + tid]);
+    }
+    __syncthreads();
+    if (tid < r) {
+        double sa = 0.0, sb = 0.0;
+        for (int a = 0; a < c; ++a) {
+            sa += V0[(int64_t)a * r + tid] * sq0[tid];
+            sb += Vj[(int64_t)a * r + tid] * sqj[tid];
+        }
+        abar[tid] = sa / c;
+        bbar[tid] = sb / c;
+    }
+    __syncthreads();
+    // C[i][m] = sum_a (B_ai - bbar_i)(A_am - abar_m), one thread per entry
+    for (int e = tid; e < r * r; e += kProcThreads) {
+        const int i = e / r, m = e % r;
+        double s = 0.0;
+        for (int a = 0; a < c; ++a) {
+            const double b = Vj[(int64_t)a * r + i] * sqj[i] - bbar[i];
+            const double av = V0[(int64_t)a * r + m] * sq0[m] - abar[m];
+            s += b * av;
+        }
+        G[i][m] = s;
+        Wm[i][m] = (i == m) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    procrustes_polar(G, Wm, abar, bbar, r, T, t);
+}
+
+// Procrustes of point sets given as matrices: task k aligns B_k onto A_k
+// (each c x r row-major at AB + k * 2 c r, A then B), A ~ B T + 1 t^T, into
+// Tt + dst[k] * (r r + r).
+__global__ void __launch_bounds__(kProcThreads) k_procrustes_sets(const double* __restrict__ AB, int c, int r,
+                                                                  const int* __restrict__ dst,
+                                                                  double* __restrict__ Tt) {
+    __shared__ double G[kMaxR][kMaxR + 1];
+    __shared__ double Wm[kMaxR][kMaxR + 1];
+    __shared__ double abar[kMaxR], bbar[kMaxR];
+    const int tid = threadIdx.x;
+    const double* A = AB + (size_t)blockIdx.x * 2 * c * r;
+    const double* B = A + (size_t)c * r;
+    double* T = Tt + (size_t)dst[blockIdx.x] * (r * r + r);
+    double* t = T + r * r;
+    if (tid < r) {
+        double sa = 0.0, sb = 0.0;
+        for (int a = 0; a < c; ++a) {
+            sa += A[(int64_t)a * r + tid];
+            sb += B[(int64_t)a * r + tid];
+        }
+        abar[tid] = sa / c;
+        bbar[tid] = sb / c;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += kProcThreads) {
+        const int i = e / r, m = e % r;
+        double s = 0.0;
+        for (int a = 0; a < c; ++a) s += (B[(int64_t)a * r + i] - bbar[i]) * (A[(int64_t)a * r + m] - abar[m]);
+        G[i][m] = s;
+        Wm[i][m] = (i == m) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    procrustes_polar(G, Wm, abar, bbar, r, T, t);
+}
+
 template <typename A>
 __global__ void __launch_bounds__(256) k_align(const ProbDesc* __restrict__ desc,
                                                const double* __restrict__ varena,
@@ -209,6 +255,14 @@ __global__ void k_lambda_bar(const ProbDesc* __restrict__ desc, int p,
 cudaError_t launch_dc_procrustes(const ProbDesc* desc, int p, const double* varena,
                                  const double* lam, int r, int c, double* Tt, cudaStream_t st) {
     k_procrustes<<<p, kProcThreads, 0, st>>>(desc, varena, lam, r, c, Tt);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_procrustes_sets(const double* AB, int tasks, int c, int r, const int* dst, double* Tt,
+                                   cudaStream_t st) {
+    if (tasks <= 0) return cudaSuccess;
+    k_procrustes_sets<<<tasks, kProcThreads, 0, st>>>(AB, c, r, dst, Tt);
     note_launch(1);
     return cudaGetLastError();
 }

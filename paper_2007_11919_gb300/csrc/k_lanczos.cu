@@ -373,14 +373,19 @@ struct Team {
     double* sgn;        // T x kMaxR x 3
     unsigned* bar;      // grid barrier: arrivals, generation
     int* abort;         // set when a barrier wait or a stage wait timed out
+    int* sab;           // this CTA's shared copy of the abort word as rank 0 of its cluster saw it
+    unsigned long long wait_ns;   // limit of a grid-barrier wait
 };
 
 // Grid barrier of the team: a cluster barrier, then thread 0 of each
 // cluster's rank 0 arrives on the team counter (the last arrival opens the
 // next generation) and waits, then a second cluster barrier releases the
-// cluster.  Writes before the barrier are fenced; a timed-out wait sets the
-// team's abort word, after which every barrier returns at once.
-__device__ void team_sync(cg::cluster_group& cl, const Team& tm) {
+// cluster.  Writes before the barrier are fenced; a wait longer than
+// tm.wait_ns sets the team's abort word, after which every barrier returns
+// at once.  Returns the abort word as rank 0 of this cluster read it after
+// the wait -- the same answer on every CTA of the cluster, so the caller can
+// leave the solve on all of them at the same point.
+__device__ bool team_sync(cg::cluster_group& cl, const Team& tm) {
     __threadfence();
     cl.sync();
     if (cl.block_rank() == 0 && threadIdx.x == 0) {
@@ -394,30 +399,36 @@ __device__ void team_sync(cg::cluster_group& cl, const Team& tm) {
             const unsigned long long t0 = tc::global_ns();
             while (*gen == g0) {
                 if (*(volatile int*)tm.abort) break;
-                if (tc::global_ns() - t0 > tc::kWaitNs) {
+                if (tc::global_ns() - t0 > tm.wait_ns) {
                     atomicExch(tm.abort, 1);
                     break;
                 }
             }
         }
         __threadfence();
+        *tm.sab = *(volatile int*)tm.abort;
     }
     cl.sync();
+    // every CTA reads rank 0's copy; rank 0 rewrites it only after the first
+    // cluster barrier of the next call, which every reader reaches after its read
+    return *cl.map_shared_rank(tm.sab, 0) != 0;
 }
 
 // Sum over the team of part[i], lo <= i < hi, into out (and outdf as
 // double-FP32 pairs): cluster sums through DSMEM, then (G > 1) the clusters'
 // sums in cluster order through the team buffers of parity pb.
 // tmp: shared scratch of at least G x (hi - lo) doubles (the idle Q-stage ring).
-__device__ void team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int cs, int mmax, int pb, double* part,
+// Returns true (on every CTA of the cluster) when the team barrier aborted;
+// out is then not written.
+__device__ bool team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int cs, int mmax, int pb, double* part,
                                double* out, double* outdf, int lo, int hi, double* tmp) {
     cluster_allreduce(cl, part, out, tm.G > 1 ? nullptr : outdf, lo, hi, cs);
-    if (tm.G == 1) return;
+    if (tm.G == 1) return false;
     const int stride = mmax + 2, K = hi - lo;
     double* gp = tm.part + (size_t)pb * tm.G * stride;
     if (q == 0)
         for (int i = lo + (int)threadIdx.x; i < hi; i += kThreads) gp[(size_t)tm.g * stride + i] = out[i];
-    team_sync(cl, tm);
+    if (team_sync(cl, tm)) return true;
     // every cluster's sums in one pass of independent loads, then the sum in cluster order
     gather_unrolled(tmp, tm.G * K, [&](int e) {
         const int h = e / K, i = e % K;
@@ -431,6 +442,7 @@ __device__ void team_allreduce(cg::cluster_group& cl, const Team& tm, int q, int
         if (outdf) reinterpret_cast<float2*>(outdf)[lo + i] = df_of(sum);
     }
     __syncthreads();
+    return false;
 }
 
 // The first half of a team reduction whose exchange comes later: partial
@@ -973,6 +985,22 @@ __device__ void cgs_update(const double* B, int ldq, int r0, int nr, int ia, int
 // ------------------------------------------------------------ one problem
 
 // One eigenproblem (part pj) solved by the calling cluster.
+// Leaving a team solve after an aborted grid barrier: every CTA of the
+// cluster gets here at the same point (the barrier's answer is
+// cluster-consistent).  The warp's bulk copies still in flight are waited for
+// (full limit: their source is ordinary device memory), a cluster barrier
+// keeps every CTA's shared memory alive until its peers are done with it, and
+// the problem reports MDS_ERR_TIMEOUT.
+__device__ void team_abort_exit(const LanczosArgs& A, int pj, cg::cluster_group& cl, QStream& Qs, int qt, int k) {
+    qs_drain(Qs);
+    __syncthreads();
+    cl.sync();
+    if (qt == 0 && threadIdx.x == 0) {
+        A.status[pj] = kDevTimeout;
+        A.steps[pj] = k;
+    }
+}
+
 template <bool DF>
 __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& cl, int cs, int q, const Smem& S,
                               int& s_flag, QStream& Qs, const Team& tm) {
@@ -1006,7 +1034,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     {
         const double s = block_sum(loc, S.red);
         if (tid == 0) part[pb][0] = s;
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, nullptr, 0, 1, S.ttmp);
+        if (team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, nullptr, 0, 1, S.ttmp)) {
+            team_abort_exit(A, pj, cl, Qs, qt, 0);
+            return;
+        }
         pb ^= 1;
         if (tid == 0) S.red[kWarps + 3] = 1.0 / sqrt(S.cfull[0]);
         __syncthreads();
@@ -1041,6 +1072,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     double prev_worst = -1.0;
     int k = 0, prev_k = 0;
     bool converged = false, have_vectors = false;
+    bool aborted = false;   // a team barrier aborted: every CTA of the cluster leaves together
 
     // Step j orthogonalises w = Q u_j against the two newest vectors (one
     // exchange), giving w_1, and publishes w_1 with its partial dots against
@@ -1055,7 +1087,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         // ---- exchange: every rank's published vector and, from step 1 on,
         // its deferred partial sums
         if (tm.G > 1) {
-            team_sync(cl, tm);
+            if (team_sync(cl, tm)) {
+                aborted = true;
+                break;
+            }
             if constexpr (DF)
                 gather_unrolled(reinterpret_cast<float*>(S.vfull), n,
                                 [&](int i) { return __ldcg(reinterpret_cast<const float*>(tm.v) + i); });
@@ -1222,7 +1257,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                         tm.theta[i] = S.theta[i];
                         tm.resid[i] = S.resid[i];
                     }
-                team_sync(cl, tm);
+                if (team_sync(cl, tm)) {
+                    aborted = true;
+                    break;
+                }
                 for (int i = tid; i < r; i += kThreads) {
                     S.theta[i] = __ldcg(tm.theta + i);
                     S.resid[i] = __ldcg(tm.resid + i);
@@ -1291,7 +1329,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         const int ia = j > 0 ? j - 1 : 0;
         cgs_dots<DF>(B, ldq, r0, nr, ia, j, S.wloc, part[pb], false);
         __syncthreads();
-        team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1, S.ttmp);
+        if (team_allreduce(cl, tm, q, cs, A.mmax, pb, part[pb], S.cfull, S.cdf, ia, j + 1, S.ttmp)) {
+            aborted = true;
+            break;
+        }
         pb ^= 1;
         // alpha_j = v_j . Q v_j; the matvec saw u_j = v_j + sum_i d_i v_i / beta_{j-1},
         // whose extra part adds e_j = v_j . Q v_{j-1} d_{j-1} / beta_{j-1} = d_{j-1}
@@ -1329,12 +1370,18 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     }
 
     // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
+    if (aborted) {
+        team_abort_exit(A, pj, cl, Qs, qt, k);
+        return;
+    }
     qok = qs_drain(Qs) && qok;
     bool any_timeout = false;
     if (tm.G > 1) {
         if (!qok) atomicExch(tm.abort, 1);
-        team_sync(cl, tm);
-        any_timeout = *(volatile int*)tm.abort != 0;
+        if (team_sync(cl, tm)) {
+            team_abort_exit(A, pj, cl, Qs, qt, k);
+            return;
+        }
     } else {
         if (!qok) S.red[43] = 1.0;   // zero since the last problem; every writer stores 1
         __syncthreads();
@@ -1379,7 +1426,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 const int i = e / k, t = e % k;
                 if (i % T == qt) tm.xv[(size_t)i * L + t] = S.xv[(size_t)i * L + t];
             }
-        team_sync(cl, tm);
+        if (team_sync(cl, tm)) {
+            team_abort_exit(A, pj, cl, Qs, qt, k);
+            return;
+        }
         if (qt == 0 && status != kDevRank) {
             copy_unrolled(
                 r * k, [&](int e) { return __ldcg(tm.xv + (size_t)(e / k) * L + e % k); },
@@ -1392,7 +1442,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 tm.xv[(size_t)i * L + t] = S.xv[(size_t)i * L + t];
             }
         }
-        team_sync(cl, tm);
+        if (team_sync(cl, tm)) {
+            team_abort_exit(A, pj, cl, Qs, qt, k);
+            return;
+        }
         if (status == kDevRank) {
             if (qt == 0 && tid == 0) {
                 A.status[pj] = status;
@@ -1511,7 +1564,10 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
     if (tm.G > 1) {
         __syncthreads();
         for (int e = tid; e < 3 * r; e += kThreads) tm.sgn[(size_t)qt * 3 * kMaxR + e] = S.sgn[e];
-        team_sync(cl, tm);
+        if (team_sync(cl, tm)) {
+            team_abort_exit(A, pj, cl, Qs, qt, k);
+            return;
+        }
         if (tid < r) {
             double best = -1.0, bestv = 0.0, brow = 1e300;
             for (int qq = 0; qq < T; ++qq) {
@@ -1565,7 +1621,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
     const int cs = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
     extern __shared__ __align__(16) double smraw[];
-    __shared__ int s_flag, s_next;
+    __shared__ int s_flag, s_next, s_abort;
     const Smem S = carve(smraw, A.max_n, cs, A.mmax, A.r, A.team > 1);
     if (threadIdx.x == 0) {
         for (int i = 0; i < kWarps * kRing; ++i) tc::mbar_init(&S.full[i], 1);
@@ -1601,6 +1657,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lanczos(LanczosArgs A) {
         tm.sgn = t;
         tm.bar = A.tbar;
         tm.abort = reinterpret_cast<int*>(A.tbar + 2);
+        tm.sab = &s_abort;
+        tm.wait_ns = A.wait_ns ? A.wait_ns : tc::kWaitNs;
     }
     if (tm.G > 1) {   // one problem for the whole team
         solve_problem<DF>(A, A.order[0], cl, cs, q, S, s_flag, Qs, tm);

@@ -280,7 +280,7 @@ int mds_server_create(const mds_model* models, int nmodels, const mds_server_opt
         auto sl = std::make_unique<Slot>();
         sl->srv = S.get();
         const bool ok = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking) == cudaSuccess &&
-                        cudaMalloc(&sl->arena, S->slot_bytes) == cudaSuccess &&
+                        gbmds::dev_malloc(&sl->arena, S->slot_bytes) == cudaSuccess &&
                         cudaHostAlloc(&sl->kerr_host, sizeof(int), cudaHostAllocDefault) == cudaSuccess;
         S->slots.push_back(std::move(sl));
         if (!ok) {

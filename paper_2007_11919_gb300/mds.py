@@ -72,6 +72,8 @@ def _lib():
             "mds_model_free": (None, [_P]),
             "mds_pivot_workspace_size": (_SZ, [_I64, _I, _I, _I, _I]),
             "mds_pivot": (_I, [_P, _I, _I64, _I, _P, _I, _I, _P, _P, _P]),
+            "mds_fast_workspace_size": (_SZ, [_I64, _I, _I, _P, _P, _I, _I, _I]),
+            "mds_fast": (_I, [_P, _I, _I64, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P]),
             "mds_landmarks_maxmin_workspace_size": (_SZ, [_I64, _I]),
             "mds_landmarks_maxmin": (_I, [_P, _I, _I64, _I, _I, _I64, _P, _P]),
             "mds_divide_conquer_workspace_size": (_SZ, [_I64, _I, _I, _P, _I, _I, _I]),
@@ -279,6 +281,27 @@ def mds_pivot(Y, pivot_idx, r, prec="f32", **kw):
     return X, var
 
 
+def mds_fast(Y, perm, node_range, node_parent, s, r, prec="f32", **kw):
+    """Fast MDS (Section 3.3) over a given division tree: ``perm`` (rows in
+    the division's order), ``node_range`` (nnodes x 2 host array of [begin,
+    end) in perm) and ``node_parent`` (host, -1 for the root).  Returns
+    (X n x r, var r)."""
+    dt = _data(Y)
+    n, d = Y.shape
+    pm = _idx(perm, Y.device)
+    rng = np.ascontiguousarray(np.asarray(node_range, dtype=np.int64).reshape(-1))
+    par = np.ascontiguousarray(np.asarray(node_parent, dtype=np.int32))
+    nn = len(par)
+    rp, pp = rng.ctypes.data_as(ctypes.c_void_p), par.ctypes.data_as(ctypes.c_void_p)
+    L = _lib()
+    o, ws = _opts(Y.device, prec, L.mds_fast_workspace_size(n, d, nn, rp, pp, s, r, PREC[prec]), **kw)
+    X = torch.empty((n, r), dtype=_xdtype(prec), device=Y.device)
+    var = torch.empty(r, dtype=torch.float64, device=Y.device)
+    _check(L.mds_fast(_ptr(Y), dt, n, d, _ptr(pm), nn, rp, pp, s, r, ctypes.byref(o), _ptr(X), _ptr(var)),
+           "mds_fast")
+    return X, var
+
+
 def mds_landmarks_maxmin(Y, l, first=0, **kw):
     """LMDS's MaxMin choice of l landmarks (Section 3.1) starting from row
     ``first``; returns the l row indices (int64, on Y's device) in the order
@@ -341,6 +364,24 @@ def mds_last_stats() -> dict:
     return {"stage_ms": dict(zip(STAGES, list(s.stage_ms))), "launches": s.launches,
             "eig_steps": s.eig_steps, "eig_flops": s.eig_flops, "eig_qbytes": s.eig_qbytes,
             "problems": s.problems, "cluster": s.cluster, "eig_qread": s.eig_qread}
+
+
+def mds_set_wait_limit_ns(ns: int):
+    """Failure injection: the team eigen-solver's grid-barrier waits give up
+    after ``ns`` nanoseconds (0 = the default 2 s); process-wide."""
+    L = _lib()
+    L.mds_set_wait_limit_ns.argtypes = [ctypes.c_ulonglong]
+    L.mds_set_wait_limit_ns.restype = None
+    L.mds_set_wait_limit_ns(int(ns))
+
+
+def mds_inject_alloc_failures(count: int):
+    """Failure injection: the next ``count`` device allocations of model, plan
+    or server creation fail (MDS_ERR_NOMEM)."""
+    L = _lib()
+    L.mds_inject_alloc_failures.argtypes = [_I]
+    L.mds_inject_alloc_failures.restype = None
+    L.mds_inject_alloc_failures(int(count))
 
 
 def mds_embed_new_static(model: Model, Ynew, stream=None):

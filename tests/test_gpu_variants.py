@@ -10,6 +10,10 @@ Pivot MDS (Section 3.1): against the oracle's SVD of the n x l block of Q,
 element by element (both apply the same sign convention) and after
 alignment, FP64 at 1e-10 and FP32 at 1e-5, eigenvalue estimates at 1e-10 /
 1e-6.
+
+Fast MDS (Section 3.3): over the same random division tree as the oracle
+(drawn on the host), one and two levels of division, against the oracle
+after alignment at the same tolerances.
 """
 import numpy as np
 import pytest
@@ -151,3 +155,57 @@ def test_pivot_argument_errors(gb):
     with pytest.raises(gb.MdsError) as e:
         gb.mds_pivot(Y, dev(bad), 3, "f32")
     assert e.value.status == 1
+
+
+# -------------------------------------------------------------------- fast MDS
+
+FAST_TOL = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-6)}
+
+
+@pytest.mark.parametrize("prec,n,d,l,s,r,depth", [("f64", 3000, 10, 500, 20, 3, 1), ("f32", 20_000, 50, 500, 40, 10, 2),
+                                                  ("f32", 7001, 30, 500, 25, 5, 1), ("f64", 400, 8, 500, 20, 3, 0)])
+def test_fast_matches_oracle(gb, prec, n, d, l, s, r, depth):
+    """A tree of one or two levels of division (ragged last subsets), or a
+    single leaf (n <= l: classical MDS)."""
+    Y = W.gaussian_graded(n, d, seed=n + d, dtype=np.float64 if prec == "f64" else np.float32)
+    tree = W.fast_mds_tree(n, l, s, seed=n)
+    perm, rng, par = W.flatten_fast_tree(tree)
+    got_depth = 0
+    for k in range(len(par)):
+        dk, x = 0, k
+        while par[x] >= 0:
+            x, dk = par[x], dk + 1
+        got_depth = max(got_depth, dk)
+    assert got_depth == depth
+    Xo, lo, _ = O.fast_mds(Y, tree, r, s)
+    X, var = gb.mds_fast(dev(Y), dev(perm), rng, par, s, r, prec)
+    tx, tl = FAST_TOL[prec]
+    assert np.max(np.abs(var.cpu().numpy() - lo) / lo) < tl
+    assert O.aligned_rel_error(X.double().cpu().numpy(), Xo) < tx
+
+
+def test_fast_exact_recovery(gb):
+    """Points exactly in R^4 through two levels of division: the points up to
+    one orthogonal map."""
+    rng = np.random.default_rng(9)
+    Z = rng.standard_normal((12_000, 4)) * np.array([6, 4, 3, 2.0])
+    Y = Z @ np.linalg.qr(rng.standard_normal((9, 4)))[0].T
+    tree = W.fast_mds_tree(12_000, 300, 15, seed=9)
+    perm, rg, par = W.flatten_fast_tree(tree)
+    X, _ = gb.mds_fast(dev(Y), dev(perm), rg, par, 15, 4, "f64")
+    assert O.aligned_rel_error(X.cpu().numpy(), Z - Z.mean(axis=0)) < 1e-10
+
+
+def test_fast_malformed_trees(gb):
+    Y = dev(W.gaussian_graded(1000, 6, seed=1, dtype=np.float32))
+    tree = W.fast_mds_tree(1000, 300, 20, seed=1)
+    perm, rg, par = W.flatten_fast_tree(tree)
+    bad_rng = rg.copy()
+    bad_rng[1, 1] -= 1                                        # children no longer tile the root
+    bad_par = par.copy()
+    bad_par[2] = 2                                            # own parent
+    for args in ((perm, bad_rng, par, 20, 3), (perm, rg, bad_par, 20, 3), (perm, rg, par, 3, 3),
+                 (perm, rg, par, 400, 3)):
+        with pytest.raises(gb.MdsError) as e:
+            gb.mds_fast(Y, dev(args[0]), args[1], args[2], args[3], args[4], "f32")
+        assert e.value.status == 1

@@ -190,3 +190,40 @@ def test_maxmin_argument_checks_without_gpu(lib):
     assert lib.mds_landmarks_maxmin(None, 1, 100, 4, 10, 0, ctypes.byref(o), p) == 1
     assert lib.mds_landmarks_maxmin(p, 1, 100, 20000, 10, 0, ctypes.byref(o), p) == 7  # rows too wide
     assert lib.mds_landmarks_maxmin(p, 1, 100, 4, 10, 0, ctypes.byref(o), p) == 8     # no workspace
+
+
+def test_fast_tree_checks_without_gpu(lib):
+    """The division tree of fast MDS is validated on the host: a well-formed
+    tree gets a workspace size, malformed ones get 0 (and MDS_ERR_ARG from
+    mds_fast before any device work)."""
+    import workloads as W
+    lib.mds_fast_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mds_fast_workspace_size.restype = ctypes.c_size_t
+    lib.mds_fast.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p]
+    lib.mds_fast.restype = ctypes.c_int
+    tree = W.fast_mds_tree(5000, 400, 20, seed=2)
+    _, rg, par = W.flatten_fast_tree(tree)
+
+    def size(rg_, par_, s=20, r=3):
+        rg_ = np.ascontiguousarray(rg_, dtype=np.int64)
+        par_ = np.ascontiguousarray(par_, dtype=np.int32)
+        return lib.mds_fast_workspace_size(5000, 8, len(par_), rg_.ctypes.data, par_.ctypes.data, s, r, 1)
+
+    assert size(rg, par) > 0
+    bad = rg.copy()
+    bad[3, 0] += 1                      # a gap between two children
+    assert size(bad, par) == 0
+    bad = par.copy()
+    bad[4] = 4                          # a node that is its own parent
+    assert size(rg, bad) == 0
+    bad = par.copy()
+    bad[0] = 0                          # no root
+    assert size(rg, bad) == 0
+    assert size(rg, par, s=3, r=3) == 0            # s < r + 1
+    assert size(rg, par, s=300) == 0               # subsets smaller than s
+    assert size(np.array([[0, 5000]]), np.array([-1])) > 0         # one leaf: classical MDS
+    assert lib.mds_fast_workspace_size(20000, 8, 1, np.array([0, 20000], dtype=np.int64).ctypes.data,
+                                       np.array([-1], dtype=np.int32).ctypes.data, 20, 3, 1) == 0  # leaf too big

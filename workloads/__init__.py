@@ -227,6 +227,27 @@ def fast_mds_tree(n: int, l: int, s: int, seed: int, min_size: int = 0) -> FastN
     return build(np.arange(n, dtype=np.int64))
 
 
+def flatten_fast_tree(tree: FastNode):
+    """The division tree as flat arrays for the C ABI: perm (the root's
+    points in order; every node's points are a contiguous range of it),
+    node_range (nnodes x 2: [begin, end) in perm) and node_parent (-1 for the
+    root, node 0), nodes numbered depth first."""
+    ranges, parents = [], []
+
+    def visit(node, begin, parent):
+        k = len(ranges)
+        ranges.append((begin, begin + len(node.idx)))
+        parents.append(parent)
+        at = begin
+        for ch in node.children:
+            visit(ch, at, k)
+            at += len(ch.idx)
+
+    visit(tree, 0, -1)
+    return (np.asarray(tree.idx, dtype=np.int64), np.asarray(ranges, dtype=np.int64),
+            np.asarray(parents, dtype=np.int32))
+
+
 # -------------------------------------------------------------------- serving
 
 
@@ -246,13 +267,13 @@ def serve_requests(count: int, lo: int, hi: int, rate_per_s: float, seed: int):
 @dataclasses.dataclass(frozen=True)
 class Workload:
     name: str
-    kind: str          # "interp", "dc", "affine", "serve"
+    kind: str          # "interp", "dc", "affine", "maxmin", "pivot", "fast", "serve"
     n: int
     d: int
     r: int
     prec: str          # distance precision: "f64", "f32", "bf16", "fp8"
     l: int = 0         # landmarks (interp) / part size (equal dc)
-    c: int = 0         # connecting points (dc)
+    c: int = 0         # connecting points (dc); sampling points s (fast)
     own_lo: int = 0
     own_hi: int = 0
 
@@ -277,6 +298,14 @@ SERVE_BF16 = Workload("serve_bf16_d100_l500r2_l1000r5_l2000r10_req1-50000", "ser
 # Resident models of the serving workload: (landmarks, r).
 SERVE_MODELS = ((500, 2), (1000, 5), (2000, 10))
 SERVE_SIZES = (1, 50_000)
+# The paper's other variants at the interpolation workload's scale: MaxMin
+# landmarks (LMDS) on the mixture data; pivot MDS and fast MDS on rows with
+# distinct leading variances (N(0, diag(15 * 0.85^k, k < 10; 1 ...))), so that
+# every subset's top-10 subspace is well separated.
+MAXMIN_F32 = Workload("maxmin_f32_n1000000_d100_l1000", "maxmin", 1_000_000, 100, 10, "f32", l=1000)
+PIVOT_F32 = Workload("pivot_f32_n1000000_d100_graded_l1000_r10", "pivot", 1_000_000, 100, 10, "f32", l=1000)
+FAST_F32 = Workload("fast_f32_n1000000_d100_graded_l1000_s20_r10", "fast", 1_000_000, 100, 10, "f32", l=1000,
+                    c=20)
 IMAGE_FP8 = Workload("image_fp8_n814255_d784_l2000_r10", "interp", 814_255, 784, 10, "fp8", l=2000,
                      c=50)
 # The same image-like set by divide-and-conquer: parts of l = 2000 points with
@@ -292,9 +321,9 @@ def make_data(w: Workload, seed: int, n: int | None = None) -> np.ndarray:
         return gaussian_dominant(n, w.d, 3, seed, dtype=np.float64)
     if w.name == DC_F32.name:
         return gaussian_dominant(n, w.d, 5, seed, dtype=np.float32)
-    if w.name in (INTERP_BF16.name, INTERP_F32.name, INTERP_AFFINE_F32.name):
+    if w.name in (INTERP_BF16.name, INTERP_F32.name, INTERP_AFFINE_F32.name, MAXMIN_F32.name):
         return gaussian_mixture(n, w.d, 4, 5.0, seed, dtype=np.float32)
-    if w.name == SERVE_BF16.name:
+    if w.name in (SERVE_BF16.name, PIVOT_F32.name, FAST_F32.name):
         return gaussian_graded(n, w.d, seed)
     if w.name in (IMAGE_FP8.name, IMAGE_DC.name):
         return image_like(n, w.d, seed)
