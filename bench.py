@@ -827,7 +827,8 @@ def ours(args):
     launches = int(sum(s["launches"] for lg in legs for s in stats[lg.name]))
 
     cpu_on = not args.no_cpu_baseline
-    reps = {lg.name: leg_report(lg, ms[lg.name], stats[lg.name], world, dev, cpu_on, one_thread=True)
+    reps = {lg.name: leg_report(lg, ms[lg.name], stats[lg.name], world, dev, cpu_on,
+                                one_thread=lg.method in ("interp", "dc"))
             for lg in legs}
     # the step's roofline: the dominant kernel of the longest leg
     top = max(legs, key=lambda lg: reps[lg.name]["ms_per_step"])
@@ -841,10 +842,12 @@ def ours(args):
     if all("cpu_baseline" in reps[lg.name] for lg in legs):
         # the oracle's rate for a step of the same composition: n points through every leg
         sec = sum(n / reps[lg.name]["cpu_baseline"]["value"] for lg in legs)
-        sec1 = sum(n / reps[lg.name]["cpu_baseline"]["one_thread"]["value"] for lg in legs)
         cpu = {"value": n / sec, "unit": "points/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": "; ".join(f"{lg.name}: {reps[lg.name]['cpu_baseline']['sample']}" for lg in legs),
-               "one_thread": {"value": n / sec1, "cores": 1}, "cpu_model": cpu_model(), "host_cpus": os.cpu_count()}
+               "cpu_model": cpu_model(), "host_cpus": os.cpu_count()}
+        if all("one_thread" in reps[lg.name]["cpu_baseline"] for lg in legs):
+            sec1 = sum(n / reps[lg.name]["cpu_baseline"]["one_thread"]["value"] for lg in legs)
+            cpu["one_thread"] = {"value": n / sec1, "cores": 1}
     err = max((reps[lg.name].get("procrustes_rel_err_vs_oracle") or 0.0) for lg in legs) if cpu else None
 
     configs = None

@@ -634,6 +634,7 @@ int mds_last_stats(mds_stats* out) {
 static size_t maxmin_layout(MaxminWs& M, char* base, int64_t n) {
     Arena A{base, 0};
     M.mind = A.take<double>(n);
+    M.nrm8 = A.take<int>(n);
     M.cur = A.take<int64_t>(1);
     M.part_v = A.take<double>(kMaxminGridCap);
     M.part_i = A.take<int64_t>(kMaxminGridCap);

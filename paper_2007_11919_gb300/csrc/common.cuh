@@ -335,6 +335,7 @@ constexpr int kMaxminD = 12288;      // widest rows (the landmark row is staged 
 constexpr int kMaxminGridCap = 4096; // most CTAs of a round (partials sized for this many)
 struct MaxminWs {
     double* mind;
+    int* nrm8;          // byte rows: exact squared norms (n)
     int64_t* cur;
     double* part_v;
     int64_t* part_i;

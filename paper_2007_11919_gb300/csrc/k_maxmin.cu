@@ -10,13 +10,16 @@
 // (m, i) pair; the last CTA to finish reduces them and records the pick.
 //
 // Exactness.  The pick is an argmax of FP64 values, taken in FP64 as in the
-// FP64 definition:
+// FP64 definition (a general round with one warp per row, and a tiled round
+// with one thread per row for FP32 and byte rows, below):
 //   byte rows   integer differences and sums (exact; the FP64 value too),
 //   FP64 rows   the FP64 difference form sum_k (y_k - l_k)^2,
 //   FP32 rows   first an FP32 difference form; when it exceeds m_i by more
 //               than its rounding bound, (d + 4) 2^-23 relative for d
 //               non-negative terms, m_i cannot change and the row is done;
 //               otherwise the FP64 difference form decides, as for FP64 rows.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gbmds {
@@ -172,6 +175,223 @@ __global__ void __launch_bounds__(kMmThreads) k_maxmin_round(const T* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled form for FP32 rows (d a multiple of 4) and byte rows (d a multiple of
+// 16): thread per row.  Each warp owns tiles of 32 consecutive rows (32 d
+// contiguous elements of Y), copied into its shared-memory buffer with
+// cp.async while the previous tile is worked on, the row stride padded to an
+// odd number of 16-byte groups so that 32 lanes reading 32 rows hit distinct
+// banks; the landmark row is broadcast from shared memory.  Lane q owns row q
+// of the tile: no warp reductions.
+//   byte rows   d^2 = |y|^2 + |l|^2 - 2 y.l in integers (y.l by __dp4a, the
+//               row norms computed once): exact.
+//   FP32 rows   the bounded FP32 difference form, and the FP64 difference
+//               form where the running minimum may change (as above).
+constexpr int kTw = 4;   // warps per CTA of the tiled round
+
+__device__ __forceinline__ void mm_cp16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void mm_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void mm_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The CTA's best (v, i) pair from every thread's, then the round's pick by the
+// last CTA to finish (as in k_maxmin_round).
+__device__ void mm_pick(double bv, int64_t bi, double* __restrict__ part_v, int64_t* __restrict__ part_i,
+                        unsigned* __restrict__ counter, int64_t* __restrict__ cur, double* __restrict__ mind,
+                        int64_t* __restrict__ idx_out, int k) {
+    __shared__ double wv[32];
+    __shared__ int64_t wi[32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_best(bv, bi);
+    if (lane == 0) {
+        wv[warp] = bv;
+        wi[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = wv[0];
+        int64_t j = wi[0];
+        for (int w = 1; w < nw; ++w)
+            if (beats(wv[w], wi[w], v, j)) {
+                v = wv[w];
+                j = wi[w];
+            }
+        part_v[blockIdx.x] = v;
+        part_i[blockIdx.x] = j;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = -2.0;
+    int64_t j = INT64_MAX;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double pv = __ldcg(part_v + b);
+        const int64_t pi = __ldcg(part_i + b);
+        if (beats(pv, pi, v, j)) {
+            v = pv;
+            j = pi;
+        }
+    }
+    warp_best(v, j);
+    __syncthreads();
+    if (lane == 0) {
+        wv[warp] = v;
+        wi[warp] = j;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w)
+            if (beats(wv[w], wi[w], wv[0], wi[0])) {
+                wv[0] = wv[w];
+                wi[0] = wi[w];
+            }
+        const int64_t pick = wi[0];
+        idx_out[k] = pick;
+        cur[0] = pick;
+        mind[pick] = -1.0;
+        *counter = 0u;
+    }
+}
+
+template <bool U8>
+__global__ void __launch_bounds__(32 * kTw) k_maxmin_tiles(const void* __restrict__ Yv, int64_t n, int d,
+                                                           const int* __restrict__ nrm8, int64_t* __restrict__ cur,
+                                                           double* __restrict__ mind, double* __restrict__ part_v,
+                                                           int64_t* __restrict__ part_i, unsigned* __restrict__ counter,
+                                                           int64_t* __restrict__ idx_out, int k) {
+    extern __shared__ __align__(16) unsigned char mm_smem[];
+    __shared__ int s_lnorm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g16 = U8 ? d >> 4 : d >> 2;       // 16-byte groups per row
+    const int s16 = g16 | 1;                    // padded row stride (odd)
+    // landmark row: bytes (U8), or floats then doubles (FP32)
+    uint4* lm16 = reinterpret_cast<uint4*>(mm_smem);
+    double* lm64 = reinterpret_cast<double*>(mm_smem + (size_t)g16 * 16);
+    uint4* bufs = reinterpret_cast<uint4*>(mm_smem + (size_t)g16 * 16 + (U8 ? 0 : (size_t)d * 8));
+    uint4* const b0 = bufs + (size_t)(2 * warp) * 32 * s16;
+    uint4* const b1 = b0 + (size_t)32 * s16;
+    const int64_t lrow = cur[0];
+    const uint4* Y16 = reinterpret_cast<const uint4*>(Yv);
+    for (int g = threadIdx.x; g < g16; g += blockDim.x) lm16[g] = Y16[lrow * g16 + g];
+    if (threadIdx.x == 0) s_lnorm = 0;
+    __syncthreads();
+    if (U8) {
+        unsigned sq = 0;
+        for (int g = threadIdx.x; g < g16; g += blockDim.x) {
+            const uint4 w = lm16[g];
+            sq = __dp4a(w.x, w.x, sq);
+            sq = __dp4a(w.y, w.y, sq);
+            sq = __dp4a(w.z, w.z, sq);
+            sq = __dp4a(w.w, w.w, sq);
+        }
+        atomicAdd(&s_lnorm, (int)sq);
+    } else {
+        const float* lf = reinterpret_cast<const float*>(lm16);
+        for (int c = threadIdx.x; c < d; c += blockDim.x) lm64[c] = (double)lf[c];
+    }
+    __syncthreads();
+    const int lnorm = s_lnorm;
+    const int64_t tiles = (n + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * kTw;
+    int64_t t = (int64_t)blockIdx.x * kTw + warp;
+    auto issue = [&](int64_t tile, uint4* dst) {
+        if (tile < tiles) {
+            const int64_t row0 = tile * 32;
+            const int rows = (int)(n - row0 < 32 ? n - row0 : 32);
+            const uint4* src = Y16 + row0 * g16;
+            for (int j = lane; j < rows * g16; j += 32) {
+                const int row = j / g16, c = j - row * g16;
+                mm_cp16(dst + row * s16 + c, src + j);
+            }
+        }
+        mm_commit();
+    };
+    double bv = -2.0;
+    int64_t bi = INT64_MAX;
+    issue(t, b0);
+    for (int it = 0; t < tiles; t += wstride, ++it) {
+        const uint4* curb = (it & 1) ? b1 : b0;
+        issue(t + wstride, (it & 1) ? b0 : b1);
+        mm_wait<1>();
+        __syncwarp();
+        const int64_t row = t * 32 + lane;
+        if (row < n) {
+            double m = mind[row];
+            if (m >= 0.0) {
+                const uint4* y = curb + lane * s16;
+                double dn;
+                if (U8) {
+                    unsigned dot = 0;
+                    for (int g = 0; g < g16; ++g) {
+                        const uint4 a = y[g], b = lm16[g];
+                        dot = __dp4a(a.x, b.x, dot);
+                        dot = __dp4a(a.y, b.y, dot);
+                        dot = __dp4a(a.z, b.z, dot);
+                        dot = __dp4a(a.w, b.w, dot);
+                    }
+                    dn = (double)((long long)nrm8[row] + lnorm - 2ll * (long long)dot);
+                } else {
+                    const float4* y4 = reinterpret_cast<const float4*>(y);
+                    const float4* l4 = reinterpret_cast<const float4*>(lm16);
+                    float s = 0.f;
+                    for (int g = 0; g < g16; ++g) {
+                        const float4 a = y4[g], b = l4[g];
+                        const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+                        s = fmaf(t0, t0, s);
+                        s = fmaf(t1, t1, s);
+                        s = fmaf(t2, t2, s);
+                        s = fmaf(t3, t3, s);
+                    }
+                    // FP32 value within (d + 4) 2^-24 relative of the exact sum
+                    const double bound = (double)s * (1.0 - (double)(d + 4) * 0x1p-23);
+                    if (bound > m) {
+                        dn = m;
+                    } else {
+                        const float* yf = reinterpret_cast<const float*>(y);
+                        double s64 = 0.0;
+                        for (int c = 0; c < d; ++c) {
+                            const double t64 = (double)yf[c] - lm64[c];
+                            s64 = fma(t64, t64, s64);
+                        }
+                        dn = s64;
+                    }
+                }
+                if (dn < m) {
+                    m = dn;
+                    mind[row] = m;
+                }
+            }
+            if (beats(m, row, bv, bi)) {
+                bv = m;
+                bi = row;
+            }
+        }
+        __syncwarp();
+    }
+    mm_wait<0>();
+    mm_pick(bv, bi, part_v, part_i, counter, cur, mind, idx_out, k);
+}
+
+// Squared norms of byte rows (exact, int): one warp per row.
+__global__ void k_norms8(const uint8_t* __restrict__ Y, int64_t n, int d, int* __restrict__ nrm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= n) return;
+    int s = 0;
+    for (int c = lane; c < d; c += 32) {
+        const int v = Y[row * d + c];
+        s += v * v;
+    }
+    s = warp_sum(s);
+    if (lane == 0) nrm[row] = s;
+}
+
 __global__ void k_maxmin_init(int64_t n, int64_t first, double* __restrict__ mind, int64_t* __restrict__ cur,
                               int64_t* __restrict__ idx_out, unsigned* __restrict__ counter) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,9 +430,43 @@ int maxmin_grid() {
     return g < kMaxminGridCap ? g : kMaxminGridCap;
 }
 
+// Shared memory of the tiled round (0: the shapes it does not take).
+size_t maxmin_tiles_smem(int dt, int d) {
+    if (dt == MDS_IN_U8 && d % 16 == 0) return (size_t)(d / 16) * 16 + (size_t)2 * kTw * 32 * ((d / 16) | 1) * 16;
+    if (dt == MDS_IN_F32 && d % 4 == 0) return (size_t)(d / 4) * 16 + (size_t)d * 8 + (size_t)2 * kTw * 32 * ((d / 4) | 1) * 16;
+    return 0;
+}
+
+template <bool U8>
+cudaError_t maxmin_tiled(const void* Y, int64_t n, int d, int l, int64_t first, MaxminWs ws, int64_t* idx_out,
+                         size_t smem, cudaStream_t st) {
+    k_maxmin_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, first, ws.mind, ws.cur, idx_out, ws.counter);
+    if (U8) k_norms8<<<(unsigned)((n + 7) / 8), 256, 0, st>>>((const uint8_t*)Y, n, d, ws.nrm8);
+    cudaError_t e = cudaFuncSetAttribute(k_maxmin_tiles<U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_maxmin_tiles<U8>, 32 * kTw, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (n + 31) / 32;
+    int64_t grid = std::min<int64_t>((int64_t)sms * std::max(per, 1), (tiles + kTw - 1) / kTw);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxminGridCap));
+    for (int k = 1; k < l; ++k)
+        k_maxmin_tiles<U8><<<(unsigned)grid, 32 * kTw, smem, st>>>(Y, n, d, ws.nrm8, ws.cur, ws.mind, ws.part_v,
+                                                                  ws.part_i, ws.counter, idx_out, k);
+    note_launch(l + (U8 ? 1 : 0));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t first, MaxminWs ws,
                           int64_t* idx_out, cudaStream_t st) {
     if (n <= 0 || d <= 0 || l <= 0 || d > kMaxminD) return cudaErrorInvalidValue;
+    const size_t tsm = maxmin_tiles_smem(dt, d);
+    if (tsm > 0 && tsm <= 200 * 1024 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+        if (dt == MDS_IN_U8) return maxmin_tiled<true>(Y, n, d, l, first, ws, idx_out, tsm, st);
+        return maxmin_tiled<false>(Y, n, d, l, first, ws, idx_out, tsm, st);
+    }
     const int grid = maxmin_grid();
     if (dt == MDS_IN_F64) return maxmin_rounds((const double*)Y, n, d, l, first, ws, idx_out, grid, st);
     if (dt == MDS_IN_F32) return maxmin_rounds((const float*)Y, n, d, l, first, ws, idx_out, grid, st);

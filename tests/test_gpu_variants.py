@@ -61,13 +61,16 @@ def test_maxmin_ties_and_duplicates(gb, dtype):
     the duplicates (distance 0) are chosen in index order; l = n takes every
     row exactly once."""
     g = np.stack(np.meshgrid(np.arange(7), np.arange(5), np.arange(3), indexing="ij"), -1).reshape(-1, 3)
-    Y = np.concatenate([g, g])[np.random.default_rng(1).permutation(2 * len(g))].astype(dtype)
-    n = len(Y)
-    for l, first in ((n, 0), (60, 33), (n, n - 1)):
-        want = O.maxmin_landmarks(Y, l, first)
-        got = gb.mds_landmarks_maxmin(dev(Y), l, first).cpu().numpy()
-        assert np.array_equal(got, want)
-    assert sorted(gb.mds_landmarks_maxmin(dev(Y), n, 0).cpu().numpy()) == list(range(n))
+    Y3 = np.concatenate([g, g])[np.random.default_rng(1).permutation(2 * len(g))].astype(dtype)
+    n = len(Y3)
+    # d = 3 takes the general round; zero columns up to d = 16 (the same
+    # distances) take the tiled round of FP32 and byte rows
+    for Y in (Y3, np.concatenate([Y3, np.zeros((n, 13), dtype=dtype)], axis=1)):
+        for l, first in ((n, 0), (60, 33), (n, n - 1)):
+            want = O.maxmin_landmarks(Y, l, first)
+            got = gb.mds_landmarks_maxmin(dev(Y), l, first).cpu().numpy()
+            assert np.array_equal(got, want)
+        assert sorted(gb.mds_landmarks_maxmin(dev(Y), n, 0).cpu().numpy()) == list(range(n))
 
 
 def test_maxmin_full_size_prefix_and_gaps(gb):
