@@ -715,6 +715,26 @@ class Leg:
         return out
 
 
+PHASES = ("exchange", "checks", "matvec", "pass_newest", "publish", "finish")
+
+
+def lanczos_phases(reset=False):
+    """The eigen-solver's phase cycles (a library built with
+    GBMDS_PHASE_TIMERS=1), or None."""
+    from paper_2007_11919_gb300 import mds as M
+    L = M._lib()
+    L.mds_lanczos_phase_cycles.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.mds_lanczos_phase_cycles.restype = ctypes.c_int
+    out = (ctypes.c_double * 7)()
+    if L.mds_lanczos_phase_cycles(out if not reset else None, 1 if reset else 0) != 0:
+        return None
+    if reset:
+        return {}
+    tot = sum(out[:6]) or 1.0
+    return {"cta_steps": out[6], "cycles_per_cta_step": {k: out[i] / max(out[6], 1.0) for i, k in enumerate(PHASES)},
+            "share": {k: out[i] / tot for i, k in enumerate(PHASES)}}
+
+
 def time_legs(legs, steps, flush, stream):
     """Steps of all legs in turn, the L2 flushed before each call; per leg the
     CUDA-event time of every call and the library's stats of that call."""
@@ -815,8 +835,10 @@ def ours(args):
         tdist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    have_phases = lanczos_phases(reset=True) is not None
     ms, stats = time_legs(legs, args.steps, flush, stream)
     torch.cuda.synchronize()
+    phases = lanczos_phases() if have_phases else None
     if world > 1:
         tdist.barrier()
     clk = clocks.stop()
@@ -876,7 +898,8 @@ def ours(args):
                          "l2": "flushed before every call (256 MB write)", "parallelism": f"replicas{world}"},
               "procrustes_rel_err_vs_oracle": err, "legs": reps, "roofline": roof, "cpu_baseline": cpu,
               "e2e": e2e, "gpu_launches": launches, "clocks": clk, "gpu": torch.cuda.get_device_name(dev),
-              "configs": configs, "serve": serve})
+              "configs": configs, "serve": serve,
+              **({"lanczos_phases": dict(phases, build="GBMDS_PHASE_TIMERS=1 (instrumented)")} if phases else {})})
     if world > 1:
         tdist.destroy_process_group()
 

@@ -435,6 +435,16 @@ typedef struct {
 void mds_set_timing(int on);
 int mds_last_stats(mds_stats* out);
 
+/* Eigen-solver phase timers, compiled in only when the library is built with
+ * GBMDS_PHASE_TIMERS=1 (otherwise MDS_ERR_UNSUPPORTED).  out[0..6]: clock
+ * cycles summed over all CTAs of every launch since the last reset, spent in
+ * [0] the exchange and completion of the second Gram-Schmidt pass, [1] the
+ * convergence checks, [2] the matrix-vector product, [3] the pass against the
+ * two newest vectors, [4] publishing the new vector, [5] the finish (Ritz
+ * vectors, signs); out[6] the CTA-steps.  reset = 1 zeroes the counters
+ * (out may then be NULL).  Process-wide; the cycles are SM clocks. */
+int mds_lanczos_phase_cycles(double* out, int reset);
+
 /* ------------------------------------------------------------------ */
 /* Failure injection (testing the error paths; the paper has no
  * counterpart).  Neither faults the GPU: each makes an ordinary, bounded

@@ -31,9 +31,16 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _flags() -> list[str]:
+    """Compiler flags; GBMDS_PHASE_TIMERS=1 compiles the eigen-solver's phase
+    timers in (mds_lanczos_phase_cycles)."""
+    extra = ["-DGBMDS_PHASE_TIMERS"] if os.environ.get("GBMDS_PHASE_TIMERS") == "1" else []
+    return FLAGS + extra
+
+
 def _compile(src: str, ptxas_v: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *_flags(), "-c", src, "-o", obj]
     if ptxas_v:
         cmd += ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -50,7 +57,10 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     deps.append(os.path.join(HERE, "..", "include", "gbmds.h"))
-    if (not force and not verbose_ptxas and os.path.exists(LIB)
+    stamp = os.path.join(BUILD, "flags")
+    flags = " ".join(_flags())
+    same_flags = os.path.exists(stamp) and open(stamp).read() == flags
+    if (not force and not verbose_ptxas and same_flags and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in deps)):
         return LIB
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
@@ -61,6 +71,8 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return LIB
 
 

@@ -619,6 +619,11 @@ int mds_version(void) { return 1; }
 
 void mds_set_timing(int on) { g_timing = on != 0; }
 
+int mds_lanczos_phase_cycles(double* out, int reset) {
+    if (!out && !reset) return MDS_ERR_ARG;
+    return lanczos_phase_cycles(out, reset);
+}
+
 void mds_set_wait_limit_ns(unsigned long long ns) { g_wait_ns.store(ns); }
 
 void mds_inject_alloc_failures(int count) { g_fail_allocs.store(count > 0 ? count : 0); }

@@ -174,6 +174,9 @@ cudaError_t launch_lanczos(const LanczosArgs& a, int cluster, cudaStream_t st, b
 double lanczos_step_bytes(int n, int cs, int q_f32, int sym, int team);
 // 1 when the last launch_lanczos on this thread ran a team of clusters.
 int lanczos_last_team();
+// The phase-timer build's cycle counters (7 values; reset = 1 zeroes them);
+// MDS_ERR_UNSUPPORTED in a build without them.
+int lanczos_phase_cycles(double* out, int reset);
 // Shared memory one CTA of the eigen-solver needs for a cluster of cs CTAs.
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r);
 constexpr size_t kMaxSmem = 220 * 1024;

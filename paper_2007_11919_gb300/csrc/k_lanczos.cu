@@ -65,10 +65,42 @@
 namespace cg = cooperative_groups;
 
 namespace gbmds {
+
+__device__ unsigned long long g_phase_cycles[8];
+
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+
+// Phase timers of the eigen-solver, compiled in only with -DGBMDS_PHASE_TIMERS
+// (the build's GBMDS_PHASE_TIMERS=1): per CTA, clock64 cycles spent in each
+// phase of the Lanczos steps, added over all CTAs into g_phase_cycles at the
+// end of each problem: [0] exchange and completion of the second pass,
+// [1] convergence checks, [2] matvec (with the symmetric ranges' collection),
+// [3] the pass against v_{j-1}, v_j, [4] publishing w_1, [5] the finish
+// (eigenvectors of T, Ritz vectors, signs), [6] CTA-steps.
+#ifdef GBMDS_PHASE_TIMERS
+#define PHASE_DECL long long ph_t = clock64(), ph[6] = {0, 0, 0, 0, 0, 0}
+#define PHASE(i)                           \
+    do {                                   \
+        const long long ph_n = clock64();  \
+        ph[i] += ph_n - ph_t;              \
+        ph_t = ph_n;                       \
+    } while (0)
+#define PHASE_DUMP(steps)                                                                        \
+    do {                                                                                         \
+        if (threadIdx.x == 0) {                                                                  \
+            for (int ph_i = 0; ph_i < 6; ++ph_i)                                                 \
+                atomicAdd(&g_phase_cycles[ph_i], (unsigned long long)ph[ph_i]);                  \
+            atomicAdd(&g_phase_cycles[6], (unsigned long long)(steps));                          \
+        }                                                                                        \
+    } while (0)
+#else
+#define PHASE_DECL
+#define PHASE(i)
+#define PHASE_DUMP(steps)
+#endif
 constexpr int kRing = 4;           // stage barriers per warp (stages in use: as many as fit)
 constexpr int kChunkB = 4096;      // longest row segment of Q
 constexpr int kWarpRingB = 8192;   // stage bytes per warp
@@ -1069,6 +1101,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
 
     const int kmin = min(kmax, max(2 * r, 8));
     int next_check = kmin;
+    PHASE_DECL;
     double prev_worst = -1.0;
     int k = 0, prev_k = 0;
     bool converged = false, have_vectors = false;
@@ -1179,6 +1212,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
         const double tnorm = S.red[40];
         const bool breakdown = j > 0 && S.red[41] != 0.0;
         const bool do_check = j > 0 && (breakdown || k == kmax || k >= next_check);
+        PHASE(0);
         if (do_check && k >= r) {
             // the stage rings hold the check's workspace from here on
             qok = qs_drain(Qs) && qok;
@@ -1311,6 +1345,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             next_check = k + gap;
             if (!breakdown) qs_prime(Qs);   // the stages are Q stages again
         }
+        PHASE(1);
         if (breakdown || k == kmax) break;  // breakdown with k < r: fewer Ritz values than wanted
 
         // ---- w = Q u_j on this CTA's rows (streamed); no prefetch into a step
@@ -1324,6 +1359,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             qok = qs_matvec<DF>(Qs, n, r0, S.vfull, S.wloc, j + 1 < next_check && j + 1 < kmax) && qok;
         }
         __syncthreads();
+        PHASE(2);
 
         // ---- pass against v_{j-1}, v_j: w_1 = w - c_{j-1} v_{j-1} - c_j v_j
         const int ia = j > 0 ? j - 1 : 0;
@@ -1350,6 +1386,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             cgs_update<DF>(B, ldq, r0, nr, ia, j, S.cfull, S.cdf, S.wloc);
         }
         __syncthreads();
+        PHASE(3);
 
         // ---- publish w_1 and its partial dots against v_0..v_j with ||w_1||^2
         cgs_dots<DF>(B, ldq, r0, nr, 0, j, S.wloc, part[pb], true);
@@ -1367,6 +1404,7 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
                 if (tm.G > 1) tm.v[r0 + rr] = S.wloc[rr];
             }
         }
+        PHASE(4);
     }
 
     // ---- finish: status, orthonormal eigenvectors of T_k (rank 0), Ritz vectors (all)
@@ -1610,6 +1648,8 @@ __device__ void solve_problem(const LanczosArgs& A, int pj, cg::cluster_group& c
             scr[t] = S.alpha[t];
             scr[L + t] = S.beta[t];
         }
+    PHASE(5);
+    PHASE_DUMP(k);
 }
 
 // Persistent batched solver: each cluster takes parts from an atomic queue in
@@ -1693,6 +1733,20 @@ double lanczos_step_bytes(int n, int cs, int q_f32, int sym, int team) {
 }
 
 int lanczos_last_team() { return g_last_team; }
+
+int lanczos_phase_cycles(double* out, int reset) {
+#ifdef GBMDS_PHASE_TIMERS
+    unsigned long long h[8] = {};
+    if (reset) return cudaMemcpyToSymbol(g_phase_cycles, h, sizeof(h)) == cudaSuccess ? 0 : MDS_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(h, g_phase_cycles, sizeof(h)) != cudaSuccess) return MDS_ERR_CUDA;
+    for (int i = 0; i < 7; ++i) out[i] = (double)h[i];
+    return 0;
+#else
+    (void)out;
+    (void)reset;
+    return MDS_ERR_UNSUPPORTED;
+#endif
+}
 
 size_t lanczos_smem_bytes(int max_n, int cs, int mmax, int r) {
     return smem_doubles(max_n, cs, mmax, r) * sizeof(double) + kMaxR * sizeof(double);

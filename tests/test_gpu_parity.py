@@ -97,12 +97,14 @@ def test_cluster_sizes_agree(gb, cluster):
 
 
 @pytest.mark.parametrize("n,cluster", [(500, 3), (500, 4), (500, 5), (500, 8), (500, 16), (1021, 3),
-                                       (1021, 6), (1021, 7), (130, 5), (130, 16), (2050, 8)])
+                                       (1021, 6), (1021, 7), (130, 5), (130, 16), (2050, 8), (1100, 3),
+                                       (1500, 4), (2050, 5), (2050, 16), (3001, 9), (4000, 16)])
 def test_symmetric_ranges_classical_f32(gb, n, cluster):
     """FP32 Q in one cluster: the symmetric ranges (each off-diagonal block of
     Q read once, used for both triangles) against the oracle and against the
     whole-row matvec, for odd and even cluster sizes, ranges that wrap, and
-    sizes where the ranges are not used (too few rows per CTA, rows too long)."""
+    sizes where the ranges are not used (too few rows per CTA; ranges longer
+    than one stage: n = 1,100 ... 4,000)."""
     Y = W.gaussian_dominant(n, 30, 5, seed=n + cluster, dtype=np.float32)
     Xo, lo, _, _ = O.classical_mds(O.sq_dist(Y, Y), 5)
     X, lam = gb.mds_classical(dev(Y), 5, "f32", cluster=cluster)
