@@ -64,7 +64,13 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NCU_TRAFFIC = {
     "k_gower_tck.cu": {"sha": "54d0c9db6af3e843", "per": "row", "bytes": 1688.6},
     "k_gower_tc.cu": {"sha": "a89affadd1612472", "per": "row", "bytes": 452.0},
-    "k_lanczos.cu": {"sha": "2b3722bfea4ec539", "per": "streamed byte", "bytes": 0.8287, "workloads": ("dc",)},
+    # per byte of Q streamed, per workload
+    # (profiles/k_lanczos_image_dc_fp8_n814255.md, profiles/k_lanczos_dc_f32_n100000.md)
+    "k_lanczos.cu": {"sha": "8551ed1188245aa2", "per": "streamed byte", "bytes": {"image_dc": 1.0342, "dc": 0.8236}},
+    # per row of Y per round (profiles/k_maxmin_tiles_maxmin_f32_n1000000.md)
+    "k_maxmin.cu": {"sha": "ed0ac2bd3bb43525", "per": "row per round", "bytes": 412.0},
+    # per row of Y (profiles/k_affine_project_bulk_affine_f32_n1000000.md)
+    "k_affine.cu": {"sha": "f592f8bbd752a734", "per": "row", "bytes": 432.2},
 }
 
 # name -> (workload, method)
@@ -176,6 +182,13 @@ class ClockSampler:
                  "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi's start-up (NVML initialisation) can hold up this
+        # process's CUDA calls for up to a second: the timed region starts
+        # only once its first sample is written
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -558,9 +571,9 @@ class Leg:
         if self.method in ("dc", "fast"):
             return lan, None
         if self.method == "pivot":
-            pass_ms = sum(statistics.mean(s["stage_ms"][k] for s in stats) for k in ("prep", "dist", "post"))
-            other = self._passes_roof(pass_ms, peaks)
-            return (other, lan) if pass_ms > eig_ms else (lan, other)
+            dist_ms = statistics.mean(s["stage_ms"]["dist"] for s in stats)
+            other = self._scatter_roof(dist_ms)
+            return (other, lan) if dist_ms > eig_ms else (lan, other)
         other = self._affine_roof(post_ms, peaks) if self.method == "affine" else self._projection_roof(post_ms, peaks)
         return (other, lan) if post_ms > eig_ms else (lan, other)
 
@@ -586,8 +599,8 @@ class Leg:
                 "fp64_equiv_flops_per_launch": flops, "traffic": None}
         src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_lanczos.cu")
         tr = NCU_TRAFFIC["k_lanczos.cu"]
-        if tr["sha"] == file_sha(src) and self.name in tr["workloads"]:
-            roof["traffic"] = tr["bytes"] * qread
+        if tr["sha"] == file_sha(src) and self.name in tr["bytes"]:
+            roof["traffic"] = tr["bytes"][self.name] * qread
         return roof
 
     def _projection_roof(self, kms, peaks):
@@ -626,10 +639,14 @@ class Leg:
         nbytes = w.n * w.d * self.Y.dtype.itemsize + w.n * w.r * (8 if w.prec == "f64" else 4)
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = nbytes / (kms * 1e-3) / 1e9
-        return {"kernel": "k_affine_project (one pass over Y: X = (Y - y_L) U_r), with the model and axes kernels",
+        tr = NCU_TRAFFIC["k_affine.cu"]
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_affine.cu")
+        traffic = tr["bytes"] * w.n if (tr["sha"] == file_sha(src) and self.Y.dtype == np.float32) else None
+        return {"kernel": "k_affine_project_bulk (one pass over Y: X = (Y - y_L) U_r; the stage holds this "
+                          "launch alone)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
-                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": None}
+                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": traffic}
 
     def _maxmin_roof(self, stats, peaks):
         # Algorithmic bytes: every round streams all n rows once (l - 1 rounds)
@@ -638,22 +655,30 @@ class Leg:
         nbytes = (w.l - 1) * w.n * w.d * self.Y.dtype.itemsize
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = nbytes / (kms * 1e-3) / 1e9
-        return {"kernel": "k_maxmin_round (one streaming pass over Y per landmark, running minima, argmax)",
+        tr = NCU_TRAFFIC["k_maxmin.cu"]
+        src = os.path.join(ROOT, "paper_2007_11919_gb300", "csrc", "k_maxmin.cu")
+        traffic = tr["bytes"] * w.n * (w.l - 1) if tr["sha"] == file_sha(src) else None
+        return {"kernel": "k_maxmin_tiles (one streaming pass over Y per landmark, running minima, argmax; "
+                          "all l - 1 rounds)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
-                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": None}
+                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": traffic}
 
-    def _passes_roof(self, kms, peaks):
-        # Pivot MDS outside the eigen-solve: three passes over Y (column means,
-        # scatter matrix, projection) and X written once
+    def _scatter_roof(self, kms):
+        # Pivot MDS's scatter matrix S = Y_c^T Y_c: FP32 products (double-FP32
+        # sums), d (d + 1) / 2 distinct products per row; bound by the FP32 FMA
+        # pipe: SMs x 128 lanes x 2 flops x the 2,070 MHz maximum SM clock.
+        import torch
         w = self.w
-        nbytes = 3 * w.n * w.d * self.Y.dtype.itemsize + w.n * w.r * 4
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        achieved = nbytes / (kms * 1e-3) / 1e9
-        return {"kernel": "k_colsum + k_scatter_tiles + k_affine_project (three passes over Y)", "bound": "hbm",
-                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
-                "launch_ms": kms, "bytes_per_launch": nbytes, "traffic": None}
+        flops = 2.0 * w.n * w.d * (w.d + 1) / 2
+        sms = torch.cuda.get_device_properties(self.Y.device).multi_processor_count
+        peak = sms * 128 * 2 * 2.070e9 / 1e12
+        achieved = flops / (kms * 1e-3) / 1e12
+        return {"kernel": "k_scatter_tri (scatter matrix of all n rows, upper triangle of 4 x 4 thread tiles, "
+                          "FP32 FMA)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flops x 2.07 GHz (derived)",
+                "launch_ms": kms, "flops_per_launch": flops, "traffic": None}
 
     def describe(self):
         w = self.w

@@ -206,7 +206,8 @@ int mds_landmarks_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t
  * of X has its entry of largest magnitude positive (lowest row on a tie).
  * opts->prec: MDS_PREC_F64 (FP64 throughout) or MDS_PREC_F32 (the scatter
  * matrix from FP32 products summed in double-FP32, the projection in FP32;
- * the means, C^T C and the eigen-solve in FP64); else MDS_ERR_UNSUPPORTED.
+ * the means, C^T C and the eigen-solve in FP64); else MDS_ERR_UNSUPPORTED,
+ * which d > 4096 also returns (the workspace size is then 0).
  * Requires 1 <= r <= min(l, d, 32); MDS_ERR_RANK if sigma_r^2 <=
  * rank_tol * sigma_1^2. */
 size_t mds_pivot_workspace_size(int64_t n, int d, int l, int r, int prec);
@@ -324,7 +325,10 @@ int mds_fast(const void* Y, int dt, int64_t n, int d, const int64_t* perm, int n
  *         `stream` (NULL = opts->stream); execute waits for it and returns
  *         the status of the run.
  *   info: cluster size in use, nodes of the captured graph, and per cluster
- *         size 0..16 the autotuner's time in ms (0 = not tried). */
+ *         size 0..16 the autotuner's time in ms (0 = not tried).
+ * With a tuning cache (mds_set_tune_cache) the autotuner first looks its
+ * batch shape up there and, on a hit, takes the stored cluster size and
+ * trial times without timing anything; after timing it stores its choice. */
 typedef struct mds_dc_plan_s* mds_dc_plan;
 int mds_dc_plan_create(int64_t n, int d, int dt, int p, const int64_t* part_ptr, int c, int r,
                        const mds_opts* opts, int tune, mds_dc_plan* out);
@@ -462,6 +466,33 @@ int mds_lanczos_phase_cycles(double* out, int reset);
  *   library loads. */
 void mds_set_wait_limit_ns(unsigned long long ns);
 void mds_inject_alloc_failures(int count);
+
+/* ------------------------------------------------------------------ */
+/* Tuning cache (the autotuner's memory across processes; the paper has no
+ * counterpart).  A JSON file, one entry per line:
+ *   {"key": "<kernel and the quantities its choice depends on>", "value": V,
+ *    "trial_ms": [...]}
+ * Today it holds the eigen-solver's cluster size (CTAs per eigenproblem,
+ * 1..16) per batch shape: problem count, largest problem, sum of squared
+ * sizes, step cap, r, Q precision, symmetric ranges allowed, SM count and
+ * compute capability.  D&C plans created with tune store what they measured
+ * and reuse a stored value; every call whose opts->cluster is 0 uses a stored
+ * value for its batch shape instead of the heuristic.  Updates replace the
+ * file through a temporary file and a rename; concurrent writers can lose an
+ * update, never corrupt the file.
+ * mds_set_tune_cache(path): the cache file (NULL or "" turns the cache off).
+ *   Without a call, the environment variable GBMDS_TUNE_CACHE names it at
+ *   first use; otherwise the cache is off.  Process-wide.  Returns MDS_OK.
+ * mds_tune_cache_lookup(key, &value): value = the stored value, or 0 when the
+ *   key is absent or the cache is off; MDS_ERR_ARG for a null or malformed
+ *   key (empty, longer than 1,024 bytes, or holding a quote, a backslash or
+ *   a line break).
+ * mds_tune_cache_store(key, value): adds or replaces an entry; MDS_ERR_ARG
+ *   for a malformed key, a cache that is off or a file that cannot be
+ *   written. */
+int mds_set_tune_cache(const char* path);
+int mds_tune_cache_lookup(const char* key, int* value);
+int mds_tune_cache_store(const char* key, int value);
 
 #ifdef __cplusplus
 }

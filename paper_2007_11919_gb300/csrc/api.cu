@@ -8,6 +8,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 using namespace gbmds;
@@ -90,8 +92,28 @@ thread_local int g_cluster = 0;
 // events as event-record nodes of the graph.
 thread_local cudaEvent_t* g_capture_ev = nullptr;
 
-// Marks the start (stage = -1) or the end of a pipeline stage on the stream.
-void tmark(int stage, cudaStream_t st) {
+// NVTX ranges for profilers (nvtx3, header-only; inert unless a tool is
+// attached): one range per call, named for its entry point, and inside it one
+// per pipeline stage (the stages of mds_stats), on the host thread that issues
+// the call's launches.  A range left open by an early error return is closed
+// by the next call on the thread.
+thread_local nvtxRangeId_t g_nvtx_call = 0, g_nvtx_stage = 0;
+const char* const kStageNames[5] = {"gbmds prep", "gbmds dist", "gbmds center", "gbmds eig", "gbmds post"};
+
+// Closes the open stage range and opens stage `next` (none when next > 4).
+void nvtx_stage(int next) {
+    if (g_nvtx_stage) nvtxRangeEnd(g_nvtx_stage);
+    g_nvtx_stage = 0;
+    if (next >= 0 && next <= 4) g_nvtx_stage = nvtxRangeStartA(kStageNames[next]);
+}
+
+void nvtx_end_call() {
+    nvtx_stage(5);
+    if (g_nvtx_call) nvtxRangeEnd(g_nvtx_call);
+    g_nvtx_call = 0;
+}
+
+void record_mark(int stage, cudaStream_t st) {
     if (g_capture_ev) {
         cudaEventRecordWithFlags(g_capture_ev[stage + 1], st, cudaEventRecordExternal);
         return;
@@ -104,12 +126,21 @@ void tmark(int stage, cudaStream_t st) {
     cudaEventRecord(g_ev[stage + 1], st);
 }
 
-void begin_call(cudaStream_t st) {
+// Marks the start (stage = -1) or the end of a pipeline stage on the stream.
+void tmark(int stage, cudaStream_t st) {
+    record_mark(stage, st);
+    nvtx_stage(stage + 1);
+}
+
+void begin_call(cudaStream_t st, const char* what) {
+    nvtx_end_call();
+    g_nvtx_call = nvtxRangeStartA(what);
     g_launches = 0;
     g_cluster = 0;
     g_last = mds_stats{};
     if (g_timing || g_capture_ev)
-        for (int i = 0; i <= 5; ++i) tmark(i - 1, st);  // all stages empty by default
+        for (int i = 0; i <= 5; ++i) record_mark(i - 1, st);  // all stages empty by default
+    nvtx_stage(0);
 }
 
 struct Arena {
@@ -239,6 +270,14 @@ void carve_batch(Batch& B, Arena& A) {
     }
 }
 
+// Tuning-cache key of a batch's eigen-solve (the batch shape, Q precision,
+// whether symmetric ranges are allowed, the device).
+std::string batch_tune_key(const Batch& B, int q_f32, int sym) {
+    double sum_n2 = 0.0;
+    for (const ProbDesc& P : B.desc) sum_n2 += (double)P.n * P.n;
+    return lanczos_tune_key(B.p, B.max_n, sum_n2, B.mmax, B.r, q_f32, sym);
+}
+
 int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
     if (requested > 0) return std::min(requested, 16);
     int dev = 0, sms = 148;
@@ -281,7 +320,7 @@ struct GramOp {
 // vector work run in double-FP32 (with FP64 scalars).
 int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
                   const int64_t* anchors, const int64_t* own, int acc_f64, int eig_f64, const Opts& o,
-                  bool upload = true, const GramOp* gram = nullptr, bool center = true) {
+                  bool upload = true, const GramOp* gram = nullptr, bool center = true, bool mark_dist = true) {
     if (upload) {
         CK(cudaMemcpyAsync(B.d_desc, B.desc.data(), sizeof(ProbDesc) * B.p, cudaMemcpyHostToDevice, o.st));
         CK(cudaMemcpyAsync(B.d_order, B.order.data(), sizeof(int) * B.p, cudaMemcpyHostToDevice, o.st));
@@ -302,7 +341,7 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
         CK(launch_sqdist_batched(Y, dt, d, nrm, anchors, own, B.d_desc, B.p, B.max_tiles, acc_f64, eig_f64,
                                  B.q, B.rp, o.st));
     }
-    tmark(1, o.st);
+    if (mark_dist) tmark(1, o.st);   // else the caller marked the end of its distance stage
     // An FP64 eigenproblem keeps Q and the products in IEEE FP64.  The
     // divide-and-conquer parts of the other precisions, whose Q carries
     // FP32-level distance rounding anyway, store Q in FP32 and run the
@@ -338,6 +377,13 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     if (B.tbar) CK(cudaMemsetAsync(B.tbar, 0, 4 * sizeof(unsigned), o.st));
     tmark(2, o.st);
     g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r);
+    if (o.cluster == 0 && tune_enabled()) {
+        // a cluster size an autotuner measured for this batch shape
+        int v = 0;
+        if (tune_lookup(batch_tune_key(B, q_f32, a.sym), &v, nullptr, 0) && v >= 1 && v <= 16 &&
+            lanczos_smem_bytes(B.max_n, v, B.mmax, B.r) <= kMaxSmem)
+            g_cluster = v;
+    }
     CK(launch_lanczos(a, g_cluster, o.st, o.cluster == 0));
     B.team = lanczos_last_team();
     tmark(3, o.st);
@@ -370,6 +416,7 @@ int finish(const Batch* B, const int* d_flag, const Opts& o, const int* d_kerr =
             cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]);
             g_last.stage_ms[i] = ms;
         }
+    nvtx_end_call();
     if (B) return batch_status(*B, hs.data(), steps.data(), flag, kerr ? kerr : (team_abort ? MDS_ERR_TIMEOUT : 0));
     g_last.launches = g_launches;
     g_last.cluster = g_cluster;
@@ -665,7 +712,7 @@ int mds_landmarks_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t
     const size_t need = maxmin_layout(M, nullptr, n);
     if ((s = check_ws(o, need))) return s;
     maxmin_layout(M, o.ws, n);
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     tmark(0, o.st);
     CK(launch_maxmin(Y, dt, n, d, l, first, M, idx_out, o.st));
     tmark(1, o.st);   // stage "dist": the l - 1 distance passes and picks
@@ -697,7 +744,7 @@ int mds_classical(const void* Y, int dt, int64_t n, int d, int r, const mds_opts
     const size_t need = classical_layout(W, nullptr, n, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (classical_layout(W, o.ws, n, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(launch_iota(W.iota, n, o.st));
     const int f64 = o.prec == MDS_PREC_F64;
@@ -725,7 +772,7 @@ int mds_classical_dist(const double* D2, int64_t n, int r, const mds_opts* opts,
     const size_t need = classical_layout(W, nullptr, n, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (classical_layout(W, o.ws, n, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     CK(cudaMemcpyAsync(W.B.d_desc, W.B.desc.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, o.st));
     tmark(0, o.st);
     CK(launch_load_dist(D2, W.B.d_desc, W.B.q, W.B.rp, (int)n, W.B.max_tiles, o.st));
@@ -802,6 +849,7 @@ static int make_model(InterpWs& W, int kind, const Opts& o, int l, int d, int r,
 
 struct AffineWs {
     int* flag;
+    int* kerr;        // status word of the pass over Y
     double* Lg;       // l x d: the landmark rows, gathered as FP64
     int64_t* iota;    // l
     double* nrm;      // l: their squared norms (the landmark problem indexes Lg through iota)
@@ -817,6 +865,7 @@ struct AffineWs {
 static size_t affine_layout(AffineWs& W, char* base, int d, int l, int r, int mmax) {
     Arena A{base, 0};
     W.flag = A.take<int>(1);
+    W.kerr = A.take<int>(1);
     W.Lg = A.take<double>((size_t)l * d);
     W.iota = A.take<int64_t>(l);
     W.nrm = A.take<double>(l);
@@ -851,9 +900,10 @@ int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_
     const size_t need = affine_layout(W, nullptr, d, l, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (affine_layout(W, o.ws, d, l, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
     CK(launch_check_idx(landmark_idx, l, n, W.flag, o.st));
     // the landmark problem of mds_interpolate on the gathered landmark rows
     // (FP64 copies of the inputs: the same distances in the same arithmetic)
@@ -864,15 +914,17 @@ int mds_interpolate_affine(const void* Y, int dt, int64_t n, int d, const int64_
     if ((s = run_eig_batch(W.B, W.Lg, MDS_IN_F64, d, W.nrm, nullptr, W.iota, f64, 1, o))) return s;
     CK(launch_interp_model(W.B.v, W.B.lam, W.B.q, W.B.desc[0].ldq, 0, l, r, nullptr, nullptr, nullptr,
                            nullptr, W.bias, var, o.st));
-    CK(launch_affine(Y, dt, n, d, W.Lg, l, W.B.v, W.B.lam, r, f64, W.scale, W.ybar, W.ybar_f, W.U, W.U_f, X,
-                     o.st));
-    return finish(&W.B, W.flag, o);
+    CK(launch_affine_axes(W.Lg, l, d, W.B.v, W.B.lam, r, W.scale, W.ybar, W.ybar_f, W.U, W.U_f, o.st));
+    tmark(3, o.st);   // the stage "post" is the one pass over Y
+    CK(launch_affine_project(Y, dt, n, d, W.ybar, W.ybar_f, W.U, W.U_f, r, f64, X, W.kerr, o.st));
+    return finish(&W.B, W.flag, o, W.kerr);
 }
 
 // ---------------------------------------------------------------- pivot MDS
 
 struct PivotWs {
     int* flag;
+    int* kerr;        // status word of the pass over Y
     double* cpart;    // column-sum partials
     double* mean;     // d: mean of all n rows
     float* mean_f;
@@ -893,6 +945,7 @@ struct PivotWs {
 static size_t pivot_layout(PivotWs& W, char* base, int64_t n, int d, int l, int r, int mmax) {
     Arena A{base, 0};
     W.flag = A.take<int>(1);
+    W.kerr = A.take<int>(1);
     W.cpart = A.take<double>(colmean_part_doubles(n, d));
     W.mean = A.take<double>(d);
     W.mean_f = A.take<float>(d);
@@ -914,7 +967,7 @@ static size_t pivot_layout(PivotWs& W, char* base, int64_t n, int d, int l, int 
 }
 
 size_t mds_pivot_workspace_size(int64_t n, int d, int l, int r, int prec) {
-    if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0 || r > kMaxR) return 0;
+    if (n <= 0 || d <= 0 || l <= 0 || l > kMaxEigN || r <= 0 || r > kMaxR || !scatter_supported(d)) return 0;
     if (prec != MDS_PREC_F64 && prec != MDS_PREC_F32) return 0;
     PivotWs W;
     return pivot_layout(W, nullptr, n, d, l, r, kDefaultSteps) + 256;
@@ -928,14 +981,15 @@ int mds_pivot(const void* Y, int dt, int64_t n, int d, const int64_t* pivot_idx,
     if (!Y || !X || !var || !pivot_idx || !valid_dt(dt) || n < 2 || d <= 0 || l < 1 || l > n || l > kMaxEigN ||
         r <= 0 || r > kMaxR || r > l || r > d)
         return MDS_ERR_ARG;
-    if (o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) return MDS_ERR_UNSUPPORTED;
+    if ((o.prec != MDS_PREC_F64 && o.prec != MDS_PREC_F32) || !scatter_supported(d)) return MDS_ERR_UNSUPPORTED;
     PivotWs W;
     const size_t need = pivot_layout(W, nullptr, n, d, l, r, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (pivot_layout(W, o.ws, n, d, l, r, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
+    CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
     CK(cudaMemsetAsync(W.sg_cnt, 0, sizeof(unsigned), o.st));
     CK(launch_check_idx(pivot_idx, l, n, W.flag, o.st));
     // the centre and the scatter matrix of all n rows, the pivot rows
@@ -943,18 +997,20 @@ int mds_pivot(const void* Y, int dt, int64_t n, int d, const int64_t* pivot_idx,
     CK(launch_gather_rows(Y, dt, n, d, pivot_idx, l, 1, W.Lg, nullptr, nullptr, o.st));
     tmark(0, o.st);
     CK(launch_scatter(Y, dt, n, d, W.mean, f64, W.spart, W.S, o.st));
+    tmark(1, o.st);   // the stage "dist" is the scatter matrix; "center" forms C^T C
     // C^T C = P_c S P_c^T into the eigen-solver's Q slot (FP64)
-    CK(launch_gemm_nt(W.Lg, d, W.mean, W.S, d, nullptr, l, d, d, W.T, d, o.st));
+    CK(launch_gemm_nt(W.Lg, d, W.mean, W.S, d, nullptr, l, d, d, W.T, d, 0, o.st));
     const ProbDesc& P0 = W.B.desc[0];
-    CK(launch_gemm_nt(W.T, d, nullptr, W.Lg, d, W.mean, l, l, d, W.B.q + P0.q_off, P0.ldq, o.st));
-    tmark(1, o.st);
-    if ((s = run_eig_batch(W.B, nullptr, 0, 0, nullptr, nullptr, nullptr, 1, 1, o, true, nullptr, false))) return s;
+    CK(launch_gemm_nt(W.T, d, nullptr, W.Lg, d, W.mean, l, l, d, W.B.q + P0.q_off, P0.ldq, 1, o.st));
+    if ((s = run_eig_batch(W.B, nullptr, 0, 0, nullptr, nullptr, nullptr, 1, 1, o, true, nullptr, false, false)))
+        return s;
     // M = P_c^T W_r Sigma_r^{-1} Lambda_r^{1/2}; X = Y_c M; the sign convention
     CK(launch_pivot_scale(W.B.lam, r, n, l, W.scale, var, o.st));
     CK(launch_axes(W.Lg, l, d, W.mean, W.B.v, W.scale, r, W.U, W.U_f, o.st));
-    CK(launch_affine_project(Y, dt, n, d, W.mean, W.mean_f, W.U, W.U_f, r, f64, X, o.st));
+    tmark(3, o.st);   // the stage "post": the pass over Y for X and the sign convention
+    CK(launch_affine_project(Y, dt, n, d, W.mean, W.mean_f, W.U, W.U_f, r, f64, X, W.kerr, o.st));
     CK(launch_colsign(X, f64, n, r, W.sg_v, W.sg_i, W.sg_cnt, W.sign, o.st));
-    return finish(&W.B, W.flag, o);
+    return finish(&W.B, W.flag, o, W.kerr);
 }
 
 int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* landmark_idx, int l,
@@ -972,7 +1028,7 @@ int mds_interpolate(const void* Y, int dt, int64_t n, int d, const int64_t* land
     const size_t need = interp_layout(W, nullptr, n, d, l, r, o.prec, kind, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (interp_layout(W, o.ws, n, d, l, r, o.prec, kind, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     const int f64 = o.prec == MDS_PREC_F64;
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
@@ -1135,7 +1191,7 @@ int mds_interpolate_host(const void* Y, int dt, int64_t n, int d, const int64_t*
 
     HostPipe P;
     CK(P.make(2 * nch + 1));
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     CK(cudaMemsetAsync(W.flag, 0, sizeof(int), o.st));
     CK(cudaMemsetAsync(W.kerr, 0, sizeof(int), o.st));
     CK(cudaMemcpyAsync(H.Ylm, lm.data(), lm.size(), cudaMemcpyHostToDevice, o.st));
@@ -1226,7 +1282,7 @@ int mds_embed_new(mds_model m, const void* Ynew, int dt, int64_t rows, const mds
     if (!m || !Ynew || !X || !valid_dt(dt) || rows <= 0) return MDS_ERR_ARG;
     if (o.prec != m->prec) return MDS_ERR_ARG;
     if ((s = check_ws(o, mds_embed_new_workspace_size(m, rows) - 256))) return s;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     int* kerr = nullptr;
     if ((s = gbmds::embed_enqueue(m, Ynew, dt, rows, o.ws, o.st, X, &kerr))) return s;
     return finish(nullptr, nullptr, o, kerr);
@@ -1383,7 +1439,7 @@ int mds_divide_conquer(const void* Y, int dt, int64_t n, int d, int p, const int
     const size_t need = dc_layout(W, nullptr, n, d, p, part_ptr, c, r, o.prec, o.mmax);
     if ((s = check_ws(o, need))) return s;
     if (dc_layout(W, o.ws, n, d, p, part_ptr, c, r, o.prec, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     if ((s = dc_enqueue(W, Y, dt, n, d, p, part_ptr, part_own, anchors, c, r, o, X, var, true))) return s;
     return finish(&W.B, W.flag, o, W.G.mode >= 0 ? W.G.kerr : nullptr);
 }
@@ -1580,7 +1636,7 @@ int mds_fast(const void* Y, int dt, int64_t n, int d, const int64_t* perm, int n
     const size_t need = fast_layout(W, F, nullptr, n, o.mmax);
     if ((st = check_ws(o, need))) return st;
     if (fast_layout(W, F, o.ws, n, o.mmax) != need) return MDS_ERR_WORKSPACE;
-    begin_call(o.st);
+    begin_call(o.st, __func__);
     const int f64 = o.prec == MDS_PREC_F64;
     std::vector<FastTask> all_tasks;
     std::vector<int> all_dst;
@@ -1678,7 +1734,7 @@ int plan_trial(mds_dc_plan P, int cs, const void* Y, const int64_t* own, const i
     Opts o = P->o;
     o.st = st;
     o.cluster = cs;
-    begin_call(st);
+    begin_call(st, __func__);
     CK(cudaEventRecord(P->ev[0], st));
     int s = dc_enqueue(P->W, Y, P->dt, P->n, P->d, P->p, P->ptr.data(), own, anc, P->c, P->r, o, X, var, false);
     if (s) return s;
@@ -1770,6 +1826,19 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
     CK(cudaEventRecord(P->join, ust));
     CK(cudaStreamWaitEvent(st, P->join, 0));
     const Batch& B = P->W.B;
+    const std::string tkey =
+        batch_tune_key(B, P->o.prec != MDS_PREC_F64, (P->o.flags & MDS_FLAG_FULL_MATVEC) == 0);
+    if (P->cs == 0 && P->tune && tune_enabled()) {
+        // a cluster size measured before for this batch shape on this kind of GPU
+        int v = 0;
+        double tms[17] = {};
+        if (tune_lookup(tkey, &v, tms, 17) && v >= 1 && v <= 16 &&
+            lanczos_smem_bytes(B.max_n, v, B.mmax, B.r) <= kMaxSmem) {
+            P->cs = v;
+            P->tuned = true;
+            for (int i = 0; i < 17; ++i) P->trial_ms[i] = tms[i];
+        }
+    }
     if (P->cs == 0 && P->tune) {
         // autotuner: every cluster size that fits, timed on these buffers
         // (each trial is a complete, correct run); the fastest one is kept
@@ -1795,6 +1864,7 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         P->tuned = true;
         P->trial_ms[0] = 0.0;
         if (P->cs == 0) return MDS_ERR_CUDA;
+        tune_store(tkey, P->cs, P->trial_ms, 17);
     }
     if (P->cs == 0) P->cs = pick_cluster(0, B.p, B.max_n, B.mmax, B.r);
     if (!P->exec || Y != P->cY || part_own != P->cown || anchors != P->canc || X != P->cX || var != P->cvar) {
@@ -1804,7 +1874,7 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         o.cluster = P->cs;
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MDS_ERR_CUDA;
         g_capture_ev = P->ev;
-        begin_call(st);
+        begin_call(st, __func__);
         int s = dc_enqueue(P->W, Y, P->dt, P->n, P->d, P->p, P->ptr.data(), part_own, anchors, P->c, P->r, o, X,
                            var, false);
         const int p = P->p;
@@ -1833,9 +1903,12 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         P->cvar = var;
     }
     g_last = mds_stats{};
+    nvtx_end_call();
+    g_nvtx_call = nvtxRangeStartA("mds_dc_plan_execute (graph)");
     CK(cudaGraphLaunch(P->exec, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    nvtx_end_call();
     g_launches = P->launches;
     g_cluster = P->cs;
     if (g_timing)

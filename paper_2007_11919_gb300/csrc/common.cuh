@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/gbmds.h"
 
 // Device-resident landmark configuration behind an mds_model handle.
@@ -191,20 +193,22 @@ cudaError_t launch_interp_model(const double* V, const double* lam, const double
                                 cudaStream_t st);
 
 // Affine form of Eq. (2) for coordinate rows, from the gathered landmark rows
-// Lg (dense l x d FP64): y_L (FP64 and FP32 copies), scale = Lambda^{-1/2},
-// U_r = L_c^T V Lambda^{-1/2} (d x r, both copies) and X = (Y - y_L) U_r for
-// all n rows (double X when f64, else float).
-cudaError_t launch_affine(const void* Y, int dt, int64_t n, int d, const double* Lg, int l, const double* V,
-                          const double* lam, int r, int f64, double* scale, double* ybar, float* ybar_f, double* U,
-                          float* U_f, void* X, cudaStream_t st);
+// Lg (dense l x d FP64): y_L (FP64 and FP32 copies), scale = Lambda^{-1/2} and
+// U_r = L_c^T V Lambda^{-1/2} (d x r, both copies); then launch_affine_project
+// gives X = (Y - y_L) U_r for all n rows (double X when f64, else float).
+cudaError_t launch_affine_axes(const double* Lg, int l, int d, const double* V, const double* lam, int r,
+                               double* scale, double* ybar, float* ybar_f, double* U, float* U_f, cudaStream_t st);
 // The pieces (k_affine.cu): row mean of a dense l x d FP64 matrix; axes
 // U[k][i] = scale_i sum_j (L[j][k] - c_k) V[j][i]; projection X = (Y - 1 c^T) U
 // (FP64 when f64, else FP32 with the FP32 copies cen_f, U_f).
 cudaError_t launch_rows_mean(const double* L, int l, int d, double* mean, float* mean_f, cudaStream_t st);
 cudaError_t launch_axes(const double* L, int l, int d, const double* c, const double* V, const double* scale, int r,
                         double* U, float* U_f, cudaStream_t st);
+// err (device, non-null) receives MDS_ERR_TIMEOUT if a bounded wait on a tile
+// copy gives up.
 cudaError_t launch_affine_project(const void* Y, int dt, int64_t n, int d, const double* cen, const float* cen_f,
-                                  const double* U, const float* U_f, int r, int f64, void* X, cudaStream_t st);
+                                  const double* U, const float* U_f, int r, int f64, void* X, int* err,
+                                  cudaStream_t st);
 
 // Pivot MDS pieces (k_pivot.cu): column means of all n rows (partials of
 // colmean_part_doubles(n, d)), the scatter matrix S = Y_c^T Y_c (d x d FP64,
@@ -219,8 +223,19 @@ cudaError_t launch_colmean(const void* Y, int dt, int64_t n, int d, double* part
                            cudaStream_t st);
 cudaError_t launch_scatter(const void* Y, int dt, int64_t n, int d, const double* mean, int f64, double* part,
                            double* S, cudaStream_t st);
+// sym: the product is known to be symmetric (m == nb); the upper tiles are
+// computed and mirrored.
 cudaError_t launch_gemm_nt(const double* A, int lda, const double* ca, const double* B, int ldb, const double* cb,
-                           int m, int nb, int K, double* C, int ldc, cudaStream_t st);
+                           int m, int nb, int K, double* C, int ldc, int sym, cudaStream_t st);
+// Whether the scatter matrix kernel takes rows of width d (d <= 4096).
+bool scatter_supported(int d);
+
+// Persistent tuning cache (tune.cu): off unless a file is named.  Keys name a
+// kernel and every quantity its launch choice depends on.
+bool tune_enabled();
+bool tune_lookup(const std::string& key, int* value, double* trial_ms, int ntrial);
+bool tune_store(const std::string& key, int value, const double* trial_ms, int ntrial);
+std::string lanczos_tune_key(int p, int max_n, double sum_n2, int mmax, int r, int q_f32, int sym);
 cudaError_t launch_pivot_scale(const double* mu, int r, int64_t n, int l, double* scale, double* var,
                                cudaStream_t st);
 cudaError_t launch_colsign(void* X, int out_f64, int64_t n, int r, double* part_v, int64_t* part_i, unsigned* counter,

@@ -29,13 +29,15 @@ constexpr int kKC = 16;      // rows (or k) staged per step
 // ---------------------------------------------------------- column means
 
 // part[c][k] = sum of column k over the rows of chunk c: bytes exactly in
-// 64-bit integers, FP32 in double-FP32, FP64 in FP64.
+// 64-bit integers, FP32 in double-FP32, FP64 in FP64.  Thread per column,
+// eight rows loaded ahead of their sums.
 template <typename T>
 __global__ void __launch_bounds__(128) k_colsum(const T* __restrict__ Y, int64_t n, int d, int64_t R,
                                                 double* __restrict__ part) {
     const int k = blockIdx.x * 128 + threadIdx.x;
     if (k >= d) return;
     const int64_t r0 = (int64_t)blockIdx.y * R, r1 = r0 + R < n ? r0 + R : n;
+    constexpr int U = 8;
     double out;
     if constexpr (sizeof(T) == 1) {
         long long s = 0;
@@ -43,7 +45,15 @@ __global__ void __launch_bounds__(128) k_colsum(const T* __restrict__ Y, int64_t
         out = (double)s;
     } else if constexpr (sizeof(T) == 4) {
         float h = 0.f, l = 0.f;
-        for (int64_t i = r0; i < r1; ++i) df_add(h, l, Y[i * d + k], 0.f);
+        int64_t i = r0;
+        for (; i + U <= r1; i += U) {
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = Y[(i + u) * d + k];
+#pragma unroll
+            for (int u = 0; u < U; ++u) df_add(h, l, v[u], 0.f);
+        }
+        for (; i < r1; ++i) df_add(h, l, Y[i * d + k], 0.f);
         out = (double)h + (double)l;
     } else {
         double s = 0.0;
@@ -53,131 +63,182 @@ __global__ void __launch_bounds__(128) k_colsum(const T* __restrict__ Y, int64_t
     part[(int64_t)blockIdx.y * d + k] = out;
 }
 
+// Warp per column: the chunks' sums in a fixed order (lane-strided, then a
+// fixed tree).
 __global__ void k_colmean_final(const double* __restrict__ part, int nch, int d, int64_t n,
                                 double* __restrict__ mean, float* __restrict__ mean_f) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (k >= d) return;
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += part[(int64_t)c * d + k];
-    const double m = s / (double)n;
-    mean[k] = m;
-    mean_f[k] = (float)m;
+    for (int c = lane; c < nch; c += 32) s += part[(int64_t)c * d + k];
+    s = warp_sum(s);
+    if (lane == 0) {
+        const double m = s / (double)n;
+        mean[k] = m;
+        mean_f[k] = (float)m;
+    }
 }
 
 // ------------------------------------------------------- scatter matrix
 
-// One CTA: the 64 x 64 tile (ta, tb), ta <= tb, of S = sum (y - m)(y - m)^T
-// over the rows of chunk blockIdx.y, written to part[chunk][a][b].  FP32
-// (float and byte rows): products summed in FP32 over 16 rows, then folded
-// into double-FP32 accumulators; FP64 rows: FP64.
+// S = sum over rows of (y - m)(y - m)^T, upper triangle of 4 x 4 blocks:
+// thread-tile t is block (bi, bj), bi <= bj, numbered row by row over the
+// nb = ceil(d / 4) block rows, so the products cover the triangle and little
+// else.  One CTA: thread-tiles [blockIdx.x * blockDim.x, ...) over the rows
+// of chunk blockIdx.y, kc rows at a time: the rows are centred into shared
+// memory (each thread's share of the next kc rows is loaded into registers
+// while the current ones are multiplied), then each thread takes its two
+// 16-byte column groups per row.  FP32 (float and byte rows): products summed
+// in FP32 over 32 rows, then folded into double-FP32 accumulators; FP64:
+// FP64 sums.  part[chunk][t * 16 + 4 i + j] = block entry (4 bi + i, 4 bj + j).
+constexpr int kScPre = 8;   // staged elements per thread and step
+
 template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_scatter_tiles(const T* __restrict__ Y, int64_t n, int d,
-                                                       const double* __restrict__ mean, int64_t R, int tiles,
-                                                       double* __restrict__ part) {
-    __shared__ __align__(16) A As[kKC][kCT + 4];
-    __shared__ __align__(16) A Bs[kKC][kCT + 4];
-    __shared__ A ma[kCT], mb[kCT];
-    int t = blockIdx.x;
-    int ta = 0;
-    while (t >= tiles - ta) {
-        t -= tiles - ta;
-        ++ta;
+__global__ void __launch_bounds__(512) k_scatter_tri(const T* __restrict__ Y, int64_t n, int d,
+                                                     const double* __restrict__ mean, int64_t R, int nt, int kc,
+                                                     double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sc_raw[];
+    A* const Ys = reinterpret_cast<A*>(sc_raw);   // kc x dp centred rows (zero past d and past the chunk)
+    const int dp = (d + 3) & ~3, nb = dp >> 2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < nt;
+    int bi = 0, rem = active ? t : 0;
+    while (rem >= nb - bi) {
+        rem -= nb - bi;
+        ++bi;
     }
-    const int tb = ta + t;
-    const int a0 = ta * kCT, b0 = tb * kCT;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    if (tid < kCT) ma[tid] = a0 + tid < d ? (A)mean[a0 + tid] : A(0);
-    else if (tid < 2 * kCT) mb[tid - kCT] = b0 + tid - kCT < d ? (A)mean[b0 + tid - kCT] : A(0);
-    __syncthreads();
+    const int bj = bi + rem;
     const int64_t r0 = (int64_t)blockIdx.y * R, r1 = r0 + R < n ? r0 + R : n;
-    A acc[4][4];
+    // this thread's staged elements: e = tid + blockDim * u < kc * dp -> (row e / dp, column e % dp)
+    const int ne = kc * dp;
+    int erow[kScPre], ecol[kScPre];
+#pragma unroll
+    for (int u = 0; u < kScPre; ++u) {
+        const int e = threadIdx.x + (int)blockDim.x * u;
+        erow[u] = e < ne ? e / dp : -1;
+        ecol[u] = e < ne ? e - (e / dp) * dp : 0;
+    }
+    A pre[kScPre];
+    auto fetch = [&](int64_t rs) {
+#pragma unroll
+        for (int u = 0; u < kScPre; ++u) {
+            const int64_t row = rs + erow[u];
+            pre[u] = (erow[u] >= 0 && row < r1 && ecol[u] < d)
+                         ? load_as<A, T>(Y + row * d + ecol[u]) - (A)__ldg(mean + ecol[u])
+                         : A(0);
+        }
+    };
+    A acc[4][4], run[4][4];
     float lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             acc[i][j] = A(0);
+            run[i][j] = A(0);
             lo[i][j] = 0.f;
         }
-    for (int64_t rs = r0; rs < r1; rs += kKC) {
-        for (int e = tid; e < kKC * kCT; e += 256) {
-            const int kk = e / kCT, x = e % kCT;
-            const int64_t row = rs + kk;
-            const bool ok = row < r1;
-            As[kk][x] = (ok && a0 + x < d) ? load_as<A, T>(Y + row * d + a0 + x) - ma[x] : A(0);
-            Bs[kk][x] = (ok && b0 + x < d) ? load_as<A, T>(Y + row * d + b0 + x) - mb[x] : A(0);
-        }
+    fetch(r0);
+    int since = 0;   // rows summed into run since the last fold
+    for (int64_t rs = r0; rs < r1; rs += kc) {
+#pragma unroll
+        for (int u = 0; u < kScPre; ++u)
+            if (erow[u] >= 0) Ys[erow[u] * dp + ecol[u]] = pre[u];
         __syncthreads();
-        A run[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) run[i][j] = A(0);
-#pragma unroll
-        for (int kk = 0; kk < kKC; ++kk) {
-            A av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                av[i] = As[kk][ty * 4 + i];
-                bv[i] = Bs[kk][tx * 4 + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) run[i][j] += av[i] * bv[j];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if constexpr (sizeof(A) == 8) {
-                    acc[i][j] += run[i][j];
+        if (rs + kc < r1) fetch(rs + kc);
+        if (active) {
+            for (int kk = 0; kk < kc; ++kk) {
+                A av[4], bv[4];
+                const A* row = Ys + kk * dp;
+                if constexpr (sizeof(A) == 4) {
+                    const float4 a4 = *reinterpret_cast<const float4*>(row + 4 * bi);
+                    const float4 b4 = *reinterpret_cast<const float4*>(row + 4 * bj);
+                    av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+                    bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
                 } else {
-                    float h = acc[i][j], l = lo[i][j];
-                    df_add(h, l, run[i][j], 0.f);
-                    acc[i][j] = h;
-                    lo[i][j] = l;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        av[i] = row[4 * bi + i];
+                        bv[i] = row[4 * bj + i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) run[i][j] += av[i] * bv[j];
+            }
+            since += kc;
+            if constexpr (sizeof(A) == 4) {
+                if (since >= 32 || rs + kc >= r1) {   // fold every 32 rows or so (and at the end)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float h = acc[i][j], l = lo[i][j];
+                            df_add(h, l, run[i][j], 0.f);
+                            acc[i][j] = h;
+                            lo[i][j] = l;
+                            run[i][j] = A(0);
+                        }
+                    since = 0;
                 }
             }
+        }
         __syncthreads();
     }
-    double* P = part + (int64_t)blockIdx.y * d * d;
+    if (!active) return;
+    double* P = part + ((int64_t)blockIdx.y * nt + t) * 16;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int a = a0 + ty * 4 + i;
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int b = b0 + tx * 4 + j;
-            if (a < d && b < d) P[(int64_t)a * d + b] = (double)acc[i][j] + (double)lo[i][j];
-        }
-    }
+        for (int j = 0; j < 4; ++j)
+            P[4 * i + j] = sizeof(A) == 8 ? (double)run[i][j] : (double)acc[i][j] + (double)lo[i][j];
 }
 
-// S[a][b] = sum over chunks of the tile holding (a, b) or its mirror, fixed order.
-__global__ void k_scatter_final(const double* __restrict__ part, int nch, int d, double* __restrict__ S) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)d * d) return;
-    int a = (int)(e / d), b = (int)(e % d);
-    if (a / kCT > b / kCT) {   // lower tile: read the mirrored upper entry
-        const int t = a;
-        a = b;
-        b = t;
-    }
+// Warp per entry (a, b), a <= b, of S: the chunks' partials in a fixed order
+// (lane-strided, then a fixed tree), written to S[a][b] and S[b][a].
+__global__ void k_scatter_final(const double* __restrict__ part, int nch, int nt, int d, double* __restrict__ S) {
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)d * d) return;
+    const int a = (int)(w / d), b = (int)(w % d);
+    if (a > b) return;
+    const int nb = ((d + 3) & ~3) >> 2, bi = a >> 2, bj = b >> 2;
+    const int64_t t = (int64_t)bi * nb - (int64_t)bi * (bi - 1) / 2 + (bj - bi);
+    const int64_t off = t * 16 + 4 * (a & 3) + (b & 3);
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += part[(int64_t)c * d * d + (int64_t)a * d + b];
-    S[e] = s;
+    for (int c = lane; c < nch; c += 32) s += part[(int64_t)c * nt * 16 + off];
+    s = warp_sum(s);
+    if (lane == 0) {
+        S[(int64_t)a * d + b] = s;
+        S[(int64_t)b * d + a] = s;
+    }
 }
 
 // ------------------------------------------------------------ FP64 products
 
 // C[i][j] = sum_k (A[i][k] - ca[k]) (B[j][k] - cb[k]) (ca, cb may be null),
 // A m x K (lda), B nb x K (ldb), C m x nb (ldc), FP64, 64 x 64 tiles.
+// With sym the product is known to be symmetric (m == nb): only the tiles
+// (ti, tj), ti <= tj, are computed (blockIdx.x numbers them row by row) and
+// each is written to both triangles, so C is exactly symmetric.
 __global__ void __launch_bounds__(256) k_gemm_nt(const double* __restrict__ A, int lda, const double* __restrict__ ca,
                                                  const double* __restrict__ B, int ldb, const double* __restrict__ cb,
-                                                 int m, int nb, int K, double* __restrict__ C, int ldc) {
+                                                 int m, int nb, int K, double* __restrict__ C, int ldc, int sym) {
     __shared__ double As[kKC][kCT + 1];
     __shared__ double Bs[kKC][kCT + 1];
-    const int i0 = blockIdx.x * kCT, j0 = blockIdx.y * kCT;
+    int ti = blockIdx.x, tj = blockIdx.y;
+    if (sym) {
+        const int nt = (m + kCT - 1) / kCT;
+        int rem = blockIdx.x;
+        ti = 0;
+        while (rem >= nt - ti) {
+            rem -= nt - ti;
+            ++ti;
+        }
+        tj = ti + rem;
+    }
+    const int i0 = ti * kCT, j0 = tj * kCT;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < K; k0 += kKC) {
@@ -209,7 +270,10 @@ __global__ void __launch_bounds__(256) k_gemm_nt(const double* __restrict__ A, i
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int j = j0 + tx * 4 + w;
-            if (i < m && j < nb) C[(int64_t)i * ldc + j] = acc[q][w];
+            if (i < m && j < nb) {
+                C[(int64_t)i * ldc + j] = acc[q][w];
+                if (sym) C[(int64_t)j * ldc + i] = acc[q][w];
+            }
         }
     }
 }
@@ -231,8 +295,13 @@ __global__ void k_pivot_scale(const double* __restrict__ mu, int r, int64_t n, i
 constexpr int kSgThreads = 256;
 
 // Per column of X (n x r): the entry of largest magnitude (lowest row on a
-// tie); the last CTA to finish sets sign[i] = -1 where that entry is
-// negative, else +1, and re-arms the counter.
+// tie), in one coalesced pass over X: element e (row e / r, column e % r) is
+// read by thread e mod S of the grid, S = the grid's threads rounded down to
+// a multiple of r, so each thread meets one column only and keeps its best;
+// thread i < r of each CTA combines the CTA's threads of column i.  The last
+// CTA to finish sets sign[i] = -1 where that entry is negative, else +1, and
+// re-arms the counter.  The order of the comparisons does not matter: the
+// winner is the largest (|x|, -row).
 template <typename A>
 __global__ void __launch_bounds__(kSgThreads) k_colsign(const A* __restrict__ X, int64_t n, int r,
                                                         double* __restrict__ part_v, int64_t* __restrict__ part_i,
@@ -240,57 +309,73 @@ __global__ void __launch_bounds__(kSgThreads) k_colsign(const A* __restrict__ X,
     __shared__ double sv[kSgThreads];
     __shared__ int64_t si[kSgThreads];
     __shared__ bool last;
-    for (int i = 0; i < r; ++i) {
-        double bv = -1.0;
-        int64_t bi = INT64_MAX;
-        for (int64_t row = (int64_t)blockIdx.x * kSgThreads + threadIdx.x; row < n;
-             row += (int64_t)gridDim.x * kSgThreads) {
-            const double v = fabs((double)X[row * r + i]);
+    const int64_t q = (int64_t)gridDim.x * kSgThreads / r, S = q * r;
+    const int64_t e0 = (int64_t)blockIdx.x * kSgThreads + threadIdx.x;
+    double bv = -1.0;
+    int64_t bi = INT64_MAX;
+    if (e0 < S) {
+        int64_t row = e0 / r;
+        for (int64_t e = e0; e < n * r; e += S, row += q) {
+            const double v = fabs((double)X[e]);
             if (v > bv || (v == bv && row < bi)) {
                 bv = v;
                 bi = row;
             }
         }
-        sv[threadIdx.x] = bv;
-        si[threadIdx.x] = bi;
-        __syncthreads();
-        for (int h = kSgThreads / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) {
-                const double w = sv[threadIdx.x + h];
-                const int64_t j = si[threadIdx.x + h];
-                if (w > sv[threadIdx.x] || (w == sv[threadIdx.x] && j < si[threadIdx.x])) {
-                    sv[threadIdx.x] = w;
-                    si[threadIdx.x] = j;
-                }
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            part_v[(int64_t)blockIdx.x * r + i] = sv[0];
-            part_i[(int64_t)blockIdx.x * r + i] = si[0];
-        }
-        __syncthreads();
     }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    if (threadIdx.x < r) {
+        const int i = threadIdx.x;
+        const int t0 = (int)((((int64_t)i - (int64_t)blockIdx.x * kSgThreads) % r + r) % r);
+        double cv = -1.0;
+        int64_t ci = INT64_MAX;
+        for (int t = t0; t < kSgThreads; t += r) {
+            const double w = sv[t];
+            const int64_t j = si[t];
+            if (w > cv || (w == cv && j < ci)) {
+                cv = w;
+                ci = j;
+            }
+        }
+        part_v[(int64_t)blockIdx.x * r + i] = cv;
+        part_i[(int64_t)blockIdx.x * r + i] = ci;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x >= r) return;
+    if (!last) return;
     __threadfence();
-    const int i = threadIdx.x;
-    double bv = -1.0;
-    int64_t bi = INT64_MAX;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-        const double w = __ldcg(part_v + (int64_t)b * r + i);
-        const int64_t j = __ldcg(part_i + (int64_t)b * r + i);
-        if (w > bv || (w == bv && j < bi)) {
-            bv = w;
-            bi = j;
+    // warp w takes the columns w, w + 8, ...: lanes stride over the CTAs'
+    // partials, then a shuffle tree
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < r; i += kSgThreads / 32) {
+        double cv = -1.0;
+        int64_t ci = INT64_MAX;
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const double w = __ldcg(part_v + (int64_t)b * r + i);
+            const int64_t j = __ldcg(part_i + (int64_t)b * r + i);
+            if (w > cv || (w == cv && j < ci)) {
+                cv = w;
+                ci = j;
+            }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, cv, o);
+            const int64_t j = __shfl_xor_sync(0xffffffffu, ci, o);
+            if (w > cv || (w == cv && j < ci)) {
+                cv = w;
+                ci = j;
+            }
+        }
+        if (lane == 0) sign[i] = (ci < n && X[ci * r + i] < A(0)) ? -1.0 : 1.0;
     }
-    sign[i] = (bi < n && X[bi * r + i] < A(0)) ? -1.0 : 1.0;
-    if (i == 0) *counter = 0u;
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 template <typename A>
@@ -301,14 +386,30 @@ __global__ void k_colscale(A* __restrict__ X, int64_t n, int r, const double* __
 
 }  // namespace
 
-int64_t colsum_chunk_rows(int64_t n) { return n < 4096 ? (n > 0 ? n : 1) : 4096; }
+int64_t colsum_chunk_rows(int64_t n) { return n < 512 ? (n > 0 ? n : 1) : 512; }
 
-int64_t scatter_chunk_rows(int64_t n, int d) {
-    // at most ~32 MiB of FP64 partial tiles, at least 8192 rows per chunk
-    const int64_t maxch = std::max<int64_t>(1, (int64_t)(4u << 20) / ((int64_t)d * d));
-    int64_t nch = std::min<int64_t>(maxch, (n + 8191) / 8192);
+// Geometry of the scatter matrix's triangle kernel: nt thread-tiles in ncta
+// CTAs of `threads`, kc rows per step, nch chunks of R rows (about 608 CTAs
+// in all, at most 64 MiB of partials, at least 256 rows per chunk).
+struct ScatterGeo {
+    int nt, ncta, threads, kc, nch;
+    int64_t R;
+};
+
+static bool scatter_geo(int64_t n, int d, ScatterGeo& g) {
+    const int dp = (d + 3) & ~3, nb = dp / 4;
+    g.nt = nb * (nb + 1) / 2;
+    g.ncta = (g.nt + 511) / 512;
+    g.threads = (int)round_up((g.nt + g.ncta - 1) / g.ncta, 32);
+    g.kc = std::min(32, kScPre * g.threads / dp);
+    if (g.kc < 1) return false;
+    const int64_t maxch = std::max<int64_t>(1, (int64_t)(8u << 20) / ((int64_t)g.nt * 16));
+    int64_t nch = std::max<int64_t>(1, (608 + g.ncta - 1) / g.ncta);
+    nch = std::min<int64_t>(nch, std::min<int64_t>(maxch, (n + 255) / 256));
     nch = std::max<int64_t>(1, nch);
-    return (n + nch - 1) / nch;
+    g.R = (n + nch - 1) / nch;
+    g.nch = (int)((n + g.R - 1) / g.R);
+    return true;
 }
 
 cudaError_t launch_colmean(const void* Y, int dt, int64_t n, int d, double* part, double* mean, float* mean_f,
@@ -320,37 +421,43 @@ cudaError_t launch_colmean(const void* Y, int dt, int64_t n, int d, double* part
     if (dt == MDS_IN_F64) k_colsum<double><<<grid, 128, 0, st>>>((const double*)Y, n, d, R, part);
     else if (dt == MDS_IN_F32) k_colsum<float><<<grid, 128, 0, st>>>((const float*)Y, n, d, R, part);
     else k_colsum<uint8_t><<<grid, 128, 0, st>>>((const uint8_t*)Y, n, d, R, part);
-    k_colmean_final<<<(d + 255) / 256, 256, 0, st>>>(part, nch, d, n, mean, mean_f);
+    k_colmean_final<<<(d + 7) / 8, 256, 0, st>>>(part, nch, d, n, mean, mean_f);
     note_launch(2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const void* Y, int dt, int64_t n, int d, const double* mean, int f64, double* part,
                            double* S, cudaStream_t st) {
-    if (n <= 0 || d <= 0) return cudaErrorInvalidValue;
-    const int64_t R = scatter_chunk_rows(n, d);
-    const int nch = (int)((n + R - 1) / R);
-    const int tiles = (d + kCT - 1) / kCT;
-    const dim3 grid((unsigned)(tiles * (tiles + 1) / 2), (unsigned)nch);
+    ScatterGeo g;
+    if (n <= 0 || d <= 0 || !scatter_geo(n, d, g)) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)g.ncta, (unsigned)g.nch);
+    const int dp = (d + 3) & ~3;
+    const size_t smem = (size_t)g.kc * dp * (f64 ? 8 : 4);
     if (dt == MDS_IN_F64) {
-        if (f64) k_scatter_tiles<double, double><<<grid, 256, 0, st>>>((const double*)Y, n, d, mean, R, tiles, part);
-        else k_scatter_tiles<double, float><<<grid, 256, 0, st>>>((const double*)Y, n, d, mean, R, tiles, part);
+        if (f64) k_scatter_tri<double, double><<<grid, g.threads, smem, st>>>((const double*)Y, n, d, mean, g.R, g.nt, g.kc, part);
+        else k_scatter_tri<double, float><<<grid, g.threads, smem, st>>>((const double*)Y, n, d, mean, g.R, g.nt, g.kc, part);
     } else if (dt == MDS_IN_F32) {
-        if (f64) k_scatter_tiles<float, double><<<grid, 256, 0, st>>>((const float*)Y, n, d, mean, R, tiles, part);
-        else k_scatter_tiles<float, float><<<grid, 256, 0, st>>>((const float*)Y, n, d, mean, R, tiles, part);
+        if (f64) k_scatter_tri<float, double><<<grid, g.threads, smem, st>>>((const float*)Y, n, d, mean, g.R, g.nt, g.kc, part);
+        else k_scatter_tri<float, float><<<grid, g.threads, smem, st>>>((const float*)Y, n, d, mean, g.R, g.nt, g.kc, part);
     } else {
-        if (f64) k_scatter_tiles<uint8_t, double><<<grid, 256, 0, st>>>((const uint8_t*)Y, n, d, mean, R, tiles, part);
-        else k_scatter_tiles<uint8_t, float><<<grid, 256, 0, st>>>((const uint8_t*)Y, n, d, mean, R, tiles, part);
+        if (f64) k_scatter_tri<uint8_t, double><<<grid, g.threads, smem, st>>>((const uint8_t*)Y, n, d, mean, g.R, g.nt, g.kc, part);
+        else k_scatter_tri<uint8_t, float><<<grid, g.threads, smem, st>>>((const uint8_t*)Y, n, d, mean, g.R, g.nt, g.kc, part);
     }
     const int64_t dd = (int64_t)d * d;
-    k_scatter_final<<<(unsigned)((dd + 255) / 256), 256, 0, st>>>(part, nch, d, S);
+    k_scatter_final<<<(unsigned)((dd + 7) / 8), 256, 0, st>>>(part, g.nch, g.nt, d, S);
     note_launch(2);
     return cudaGetLastError();
 }
 
 size_t scatter_part_doubles(int64_t n, int d) {
-    const int64_t R = scatter_chunk_rows(n, d);
-    return (size_t)((n + R - 1) / R) * d * d;
+    ScatterGeo g;
+    if (n <= 0 || d <= 0 || !scatter_geo(n, d, g)) return 0;
+    return (size_t)g.nch * g.nt * 16;
+}
+
+bool scatter_supported(int d) {
+    ScatterGeo g;
+    return d > 0 && scatter_geo(1, d, g);
 }
 
 size_t colmean_part_doubles(int64_t n, int d) {
@@ -359,10 +466,11 @@ size_t colmean_part_doubles(int64_t n, int d) {
 }
 
 cudaError_t launch_gemm_nt(const double* A, int lda, const double* ca, const double* B, int ldb, const double* cb,
-                           int m, int nb, int K, double* C, int ldc, cudaStream_t st) {
-    if (m <= 0 || nb <= 0 || K <= 0) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((m + kCT - 1) / kCT), (unsigned)((nb + kCT - 1) / kCT));
-    k_gemm_nt<<<grid, 256, 0, st>>>(A, lda, ca, B, ldb, cb, m, nb, K, C, ldc);
+                           int m, int nb, int K, double* C, int ldc, int sym, cudaStream_t st) {
+    if (m <= 0 || nb <= 0 || K <= 0 || (sym && m != nb)) return cudaErrorInvalidValue;
+    const int tm = (m + kCT - 1) / kCT;
+    const dim3 grid = sym ? dim3((unsigned)(tm * (tm + 1) / 2), 1u) : dim3((unsigned)tm, (unsigned)((nb + kCT - 1) / kCT));
+    k_gemm_nt<<<grid, 256, 0, st>>>(A, lda, ca, B, ldb, cb, m, nb, K, C, ldc, sym);
     note_launch(1);
     return cudaGetLastError();
 }

@@ -384,6 +384,34 @@ def mds_inject_alloc_failures(count: int):
     L.mds_inject_alloc_failures(int(count))
 
 
+def mds_set_tune_cache(path):
+    """Tuning cache file (None turns it off): plans created with ``tune`` store
+    the cluster size they measured there and later processes reuse it for the
+    same batch shape on the same kind of GPU; process-wide."""
+    L = _lib()
+    L.mds_set_tune_cache.argtypes = [ctypes.c_char_p]
+    L.mds_set_tune_cache.restype = _I
+    _check(L.mds_set_tune_cache(None if path is None else os.fsencode(path)), "mds_set_tune_cache")
+
+
+def mds_tune_cache_lookup(key: str) -> int:
+    """The value stored under ``key`` (0 when absent or the cache is off)."""
+    L = _lib()
+    L.mds_tune_cache_lookup.argtypes = [ctypes.c_char_p, _P]
+    L.mds_tune_cache_lookup.restype = _I
+    v = ctypes.c_int(0)
+    _check(L.mds_tune_cache_lookup(key.encode(), ctypes.byref(v)), "mds_tune_cache_lookup")
+    return v.value
+
+
+def mds_tune_cache_store(key: str, value: int):
+    """Adds or replaces the entry ``key`` of the tuning cache."""
+    L = _lib()
+    L.mds_tune_cache_store.argtypes = [ctypes.c_char_p, _I]
+    L.mds_tune_cache_store.restype = _I
+    _check(L.mds_tune_cache_store(key.encode(), int(value)), "mds_tune_cache_store")
+
+
 def mds_embed_new_static(model: Model, Ynew, stream=None):
     """mds_embed_new without any device allocation: scratch comes from a fixed
     array inside the library, so the only tensors created here are the

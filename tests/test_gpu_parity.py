@@ -218,6 +218,25 @@ def test_interp_affine(gb, prec, kind, n, d, l, r):
     assert O.aligned_rel_error(host(X), Xg) < TOL[prec]
 
 
+@pytest.mark.parametrize("n,d,l,r", [(1001, 8, 120, 3), (4097, 100, 400, 1), (3000, 64, 300, 15),
+                                     (2000, 128, 250, 16), (999, 4, 100, 2), (5003, 36, 333, 7)])
+def test_interp_affine_f32_tile_shapes(gb, n, d, l, r):
+    """The FP32 pass over Y at row widths whose tiles come as one copy (d/4
+    odd) or one copy per row (d/4 even), odd and even r, ragged last tiles;
+    the same rows at a base that is not 16-byte aligned take the general
+    kernel and give the same embedding."""
+    Y = W.gaussian_dominant(n, d, min(r, d), seed=d + r, dtype=np.float32)
+    idx = W.landmarks(n, l, seed=n)
+    Xo, vo, _ = O.affine_interpolation(Y, idx, r)
+    X, var = gb.mds_interpolate_affine(dev(Y), dev(idx), r, "f32")
+    assert rel(host(var), vo) < LAM_TOL["f32"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f32"]
+    buf = torch.zeros(n * d + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = dev(Y).reshape(-1)
+    Xu, _ = gb.mds_interpolate_affine(buf[1:].view(n, d), dev(idx), r, "f32")
+    assert np.linalg.norm(host(Xu) - host(X)) < 1e-6 * np.linalg.norm(host(X))
+
+
 def test_interp_affine_all_landmarks_and_errors(gb):
     """l = n: every row is a landmark, the result is classical MDS; BF16
     is not offered for the affine form."""
@@ -472,6 +491,43 @@ def test_dc_plan_autotuned_graph(gb):
     Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, 10)
     assert O.aligned_rel_error(host(X2), Xo) < TOL["f32"]
     plan.close()
+
+
+def test_tune_cache_round_trip(gb, tmp_path):
+    """A tuning plan stores its measured cluster size in the cache file; a
+    value stored under the same batch shape is then used, without timing, by
+    a new tuning plan and by direct calls (whose results equal those of an
+    explicit cluster size bit for bit)."""
+    import json
+    from paper_2007_11919_gb300 import mds as M
+    path = tmp_path / "tune.json"
+    M.mds_set_tune_cache(str(path))
+    try:
+        Y = W.gaussian_dominant(6000, 20, 4, seed=8, dtype=np.float32)
+        part = W.partitions_uneven(6000, 12, 500, 700, seed=8)
+        Yd, anc, own = dev(Y), dev(part.anchors), dev(part.own)
+        plan = M.DcPlan(6000, 20, torch.float32, part.ptr, 12, 4, "f32", tune=True)
+        plan.execute(Yd, anc, own)
+        chosen = plan.info()["cluster"]
+        plan.close()
+        entries = json.loads(path.read_text())["entries"]
+        assert len(entries) == 1 and entries[0]["value"] == chosen
+        key = entries[0]["key"]
+        assert key.startswith("k_lanczos") and "r=4" in key and "q=f32" in key
+        assert M.mds_tune_cache_lookup(key) == chosen
+        other = 3 if chosen != 3 else 2
+        M.mds_tune_cache_store(key, other)
+        plan = M.DcPlan(6000, 20, torch.float32, part.ptr, 12, 4, "f32", tune=True)
+        X1, v1 = plan.execute(Yd, anc, own)
+        info = plan.info()
+        assert info["cluster"] == other and not any(info["trial_ms"])   # taken from the cache, nothing timed
+        plan.close()
+        X2, v2 = gb.mds_divide_conquer(Yd, anc, part.ptr, own, 4, "f32")
+        Xe, ve = gb.mds_divide_conquer(Yd, anc, part.ptr, own, 4, "f32", cluster=other)
+        assert torch.equal(X1, Xe) and torch.equal(X2, Xe) and torch.equal(v2, ve)
+    finally:
+        M.mds_set_tune_cache(None)
+    assert M.mds_tune_cache_lookup("k_lanczos anything") == 0
 
 
 def test_dc_plan_fixed_cluster_f64(gb):

@@ -227,3 +227,53 @@ def test_fast_tree_checks_without_gpu(lib):
     assert size(np.array([[0, 5000]]), np.array([-1])) > 0         # one leaf: classical MDS
     assert lib.mds_fast_workspace_size(20000, 8, 1, np.array([0, 20000], dtype=np.int64).ctypes.data,
                                        np.array([-1], dtype=np.int32).ctypes.data, 20, 3, 1) == 0  # leaf too big
+
+
+def test_pivot_argument_checks_without_gpu(lib):
+    """Pivot MDS: argument errors, unsupported precisions and row widths
+    beyond the scatter kernel's staging (d > 4096) answer on the host."""
+    o = _opts(prec=1)
+    p = ctypes.c_void_p(8)
+    lib.mds_pivot_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mds_pivot_workspace_size.restype = ctypes.c_size_t
+    lib.mds_pivot.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mds_pivot.restype = ctypes.c_int
+    assert lib.mds_pivot_workspace_size(100000, 100, 1000, 10, 1) > 100 * 100 * 8
+    assert lib.mds_pivot_workspace_size(100000, 4096, 1000, 10, 1) > 0
+    assert lib.mds_pivot_workspace_size(100000, 4097, 1000, 10, 1) == 0
+    assert lib.mds_pivot_workspace_size(100000, 100, 1000, 10, 2) == 0          # BF16
+    assert lib.mds_pivot(None, 1, 1000, 8, p, 100, 3, ctypes.byref(o), p, p) == 1
+    assert lib.mds_pivot(p, 1, 1000, 8, p, 100, 9, ctypes.byref(o), p, p) == 1    # r > d
+    assert lib.mds_pivot(p, 1, 1000, 8, p, 2000, 3, ctypes.byref(o), p, p) == 1   # l > n
+    assert lib.mds_pivot(p, 1, 1000, 4097, p, 100, 3, ctypes.byref(o), p, p) == 7
+    assert lib.mds_pivot(p, 1, 1000, 8, p, 100, 3, ctypes.byref(_opts(prec=2)), p, p) == 7
+    assert lib.mds_pivot(p, 1, 1000, 8, p, 100, 3, ctypes.byref(o), p, p) == 8    # no workspace
+
+
+def test_tune_cache_file_without_gpu(lib, tmp_path):
+    """The tuning cache: absent keys read 0, stores add and replace entries in
+    a JSON file, malformed keys and a cache that is off are refused."""
+    import json
+    from paper_2007_11919_gb300 import mds as M
+    path = tmp_path / "tune.json"
+    assert M.mds_tune_cache_lookup("k_lanczos cluster p=1") == 0          # cache off
+    with pytest.raises(M.MdsError):
+        M.mds_tune_cache_store("k_lanczos cluster p=1", 4)
+    M.mds_set_tune_cache(str(path))
+    try:
+        assert M.mds_tune_cache_lookup("k_lanczos cluster p=1") == 0
+        M.mds_tune_cache_store("k_lanczos cluster p=1", 4)
+        M.mds_tune_cache_store("k_lanczos cluster p=2", 7)
+        M.mds_tune_cache_store("k_lanczos cluster p=1", 5)                # replaces
+        doc = json.loads(path.read_text())
+        assert doc["gbmds_tune_cache"] == 1
+        assert {e["key"]: e["value"] for e in doc["entries"]} == {"k_lanczos cluster p=1": 5,
+                                                                  "k_lanczos cluster p=2": 7}
+        assert M.mds_tune_cache_lookup("k_lanczos cluster p=2") == 7
+        for bad in ['a"b', "a\\b", "a\nb", "", "x" * 1025]:
+            with pytest.raises(M.MdsError):
+                M.mds_tune_cache_store(bad, 1)
+        assert not any(p.name.startswith("tune.json.tmp") for p in tmp_path.iterdir())
+    finally:
+        M.mds_set_tune_cache(None)
