@@ -68,7 +68,7 @@ NCU_TRAFFIC = {
     # (profiles/k_lanczos_image_dc_fp8_n814255.md, profiles/k_lanczos_dc_f32_n100000.md)
     "k_lanczos.cu": {"sha": "8551ed1188245aa2", "per": "streamed byte", "bytes": {"image_dc": 1.0342, "dc": 0.8236}},
     # per row of Y per round (profiles/k_maxmin_tiles_maxmin_f32_n1000000.md)
-    "k_maxmin.cu": {"sha": "ed0ac2bd3bb43525", "per": "row per round", "bytes": 412.0},
+    "k_maxmin.cu": {"sha": "ea7609f60cd2d721", "per": "row per round", "bytes": 411.5},
     # per row of Y (profiles/k_affine_project_bulk_affine_f32_n1000000.md)
     "k_affine.cu": {"sha": "f592f8bbd752a734", "per": "row", "bytes": 432.2},
 }
@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of measured capacity")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (for launch lists)")
+    ap.add_argument("--eig-tol", type=float, default=0.0,
+                    help="D&C eigen-solver residual tolerance (relative to lambda_1); 0 = the library default")
     ap.add_argument("--full-matvec", action="store_true",
                     help="divide-and-conquer eigen-solver: stream whole rows of Q instead of the symmetric ranges")
     ap.add_argument("--n", type=int, default=0,
@@ -473,7 +475,8 @@ class Leg:
             self.own = torch.from_numpy(part.own).to(dev)
             # the whole divide-and-conquer call as one autotuned, graph-captured plan
             self.plan = M.DcPlan(w.n, w.d, self.Yd.dtype, part.ptr, w.c, w.r, w.prec, tune=args.cluster == 0,
-                                 cluster=args.cluster, device=dev, full_matvec=args.full_matvec)
+                                 cluster=args.cluster, device=dev, full_matvec=args.full_matvec,
+                                 eig_tol=args.eig_tol)
             self.X = torch.zeros((w.n, w.r), dtype=self.xdt, device=dev)
             self.var = torch.empty(w.r, dtype=torch.float64, device=dev)
         elif self.method == "maxmin":
@@ -503,7 +506,8 @@ class Leg:
         if self.method == "pivot":
             return G.mds_pivot(self.Yd, self.idx, w.r, w.prec, workspace=self.ws)
         if self.method == "fast":
-            return G.mds_fast(self.Yd, self.perm, self.rng, self.par, w.c, w.r, w.prec, workspace=self.ws)
+            return G.mds_fast(self.Yd, self.perm, self.rng, self.par, w.c, w.r, w.prec, workspace=self.ws,
+                              cluster=self.args.cluster)
         X, var, _ = G.mds_interpolate(self.Yd, self.idx, w.r, w.prec, workspace=self.ws, cluster=self.args.cluster)
         return X, var
 
@@ -671,7 +675,7 @@ class Leg:
         import torch
         w = self.w
         flops = 2.0 * w.n * w.d * (w.d + 1) / 2
-        sms = torch.cuda.get_device_properties(self.Y.device).multi_processor_count
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         peak = sms * 128 * 2 * 2.070e9 / 1e12
         achieved = flops / (kms * 1e-3) / 1e12
         return {"kernel": "k_scatter_tri (scatter matrix of all n rows, upper triangle of 4 x 4 thread tiles, "

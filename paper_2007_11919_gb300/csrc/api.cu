@@ -278,16 +278,35 @@ std::string batch_tune_key(const Batch& B, int q_f32, int sym) {
     return lanczos_tune_key(B.p, B.max_n, sum_n2, B.mmax, B.r, q_f32, sym);
 }
 
-int pick_cluster(int requested, int p, int max_n, int mmax, int r) {
+// CTAs per eigenproblem when the call does not fix it (and no tuned value is
+// cached).  Two CTAs per SM are resident, so `slots / cs` problems run at a
+// time.  Many small problems (enough to fill every slot): the smallest
+// cs <= 4 whose concurrently active Q matrices fit in ~112 MB of L2 (they are re-read every Lanczos step; fast
+// MDS's 400-point leaves: 35 ms at cs = 2 against 47 ms at 1 and 46 ms at 4).
+// Otherwise about 1.5 problems per cluster slot, so that largest-first
+// scheduling evens out uneven sizes, and at least one CTA per ~400 rows
+// (D&C parts of 1,000 points: cs = 5; of 2,050 points: cs = 5, 211 ms
+// against 283 ms at cs = 1).
+int pick_cluster(int requested, int p, int max_n, int mmax, int r, double sum_n2, int q_bytes) {
     if (requested > 0) return std::min(requested, 16);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int cs;
-    // Persistent queue: about 1.5 parts per cluster slot (two CTAs per SM)
-    // lets largest-first scheduling even out uneven part sizes.
-    if (p == 1) cs = 16;
-    else cs = std::max(1, std::min(8, (int)std::lround(2.0 * sms * 1.5 / p)));
+    const int slots = 2 * sms;
+    int cs = 0;
+    if (p == 1) {
+        cs = 16;
+    } else {
+        const double mean_q = sum_n2 / p * q_bytes;
+        for (int c = 1; c <= 4 && cs == 0; ++c)
+            if ((int64_t)p * c >= slots && (slots / c) * mean_q <= 112.0 * (1 << 20) &&
+                lanczos_smem_bytes(max_n, c, mmax, r) <= kMaxSmem)
+                cs = c;
+        if (cs == 0) {
+            cs = std::max(1, std::min(8, (int)std::lround(2.0 * sms * 1.5 / p)));
+            cs = std::max(cs, std::min(16, (int)std::lround(max_n / 400.0)));
+        }
+    }
     cs = std::min(cs, std::max(1, max_n / 64));
     while (cs < 16 && lanczos_smem_bytes(max_n, cs, mmax, r) > kMaxSmem) ++cs;
     return cs;
@@ -376,7 +395,9 @@ int run_eig_batch(Batch& B, const void* Y, int dt, int d, const double* nrm,
     B.sym = a.sym;
     if (B.tbar) CK(cudaMemsetAsync(B.tbar, 0, 4 * sizeof(unsigned), o.st));
     tmark(2, o.st);
-    g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r);
+    double sum_n2 = 0.0;
+    for (const ProbDesc& P : B.desc) sum_n2 += (double)P.n * P.n;
+    g_cluster = pick_cluster(o.cluster, B.p, B.max_n, B.mmax, B.r, sum_n2, q_f32 ? 4 : 8);
     if (o.cluster == 0 && tune_enabled()) {
         // a cluster size an autotuner measured for this batch shape
         int v = 0;
@@ -691,6 +712,7 @@ static size_t maxmin_layout(MaxminWs& M, char* base, int64_t n) {
     M.part_v = A.take<double>(kMaxminGridCap);
     M.part_i = A.take<int64_t>(kMaxminGridCap);
     M.counter = A.take<unsigned>(1);
+    M.err = A.take<int>(1);
     return A.off;
 }
 
@@ -713,12 +735,13 @@ int mds_landmarks_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t
     if ((s = check_ws(o, need))) return s;
     maxmin_layout(M, o.ws, n);
     begin_call(o.st, __func__);
+    CK(cudaMemsetAsync(M.err, 0, sizeof(int), o.st));
     tmark(0, o.st);
     CK(launch_maxmin(Y, dt, n, d, l, first, M, idx_out, o.st));
     tmark(1, o.st);   // stage "dist": the l - 1 distance passes and picks
     tmark(2, o.st);
     tmark(3, o.st);
-    return finish(nullptr, nullptr, o);
+    return finish(nullptr, nullptr, o, M.err);
 }
 
 // ------------------------------------------------------------- classical
@@ -1866,7 +1889,11 @@ int mds_dc_plan_execute(mds_dc_plan P, const void* Y, const int64_t* part_own, c
         if (P->cs == 0) return MDS_ERR_CUDA;
         tune_store(tkey, P->cs, P->trial_ms, 17);
     }
-    if (P->cs == 0) P->cs = pick_cluster(0, B.p, B.max_n, B.mmax, B.r);
+    if (P->cs == 0) {
+        double sum_n2 = 0.0;
+        for (const ProbDesc& D : B.desc) sum_n2 += (double)D.n * D.n;
+        P->cs = pick_cluster(0, B.p, B.max_n, B.mmax, B.r, sum_n2, P->o.prec == MDS_PREC_F64 ? 8 : 4);
+    }
     if (!P->exec || Y != P->cY || part_own != P->cown || anchors != P->canc || X != P->cX || var != P->cvar) {
         plan_drop_graph(P);
         Opts o = P->o;

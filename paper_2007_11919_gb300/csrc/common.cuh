@@ -358,6 +358,7 @@ struct MaxminWs {
     double* part_v;
     int64_t* part_i;
     unsigned* counter;
+    int* err;           // status word of the tiled rounds' bounded waits
 };
 int maxmin_grid();
 cudaError_t launch_maxmin(const void* Y, int dt, int64_t n, int d, int l, int64_t first, MaxminWs ws,

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace gbmds {
 namespace {
@@ -178,24 +179,59 @@ __global__ void __launch_bounds__(kMmThreads) k_maxmin_round(const T* __restrict
 // ---------------------------------------------------------------------------
 // Tiled form for FP32 rows (d a multiple of 4) and byte rows (d a multiple of
 // 16): thread per row.  Each warp owns tiles of 32 consecutive rows (32 d
-// contiguous elements of Y), copied into its shared-memory buffer with
-// cp.async while the previous tile is worked on, the row stride padded to an
-// odd number of 16-byte groups so that 32 lanes reading 32 rows hit distinct
-// banks; the landmark row is broadcast from shared memory.  Lane q owns row q
-// of the tile: no warp reductions.
+// contiguous elements of Y) and brings them into its kMmStages shared-memory
+// stages with bulk asynchronous copies (cp.async.bulk, completion counted in
+// bytes on one mbarrier per stage), so kMmStages tiles per warp are in flight
+// while it computes; the row stride is an odd number of 16-byte groups so
+// that 32 lanes reading 32 rows hit distinct banks (the rows' own layout in
+// Y when d/4 (d/16 for bytes) is odd: one copy per tile; else one per row).
+// The landmark row is broadcast from shared memory.  Lane q owns row q of the
+// tile: no warp reductions.
 //   byte rows   d^2 = |y|^2 + |l|^2 - 2 y.l in integers (y.l by __dp4a, the
 //               row norms computed once): exact.
-//   FP32 rows   the bounded FP32 difference form, and the FP64 difference
-//               form where the running minimum may change (as above).
-constexpr int kTw = 4;   // warps per CTA of the tiled round
+//   FP32 rows   the bounded FP32 difference form (column pairs with packed
+//               sub.rn.f32x2 / fma.rn.f32x2 into two chains of d/2 terms,
+//               well inside the bound above), and the FP64 difference form
+//               where the running minimum may change, computed for those
+//               rows one at a time by the whole warp (lanes over the columns):
+//               FP64 issues at 1/64 of FP32, so one lane looping over d
+//               columns would hold the warp for d FP64 instructions.
+constexpr int kTw = 4;          // warps per CTA of the tiled round
+constexpr int kMmStages = 2;    // tiles in flight per warp
 
-__device__ __forceinline__ void mm_cp16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+union MmPack2 {
+    float2 f;
+    unsigned long long u;
+};
+
+__device__ __forceinline__ float2 mm_sub2(float2 a, float2 b) {
+    MmPack2 x, y, z;
+    x.f = a;
+    y.f = b;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(z.u) : "l"(x.u), "l"(y.u));
+    return z.f;
 }
-__device__ __forceinline__ void mm_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void mm_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ float2 mm_fma2(float2 a, float2 b, float2 c) {
+    MmPack2 x, y, w, z;
+    x.f = a;
+    y.f = b;
+    w.f = c;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(z.u) : "l"(x.u), "l"(y.u), "l"(w.u));
+    return z.f;
+}
+
+// Bounded wait on a tile's stage; false after ~2 s (the copy source is
+// ordinary device memory, so this only guards against a broken launch).
+__device__ __forceinline__ bool mm_tile_wait(uint64_t* bar, uint32_t parity) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = tc::global_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (tc::mbar_try_wait(bar, parity)) return true;
+        if (tc::global_ns() - t0 > tc::kWaitNs) return false;
+    }
+}
 
 // The CTA's best (v, i) pair from every thread's, then the round's pick by the
 // last CTA to finish (as in k_maxmin_round).
@@ -264,22 +300,26 @@ __global__ void __launch_bounds__(32 * kTw) k_maxmin_tiles(const void* __restric
                                                            const int* __restrict__ nrm8, int64_t* __restrict__ cur,
                                                            double* __restrict__ mind, double* __restrict__ part_v,
                                                            int64_t* __restrict__ part_i, unsigned* __restrict__ counter,
-                                                           int64_t* __restrict__ idx_out, int k) {
+                                                           int64_t* __restrict__ idx_out, int k, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char mm_smem[];
     __shared__ int s_lnorm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g16 = U8 ? d >> 4 : d >> 2;       // 16-byte groups per row
     const int s16 = g16 | 1;                    // padded row stride (odd)
-    // landmark row: bytes (U8), or floats then doubles (FP32)
+    // landmark row: bytes (U8), or floats then doubles (FP32); the stages; their barriers
     uint4* lm16 = reinterpret_cast<uint4*>(mm_smem);
     double* lm64 = reinterpret_cast<double*>(mm_smem + (size_t)g16 * 16);
     uint4* bufs = reinterpret_cast<uint4*>(mm_smem + (size_t)g16 * 16 + (U8 ? 0 : (size_t)d * 8));
-    uint4* const b0 = bufs + (size_t)(2 * warp) * 32 * s16;
-    uint4* const b1 = b0 + (size_t)32 * s16;
+    uint4* const ring = bufs + (size_t)warp * kMmStages * 32 * s16;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(bufs + (size_t)kTw * kMmStages * 32 * s16) + warp * kMmStages;
     const int64_t lrow = cur[0];
     const uint4* Y16 = reinterpret_cast<const uint4*>(Yv);
     for (int g = threadIdx.x; g < g16; g += blockDim.x) lm16[g] = Y16[lrow * g16 + g];
     if (threadIdx.x == 0) s_lnorm = 0;
+    if (lane == 0) {
+        for (int st = 0; st < kMmStages; ++st) tc::mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     if (U8) {
         unsigned sq = 0;
@@ -299,73 +339,115 @@ __global__ void __launch_bounds__(32 * kTw) k_maxmin_tiles(const void* __restric
     const int lnorm = s_lnorm;
     const int64_t tiles = (n + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * kTw;
-    int64_t t = (int64_t)blockIdx.x * kTw + warp;
-    auto issue = [&](int64_t tile, uint4* dst) {
-        if (tile < tiles) {
-            const int64_t row0 = tile * 32;
-            const int rows = (int)(n - row0 < 32 ? n - row0 : 32);
-            const uint4* src = Y16 + row0 * g16;
-            for (int j = lane; j < rows * g16; j += 32) {
-                const int row = j / g16, c = j - row * g16;
-                mm_cp16(dst + row * s16 + c, src + j);
-            }
+    const int64_t t0 = (int64_t)blockIdx.x * kTw + warp;
+    const bool one_copy = s16 == g16;
+    // the whole warp calls this with the same tile
+    auto issue = [&](int64_t tile, int st) {
+        if (tile >= tiles) return;
+        const int64_t row0 = tile * 32;
+        const int rows = (int)(n - row0 < 32 ? n - row0 : 32);
+        uint4* dst = ring + (size_t)st * 32 * s16;
+        const uint4* src = Y16 + row0 * g16;
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc::mbar_expect_tx(&bar[st], (uint32_t)rows * (uint32_t)g16 * 16u);
         }
-        mm_commit();
+        __syncwarp();
+        if (one_copy) {
+            if (lane == 0) tc::bulk_load(dst, src, (uint32_t)rows * (uint32_t)g16 * 16u, &bar[st]);
+        } else if (lane < rows) {
+            tc::bulk_load(dst + (size_t)lane * s16, src + (int64_t)lane * g16, (uint32_t)g16 * 16u, &bar[st]);
+        }
     };
+#pragma unroll
+    for (int st = 0; st < kMmStages; ++st) issue(t0 + st * wstride, st);
     double bv = -2.0;
     int64_t bi = INT64_MAX;
-    issue(t, b0);
-    for (int it = 0; t < tiles; t += wstride, ++it) {
-        const uint4* curb = (it & 1) ? b1 : b0;
-        issue(t + wstride, (it & 1) ? b0 : b1);
-        mm_wait<1>();
-        __syncwarp();
+    int it = 0;
+    for (int64_t t = t0; t < tiles; t += wstride, ++it) {
+        const int st = it % kMmStages;
         const int64_t row = t * 32 + lane;
+        double m = row < n ? mind[row] : -1.0;   // loaded while the tile lands
+        if (!mm_tile_wait(&bar[st], (uint32_t)(it / kMmStages) & 1u)) {
+            // give up on this round after the warp's copies in flight have
+            // landed; the CTA still takes part in the pick (its barriers)
+            if (lane == 0) atomicExch(err, MDS_ERR_TIMEOUT);
+            for (int q = 0; q < kMmStages; ++q)
+                if (t + (int64_t)q * wstride < tiles)
+                    tc::mbar_drain(&bar[(it + q) % kMmStages], (uint32_t)((it + q) / kMmStages) & 1u, err);
+            break;
+        }
+        const uint4* const tile = ring + (size_t)st * 32 * s16;
+        bool need64 = false;   // FP32 rows: the FP64 difference form decides
+        double dn = m;
+        if (row < n && m >= 0.0) {
+            const uint4* y = tile + (size_t)lane * s16;
+            if (U8) {
+                unsigned dot = 0;
+                for (int g = 0; g < g16; ++g) {
+                    const uint4 a = y[g], b = lm16[g];
+                    dot = __dp4a(a.x, b.x, dot);
+                    dot = __dp4a(a.y, b.y, dot);
+                    dot = __dp4a(a.z, b.z, dot);
+                    dot = __dp4a(a.w, b.w, dot);
+                }
+                dn = (double)((long long)nrm8[row] + lnorm - 2ll * (long long)dot);
+            } else {
+                const float4* y4 = reinterpret_cast<const float4*>(y);
+                const float4* l4 = reinterpret_cast<const float4*>(lm16);
+                float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll 2
+                for (int g = 0; g < g16; ++g) {
+                    const float4 a = y4[g], b = l4[g];
+                    const float2 t01 = mm_sub2(make_float2(a.x, a.y), make_float2(b.x, b.y));
+                    const float2 t23 = mm_sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
+                    s2 = mm_fma2(t01, t01, s2);
+                    s2 = mm_fma2(t23, t23, s2);
+                }
+                const float s = s2.x + s2.y;
+                // FP32 value within (d + 4) 2^-24 relative of the exact sum
+                const double bound = (double)s * (1.0 - (double)(d + 4) * 0x1p-23);
+                need64 = !(bound > m);
+            }
+        }
+        if (!U8) {
+            // the rows whose minimum may change: the FP64 difference form.  A
+            // few rows (the usual case after the first rounds) one at a time
+            // by the whole warp, lanes over the columns and a fixed butterfly
+            // sum (every lane holds the same total); many rows each by its
+            // own lane, columns in order (one FP64 pass of d columns for the
+            // warp, cheaper than ~d/32 + 5 FP64 instructions per row from ~14
+            // rows on).
+            unsigned pend = __ballot_sync(0xffffffffu, need64);
+            if (__popc(pend) > 13) {
+                if (need64) {
+                    const float* yf = reinterpret_cast<const float*>(tile + (size_t)lane * s16);
+                    double s64 = 0.0;
+                    for (int c = 0; c < d; ++c) {
+                        const double t64 = (double)yf[c] - lm64[c];
+                        s64 = fma(t64, t64, s64);
+                    }
+                    dn = s64;
+                }
+                pend = 0;
+            }
+            while (pend) {
+                const int q = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const float* yq = reinterpret_cast<const float*>(tile + (size_t)q * s16);
+                double s64 = 0.0;
+                for (int c = lane; c < d; c += 32) {
+                    const double t64 = (double)yq[c] - lm64[c];
+                    s64 = fma(t64, t64, s64);
+                }
+                s64 = warp_sum(s64);
+                if (lane == q) dn = s64;
+            }
+        }
         if (row < n) {
-            double m = mind[row];
-            if (m >= 0.0) {
-                const uint4* y = curb + lane * s16;
-                double dn;
-                if (U8) {
-                    unsigned dot = 0;
-                    for (int g = 0; g < g16; ++g) {
-                        const uint4 a = y[g], b = lm16[g];
-                        dot = __dp4a(a.x, b.x, dot);
-                        dot = __dp4a(a.y, b.y, dot);
-                        dot = __dp4a(a.z, b.z, dot);
-                        dot = __dp4a(a.w, b.w, dot);
-                    }
-                    dn = (double)((long long)nrm8[row] + lnorm - 2ll * (long long)dot);
-                } else {
-                    const float4* y4 = reinterpret_cast<const float4*>(y);
-                    const float4* l4 = reinterpret_cast<const float4*>(lm16);
-                    float s = 0.f;
-                    for (int g = 0; g < g16; ++g) {
-                        const float4 a = y4[g], b = l4[g];
-                        const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
-                        s = fmaf(t0, t0, s);
-                        s = fmaf(t1, t1, s);
-                        s = fmaf(t2, t2, s);
-                        s = fmaf(t3, t3, s);
-                    }
-                    // FP32 value within (d + 4) 2^-24 relative of the exact sum
-                    const double bound = (double)s * (1.0 - (double)(d + 4) * 0x1p-23);
-                    if (bound > m) {
-                        dn = m;
-                    } else {
-                        const float* yf = reinterpret_cast<const float*>(y);
-                        double s64 = 0.0;
-                        for (int c = 0; c < d; ++c) {
-                            const double t64 = (double)yf[c] - lm64[c];
-                            s64 = fma(t64, t64, s64);
-                        }
-                        dn = s64;
-                    }
-                }
-                if (dn < m) {
-                    m = dn;
-                    mind[row] = m;
-                }
+            if (m >= 0.0 && dn < m) {
+                m = dn;
+                mind[row] = m;
             }
             if (beats(m, row, bv, bi)) {
                 bv = m;
@@ -373,8 +455,8 @@ __global__ void __launch_bounds__(32 * kTw) k_maxmin_tiles(const void* __restric
             }
         }
         __syncwarp();
+        issue(t + (int64_t)kMmStages * wstride, st);   // the stage is consumed: the tile kMmStages ahead
     }
-    mm_wait<0>();
     mm_pick(bv, bi, part_v, part_i, counter, cur, mind, idx_out, k);
 }
 
@@ -432,8 +514,11 @@ int maxmin_grid() {
 
 // Shared memory of the tiled round (0: the shapes it does not take).
 size_t maxmin_tiles_smem(int dt, int d) {
-    if (dt == MDS_IN_U8 && d % 16 == 0) return (size_t)(d / 16) * 16 + (size_t)2 * kTw * 32 * ((d / 16) | 1) * 16;
-    if (dt == MDS_IN_F32 && d % 4 == 0) return (size_t)(d / 4) * 16 + (size_t)d * 8 + (size_t)2 * kTw * 32 * ((d / 4) | 1) * 16;
+    const size_t bars = (size_t)kTw * kMmStages * 8;
+    if (dt == MDS_IN_U8 && d % 16 == 0)
+        return (size_t)(d / 16) * 16 + (size_t)kMmStages * kTw * 32 * ((d / 16) | 1) * 16 + bars;
+    if (dt == MDS_IN_F32 && d % 4 == 0)
+        return (size_t)(d / 4) * 16 + (size_t)d * 8 + (size_t)kMmStages * kTw * 32 * ((d / 4) | 1) * 16 + bars;
     return 0;
 }
 
@@ -454,7 +539,7 @@ cudaError_t maxmin_tiled(const void* Y, int64_t n, int d, int l, int64_t first, 
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxminGridCap));
     for (int k = 1; k < l; ++k)
         k_maxmin_tiles<U8><<<(unsigned)grid, 32 * kTw, smem, st>>>(Y, n, d, ws.nrm8, ws.cur, ws.mind, ws.part_v,
-                                                                  ws.part_i, ws.counter, idx_out, k);
+                                                                  ws.part_i, ws.counter, idx_out, k, ws.err);
     note_launch(l + (U8 ? 1 : 0));
     return cudaGetLastError();
 }

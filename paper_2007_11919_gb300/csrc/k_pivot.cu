@@ -195,6 +195,132 @@ __global__ void __launch_bounds__(512) k_scatter_tri(const T* __restrict__ Y, in
             P[4 * i + j] = sizeof(A) == 8 ? (double)run[i][j] : (double)acc[i][j] + (double)lo[i][j];
 }
 
+// The same computation for FP32 rows in FP32 and FP64 rows in FP64 (element
+// type = arithmetic type), with the rows staged by cp.async into a ring of
+// kScStages steps instead of through registers: the copies of the next two
+// steps are in flight while a step is multiplied, and each thread centres its
+// own staged elements in place once they have landed (the register form
+// waited on its loads at every step).  Same products, same order, same
+// results as k_scatter_tri.
+constexpr int kScStages = 3;
+
+template <int B>
+__device__ __forceinline__ void sc_cp_async(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_scatter_tri_async(const T* __restrict__ Y, int64_t n, int d,
+                                                           const double* __restrict__ mean, int64_t R, int nt, int kc,
+                                                           double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sc_raw[];
+    const int dp = (d + 3) & ~3, nb = dp >> 2, ne = kc * dp;
+    T* const ring = reinterpret_cast<T*>(sc_raw);   // kScStages x kc x dp rows, centred in place
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < nt;
+    int bi = 0, rem = active ? t : 0;
+    while (rem >= nb - bi) {
+        rem -= nb - bi;
+        ++bi;
+    }
+    const int bj = bi + rem;
+    const int64_t r0 = (int64_t)blockIdx.y * R, r1 = r0 + R < n ? r0 + R : n;
+    const int nsteps = (int)((r1 - r0 + kc - 1) / kc);
+    int erow[kScPre], ecol[kScPre];
+#pragma unroll
+    for (int u = 0; u < kScPre; ++u) {
+        const int e = threadIdx.x + (int)blockDim.x * u;
+        erow[u] = e < ne ? e / dp : -1;
+        ecol[u] = e < ne ? e - (e / dp) * dp : 0;
+    }
+    auto issue = [&](int s) {   // step s's rows into stage s % kScStages (zero past d and past the chunk)
+        if (s < nsteps) {
+            T* stg = ring + (size_t)(s % kScStages) * ne;
+            const int64_t rs = r0 + (int64_t)s * kc;
+#pragma unroll
+            for (int u = 0; u < kScPre; ++u) {
+                if (erow[u] < 0) continue;
+                const int64_t row = rs + erow[u];
+                T* dst = stg + erow[u] * dp + ecol[u];
+                if (row < r1 && ecol[u] < d) sc_cp_async<(int)sizeof(T)>(dst, Y + row * d + ecol[u]);
+                else *dst = T(0);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    issue(0);
+    issue(1);
+    T acc[4][4], run[4][4];
+    float lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            acc[i][j] = T(0);
+            run[i][j] = T(0);
+            lo[i][j] = 0.f;
+        }
+    int since = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this thread's copies of step s
+        T* const stg = ring + (size_t)(s % kScStages) * ne;
+        const int64_t rs = r0 + (int64_t)s * kc;
+#pragma unroll
+        for (int u = 0; u < kScPre; ++u)
+            if (erow[u] >= 0 && ecol[u] < d && rs + erow[u] < r1)
+                stg[erow[u] * dp + ecol[u]] -= (T)__ldg(mean + ecol[u]);
+        __syncthreads();   // step s centred; every thread is past step s - 1
+        issue(s + 2);      // its stage was last read at step s - 1
+        if (active) {
+            for (int kk = 0; kk < kc; ++kk) {
+                T av[4], bv[4];
+                const T* row = stg + kk * dp;
+                if constexpr (sizeof(T) == 4) {
+                    const float4 a4 = *reinterpret_cast<const float4*>(row + 4 * bi);
+                    const float4 b4 = *reinterpret_cast<const float4*>(row + 4 * bj);
+                    av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+                    bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        av[i] = row[4 * bi + i];
+                        bv[i] = row[4 * bj + i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) run[i][j] += av[i] * bv[j];
+            }
+            since += kc;
+            if constexpr (sizeof(T) == 4) {
+                if (since >= 32 || rs + kc >= r1) {   // fold every 32 rows or so (and at the end)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float h = acc[i][j], l = lo[i][j];
+                            df_add(h, l, run[i][j], 0.f);
+                            acc[i][j] = h;
+                            lo[i][j] = l;
+                            run[i][j] = T(0);
+                        }
+                    since = 0;
+                }
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!active) return;
+    double* P = part + ((int64_t)blockIdx.y * nt + t) * 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            P[4 * i + j] = sizeof(T) == 8 ? (double)run[i][j] : (double)acc[i][j] + (double)lo[i][j];
+}
+
 // Warp per entry (a, b), a <= b, of S: the chunks' partials in a fixed order
 // (lane-strided, then a fixed tree), written to S[a][b] and S[b][a].
 __global__ void k_scatter_final(const double* __restrict__ part, int nch, int nt, int d, double* __restrict__ S) {
@@ -433,7 +559,19 @@ cudaError_t launch_scatter(const void* Y, int dt, int64_t n, int d, const double
     const dim3 grid((unsigned)g.ncta, (unsigned)g.nch);
     const int dp = (d + 3) & ~3;
     const size_t smem = (size_t)g.kc * dp * (f64 ? 8 : 4);
-    if (dt == MDS_IN_F64) {
+    if ((dt == MDS_IN_F64 && f64) || (dt == MDS_IN_F32 && !f64)) {
+        // element type = arithmetic type: rows staged by cp.async
+        const size_t sm = (size_t)kScStages * g.kc * dp * (f64 ? 8 : 4);
+        auto go = [&](auto kern, auto* y) {
+            cudaError_t e = cudaSuccess;
+            if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) kern<<<grid, g.threads, sm, st>>>(y, n, d, mean, g.R, g.nt, g.kc, part);
+            return e;
+        };
+        const cudaError_t e = f64 ? go(k_scatter_tri_async<double>, (const double*)Y)
+                                  : go(k_scatter_tri_async<float>, (const float*)Y);
+        if (e != cudaSuccess) return e;
+    } else if (dt == MDS_IN_F64) {
         if (f64) k_scatter_tri<double, double><<<grid, g.threads, smem, st>>>((const double*)Y, n, d, mean, g.R, g.nt, g.kc, part);
         else k_scatter_tri<double, float><<<grid, g.threads, smem, st>>>((const double*)Y, n, d, mean, g.R, g.nt, g.kc, part);
     } else if (dt == MDS_IN_F32) {

@@ -536,7 +536,7 @@ class DcPlan:
     the first ``execute`` pick the eigen-solver cluster size by timing."""
 
     def __init__(self, n, d, dtype, part_ptr, c, r, prec="f32", tune=True, cluster=0, device="cuda",
-                 full_matvec=False):
+                 full_matvec=False, eig_tol=0.0):
         L = _lib()
         for name, res, args in [
             ("mds_dc_plan_create", _I, [_I64, _I, _I, _I, _P, _I, _I, _P, _I, _P]),
@@ -552,7 +552,8 @@ class DcPlan:
         self.ptr = np.ascontiguousarray(np.asarray(part_ptr, dtype=np.int64))
         self.p = len(self.ptr) - 1
         self.n, self.d, self.r, self.prec = n, d, r, prec
-        o = MdsOpts(prec=PREC[prec], cluster=cluster, flags=FLAG_FULL_MATVEC if full_matvec else 0)
+        o = MdsOpts(prec=PREC[prec], cluster=cluster, flags=FLAG_FULL_MATVEC if full_matvec else 0,
+                    eig_tol=eig_tol)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(L.mds_dc_plan_create(n, d, DTYPE[dtype], self.p, self.ptr.ctypes.data_as(ctypes.c_void_p), c, r,
