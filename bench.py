@@ -66,7 +66,7 @@ NCU_TRAFFIC = {
     "k_gower_tc.cu": {"sha": "a89affadd1612472", "per": "row", "bytes": 452.0},
     # per byte of Q streamed, per workload
     # (profiles/k_lanczos_image_dc_fp8_n814255.md, profiles/k_lanczos_dc_f32_n100000.md)
-    "k_lanczos.cu": {"sha": "8551ed1188245aa2", "per": "streamed byte", "bytes": {"image_dc": 1.0342, "dc": 0.8236}},
+    "k_lanczos.cu": {"sha": "8a15a9c67c457db5", "per": "streamed byte", "bytes": {"image_dc": 1.0325, "dc": 0.8305}},
     # per row of Y per round (profiles/k_maxmin_tiles_maxmin_f32_n1000000.md)
     "k_maxmin.cu": {"sha": "ea7609f60cd2d721", "per": "row per round", "bytes": 411.5},
     # per row of Y (profiles/k_affine_project_bulk_affine_f32_n1000000.md)
