@@ -14,9 +14,28 @@ namespace gbmds {
 namespace {
 
 // One CTA per part.  The one-sided Jacobi sweeps rotate disjoint column pairs
-// concurrently, one warp per pair, in round-robin order (r - 1 rounds of r / 2
-// pairs per sweep, the circle method); lane i owns row i.  FP64 throughout.
-constexpr int kProcThreads = 512;   // 16 warps: r / 2 <= 16 pairs per round
+// concurrently in round-robin order (r - 1 rounds of r / 2 pairs per sweep,
+// the circle method).  A pair is a group of r lanes (lane q of the group owns
+// row q) and a warp holds floor(32 / r) groups, so a round of r = 10 takes
+// two warps instead of five: GB300 issues FP64 at 1/64 of FP32 and every FP64
+// warp instruction costs the same however few of its lanes work.  FP64
+// throughout.
+constexpr int kProcThreads = 512;   // 16 warps: enough for r / 2 <= 16 pairs at one pair per warp
+
+// Sum of v over the r lanes of this lane's group (lane q of group g is lane
+// g r + q), returned in every lane of the group: a tree into the group's
+// first lane (offsets 16, 8, ... below r, added where q + offset < r), then
+// a broadcast.  Every lane of the warp calls it.
+__device__ __forceinline__ double group_sum(double v, int q, int r, int leader) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (o < r) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            if (q + o < r) v += w;
+        }
+    }
+    return __shfl_sync(0xffffffffu, v, leader);
+}
 
 __device__ __forceinline__ void round_robin_pair(int round, int k, int n, int& p, int& q) {
     int x, y;
@@ -42,33 +61,35 @@ __device__ void procrustes_polar(double (*G)[kMaxR + 1], double (*Wm)[kMaxR + 1]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // one-sided Jacobi: rotate column pairs of G (and W) until orthogonal
     const int rr = r + (r & 1);   // column r is a dummy when r is odd
+    const int gpw = 32 / r;       // pairs (lane groups) per warp
+    const int gi = lane / r, row = lane - gi * r;
+    const int pair = warp * gpw + gi;
+    const bool in_group = gi < gpw && pair < rr / 2;
+    const int leader = gi < gpw ? gi * r : 0;
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < rr - 1; ++round) {
-            if (warp < rr / 2) {
-                int p, q;
-                round_robin_pair(round, warp, rr, p, q);
-                if (q < r) {
-                    const double gp = lane < r ? G[lane][p] : 0.0;
-                    const double gq = lane < r ? G[lane][q] : 0.0;
-                    const double al = warp_sum(gp * gp);
-                    const double be = warp_sum(gq * gq);
-                    const double ga = warp_sum(gp * gq);
-                    if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
-                        const double zeta = (be - al) / (2.0 * ga);
-                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        const double cs = 1.0 / sqrt(1.0 + tt * tt);
-                        const double sn = cs * tt;
-                        if (lane < r) {
-                            G[lane][p] = cs * gp - sn * gq;
-                            G[lane][q] = sn * gp + cs * gq;
-                            const double wp = Wm[lane][p], wq = Wm[lane][q];
-                            Wm[lane][p] = cs * wp - sn * wq;
-                            Wm[lane][q] = sn * wp + cs * wq;
-                        }
-                        if (lane == 0) s_rot = 1;
-                    }
+            if (warp * gpw < rr / 2) {   // warps holding a pair (the same for every lane of the warp)
+                int p = 0, q = 0;
+                if (in_group) round_robin_pair(round, pair, rr, p, q);
+                const bool real = in_group && q < r;
+                const double gp = real ? G[row][p] : 0.0;
+                const double gq = real ? G[row][q] : 0.0;
+                const double al = group_sum(gp * gp, row, r, leader);
+                const double be = group_sum(gq * gq, row, r, leader);
+                const double ga = group_sum(gp * gq, row, r, leader);
+                if (real && fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + tt * tt);
+                    const double sn = cs * tt;
+                    G[row][p] = cs * gp - sn * gq;
+                    G[row][q] = sn * gp + cs * gq;
+                    const double wp = Wm[row][p], wq = Wm[row][q];
+                    Wm[row][p] = cs * wp - sn * wq;
+                    Wm[row][q] = sn * wp + cs * wq;
+                    if (row == 0) s_rot = 1;
                 }
             }
             __syncthreads();
@@ -241,13 +262,17 @@ __global__ void __launch_bounds__(256) k_align(const ProbDesc* __restrict__ desc
     }
 }
 
+// var_i = (1/p) sum_j lambda^j_i / n_j: warp i, lanes over the problems, a
+// fixed butterfly sum (deterministic; the quotients are independent, so a
+// batch of thousands of problems is not one long chain of FP64 divisions).
 __global__ void k_lambda_bar(const ProbDesc* __restrict__ desc, int p,
                              const double* __restrict__ lam, int r, double* __restrict__ var) {
-    const int i = threadIdx.x;
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (i >= r) return;
     double s = 0.0;
-    for (int j = 0; j < p; ++j) s += lam[(size_t)j * r + i] / desc[j].n;
-    var[i] = s / p;
+    for (int j = lane; j < p; j += 32) s += lam[(size_t)j * r + i] / desc[j].n;
+    s = warp_sum(s);
+    if (lane == 0) var[i] = s / p;
 }
 
 }  // namespace
@@ -279,7 +304,8 @@ cudaError_t launch_dc_align(const ProbDesc* desc, int p, int max_n, const double
 
 cudaError_t launch_dc_lambda_bar(const ProbDesc* desc, int p, const double* lam, int r,
                                  double* var, cudaStream_t st) {
-    k_lambda_bar<<<1, 32, 0, st>>>(desc, p, lam, r, var);
+    if (r <= 0 || r > kMaxR) return cudaErrorInvalidValue;
+    k_lambda_bar<<<1, 32 * r, 0, st>>>(desc, p, lam, r, var);
     note_launch(1);
     return cudaGetLastError();
 }
