@@ -313,6 +313,19 @@ def test_dc_f64_small(gb):
     assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
 
 
+@pytest.mark.parametrize("r", [1, 2, 7, 11, 16, 17, 32])
+def test_dc_f64_target_dimensions(gb, r):
+    """Procrustes packs floor(32 / r) column pairs into a warp: r = 1 (a
+    dummy column only), odd r, r just past a packing boundary (11, 17) and the
+    largest r (one pair per warp), FP64 against the oracle."""
+    Y = W.gaussian_dominant(2400, 40, min(r, 40), seed=r, var_dom=30.0)
+    part = W.partitions_uneven(2400, 40, 300, 420, seed=r)
+    Xo, lo, _ = O.divide_conquer_mds(Y, part.anchors, part.ptr, part.own, r)
+    X, var = gb.mds_divide_conquer(dev(Y), dev(part.anchors), part.ptr, dev(part.own), r, "f64")
+    assert rel(host(var), lo) < LAM_TOL["f64"]
+    assert O.aligned_rel_error(host(X), Xo) < TOL["f64"]
+
+
 def test_dc_f32(gb):
     Y = W.gaussian_dominant(12_000, 100, 5, seed=4, dtype=np.float32)
     part = W.partitions_uneven(12_000, 20, 800, 1200, seed=4)
