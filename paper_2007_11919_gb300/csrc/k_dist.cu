@@ -96,15 +96,29 @@ __global__ void __launch_bounds__(256) k_sqdist(const T* __restrict__ Y, int d,
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0;
 
+    // this thread's staged elements of a chunk (fixed): e = tid + 256 u -> row e / KC, column e % KC;
+    // the next chunk's are loaded into registers while the current one is multiplied
+    constexpr int kPer = kTile * KC / 256;
+    A pa[kPer], pb[kPer];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int e = tid + 256 * u, row = e / KC, k = k0 + e % KC;
+            const int64_t ga = rowA[row], gb = rowB[row];
+            pa[u] = (ga >= 0 && k < d) ? load_as<A, T>(Y + ga * d + k) : A(0);
+            pb[u] = (gb >= 0 && k < d) ? load_as<A, T>(Y + gb * d + k) : A(0);
+        }
+    };
+    fetch(0);
     for (int k0 = 0; k0 < d; k0 += KC) {
 #pragma unroll
-        for (int e = tid; e < kTile * KC; e += 256) {
-            const int row = e / KC, kk = e % KC, k = k0 + kk;
-            const int64_t ga = rowA[row], gb = rowB[row];
-            As[kk][row] = (ga >= 0 && k < d) ? load_as<A, T>(Y + ga * d + k) : A(0);
-            Bs[kk][row] = (gb >= 0 && k < d) ? load_as<A, T>(Y + gb * d + k) : A(0);
+        for (int u = 0; u < kPer; ++u) {
+            const int e = tid + 256 * u, row = e / KC, kk = e % KC;
+            As[kk][row] = pa[u];
+            Bs[kk][row] = pb[u];
         }
         __syncthreads();
+        if (k0 + KC < d) fetch(k0 + KC);
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) {
             A av[4], bv[4];

@@ -43,7 +43,8 @@ def dev(a):
 
 @pytest.mark.parametrize("kind,n,d,l,first", [("f64", 3000, 20, 120, 17), ("f32", 5000, 100, 200, 0),
                                               ("f32", 2999, 7, 300, 2998), ("u8", 3000, 784, 150, 5),
-                                              ("u8", 1000, 37, 64, 999), ("f64", 40, 3, 40, 0)])
+                                              ("u8", 1000, 37, 64, 999), ("f64", 40, 3, 40, 0),
+                                              ("f32", 4001, 48, 150, 7), ("u8", 2501, 64, 120, 3)])
 def test_maxmin_bit_exact(gb, kind, n, d, l, first):
     if kind == "u8":
         Y = W.image_like(n, d, seed=n + d)
